@@ -1,0 +1,157 @@
+"""CPU oracle of the segregated-fit allocator (§5.1, Algorithms 4 and 5).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  The
+library in ``paper_2405_07079_gb300`` never imports it, and the two share no
+code: the only module both sides use is the seeded request generator
+(``paper_2405_07079_gb300.workloads``), which holds none of the allocator's
+arithmetic.
+
+Two independent statements of the same policy live here:
+
+* ``Oracle`` -- ``segfit_oracle.c``: the paper's own structures (hash table
+  keyed by address, doubly linked LIFO free lists per power-of-two class, a
+  64-bit availability bitmap), Algorithms 4 and 5 step by step.
+* ``interval_ref.IntervalAllocator`` -- a brute-force restatement over a
+  sorted list of intervals with push stamps, used on tiny arenas to pin the
+  first one (see that module's header).
+
+Parity of both against the paper's experiment (Fig. 3 / Fig. 4 of §6) is
+unpinned: the paper prints no data for those figures.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "segfit_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libsegfit_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FAIL = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``segfit_oracle.c`` into ``_build/libsegfit_oracle.so`` (gcc)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    stale = (not os.path.exists(_LIB)
+             or os.path.getmtime(_LIB) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+            lib.orc_create.restype = vp
+            lib.orc_create.argtypes = [u64, u64]
+            lib.orc_destroy.argtypes = [vp]
+            lib.orc_arena.restype = u64
+            lib.orc_arena.argtypes = [vp]
+            lib.orc_malloc.restype = u64
+            lib.orc_malloc.argtypes = [vp, u64]
+            lib.orc_free.restype = ctypes.c_int
+            lib.orc_free.argtypes = [vp, u64]
+            lib.orc_batch.argtypes = [vp, vp, u32, vp, vp, u32, vp]
+            lib.orc_export.restype = ctypes.c_size_t
+            lib.orc_export.argtypes = [vp, vp, ctypes.c_size_t]
+            lib.orc_stats.argtypes = [vp, vp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data if a.size else None
+
+
+class Oracle:
+    """One arena managed by the sequential oracle."""
+
+    STAT_KEYS = ("alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes",
+                 "used_blocks", "blocks", "requested_bytes", "bitmask")
+
+    def __init__(self, arena_bytes: int, min_block: int):
+        self._lib = _load()
+        self._h = self._lib.orc_create(int(arena_bytes), int(min_block))
+        if not self._h:
+            raise ValueError("invalid arena_bytes/min_block")
+        self.arena = int(self._lib.orc_arena(self._h))
+        self.min_block = int(min_block)
+
+    def close(self):
+        if self._h:
+            self._lib.orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def malloc(self, size: int) -> int:
+        return int(self._lib.orc_malloc(self._h, int(size)))
+
+    def free(self, addr: int) -> int:
+        return int(self._lib.orc_free(self._h, int(addr)))
+
+    def batch(self, frees, sizes):
+        """Apply one batch (frees in index order, then allocations).
+
+        Returns ``(out_offsets uint64[na], free_status uint8[nf])``."""
+        f = np.ascontiguousarray(frees, dtype=np.uint64)
+        s = np.ascontiguousarray(sizes, dtype=np.uint64)
+        out = np.empty(s.size, dtype=np.uint64)
+        st = np.empty(f.size, dtype=np.uint8)
+        self._lib.orc_batch(self._h, _ptr(f), f.size, _ptr(st), _ptr(s), s.size, _ptr(out))
+        return out, st
+
+    def export_state(self) -> np.ndarray:
+        n = self._lib.orc_export(self._h, None, 0)
+        buf = np.empty(n, dtype=np.uint64)
+        self._lib.orc_export(self._h, buf.ctypes.data, n)
+        return buf
+
+    def stats(self) -> dict:
+        buf = np.zeros(9, dtype=np.uint64)
+        self._lib.orc_stats(self._h, buf.ctypes.data)
+        return {k: int(v) for k, v in zip(self.STAT_KEYS, buf)}
+
+
+def decode_state(words) -> dict:
+    """Split a canonical state (R11) into its parts for readable assertions."""
+    w = [int(x) for x in words]
+    arena, min_block, nblocks = w[0], w[1], w[2]
+    blocks = []
+    i = 3
+    a = 0
+    while a < arena:
+        off = w[i]
+        if off == 0xFFFFFFFFFFFFFFFF:
+            raise AssertionError("blocks do not tile the arena")
+        sz = w[i + 1] & ((1 << 63) - 1)
+        blocks.append((off, sz, bool(w[i + 1] >> 63)))
+        a = off + sz
+        i += 2
+    bins = []
+    for _ in range(64):
+        cnt = w[i]
+        bins.append(w[i + 1:i + 1 + cnt])
+        i += 1 + cnt
+    bitmask = w[i]
+    assert i + 1 == len(w), "trailing words in canonical state"
+    return {"arena": arena, "min_block": min_block, "nblocks": nblocks,
+            "blocks": blocks, "bins": bins, "bitmask": bitmask}

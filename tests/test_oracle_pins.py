@@ -1,0 +1,330 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+* hand-derived worked examples (tests/golden/worked_examples.json);
+* closed forms (carving prefix sums, the fragmentation fill, a full arena of
+  4 KiB holes, release-all returns one block, exact powers of two);
+* invariants of every intermediate state;
+* an independent brute-force restatement (oracle/interval_ref.py), exhaustive
+  on tiny arenas and on random traces;
+* mutation checks: plausible mistakes planted in the brute-force restatement
+  (FIFO lists, 1-based class, lenient class, floor class) are caught by the
+  worked examples.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from _helpers import check_invariants
+
+import oracle
+from oracle.interval_ref import IntervalAllocator, _ceil_log2, _floor_log2
+
+FAIL = 0xFFFFFFFFFFFFFFFF
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def _canonical(arena, min_block, blocks, lists, bitmask):
+    w = [arena, min_block, len(blocks)]
+    for off, size, free in blocks:
+        w += [off, size | (int(free) << 63)]
+    for k in range(64):
+        lst = lists.get(str(k), [])
+        w += [len(lst)] + list(lst)
+    return w + [bitmask]
+
+
+def load_golden():
+    with open(GOLDEN) as f:
+        doc = json.load(f)
+    cases = []
+    for c in doc["cases"]:
+        fin = c.get("final")
+        if fin is not None:
+            blocks = fin["blocks"]
+            if isinstance(blocks, str):  # "pages:<size>:<count>:free=<offset>"
+                _, sz, cnt, fr = blocks.split(":")
+                sz, cnt, fr = int(sz), int(cnt), int(fr.split("=")[1])
+                blocks = [[i * sz, sz, i * sz == fr] for i in range(cnt)]
+            words = _canonical(c["arena"], c["min_block"], blocks, fin["lists"], fin["bitmask"])
+        else:
+            words = None
+        cases.append({"name": c["name"], "arena": c["arena"], "min_block": c["min_block"],
+                      "batches": c["batches"], "final": words})
+    return cases
+
+
+@pytest.mark.parametrize("impl", [oracle.Oracle, IntervalAllocator])
+@pytest.mark.parametrize("case", load_golden(), ids=lambda c: c["name"].split()[0])
+def test_worked_example(impl, case):
+    a = impl(case["arena"], case["min_block"])
+    for frees, sizes, expect in case["batches"]:
+        out, st = a.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        assert [int(x) for x in out] == expect
+        assert all(int(s) == 0 for s in st), "every free in the worked examples is valid"
+    assert [int(x) for x in a.export_state()] == case["final"]
+
+
+# ---- mutation checks: the worked examples catch plausible mistakes ---------
+
+class _Fifo(IntervalAllocator):
+    """Lists used as queues (pop the OLDEST push)."""
+
+    def malloc(self, size):
+        for v in self.iv:
+            v[3] = -v[3] if v[2] else v[3]
+        try:
+            return super().malloc(size)
+        finally:
+            for v in self.iv:
+                v[3] = -v[3] if v[2] and v[3] < 0 else v[3]
+
+
+class _ClassShift(IntervalAllocator):
+    """Class off by `shift` (1-based ffs reading: +1; lenient: -1)."""
+    shift = 1
+
+    def malloc(self, size):
+        if size == 0 or size > self.arena:
+            return FAIL
+        s = -(-size // self.min_block) * self.min_block
+        c = max(0, _ceil_log2(s) + self.shift)
+        cands = [(_floor_log2(v[1]), -v[3], k) for k, v in enumerate(self.iv)
+                 if v[2] and _floor_log2(v[1]) >= c and v[1] >= s]
+        if not cands:
+            return FAIL
+        k = min(cands)[2]
+        st, sz = self.iv[k][0], self.iv[k][1]
+        self.iv[k] = [st, s, False, 0]
+        if sz > s:
+            self.iv.insert(k + 1, [st + s, sz - s, True, self._tick()])
+        return st
+
+
+class _Lenient(_ClassShift):
+    shift = -1
+
+
+class _FloorClass(_ClassShift):
+    """Class floor(log2 s') instead of ceil (may pick a block that is too small
+    in class but large enough in bytes)."""
+
+    def malloc(self, size):
+        if size == 0 or size > self.arena:
+            return FAIL
+        s = -(-size // self.min_block) * self.min_block
+        self.shift = _floor_log2(s) - _ceil_log2(s)
+        return super().malloc(size)
+
+
+class _NoMerge(IntervalAllocator):
+    """Frees never coalesce."""
+
+    def free(self, addr):
+        k = next((i for i, v in enumerate(self.iv) if v[0] == addr), None)
+        if k is None or self.iv[k][2]:
+            return 1
+        self.iv[k][2] = True
+        self.iv[k][3] = self._tick()
+        return 0
+
+
+@pytest.mark.parametrize("mutant", [_Fifo, _ClassShift, _Lenient, _FloorClass, _NoMerge])
+def test_worked_examples_catch_mutants(mutant):
+    caught = False
+    for case in load_golden():
+        a = mutant(case["arena"], case["min_block"])
+        ok = True
+        for frees, sizes, expect in case["batches"]:
+            out, _ = a.batch(frees, sizes)
+            ok &= [int(x) for x in out] == expect
+        ok &= [int(x) for x in a.export_state()] == case["final"]
+        caught |= not ok
+    assert caught, f"{mutant.__name__} passes every worked example"
+
+
+# ---- closed forms -------------------------------------------------------------
+
+def test_nearly_four_times_bound():
+    """With the request's own class non-empty, the chosen block is < 4x the
+    rounded request (§5.1, text after Algorithm 4): class c = ceil(log2 s')
+    holds blocks below 2^(c+1) < 4 s'."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        mb = 256
+        o = oracle.Oracle(1 << 24, mb)
+        held = [o.malloc(int(x)) for x in rng.integers(1, 1 << 16, 60)]
+        for a in held[::2]:
+            if a != FAIL:
+                o.free(a)
+        st = oracle.decode_state(o.export_state())
+        size_of = {off: sz for off, sz, fr in st["blocks"] if fr}
+        for s in rng.integers(1, 1 << 16, 20):
+            sp = -(-int(s) // mb) * mb
+            c = _ceil_log2(sp)
+            if st["bins"][c]:
+                head = st["bins"][c][0]
+                assert o.malloc(int(s)) == head and size_of[head] < 4 * sp
+                break
+
+
+def test_carving_prefix_sums():
+    """From a fresh arena, allocations carve the front: offset_i = sum of the
+    earlier rounded sizes while the request's class fits the remainder."""
+    rng = np.random.default_rng(5)
+    for trial in range(50):
+        A, mb = 1 << 22, 1 << int(rng.integers(3, 10))
+        o = oracle.Oracle(A, mb)
+        used = 0
+        for s in rng.integers(1, 1 << 14, 100):
+            sp = -(-int(s) // mb) * mb
+            rem = A - used
+            expect = used if rem > 0 and (1 << _ceil_log2(sp)) <= rem else FAIL
+            assert o.malloc(int(s)) == expect
+            if expect != FAIL:
+                used += sp
+
+
+def test_frag_fill_and_full_arena_closed_forms():
+    """Fill with 4 KiB blocks -> offsets 4096 i.  With an arena of exactly
+    n x 4 KiB, after freeing every other block all holes are 4 KiB (class 12)
+    and any request of class >= 13 fails."""
+    n = 4096
+    o = oracle.Oracle(n * 4096, 256)
+    out, _ = o.batch(np.zeros(0, np.uint64), np.full(n, 4096, np.uint64))
+    assert np.array_equal(out, np.arange(n, dtype=np.uint64) * 4096)
+    _, st = o.batch(out[0::2], np.zeros(0, np.uint64))
+    assert not st.any()
+    out2, _ = o.batch(np.zeros(0, np.uint64), np.array([4097, 8192, 1 << 20], np.uint64))
+    assert (out2 == FAIL).all()
+    s = oracle.decode_state(o.export_state())
+    assert s["bitmask"] == 1 << 12 and len(s["bins"][12]) == n // 2
+
+
+def test_release_all_returns_one_block():
+    rng = np.random.default_rng(9)
+    for trial in range(20):
+        o = oracle.Oracle(1 << 22, 512)
+        held = []
+        for _ in range(30):
+            out, _ = o.batch(np.zeros(0, np.uint64), rng.integers(1, 1 << 17, 40).astype(np.uint64))
+            held += [int(x) for x in out if x != FAIL]
+            if held and rng.random() < 0.5:
+                k = int(rng.integers(0, len(held)))
+                o.free(held.pop(k))
+        order = rng.permutation(len(held))
+        _, st = o.batch(np.array(held, np.uint64)[order], np.zeros(0, np.uint64))
+        assert not st.any()
+        s = oracle.decode_state(o.export_state())
+        assert s["blocks"] == [(0, 1 << 22, True)] and s["bins"][22] == [0]
+
+
+def test_exact_powers_of_two_fit_from_own_class():
+    o = oracle.Oracle(1 << 20, 256)
+    for k in range(8, 20):
+        o2 = oracle.Oracle(1 << 20, 256)
+        o2.malloc(1 << 19)  # leaves [2^19, 2^20) in class 19
+        if k <= 19:
+            assert o2.malloc(1 << k) == 1 << 19
+    assert o.malloc(1 << 20) == 0 and o.malloc(256) == FAIL
+
+
+# ---- invariants and brute force -------------------------------------------
+
+def _random_batches(rng, A, mb, nb, max_ops, sizes_hi):
+    held = []
+    for _ in range(nb):
+        nf = int(rng.integers(0, max_ops + 1))
+        frees = []
+        for _ in range(nf):
+            r = rng.random()
+            if held and r < 0.7:
+                frees.append(held[int(rng.integers(0, len(held)))])
+            elif r < 0.85:
+                frees.append(int(rng.integers(0, A // mb + 2)) * mb)   # maybe a non-start
+            else:
+                frees.append(int(rng.integers(0, A + 64)))              # maybe misaligned
+        sizes = [int(x) for x in rng.integers(0, sizes_hi, int(rng.integers(0, max_ops + 1)))]
+        yield frees, sizes, held
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_oracle_equals_interval_allocator_random(seed):
+    rng = np.random.default_rng(seed)
+    mb = [8, 16, 64][seed % 3]
+    A = mb * int(rng.integers(1, 40))
+    o, r = oracle.Oracle(A, mb), IntervalAllocator(A, mb)
+    for frees, sizes, held in _random_batches(rng, A, mb, 40, 6, A + mb):
+        oo, os_ = o.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        ro, rs = r.batch(frees, sizes)
+        assert [int(x) for x in oo] == ro and [int(x) for x in os_] == rs
+        assert [int(x) for x in o.export_state()] == r.export_state()
+        check_invariants(o.export_state())
+        held[:] = [a for a in held if a not in set(frees)] + [int(x) for x in oo if x != FAIL]
+
+
+def test_oracle_equals_interval_allocator_exhaustive():
+    """Every sequence of 4 single-op batches over a small alphabet on a
+    16-granule arena, after each of three different prefixes."""
+    A, mb = 256, 16
+    alphabet = [("a", 1), ("a", 16), ("a", 17), ("a", 48), ("a", 100), ("a", 256),
+                ("f", 0), ("f", 16), ("f", 32), ("f", 64), ("f", 128), ("f", 8)]
+    prefixes = [[], [("a", 32), ("a", 16), ("a", 64), ("f", 32)], [("a", 16)] * 8 + [("f", 16), ("f", 64)]]
+    n = 0
+    for pre in prefixes:
+        for seq in itertools.product(alphabet, repeat=4):
+            o, r = oracle.Oracle(A, mb), IntervalAllocator(A, mb)
+            for op, v in list(pre) + list(seq):
+                if op == "a":
+                    assert o.malloc(v) == r.malloc(v)
+                else:
+                    assert o.free(v) == r.free(v)
+            assert [int(x) for x in o.export_state()] == r.export_state()
+            n += 1
+    assert n == 3 * len(alphabet) ** 4
+
+
+def test_invariants_on_workload_traces():
+    from paper_2405_07079_gb300 import workloads as W
+
+    for wl in (W.tiny(n_ops=3000),
+               W.Workload("l", 1 << 28, 512, lambda: W.Lifetimes(n_ops=60_000, batch=2048, mean_life=200)),
+               W.frag(n_fill=8000, n_big=800, batch=1024, arena=64 << 20)):
+        o = oracle.Oracle(wl.arena, wl.min_block)
+        cl = wl.make()
+        while (b := cl.next_batch()) is not None:
+            out, st = o.batch(*b)
+            cl.feed(out)
+            check_invariants(o.export_state())
+            stt = o.stats()
+            s = oracle.decode_state(o.export_state())
+            assert stt["used_bytes"] == sum(sz for _, sz, fr in s["blocks"] if not fr)
+            assert stt["blocks"] == len(s["blocks"])
+
+
+def test_property_hypothesis():
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    op = st.one_of(st.tuples(st.just("a"), st.integers(0, 600)),
+                   st.tuples(st.just("f"), st.integers(0, 40).map(lambda g: g * 16)))
+
+    @hyp.settings(max_examples=300, deadline=None)
+    @hyp.given(st.lists(st.lists(op, max_size=6), max_size=12))
+    def prop(batches):
+        A, mb = 512, 16
+        o, r = oracle.Oracle(A, mb), IntervalAllocator(A, mb)
+        for b in batches:
+            frees = [v for k, v in b if k == "f"]
+            sizes = [v for k, v in b if k == "a"]
+            oo, os_ = o.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+            ro, rs = r.batch(frees, sizes)
+            assert [int(x) for x in oo] == ro and [int(x) for x in os_] == rs
+            check_invariants(o.export_state())
+        assert [int(x) for x in o.export_state()] == r.export_state()
+
+    prop()
