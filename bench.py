@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Throughput of the header-free batched allocator on one GB300 (or N replicas).
+
+Workload (default ``large``): one 16 GiB arena, min block 512 B, a 10M-op
+trace in batches of 65,536 (70 % power-of-two sizes 4 KiB..2 MiB, 30 %
+log-uniform 256 B..256 MiB, geometric lifetimes with mean 1,000 ops).  A step
+is one batch: its frees, then its allocations, in one kernel launch.
+
+1. The trace is recorded untimed: the seeded client drives the GPU allocator
+   closed loop (it frees what the allocator gave it).
+2. The allocator is reset and the recorded batches are replayed: W warm-up
+   steps, then K timed steps, each bracketed by CUDA events on the launching
+   stream; between steps a 256 MiB buffer is written to flush L2 (untimed);
+   when the trace wraps the allocator is reset (untimed).
+3. e2e: the same replay through ``hba_step_host`` (pinned host buffers, the
+   copies and the result read-back inside the timed region).
+
+``--impl reference`` times the CPU oracle (the sequential statement of
+Algorithms 4/5) on the same workload, one batch per step.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "alloc+free ops/s on 1 GB300 (batched/serving vs plain GPU); p50/p99 latency; bit-exact"
+UNIT = "ops/s"
+FAIL = np.uint64(0xFFFFFFFFFFFFFFFF)
+# Algorithmic metadata bytes per request (the paper's six-word, 48-byte
+# address-keyed record, §3.3; see the design doc for the derivation).
+BYTES_ALLOC_OK = 168
+BYTES_ALLOC_FAIL = 16
+BYTES_FREE_OK = 216
+BYTES_FREE_REJECTED = 9
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.rows, self.proc = [], None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+        except Exception:
+            sel = str(device_index)
+        self.cmd = ["nvidia-smi", "-i", sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                    "-lms", "200"]
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 7
+                          for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def record_trace(wl, alloc, dev):
+    """Drive the client closed loop against the GPU allocator (untimed)."""
+    import torch
+
+    from paper_2405_07079_gb300.hba import _ptr
+
+    client = wl.make()
+    batches = []
+    while (b := client.next_batch()) is not None:
+        f, s = b
+        df = torch.from_numpy(f.view(np.int64)).to(dev)
+        ds = torch.from_numpy(s.view(np.int64)).to(dev)
+        st = torch.empty(f.size, dtype=torch.uint8, device=dev)
+        out = torch.empty(s.size, dtype=torch.int64, device=dev)
+        alloc.step(df if f.size else None, ds if s.size else None, out=out, status=st)
+        o = out.cpu().numpy().view(np.uint64)
+        client.feed(o)
+        stat = st.cpu().numpy()
+        n_ok = int((o != FAIL).sum())
+        n_fok = int((stat == 0).sum())
+        nbytes = (BYTES_ALLOC_OK * n_ok + BYTES_ALLOC_FAIL * (s.size - n_ok)
+                  + BYTES_FREE_OK * n_fok + BYTES_FREE_REJECTED * (f.size - n_fok))
+        batches.append({"f": df, "s": ds, "out": out, "st": st, "nf": f.size, "na": s.size,
+                        "ops": f.size + s.size, "bytes": nbytes,
+                        "hf": torch.from_numpy(f.view(np.int64).copy()).pin_memory(),
+                        "hs": torch.from_numpy(s.view(np.int64).copy()).pin_memory()})
+    return batches
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator, hba_step_host, workloads
+    from paper_2405_07079_gb300.hba import _ptr
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag}[args.workload]()
+    alloc = Allocator(wl.arena, wl.min_block, threads=args.threads)
+    batches = record_trace(wl, alloc, dev)
+    nb = len(batches)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    sptr = int(stream.cuda_stream)
+
+    def launch(b):
+        alloc.step(b["f"] if b["nf"] else None, b["s"] if b["na"] else None, out=b["out"], status=b["st"])
+
+    # replay: warm-up then timed steps (the trace wraps with an untimed reset)
+    alloc.reset()
+    pos = 0
+    for _ in range(args.warmup):
+        if pos == nb:
+            alloc.reset(); pos = 0
+        flush.zero_()
+        launch(batches[pos]); pos += 1
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    idx = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        for k in range(args.steps):
+            if pos == nb:
+                alloc.reset(); pos = 0
+            flush.zero_()
+            ev[k][0].record(stream)
+            launch(batches[pos])
+            ev[k][1].record(stream)
+            idx.append(pos); pos += 1
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    busy_s = sum(step_ms) / 1e3
+    ops = sum(batches[i]["ops"] for i in idx)
+    nbytes = sum(batches[i]["bytes"] for i in idx)
+
+    # e2e through the public host-buffer entry point, from a fresh state
+    alloc.reset()
+    torch.cuda.synchronize()
+    hout = torch.empty(65536, dtype=torch.int64).pin_memory()
+    e2e_ops, e2e_h2d, e2e_d2h = 0, 0, 0
+    pos = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        if pos == nb:
+            alloc.reset(); pos = 0
+        b = batches[pos]; pos += 1
+        hba_step_host(alloc.h, _ptr(b["hf"]), b["nf"], 0, _ptr(b["hs"]), b["na"], _ptr(hout), sptr)
+        e2e_ops += b["ops"]; e2e_h2d += 8 * (b["nf"] + b["na"]); e2e_d2h += 8 * b["na"]
+    e2e_s = time.perf_counter() - t0
+
+    if world > 1:
+        t = torch.tensor([busy_s, e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        busy_s, e2e_s = float(t[0]), float(t[1])
+        o = torch.tensor([ops, e2e_ops], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(o, op=torch.distributed.ReduceOp.SUM)
+        ops_all, e2e_all = float(o[0]), float(o[1])
+    else:
+        ops_all, e2e_all = float(ops), float(e2e_ops)
+    stats = alloc.stats()
+    alloc.close()
+    if rank != 0:
+        return None
+    peak, peak_src = _peaks()
+    achieved_gbs = nbytes / busy_s / 1e9
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": ops_all / busy_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * busy_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name + ": " + wl.note, "parallelism": f"replicas x{world}",
+                   "form": "plain single arena, one launch per batch", "threads_per_cta": alloc_threads(args),
+                   "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
+                   "ops_per_step_mean": ops / max(1, args.steps)},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": achieved_gbs / peak, "traffic": None,
+                     "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_single<1024>",
+                     "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
+        "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "unit": "per batch of one step"},
+        "e2e": {"value": e2e_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d // max(1, args.steps),
+                "d2h_bytes_per_step": e2e_d2h // max(1, args.steps), "api": "hba_step_host"},
+        "gpu_launches": args.steps,
+        "clocks": clocks.summary(),
+        "final_stats": {k: stats[k] for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail")},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    return line
+
+
+def alloc_threads(args):
+    return args.threads or 1024
+
+
+def oracle_steps(wl, n_steps=None, warmup=0):
+    """Closed-loop client + oracle.  The first ``warmup`` batches run untimed;
+    returns (oracle seconds, ops, timed steps) over the next ``n_steps``
+    batches (None: to the end of the trace).  The trace restarts from a fresh
+    oracle when it ends."""
+    import oracle
+
+    o = oracle.Oracle(wl.arena, wl.min_block)
+    client = wl.make()
+    t_or, ops, k, seen = 0.0, 0, 0, 0
+    while n_steps is None or k < n_steps:
+        b = client.next_batch()
+        if b is None:
+            if n_steps is None:
+                break
+            o = oracle.Oracle(wl.arena, wl.min_block)
+            client = wl.make()
+            continue
+        t0 = time.perf_counter()
+        out, _ = o.batch(*b)
+        dt = time.perf_counter() - t0
+        client.feed(out)
+        seen += 1
+        if seen > warmup:
+            t_or += dt
+            ops += b[0].size + b[1].size
+            k += 1
+    return t_or, ops, k
+
+
+def cpu_baseline(wl) -> dict:
+    t, ops, k = oracle_steps(wl)
+    return {"value": ops / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the whole trace ({k} batches, {ops} ops), closed loop, single thread; "
+                      f"oracle calls timed ({t:.3f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2405_07079_gb300 import workloads
+
+    wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag}[args.workload]()
+    t, ops, k = oracle_steps(wl, n_steps=args.steps, warmup=args.warmup)
+    v = ops / t
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": wl.name + ": " + wl.note, "parallelism": "single host thread",
+                       "form": "sequential CPU oracle, one batch per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"batches {args.warmup}..{args.warmup + args.steps - 1} of the trace "
+                                       "(wrapping to a fresh oracle), oracle calls timed"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=["large", "tiny", "frag"], default="large")
+    ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        line = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

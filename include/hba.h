@@ -1,0 +1,187 @@
+/*
+ * hba.h -- C ABI of the header-free batched allocator for GB300 (sm_103a).
+ *
+ * The allocator manages an arena of device memory that it never reads or
+ * writes.  It does not even receive the arena's address: it hands out byte
+ * OFFSETS into [0, arena_bytes) and takes offsets back.  All of its metadata
+ * (the offset-to-block table that replaces boundary tags, the power-of-two
+ * free lists and their availability bitmap) lives in separate device
+ * buffers owned by the library.  This is the system model of Bell, Kumar and
+ * Gill, "Host-Based Allocators for Device Memory" (arXiv 2405.07079): §1 and
+ * §3 (an allocator that cannot read the memory it manages, so no boundary
+ * tags), §3.3 (metadata kept out of band, keyed by block address).
+ *
+ * Policy.  HBA_POLICY_SEGFIT is the segregated-fit allocator of §5.1
+ * (Algorithm 4 allocate, Algorithm 5 deallocate), the one the paper
+ * evaluates against cudaMalloc/cudaFree in §6:
+ *   - a request of `size` bytes is rounded up to s' = a multiple of
+ *     min_block; its class is c = ceil(log2 s');
+ *   - free blocks live in LIFO lists by floor(log2 block size); a bitmap has
+ *     bit k set iff list k is non-empty;
+ *   - allocation takes the head of the lowest non-empty list with index >= c
+ *     (strict: list c-1 is never searched), carves s' bytes from its front and
+ *     pushes the remainder, if any, at the head of its own list;
+ *   - deallocation coalesces the block with a free left and/or right address
+ *     neighbour and pushes the result at the head of its list.
+ *
+ * Batch semantics.  One batch = a free call followed by an alloc call on the
+ * same stream (or one hba_step call): all frees in index order, then all
+ * allocations in index order, exactly as if applied one by one.  Results are
+ * deterministic and bit-identical to a sequential execution of Algorithms 4
+ * and 5.
+ *
+ * Errors.  API problems return a status (hba_status_t).  Per-request outcomes
+ * are data, never errors: a failed allocation yields HBA_FAIL in its output
+ * slot; a rejected free (not the start of an in-use block: unknown,
+ * misaligned, interior, already free, or an earlier duplicate in the same
+ * batch) yields status 1 and changes nothing.
+ *
+ * Streams and ownership.  Every device pointer argument is caller-owned
+ * device memory that must stay valid until the work enqueued on `stream`
+ * completes.  Calls are asynchronous with respect to the host unless stated
+ * otherwise; a handle's calls must be ordered on one stream (or ordered by the
+ * caller with events).  The library allocates its metadata and scratch in
+ * hba_create* and never in the batch calls.  `stream` is a cudaStream_t (NULL
+ * = the legacy default stream).
+ *
+ * Limits.  min_block is a power of two >= 8; arena_bytes is rounded down to a
+ * multiple of min_block; arena_bytes / min_block must be in [1, 2^29 - 1].
+ */
+#ifndef HBA_H_
+#define HBA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hba_s* hba_t;
+typedef void* hba_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    HBA_OK = 0,
+    HBA_ERR_INVALID_ARGUMENT = 1, /* bad handle, size, pointer or count */
+    HBA_ERR_OUT_OF_MEMORY = 2,    /* metadata or scratch could not be allocated */
+    HBA_ERR_CUDA = 3,             /* a CUDA call failed (launch, copy, sync) */
+    HBA_ERR_TIMEOUT = 4,          /* a bounded device-side wait gave up */
+    HBA_ERR_STATE = 5             /* the device flagged corrupted metadata */
+} hba_status_t;
+
+typedef enum {
+    HBA_POLICY_SEGFIT = 0 /* §5.1 segregated fit; other values are rejected */
+} hba_policy_t;
+
+#define HBA_FAIL ((uint64_t)~0ull)
+
+/* Counters of one handle (summed over arenas for a multi-arena handle). */
+typedef struct {
+    uint64_t alloc_ok, alloc_fail;   /* allocations served / failed */
+    uint64_t free_ok, free_fail;     /* frees applied / rejected */
+    uint64_t used_bytes;             /* bytes in in-use blocks (rounded sizes) */
+    uint64_t used_blocks;            /* in-use blocks */
+    uint64_t blocks;                 /* all blocks, in use or free */
+    uint64_t requested_bytes;        /* sum of the sizes of served requests */
+    uint64_t free_bytes;             /* arena bytes not in use */
+    uint64_t largest_free;           /* size of the largest free block */
+    uint64_t bitmask;                /* availability bitmap (bit k: list k non-empty); arena 0 */
+    uint64_t arena_bytes;            /* managed bytes (sum over arenas) */
+    uint32_t n_arenas;
+    uint32_t device_error;           /* 0, or a code the device recorded */
+} hba_stats_t;
+
+/* Create a single-arena handle on the current CUDA device (§3.3 out-of-band
+ * table, §5.1 initial state: one free block [0, arena)).  Allocates the
+ * offset-to-block table (16 bytes per min_block granule) and scratch for
+ * batches of up to 65,536 frees.  Synchronous.  *out is set only on HBA_OK. */
+hba_status_t hba_create(uint64_t arena_bytes, uint64_t min_block, int policy, hba_t* out);
+
+/* As hba_create, with scratch sized for batches of up to max_batch frees
+ * (larger batches are applied in consecutive slices of max_batch, which is
+ * exact because frees, like allocations, apply one by one in index order). */
+hba_status_t hba_create_ex(uint64_t arena_bytes, uint64_t min_block, int policy,
+                           uint32_t max_batch, hba_t* out);
+
+/* Free all metadata of the handle.  Synchronises the device first. */
+hba_status_t hba_destroy(hba_t h);
+
+/* Allocate n blocks (Algorithm 4, one by one in index order).  d_sizes:
+ * device uint64[n] of requested bytes.  d_out_offsets: device uint64[n],
+ * receives the offset of each block, or HBA_FAIL.  n may be 0. */
+hba_status_t hba_alloc_batch(hba_t h, const uint64_t* d_sizes, uint32_t n,
+                             uint64_t* d_out_offsets, hba_stream_t stream);
+
+/* Free n blocks (Algorithm 5, one by one in index order).  d_offsets: device
+ * uint64[n].  Rejected frees are counted in the stats. */
+hba_status_t hba_free_batch(hba_t h, const uint64_t* d_offsets, uint32_t n, hba_stream_t stream);
+
+/* As hba_free_batch; d_status (device uint8[n], may be NULL) receives 0 for an
+ * applied free and 1 for a rejected one. */
+hba_status_t hba_free_batch_ex(hba_t h, const uint64_t* d_offsets, uint32_t n,
+                               uint8_t* d_status, hba_stream_t stream);
+
+/* One whole batch in one launch: the nf frees, then the na allocations.
+ * Same results as hba_free_batch_ex followed by hba_alloc_batch. */
+hba_status_t hba_step(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status,
+                      const uint64_t* d_sizes, uint32_t na, uint64_t* d_out_offsets,
+                      hba_stream_t stream);
+
+/* hba_step with HOST buffers: copies the inputs to device staging buffers,
+ * runs the batch, copies the results back and waits for them.  h_status may
+ * be NULL.  Staging is sized at create for max_batch requests per side;
+ * larger nf or na return HBA_ERR_INVALID_ARGUMENT.  Pinned host memory gives
+ * asynchronous copies; pageable memory works but is slower. */
+hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_t* h_status,
+                           const uint64_t* h_sizes, uint32_t na, uint64_t* h_out_offsets,
+                           hba_stream_t stream);
+
+/* Return the arena to its initial state (one free block) and zero the
+ * counters.  Asynchronous on stream. */
+hba_status_t hba_reset(hba_t h, hba_stream_t stream);
+
+/* Read the counters.  Waits for all work on the device to finish.  Also
+ * reports HBA_ERR_STATE if the device recorded a metadata error. */
+hba_status_t hba_stats(hba_t h, hba_stats_t* out);
+
+/* Canonical state of arena `arena` (0 for a single-arena handle), as 64-bit
+ * words: arena_bytes, min_block, nblocks; then nblocks pairs
+ * (offset, size | free << 63) in address order; then for each list k = 0..63
+ * its length followed by its offsets head to tail; then the bitmap.  This is
+ * the layout-independent form used to compare with a sequential reference.
+ * Writes at most cap words into host_buf (may be NULL when cap is 0) and sets
+ * *len to the number of words needed.  Waits for the device. */
+hba_status_t hba_export_state(hba_t h, uint32_t arena, uint64_t* host_buf, size_t cap, size_t* len);
+
+/* ---- many independent arenas in one launch ------------------------------ */
+
+/* Create a handle over n_arenas independent arenas with the given sizes
+ * (host uint64[n_arenas]), one min_block for all.  max_total_frees sizes the
+ * shared scratch: the total number of frees of one hba_multi_step call. */
+hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, uint64_t min_block,
+                              int policy, uint32_t max_total_frees, hba_t* out);
+
+/* One batch for every arena in one launch.  Requests are in CSR form:
+ * arena a frees d_frees[d_free_rowptr[a] .. d_free_rowptr[a+1]) and allocates
+ * d_sizes[d_alloc_rowptr[a] .. d_alloc_rowptr[a+1]); rowptrs are device
+ * uint32[n_arenas + 1] starting at 0.  d_out is parallel to d_sizes;
+ * d_free_status (may be NULL) parallel to d_frees.  The host passes the
+ * totals nf_total = free_rowptr[n_arenas] and na_total = alloc_rowptr[n_arenas]
+ * so that the call needs no device read-back. */
+hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64_t* d_frees,
+                            uint32_t nf_total, const uint32_t* d_alloc_rowptr,
+                            const uint64_t* d_sizes, uint32_t na_total, uint64_t* d_out,
+                            uint8_t* d_free_status, hba_stream_t stream);
+
+/* Launch shape used by hba_multi_step: threads per CTA (one CTA per arena
+ * per wave) and CTAs per SM wave.  threads must be one of 64, 128, 256, 512,
+ * 1024.  Set by the autotuner or by hand. */
+hba_status_t hba_multi_set_shape(hba_t h, uint32_t threads, uint32_t ctas);
+
+/* Version string of the library. */
+const char* hba_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HBA_H_ */

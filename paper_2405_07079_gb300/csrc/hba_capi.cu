@@ -1,0 +1,376 @@
+// hba_capi.cu -- C ABI of the header-free batched allocator (include/hba.h).
+//
+// Owns the device metadata of one or many arenas and launches the batch
+// engine of hba_engine.cuh: one CTA per arena per batch.  No call here ever
+// receives, reads or writes the managed arena itself.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hba.h"
+#include "hba_engine.cuh"
+
+using hba::Arena;
+using hba::Rec;
+
+struct hba_s {
+    int device = 0;
+    uint32_t n_arenas = 0;
+    uint64_t min_block = 0;
+    uint32_t lg = 0;
+    uint64_t total_granules = 0;
+    Arena* d_arenas = nullptr;
+    Rec* d_rec = nullptr;
+    uint32_t* d_scr = nullptr;
+    uint64_t scr_frees = 0;     // scratch capacity in frees
+    uint32_t max_batch = 0;     // single arena: frees per launch slice
+    std::vector<Arena> h_init;  // initial headers (for reset)
+    // staging for hba_step_host
+    uint64_t* d_stage_f = nullptr;
+    uint64_t* d_stage_s = nullptr;
+    uint64_t* d_stage_o = nullptr;
+    uint8_t* d_stage_st = nullptr;
+    // launch shapes
+    uint32_t threads = 1024;    // single-arena CTA width
+    uint32_t m_threads = 256;   // multi-arena CTA width
+    uint32_t m_ctas = 0;        // multi-arena grid (0 = one CTA per arena)
+    uint64_t* d_largest = nullptr;
+};
+
+namespace {
+
+#define HBA_CUDA_TRY(call)                         \
+    do {                                           \
+        if ((call) != cudaSuccess) {               \
+            (void)cudaGetLastError();              \
+            return HBA_ERR_CUDA;                   \
+        }                                          \
+    } while (0)
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
+                                               uint8_t* st, const uint64_t* sizes, uint32_t na,
+                                               uint64_t* out, uint32_t* scr) {
+    __shared__ hba::Smem<NT> S;
+    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr};
+    hba::arena_step<NT>(S, a);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint32_t* frow,
+                                              const uint64_t* frees, uint8_t* st, const uint32_t* arow,
+                                              const uint64_t* sizes, uint64_t* out, uint32_t* scr,
+                                              uint32_t n_arenas) {
+    __shared__ hba::Smem<NT> S;
+    for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
+        const uint32_t f0 = frow[a], f1 = frow[a + 1], a0 = arow[a], a1 = arow[a + 1];
+        Arena* ar = ars + a;
+        hba::StepArgs args{ar,
+                           pool + ar->rec_base,
+                           frees + f0,
+                           f1 - f0,
+                           st ? st + f0 : nullptr,
+                           sizes + a0,
+                           a1 - a0,
+                           out + a0,
+                           scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE};
+        hba::arena_step<NT>(S, args);
+    }
+}
+
+// Write the initial record of every arena (one free block spanning it).
+__global__ void k_init_records(const Arena* ars, Rec* pool, uint32_t n_arenas) {
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n_arenas) {
+        const Arena& ar = ars[a];
+        const Rec r{hba::mkx(ar.G, hba::ST_FREE), hba::NIL, hba::NIL, hba::NIL};
+        *reinterpret_cast<uint4*>(pool + ar.rec_base) = make_uint4(r.x, r.y, r.z, r.w);
+    }
+}
+
+// Largest free block of every arena: its highest non-empty class's list is
+// walked (bounded by the arena's block count).
+__global__ void k_largest(const Arena* ars, const Rec* pool, uint32_t n_arenas, uint64_t* out) {
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_arenas) return;
+    const Arena& ar = ars[a];
+    uint64_t best = 0;
+    if (ar.mask) {
+        const uint32_t b = 63u - (uint32_t)__clzll((long long)ar.mask);
+        const Rec* rec = pool + ar.rec_base;
+        uint64_t guard = 0;
+        for (uint32_t h = ar.heads[b]; h != hba::NIL && guard <= (uint64_t)ar.blocks; ++guard) {
+            const uint32_t sz = hba::sz_of(rec[h].x);
+            if (sz > best) best = sz;
+            h = rec[h].z;
+        }
+    }
+    out[a] = best << ar.lg;
+}
+
+hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
+                           const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
+    Arena* ar = h->d_arenas;
+    Rec* rec = h->d_rec;
+    switch (h->threads) {
+        case 128: k_single<128><<<1, 128, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
+        case 256: k_single<256><<<1, 256, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
+        case 512: k_single<512><<<1, 512, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
+        default: k_single<1024><<<1, 1024, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+}
+
+hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
+                       uint32_t na, uint64_t* out, cudaStream_t s) {
+    if (!h || h->n_arenas != 1) return HBA_ERR_INVALID_ARGUMENT;
+    if ((nf && !frees) || (na && (!sizes || !out))) return HBA_ERR_INVALID_ARGUMENT;
+    // frees beyond the scratch capacity go in consecutive slices (exact:
+    // frees apply one by one in index order)
+    while (nf > h->max_batch) {
+        hba_status_t r = launch_single(h, frees, h->max_batch, st, nullptr, 0, nullptr, s);
+        if (r != HBA_OK) return r;
+        frees += h->max_batch;
+        if (st) st += h->max_batch;
+        nf -= h->max_batch;
+    }
+    if (nf == 0 && na == 0) return HBA_OK;
+    return launch_single(h, frees, nf, st, sizes, na, out, s);
+}
+
+hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_frees, uint32_t stage) {
+    h->h_init = init;
+    h->n_arenas = (uint32_t)init.size();
+    HBA_CUDA_TRY(cudaGetDevice(&h->device));
+    if (cudaMalloc(&h->d_arenas, sizeof(Arena) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc(&h->d_rec, sizeof(Rec) * h->total_granules) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    h->scr_frees = scr_frees;
+    if (cudaMalloc(&h->d_scr, 4ull * hba::SCRATCH_WORDS_PER_FREE * std::max<uint64_t>(scr_frees, 1)) != cudaSuccess)
+        return HBA_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc(&h->d_largest, sizeof(uint64_t) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    if (stage) {
+        if (cudaMalloc(&h->d_stage_f, 8ull * stage) != cudaSuccess ||
+            cudaMalloc(&h->d_stage_s, 8ull * stage) != cudaSuccess ||
+            cudaMalloc(&h->d_stage_o, 8ull * stage) != cudaSuccess ||
+            cudaMalloc(&h->d_stage_st, stage) != cudaSuccess)
+            return HBA_ERR_OUT_OF_MEMORY;
+    }
+    return HBA_OK;
+}
+
+hba_status_t reset_impl(hba_t h, cudaStream_t s) {
+    HBA_CUDA_TRY(cudaMemsetAsync(h->d_rec, 0, sizeof(Rec) * h->total_granules, s));
+    HBA_CUDA_TRY(cudaMemcpyAsync(h->d_arenas, h->h_init.data(), sizeof(Arena) * h->n_arenas,
+                                 cudaMemcpyHostToDevice, s));
+    k_init_records<<<(h->n_arenas + 255) / 256, 256, 0, s>>>(h->d_arenas, h->d_rec, h->n_arenas);
+    HBA_CUDA_TRY(cudaGetLastError());
+    return HBA_OK;
+}
+
+void free_all(hba_t h) {
+    cudaFree(h->d_arenas);
+    cudaFree(h->d_rec);
+    cudaFree(h->d_scr);
+    cudaFree(h->d_largest);
+    cudaFree(h->d_stage_f);
+    cudaFree(h->d_stage_s);
+    cudaFree(h->d_stage_o);
+    cudaFree(h->d_stage_st);
+}
+
+bool check_geometry(uint64_t arena_bytes, uint64_t min_block, uint32_t* lg, uint64_t* a) {
+    if (min_block < 8 || (min_block & (min_block - 1))) return false;
+    *lg = (uint32_t)__builtin_ctzll(min_block);
+    *a = arena_bytes - arena_bytes % min_block;
+    const uint64_t G = *a >> *lg;
+    return G >= 1 && G <= hba::MAX_GRANULES;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hba_version(void) { return "hba 0.1 (sm_103a)"; }
+
+hba_status_t hba_create_ex(uint64_t arena_bytes, uint64_t min_block, int policy, uint32_t max_batch,
+                           hba_t* out) {
+    if (!out || policy != HBA_POLICY_SEGFIT || max_batch == 0) return HBA_ERR_INVALID_ARGUMENT;
+    uint32_t lg;
+    uint64_t a;
+    if (!check_geometry(arena_bytes, min_block, &lg, &a)) return HBA_ERR_INVALID_ARGUMENT;
+    hba_t h = new hba_s();
+    h->min_block = min_block;
+    h->lg = lg;
+    h->total_granules = a >> lg;
+    h->max_batch = max_batch;
+    std::vector<Arena> init(1);
+    hba::arena_init_host(&init[0], a, lg, 0);
+    hba_status_t r = alloc_meta(h, init, max_batch, max_batch);
+    if (r == HBA_OK) r = reset_impl(h, 0);
+    if (r == HBA_OK && cudaDeviceSynchronize() != cudaSuccess) r = HBA_ERR_CUDA;
+    if (r != HBA_OK) {
+        free_all(h);
+        delete h;
+        return r;
+    }
+    *out = h;
+    return HBA_OK;
+}
+
+hba_status_t hba_create(uint64_t arena_bytes, uint64_t min_block, int policy, hba_t* out) {
+    return hba_create_ex(arena_bytes, min_block, policy, 65536, out);
+}
+
+hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, uint64_t min_block, int policy,
+                              uint32_t max_total_frees, hba_t* out) {
+    if (!out || !arena_bytes || n_arenas == 0 || policy != HBA_POLICY_SEGFIT) return HBA_ERR_INVALID_ARGUMENT;
+    std::vector<Arena> init(n_arenas);
+    uint64_t base = 0;
+    uint32_t lg = 0;
+    for (uint32_t i = 0; i < n_arenas; ++i) {
+        uint64_t a;
+        if (!check_geometry(arena_bytes[i], min_block, &lg, &a)) return HBA_ERR_INVALID_ARGUMENT;
+        hba::arena_init_host(&init[i], a, lg, base);
+        base += a >> lg;
+    }
+    hba_t h = new hba_s();
+    h->min_block = min_block;
+    h->lg = lg;
+    h->total_granules = base;
+    h->max_batch = max_total_frees;
+    hba_status_t r = alloc_meta(h, init, max_total_frees, 0);
+    if (r == HBA_OK) r = reset_impl(h, 0);
+    if (r == HBA_OK && cudaDeviceSynchronize() != cudaSuccess) r = HBA_ERR_CUDA;
+    if (r != HBA_OK) {
+        free_all(h);
+        delete h;
+        return r;
+    }
+    *out = h;
+    return HBA_OK;
+}
+
+hba_status_t hba_destroy(hba_t h) {
+    if (!h) return HBA_ERR_INVALID_ARGUMENT;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return HBA_OK;
+}
+
+hba_status_t hba_alloc_batch(hba_t h, const uint64_t* d_sizes, uint32_t n, uint64_t* d_out_offsets,
+                             hba_stream_t stream) {
+    return step_impl(h, nullptr, 0, nullptr, d_sizes, n, d_out_offsets, (cudaStream_t)stream);
+}
+
+hba_status_t hba_free_batch(hba_t h, const uint64_t* d_offsets, uint32_t n, hba_stream_t stream) {
+    return step_impl(h, d_offsets, n, nullptr, nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+hba_status_t hba_free_batch_ex(hba_t h, const uint64_t* d_offsets, uint32_t n, uint8_t* d_status,
+                               hba_stream_t stream) {
+    return step_impl(h, d_offsets, n, d_status, nullptr, 0, nullptr, (cudaStream_t)stream);
+}
+
+hba_status_t hba_step(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status, const uint64_t* d_sizes,
+                      uint32_t na, uint64_t* d_out_offsets, hba_stream_t stream) {
+    return step_impl(h, d_frees, nf, d_status, d_sizes, na, d_out_offsets, (cudaStream_t)stream);
+}
+
+hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_t* h_status,
+                           const uint64_t* h_sizes, uint32_t na, uint64_t* h_out_offsets, hba_stream_t stream) {
+    if (!h || h->n_arenas != 1 || !h->d_stage_f) return HBA_ERR_INVALID_ARGUMENT;
+    if (nf > h->max_batch || na > h->max_batch) return HBA_ERR_INVALID_ARGUMENT;
+    if ((nf && !h_frees) || (na && (!h_sizes || !h_out_offsets))) return HBA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nf) HBA_CUDA_TRY(cudaMemcpyAsync(h->d_stage_f, h_frees, 8ull * nf, cudaMemcpyHostToDevice, s));
+    if (na) HBA_CUDA_TRY(cudaMemcpyAsync(h->d_stage_s, h_sizes, 8ull * na, cudaMemcpyHostToDevice, s));
+    hba_status_t r = step_impl(h, h->d_stage_f, nf, h_status ? h->d_stage_st : nullptr, h->d_stage_s, na,
+                               h->d_stage_o, s);
+    if (r != HBA_OK) return r;
+    if (na) HBA_CUDA_TRY(cudaMemcpyAsync(h_out_offsets, h->d_stage_o, 8ull * na, cudaMemcpyDeviceToHost, s));
+    if (nf && h_status) HBA_CUDA_TRY(cudaMemcpyAsync(h_status, h->d_stage_st, nf, cudaMemcpyDeviceToHost, s));
+    HBA_CUDA_TRY(cudaStreamSynchronize(s));
+    return HBA_OK;
+}
+
+hba_status_t hba_reset(hba_t h, hba_stream_t stream) {
+    if (!h) return HBA_ERR_INVALID_ARGUMENT;
+    return reset_impl(h, (cudaStream_t)stream);
+}
+
+hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
+    if (!h || !out) return HBA_ERR_INVALID_ARGUMENT;
+    HBA_CUDA_TRY(cudaDeviceSynchronize());
+    k_largest<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->d_largest);
+    HBA_CUDA_TRY(cudaGetLastError());
+    std::vector<Arena> ar(h->n_arenas);
+    std::vector<uint64_t> largest(h->n_arenas);
+    HBA_CUDA_TRY(cudaMemcpy(ar.data(), h->d_arenas, sizeof(Arena) * h->n_arenas, cudaMemcpyDeviceToHost));
+    HBA_CUDA_TRY(cudaMemcpy(largest.data(), h->d_largest, 8ull * h->n_arenas, cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof(*out));
+    out->n_arenas = h->n_arenas;
+    for (uint32_t i = 0; i < h->n_arenas; ++i) {
+        const Arena& a = ar[i];
+        out->alloc_ok += a.alloc_ok;
+        out->alloc_fail += a.alloc_fail;
+        out->free_ok += a.free_ok;
+        out->free_fail += a.free_fail;
+        out->used_bytes += (uint64_t)a.used_g << a.lg;
+        out->used_blocks += a.used_blocks;
+        out->blocks += a.blocks;
+        out->requested_bytes += a.requested;
+        out->arena_bytes += a.arena_bytes;
+        out->largest_free = std::max(out->largest_free, largest[i]);
+        if (a.err && !out->device_error) out->device_error = a.err;
+    }
+    out->free_bytes = out->arena_bytes - out->used_bytes;
+    out->bitmask = ar[0].mask << ar[0].lg;
+    return out->device_error ? HBA_ERR_STATE : HBA_OK;
+}
+
+hba_status_t hba_export_state(hba_t h, uint32_t arena, uint64_t* host_buf, size_t cap, size_t* len) {
+    if (!h || !len || arena >= h->n_arenas || (cap && !host_buf)) return HBA_ERR_INVALID_ARGUMENT;
+    HBA_CUDA_TRY(cudaDeviceSynchronize());
+    Arena ar;
+    HBA_CUDA_TRY(cudaMemcpy(&ar, h->d_arenas + arena, sizeof(Arena), cudaMemcpyDeviceToHost));
+    std::vector<Rec> rec(ar.G);
+    HBA_CUDA_TRY(cudaMemcpy(rec.data(), h->d_rec + ar.rec_base, sizeof(Rec) * ar.G, cudaMemcpyDeviceToHost));
+    *len = hba::export_canonical(ar, rec.data(), host_buf, cap);
+    return HBA_OK;
+}
+
+hba_status_t hba_multi_set_shape(hba_t h, uint32_t threads, uint32_t ctas) {
+    if (!h) return HBA_ERR_INVALID_ARGUMENT;
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+        return HBA_ERR_INVALID_ARGUMENT;
+    if (h->n_arenas == 1) h->threads = threads;
+    h->m_threads = threads;
+    h->m_ctas = ctas;
+    return HBA_OK;
+}
+
+hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64_t* d_frees, uint32_t nf_total,
+                            const uint32_t* d_alloc_rowptr, const uint64_t* d_sizes, uint32_t na_total,
+                            uint64_t* d_out, uint8_t* d_free_status, hba_stream_t stream) {
+    if (!h || !d_free_rowptr || !d_alloc_rowptr) return HBA_ERR_INVALID_ARGUMENT;
+    if (nf_total > h->scr_frees) return HBA_ERR_INVALID_ARGUMENT;
+    if ((nf_total && !d_frees) || (na_total && (!d_sizes || !d_out))) return HBA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t n = h->n_arenas;
+    const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
+    switch (h->m_threads) {
+        case 64: k_multi<64><<<grid, 64, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
+        case 128: k_multi<128><<<grid, 128, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
+        case 512: k_multi<512><<<grid, 512, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
+        case 1024: k_multi<1024><<<grid, 1024, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
+        default: k_multi<256><<<grid, 256, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// hba_emu.cpp -- host emulation of the batch engine, for the test suite only.
+//
+// Compiles hba_engine.cuh with HBA_EMULATE: every phase of the CTA body runs
+// as a loop over thread indices, barriers become no-ops.  The library never
+// loads this file's build; the GPU path is the only product path.  The test
+// suite uses it to check the engine's logic (chunking, run detection, list
+// surgery) against the sequential oracle at sizes and seeds a GPU run could
+// not afford, with small CTA widths that force many chunk boundaries.
+#define HBA_EMULATE 1
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "hba_engine.cuh"
+
+using namespace hba;
+
+namespace {
+struct Emu {
+    Arena ar;
+    std::vector<Rec> rec;
+    std::vector<uint32_t> scr;
+    int nt;
+};
+
+template <int NT>
+void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
+         uint32_t na, uint64_t* out) {
+    Smem<NT>* S = new Smem<NT>();
+    if (e->scr.size() < (size_t)SCRATCH_WORDS_PER_FREE * nf) e->scr.resize((size_t)SCRATCH_WORDS_PER_FREE * nf);
+    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data()};
+    arena_step<NT>(*S, a);
+    delete S;
+}
+}  // namespace
+
+extern "C" {
+
+void* emu_create(uint64_t arena_bytes, uint64_t min_block, int nt) {
+    if (min_block < 8 || (min_block & (min_block - 1))) return nullptr;
+    const uint32_t lg = (uint32_t)__builtin_ctzll(min_block);
+    const uint64_t a = arena_bytes - arena_bytes % min_block;
+    if (a == 0 || (a >> lg) > MAX_GRANULES) return nullptr;
+    Emu* e = new Emu();
+    e->nt = nt;
+    arena_init_host(&e->ar, a, lg, 0);
+    e->rec.assign(e->ar.G, Rec{0, 0, 0, 0});
+    e->rec[0] = initial_record(e->ar);
+    return e;
+}
+
+void emu_destroy(void* h) { delete (Emu*)h; }
+
+int emu_step(void* h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
+             uint32_t na, uint64_t* out) {
+    Emu* e = (Emu*)h;
+    switch (e->nt) {
+        case 4: run<4>(e, frees, nf, st, sizes, na, out); break;
+        case 32: run<32>(e, frees, nf, st, sizes, na, out); break;
+        case 256: run<256>(e, frees, nf, st, sizes, na, out); break;
+        case 1024: run<1024>(e, frees, nf, st, sizes, na, out); break;
+        default: return 1;
+    }
+    return 0;
+}
+
+size_t emu_export(void* h, uint64_t* buf, size_t cap) {
+    Emu* e = (Emu*)h;
+    return export_canonical(e->ar, e->rec.data(), buf, cap);
+}
+
+// alloc_ok, alloc_fail, free_ok, free_fail, used_bytes, used_blocks, blocks,
+// requested_bytes, bitmask (byte classes)
+void emu_stats(void* h, uint64_t* out) {
+    Emu* e = (Emu*)h;
+    const Arena& a = e->ar;
+    out[0] = a.alloc_ok;
+    out[1] = a.alloc_fail;
+    out[2] = a.free_ok;
+    out[3] = a.free_fail;
+    out[4] = (uint64_t)a.used_g << a.lg;
+    out[5] = a.used_blocks;
+    out[6] = a.blocks;
+    out[7] = a.requested;
+    out[8] = a.mask << a.lg;
+}
+}

@@ -1,0 +1,766 @@
+// hba_engine.cuh -- per-arena batch engine of the header-free segregated-fit
+// allocator (Bell, Kumar, Gill, arXiv 2405.07079, §5.1 Algorithms 4 and 5).
+//
+// One CTA applies one batch to one arena: every free in index order, then
+// every allocation in index order, with results identical to the sequential
+// algorithms.  The arena itself is never touched: the engine only reads and
+// writes the out-of-band metadata below.
+//
+// Out-of-band metadata of one arena (the replacement for boundary tags, §3):
+//   * a dense offset-to-block table, one 16-byte record per min_block granule
+//     (a direct-indexed version of the address-keyed table of §3.3):
+//        x = size in granules (bits 0..28) | state (bits 29..31)
+//        y = granule of the previous adjacent block ("prev_adj", §3.3)
+//        z = next block in its free list (free blocks), or the free claim
+//            (in-use blocks), or the compact free index (during a free phase)
+//        w = previous block in its free list (free blocks)
+//     Only records at block starts are meaningful; every other granule has
+//     x == 0 (state NONE), which is what validates a free in O(1).
+//   * per power-of-two class: the head of a doubly linked LIFO free list
+//     (§5.1) and one bit of the availability bitmap (bit k <=> list k
+//     non-empty).  Classes are counted in granules: class k holds blocks of
+//     2^k .. 2^(k+1)-1 granules, i.e. byte class k + log2(min_block).
+//
+// How the sequential semantics is reached in parallel:
+//   Free phase.  After validation (a free must name the start of an in-use
+//   block; the lowest index wins among duplicates) the freed blocks form runs
+//   of address-adjacent free blocks together with the free blocks they touch.
+//   Applying the frees one by one leaves each run merged into one block whose
+//   list push happened at the time of the LAST free inside the run (the last
+//   free joins everything).  So: find runs by pointer jumping over
+//   "predecessor freed block" links, take per run the leftmost start, the
+//   right end and the largest free index, unlink the absorbed free blocks,
+//   and push the merged blocks in increasing order of that index.
+//   Alloc phase.  Allocations only ever pop list heads and push remainders,
+//   so the most recent remainder X is always the head of its list.  While
+//   X's class L and the rest of the bitmap stay fixed, each request is
+//   either a carve from X (lowest eligible list is L), a failure (no
+//   eligible list), or an "other" pop from another list.  A block-wide scan
+//   of carve sizes resolves a whole chunk of requests at once; the chunk
+//   ends at the first "other" (applied by one thread) or at the carve that
+//   drops X below 2^L granules.  X's record is written ("materialised") only
+//   when another remainder replaces it or the phase ends -- the
+//   intermediate push/pop pairs of the sequential algorithm cancel out.
+//
+// The same source compiles for the GPU and, with HBA_EMULATE, for a
+// host-only emulation used by the test suite: each HBA_FOR_THREADS body is a
+// phase run by every thread, HBA_SYNC is the barrier between phases.  Inside
+// a phase threads never read what another thread writes in that phase, except
+// through atomics whose result is read after the barrier (and the pointer
+// jumping, where any value read is a valid ancestor).
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#ifdef HBA_EMULATE
+#include <string.h>
+#define HBA_HD static inline
+#define HBA_DEV static inline
+#define HBA_FOR_THREADS(tid) for (int tid = 0; tid < NT; ++tid)
+#define HBA_SYNC() \
+    do {           \
+    } while (0)
+#else
+#define HBA_HD __host__ __device__ __forceinline__
+#define HBA_DEV __device__ __forceinline__
+#define HBA_FOR_THREADS(tid) for (int tid = (int)threadIdx.x; tid < NT; tid += NT)
+#define HBA_SYNC() __syncthreads()
+#endif
+
+namespace hba {
+
+constexpr uint32_t NIL = 0xFFFFFFFFu;
+constexpr uint32_t SZ_BITS = 29;
+constexpr uint32_t SZ_MASK = (1u << SZ_BITS) - 1u;
+constexpr uint32_t MAX_GRANULES = SZ_MASK;  // G <= 2^29 - 1
+constexpr uint32_t ST_NONE = 0, ST_USED = 1, ST_FREE = 2, ST_NEW = 3, ST_DEL = 4;
+constexpr uint64_t FAIL64 = ~0ull;
+constexpr int NBINS = 32;  // granule classes 0..28 are reachable
+constexpr uint32_t SCRATCH_WORDS_PER_FREE = 12;
+// device error codes (Arena::err); any of them means corrupted metadata
+constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
+constexpr uint32_t ERR_EMPTY_HEAD = 2;  // a class with its bit set had no head
+
+struct alignas(16) Rec {
+    uint32_t x, y, z, w;
+};
+
+// Per-arena header, resident in device memory between batches.
+struct Arena {
+    uint64_t arena_bytes;  // managed bytes, a multiple of min_block
+    uint64_t rec_base;     // index of the arena's first record in the record pool
+    uint32_t G;            // granules
+    uint32_t lg;           // log2(min_block)
+    uint32_t heads[NBINS]; // list heads per granule class, NIL if empty
+    uint64_t mask;         // availability bitmap over granule classes
+    int64_t alloc_ok, alloc_fail, free_ok, free_fail;
+    int64_t used_g, used_blocks, blocks, requested;
+    uint32_t err, pad;
+};
+
+HBA_HD uint32_t st_of(uint32_t x) { return x >> SZ_BITS; }
+HBA_HD uint32_t sz_of(uint32_t x) { return x & SZ_MASK; }
+HBA_HD uint32_t mkx(uint32_t sz, uint32_t st) { return sz | (st << SZ_BITS); }
+
+#ifdef HBA_EMULATE
+HBA_HD uint32_t flog2(uint32_t v) { return 31u - (uint32_t)__builtin_clz(v); }
+HBA_HD uint32_t ctz64(uint64_t v) { return (uint32_t)__builtin_ctzll(v); }
+#else
+HBA_HD uint32_t flog2(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return 31u - (uint32_t)__clz(v);
+#else
+    return 31u - (uint32_t)__builtin_clz(v);
+#endif
+}
+HBA_HD uint32_t ctz64(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return (uint32_t)(__ffsll((long long)v) - 1);
+#else
+    return (uint32_t)__builtin_ctzll(v);
+#endif
+}
+#endif
+// ceil(log2 v) for v >= 1
+HBA_HD uint32_t clog2(uint32_t v) { return v <= 1 ? 0u : flog2(v - 1) + 1u; }
+
+// ---- memory helpers ------------------------------------------------------
+#ifdef HBA_EMULATE
+HBA_DEV Rec ldr(const Rec* r, uint32_t g) { return r[g]; }
+HBA_DEV void str(Rec* r, uint32_t g, Rec v) { r[g] = v; }
+HBA_DEV uint32_t at_min_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; if (v < o) *p = v; return o; }
+HBA_DEV uint32_t at_max_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; if (v > o) *p = v; return o; }
+HBA_DEV uint32_t at_add_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; *p = o + v; return o; }
+HBA_DEV void at_add_i64(int64_t* p, int64_t v) { *p += v; }
+#else
+HBA_DEV Rec ldr(const Rec* r, uint32_t g) {
+    uint4 v = *reinterpret_cast<const uint4*>(r + g);
+    return Rec{v.x, v.y, v.z, v.w};
+}
+HBA_DEV void str(Rec* r, uint32_t g, Rec v) { *reinterpret_cast<uint4*>(r + g) = make_uint4(v.x, v.y, v.z, v.w); }
+HBA_DEV uint32_t at_min_u32(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
+HBA_DEV uint32_t at_max_u32(uint32_t* p, uint32_t v) { return atomicMax(p, v); }
+HBA_DEV uint32_t at_add_u32(uint32_t* p, uint32_t v) { return atomicAdd(p, v); }
+HBA_DEV void at_add_i64(int64_t* p, int64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+#endif
+
+// ---- shared state of one CTA --------------------------------------------
+enum : uint8_t { CL_NONE = 0, CL_FAIL = 1, CL_CARVE = 2, CL_OTHER = 3 };
+
+template <int NT>
+struct Smem {
+    uint64_t A;          // arena bytes
+    uint64_t mask;       // bitmap of classes whose list is non-empty (X excluded)
+    uint32_t heads[NBINS];
+    uint32_t G, lg;
+    // the most recent remainder X (virtual head of class xL while xok)
+    uint32_t xok, xg, xsz, xprev, xright, xL, xprev_new;
+    // loop control
+    uint32_t p, ev, W, nul, nruns, flag[3];
+    uint32_t err;        // first metadata error seen by this CTA (0 = none)
+    // counter deltas of this batch
+    int64_t c_aok, c_afail, c_fok, c_ffail, c_used_g, c_used_blocks, c_blocks, c_req;
+    int64_t warp_tot[32];
+    int64_t val[NT];
+    uint32_t cnt[NT];
+    uint32_t sgr[NT];
+    uint8_t cls[NT];
+};
+
+// ---- block-wide collectives (called by all threads, outside phases) ------
+// Inclusive prefix sum of v[0..NT) in place, followed by a barrier.
+template <int NT>
+HBA_DEV void scan_incl_i64(Smem<NT>& S, int64_t* v) {
+#ifdef HBA_EMULATE
+    for (int i = 1; i < NT; ++i) v[i] += v[i - 1];
+    (void)S;
+#else
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int64_t x = v[tid];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) S.warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        if (lane < NT / 32) S.warp_tot[lane] = t;
+    }
+    __syncthreads();
+    if (wid > 0) x += S.warp_tot[wid - 1];
+    v[tid] = x;
+    __syncthreads();
+#endif
+}
+
+// Exclusive prefix sum of c[0..NT) in place; *total receives the sum.
+// Followed by a barrier.
+template <int NT>
+HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
+#ifdef HBA_EMULATE
+    uint32_t run = 0;
+    for (int i = 0; i < NT; ++i) {
+        uint32_t t = c[i];
+        c[i] = run;
+        run += t;
+    }
+    *total = run;
+    (void)S;
+#else
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int64_t own = c[tid];
+    int64_t x = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) S.warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        if (lane < NT / 32) S.warp_tot[lane] = t;
+    }
+    __syncthreads();
+    if (wid > 0) x += S.warp_tot[wid - 1];
+    c[tid] = (uint32_t)(x - own);
+    if (tid == NT - 1) *total = (uint32_t)x;
+    __syncthreads();
+#endif
+}
+
+struct StepArgs {
+    Arena* ar;
+    Rec* rec;  // the arena's records (already offset by rec_base)
+    const uint64_t* frees;
+    uint32_t nf;
+    uint8_t* fstat;  // may be null
+    const uint64_t* sizes;
+    uint32_t na;
+    uint64_t* out;
+    uint32_t* scr;   // SCRATCH_WORDS_PER_FREE * nf words
+};
+
+// Push the virtual remainder X at the head of its list and write its record
+// (one thread).
+template <int NT>
+HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec) {
+    const uint32_t b = S.xL, old = S.heads[b];
+    str(rec, S.xg, Rec{mkx(S.xsz, ST_FREE), S.xprev, old, NIL});
+    if (old != NIL) rec[old].w = S.xg;
+    S.heads[b] = S.xg;
+    S.mask |= 1ull << b;
+    if (S.xright < S.G) rec[S.xright].y = S.xg;
+    S.xok = 0;
+}
+
+// ---------------------------------------------------------------------------
+// The free phase (Algorithm 5 for all frees of the batch).
+// ---------------------------------------------------------------------------
+template <int NT>
+HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
+    const uint32_t nf = a.nf;
+    Rec* rec = a.rec;
+    uint32_t* fg = a.scr;              // [nf] by free index: granule or NIL
+    uint32_t* runAt = fg + nf;         // [nf] by free index: run leader or NIL
+    uint32_t* cg = runAt + nf;         // [W] compact: granule
+    uint32_t* cj = cg + nf;            // [W] compact: free index
+    uint32_t* root = cj + nf;          // [W] pointer-jumping root
+    uint32_t* lh = root + nf;          // [W] leftmost block of the run at my left
+    uint32_t* rend = lh + nf;          // [W] right end of my piece (max over run at root)
+    uint32_t* rmaxj = rend + nf;       // [W] largest free index (max over run at root)
+    uint32_t* fl = rmaxj + nf;         // [W] bit0: zero left old-free, bit1: zero right old-free
+    uint32_t* ul = fl + nf;            // [2 nf] free blocks absorbed by runs
+    uint32_t* runs = ul + 2 * nf;      // [nf] run leaders in free-index order
+    const uint64_t mbm = (1ull << S.lg) - 1ull;
+    const uint32_t per = (nf + NT - 1) / NT;
+
+    // F1: validate, claim (lowest index wins among duplicates).
+    HBA_FOR_THREADS(tid) {
+        for (uint32_t j = tid; j < nf; j += NT) {
+            const uint64_t off = a.frees[j];
+            uint32_t g = NIL;
+            if (off < S.A && (off & mbm) == 0) {
+                const uint32_t gg = (uint32_t)(off >> S.lg);
+                if (st_of(rec[gg].x) == ST_USED) {
+                    g = gg;
+                    at_min_u32(&rec[gg].z, j);
+                }
+            }
+            fg[j] = g;
+            runAt[j] = NIL;
+        }
+        if (tid == 0) { S.nul = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
+    }
+    HBA_SYNC();
+    // F2: winners, statuses, per-thread counts over contiguous ranges.
+    HBA_FOR_THREADS(tid) {
+        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
+        uint32_t c = 0;
+        for (uint32_t j = lo; j < hi; ++j) {
+            const uint32_t g = fg[j];
+            const bool win = g != NIL && rec[g].z == j;
+            if (!win) fg[j] = NIL;
+            if (a.fstat) a.fstat[j] = win ? 0 : 1;
+            c += win;
+        }
+        S.cnt[tid] = c;
+    }
+    HBA_SYNC();
+    scan_excl_u32<NT>(S, S.cnt, &S.W);
+    const uint32_t W = S.W;
+    // F3: compact in free-index order.
+    HBA_FOR_THREADS(tid) {
+        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
+        uint32_t w = S.cnt[tid];
+        for (uint32_t j = lo; j < hi; ++j)
+            if (fg[j] != NIL) { cg[w] = fg[j]; cj[w] = j; ++w; }
+    }
+    HBA_SYNC();
+    // F3b: mark the freed blocks NEW, map granule -> compact index.
+    HBA_FOR_THREADS(tid) {
+        int64_t freed_g = 0;
+        for (uint32_t w = tid; w < W; w += NT) {
+            const uint32_t g = cg[w];
+            const uint32_t sz = sz_of(rec[g].x);
+            rec[g].x = mkx(sz, ST_NEW);
+            rec[g].z = w;
+            freed_g += sz;
+        }
+        if (freed_g) at_add_i64(&S.c_used_g, -freed_g);
+        if (tid == 0) {
+            S.c_fok += W;
+            S.c_ffail += (int64_t)nf - (int64_t)W;
+            S.c_used_blocks -= W;
+        }
+    }
+    HBA_SYNC();
+    // F4: neighbours.  pred = the freed block to my left inside the same run
+    // (directly adjacent, or across exactly one old free block); an old free
+    // block absorbed by a run is unlinked by the freed block to its right, or
+    // by the one to its left when it ends the run.
+    HBA_FOR_THREADS(tid) {
+        for (uint32_t w = tid; w < W; w += NT) {
+            const uint32_t g = cg[w];
+            const Rec r = ldr(rec, g);
+            const uint32_t sz = sz_of(r.x);
+            uint32_t pr = NIL, head = g, flags = 0;
+            const uint32_t L = r.y;
+            if (L != NIL) {
+                const Rec rl = ldr(rec, L);
+                const uint32_t st = st_of(rl.x);
+                if (st == ST_NEW) {
+                    pr = rl.z;
+                } else if (st == ST_FREE) {
+                    ul[at_add_u32(&S.nul, 1)] = L;
+                    const uint32_t LL = rl.y;
+                    if (LL != NIL && st_of(rec[LL].x) == ST_NEW) {
+                        pr = rec[LL].z;
+                        flags |= 1;   // L is inside the run: erase its record
+                    } else {
+                        head = L;     // L starts the run
+                    }
+                }
+            }
+            uint32_t end = g + sz;
+            if (end < S.G) {
+                const uint32_t R = end;
+                const uint32_t rx = rec[R].x;
+                if (st_of(rx) == ST_FREE) {
+                    end = R + sz_of(rx);
+                    const bool rr_new = end < S.G && st_of(rec[end].x) == ST_NEW;
+                    if (!rr_new) {
+                        ul[at_add_u32(&S.nul, 1)] = R;
+                        flags |= 2;   // R ends the run: erase its record
+                    }
+                }
+            }
+            root[w] = pr == NIL ? w : pr;
+            lh[w] = head;
+            rend[w] = end;
+            rmaxj[w] = cj[w];
+            fl[w] = flags;
+        }
+    }
+    HBA_SYNC();
+    // F5: pointer jumping to the run's leftmost freed block.
+    for (int it = 0;; ++it) {
+        HBA_FOR_THREADS(tid) {
+            bool ch = false;
+            for (uint32_t w = tid; w < W; w += NT) {
+                const uint32_t r = root[w];
+                const uint32_t rr = root[r];
+                if (rr != r) { root[w] = rr; ch = true; }
+            }
+            if (ch) S.flag[it % 3] = 1;
+            if (tid == 0) S.flag[(it + 1) % 3] = 0;
+        }
+        HBA_SYNC();
+        if (!S.flag[it % 3]) break;
+    }
+    // F6: per-run right end and last free index.
+    HBA_FOR_THREADS(tid) {
+        for (uint32_t w = tid; w < W; w += NT) {
+            const uint32_t r = root[w];
+            if (r != w) {
+                at_max_u32(&rmaxj[r], cj[w]);
+                at_max_u32(&rend[r], rend[w]);
+            }
+        }
+    }
+    // F7a: mark the absorbed old free blocks.
+    HBA_FOR_THREADS(tid) {
+        for (uint32_t i = tid; i < S.nul; i += NT) {
+            const uint32_t u = ul[i];
+            rec[u].x = mkx(sz_of(rec[u].x), ST_DEL);
+        }
+    }
+    HBA_SYNC();
+    // F7b: unlink maximal segments of absorbed blocks from their lists.
+    HBA_FOR_THREADS(tid) {
+        for (uint32_t i = tid; i < S.nul; i += NT) {
+            const uint32_t u = ul[i];
+            const Rec r = ldr(rec, u);
+            const uint32_t pv = r.w;
+            if (pv != NIL && st_of(rec[pv].x) == ST_DEL) continue;  // not a segment start
+            uint32_t n = r.z;
+            uint32_t guard = 0;
+            while (n != NIL && st_of(rec[n].x) == ST_DEL) {
+                n = rec[n].z;
+                if (++guard > S.G) { S.err = ERR_LIST_WALK; n = NIL; break; }
+            }
+            if (pv == NIL) S.heads[flog2(sz_of(r.x))] = n;
+            else rec[pv].z = n;
+            if (n != NIL) rec[n].w = pv;
+        }
+    }
+    HBA_SYNC();
+    // F8: write the merged blocks, erase absorbed records.
+    HBA_FOR_THREADS(tid) {
+        uint32_t nr = 0;
+        for (uint32_t w = tid; w < W; w += NT) {
+            const uint32_t g = cg[w];
+            const Rec r = ldr(rec, g);
+            const uint32_t sz = sz_of(r.x);
+            const bool leader = root[w] == w;
+            if (fl[w] & 1) rec[r.y].x = 0;
+            if (fl[w] & 2) rec[g + sz].x = 0;
+            if (leader) {
+                const uint32_t H = lh[w], end = rend[w];
+                rec[H].x = mkx(end - H, ST_FREE);
+                if (end < S.G) rec[end].y = H;
+                runAt[rmaxj[w]] = w;
+                ++nr;
+                if (H != g) rec[g].x = 0;
+            } else {
+                rec[g].x = 0;
+            }
+        }
+        if (nr) at_add_u32(&S.nruns, nr);
+    }
+    HBA_SYNC();
+    // F9: run leaders in increasing order of their last free index.
+    HBA_FOR_THREADS(tid) {
+        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
+        uint32_t c = 0;
+        for (uint32_t j = lo; j < hi; ++j) c += runAt[j] != NIL;
+        S.cnt[tid] = c;
+    }
+    HBA_SYNC();
+    uint32_t nruns_scan;
+    scan_excl_u32<NT>(S, S.cnt, &S.flag[0]);
+    nruns_scan = S.flag[0];
+    HBA_FOR_THREADS(tid) {
+        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
+        uint32_t k = S.cnt[tid];
+        for (uint32_t j = lo; j < hi; ++j)
+            if (runAt[j] != NIL) runs[k++] = runAt[j];
+    }
+    HBA_SYNC();
+    // F10: push the merged blocks (one thread, in order), rebuild the bitmap.
+    HBA_FOR_THREADS(tid) {
+        if (tid == 0) {
+            for (uint32_t k = 0; k < nruns_scan; ++k) {
+                const uint32_t w = runs[k];
+                const uint32_t H = lh[w];
+                const uint32_t b = flog2(rend[w] - H);
+                const uint32_t old = S.heads[b];
+                rec[H].z = old;
+                rec[H].w = NIL;
+                if (old != NIL) rec[old].w = H;
+                S.heads[b] = H;
+            }
+            uint64_t m = 0;
+            for (int b = 0; b < NBINS; ++b)
+                if (S.heads[b] != NIL) m |= 1ull << b;
+            S.mask = m;
+            S.c_blocks += (int64_t)nruns_scan - (int64_t)W - (int64_t)S.nul;
+        }
+    }
+    HBA_SYNC();
+}
+
+// ---------------------------------------------------------------------------
+// The alloc phase (Algorithm 4 for all allocations of the batch).
+// ---------------------------------------------------------------------------
+template <int NT>
+HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
+    const uint32_t na = a.na;
+    Rec* rec = a.rec;
+    const uint32_t lg = S.lg;
+    const uint64_t mbm = (1ull << lg) - 1ull;
+    HBA_FOR_THREADS(tid) {
+        if (tid == 0) { S.p = 0; S.xok = 0; }
+    }
+    HBA_SYNC();
+    while (true) {
+        const uint32_t p = S.p;
+        if (p >= na) break;
+        if (!S.xok && S.mask == 0) {
+            // nothing is free: every remaining request fails
+            HBA_FOR_THREADS(tid) {
+                for (uint32_t i = p + tid; i < na; i += NT) a.out[i] = FAIL64;
+                if (tid == 0) S.c_afail += (int64_t)(na - p);
+            }
+            HBA_SYNC();
+            break;
+        }
+        // classify the chunk [p, p + NT) against the current state
+        HBA_FOR_THREADS(tid) {
+            const uint32_t i = p + tid;
+            uint8_t cl = CL_NONE;
+            uint32_t sg = 0;
+            int64_t v = 0;
+            if (i < na) {
+                const uint64_t s = a.sizes[i];
+                if (s == 0 || s > S.A) {
+                    cl = CL_FAIL;
+                } else {
+                    sg = (uint32_t)((s + mbm) >> lg);
+                    const uint32_t c = clog2(sg);
+                    const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
+                    const uint64_t cand = (M >> c) << c;
+                    if (!cand) cl = CL_FAIL;
+                    else cl = (S.xok && ctz64(cand) == S.xL) ? CL_CARVE : CL_OTHER;
+                    if (cl == CL_CARVE) v = sg;
+                }
+            }
+            S.cls[tid] = cl;
+            S.sgr[tid] = sg;
+            S.val[tid] = v;
+            if (tid == 0) S.ev = NT;
+        }
+        HBA_SYNC();
+        scan_incl_i64<NT>(S, S.val);
+        // first event: an "other", or the carve that drops X below 2^xL
+        HBA_FOR_THREADS(tid) {
+            const uint8_t cl = S.cls[tid];
+            bool e = cl == CL_OTHER;
+            if (cl == CL_CARVE && (int64_t)S.xsz - S.val[tid] < ((int64_t)1 << S.xL)) e = true;
+            if (e) at_min_u32(&S.ev, (uint32_t)tid);
+        }
+        HBA_SYNC();
+        const uint32_t ev = S.ev;
+        const uint32_t n_here = na - p < (uint32_t)NT ? na - p : (uint32_t)NT;
+        const bool ev_carve = ev < n_here && S.cls[ev] == CL_CARVE;
+        const uint32_t nres = ev >= n_here ? n_here : ev + (ev_carve ? 1u : 0u);
+        const int64_t ptot = nres ? S.val[nres - 1] : 0;
+        // resolve lanes [0, nres): failures and carves from X
+        HBA_FOR_THREADS(tid) {
+            if ((uint32_t)tid < nres) {
+                const uint32_t i = p + tid;
+                if (S.cls[tid] == CL_FAIL) {
+                    a.out[i] = FAIL64;
+                    at_add_i64(&S.c_afail, 1);
+                } else {
+                    const uint32_t sg = S.sgr[tid];
+                    const int64_t P = S.val[tid];
+                    const uint32_t start = S.xg + (uint32_t)(P - sg);
+                    const uint32_t end = S.xg + (uint32_t)P;
+                    a.out[i] = (uint64_t)start << lg;
+                    rec[start].x = mkx(sg, ST_USED);
+                    rec[start].z = NIL;
+                    rec[start].w = NIL;
+                    if (P == (int64_t)sg) rec[start].y = S.xprev;
+                    if (end < S.G) rec[end].y = start;
+                    if (P == ptot) S.xprev_new = start;
+                    at_add_i64(&S.c_aok, 1);
+                    at_add_i64(&S.c_used_g, sg);
+                    at_add_i64(&S.c_used_blocks, 1);
+                    at_add_i64(&S.c_blocks, 1);
+                    at_add_i64(&S.c_req, (int64_t)a.sizes[i]);
+                }
+            }
+        }
+        HBA_SYNC();
+        // advance X and the cursor; apply an "other" request sequentially
+        HBA_FOR_THREADS(tid) {
+            if (tid == 0) {
+                if (ptot > 0) {
+                    S.xg += (uint32_t)ptot;
+                    S.xsz -= (uint32_t)ptot;
+                    S.xprev = S.xprev_new;
+                }
+                if (ev_carve) {
+                    if (S.xsz == 0) { S.xok = 0; S.c_blocks -= 1; }
+                    else S.xL = flog2(S.xsz);
+                }
+                S.p = p + nres;
+                if (ev < n_here && !ev_carve) {
+                    const uint32_t i = p + ev;
+                    const uint32_t sg = S.sgr[ev];
+                    const uint32_t c = clog2(sg);
+                    const uint64_t cand = (S.mask >> c) << c;  // X's class is not the winner
+                    const uint32_t k = ctz64(cand);
+                    if (S.xok) materialize_x<NT>(S, rec);
+                    const uint32_t Y = S.heads[k];
+                    if (Y >= S.G) {  // bitmap and heads disagree: record, fail the request
+                        S.err = ERR_EMPTY_HEAD;
+                        S.mask &= ~(1ull << k);
+                        a.out[i] = FAIL64;
+                        S.c_afail += 1;
+                        S.p = i + 1;
+                    } else {
+                    const Rec ry = ldr(rec, Y);
+                    const uint32_t nxt = ry.z;
+                    S.heads[k] = nxt;
+                    if (nxt == NIL) S.mask &= ~(1ull << k);
+                    else rec[nxt].w = NIL;
+                    const uint32_t ysz = sz_of(ry.x);
+                    str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
+                    a.out[i] = (uint64_t)Y << lg;
+                    S.c_aok += 1;
+                    S.c_used_g += sg;
+                    S.c_used_blocks += 1;
+                    S.c_req += (int64_t)a.sizes[i];
+                    if (ysz > sg) {
+                        S.xok = 1;
+                        S.xg = Y + sg;
+                        S.xsz = ysz - sg;
+                        S.xprev = Y;
+                        S.xright = Y + ysz;
+                        S.xL = flog2(ysz - sg);
+                        S.c_blocks += 1;
+                    }
+                    S.p = i + 1;
+                    }
+                }
+            }
+        }
+        HBA_SYNC();
+    }
+    HBA_FOR_THREADS(tid) {
+        if (tid == 0 && S.xok) materialize_x<NT>(S, rec);
+    }
+    HBA_SYNC();
+}
+
+// One batch of one arena.  All threads of the CTA call this.
+template <int NT>
+HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a) {
+    HBA_FOR_THREADS(tid) {
+        for (int b = tid; b < NBINS; b += NT) S.heads[b] = a.ar->heads[b];
+        if (tid == 0) {
+            S.A = a.ar->arena_bytes;
+            S.mask = a.ar->mask;
+            S.G = a.ar->G;
+            S.lg = a.ar->lg;
+            S.xok = 0;
+            S.nruns = 0;
+            S.err = 0;
+            S.c_aok = S.c_afail = S.c_fok = S.c_ffail = 0;
+            S.c_used_g = S.c_used_blocks = S.c_blocks = S.c_req = 0;
+        }
+    }
+    HBA_SYNC();
+    if (a.nf) free_phase<NT>(S, a);
+    if (a.na) alloc_phase<NT>(S, a);
+    HBA_FOR_THREADS(tid) {
+        for (int b = tid; b < NBINS; b += NT) a.ar->heads[b] = S.heads[b];
+        if (tid == 0) {
+            Arena* ar = a.ar;
+            ar->mask = S.mask;
+            ar->alloc_ok += S.c_aok;
+            ar->alloc_fail += S.c_afail;
+            ar->free_ok += S.c_fok;
+            ar->free_fail += S.c_ffail;
+            ar->used_g += S.c_used_g;
+            ar->used_blocks += S.c_used_blocks;
+            ar->blocks += S.c_blocks;
+            ar->requested += S.c_req;
+            if (S.err && !ar->err) ar->err = S.err;
+        }
+    }
+    HBA_SYNC();
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers shared by the library and the emulation (no device code).
+// ---------------------------------------------------------------------------
+inline void arena_init_host(Arena* ar, uint64_t arena_bytes, uint32_t lg, uint64_t rec_base) {
+    memset(ar, 0, sizeof(*ar));
+    ar->arena_bytes = arena_bytes;
+    ar->rec_base = rec_base;
+    ar->G = (uint32_t)(arena_bytes >> lg);
+    ar->lg = lg;
+    for (int b = 0; b < NBINS; ++b) ar->heads[b] = NIL;
+    const uint32_t b0 = 31u - (uint32_t)__builtin_clz(ar->G);
+    ar->heads[b0] = 0;
+    ar->mask = 1ull << b0;
+    ar->blocks = 1;
+}
+inline Rec initial_record(const Arena& ar) { return Rec{mkx(ar.G, ST_FREE), NIL, NIL, NIL}; }
+
+// Canonical state (blocks in address order, lists head to tail in byte
+// classes, bitmap in byte classes) from a host copy of the arena's header and
+// records.  Returns the number of words; writes at most cap.
+inline size_t export_canonical(const Arena& ar, const Rec* rec, uint64_t* buf, size_t cap) {
+    size_t n = 0;
+    auto put = [&](uint64_t v) { if (n < cap) buf[n] = v; ++n; };
+    const uint64_t mb = 1ull << ar.lg;
+    put(ar.arena_bytes);
+    put(mb);
+    put((uint64_t)ar.blocks);
+    uint32_t g = 0;
+    uint64_t guard = 0;
+    while (g < ar.G) {
+        const Rec r = rec[g];
+        const uint32_t sz = sz_of(r.x), st = st_of(r.x);
+        if (sz == 0 || (st != ST_USED && st != ST_FREE) || ++guard > ar.G) { put(~0ull); break; }
+        put((uint64_t)g * mb);
+        put((uint64_t)sz * mb | ((uint64_t)(st == ST_FREE) << 63));
+        g += sz;
+    }
+    for (int k = 0; k < 64; ++k) {
+        const int kb = k - (int)ar.lg;
+        const size_t at = n;
+        put(0);
+        uint64_t cnt = 0;
+        if (kb >= 0 && kb < NBINS) {
+            for (uint32_t h = ar.heads[kb]; h != NIL && cnt <= ar.G; ++cnt) {
+                put((uint64_t)h * mb);
+                h = rec[h].z;
+            }
+        }
+        if (at < cap) buf[at] = cnt;
+    }
+    put(ar.mask << ar.lg);
+    return n;
+}
+
+}  // namespace hba

@@ -1,0 +1,195 @@
+"""Thin Python binding of the C ABI (include/hba.h).
+
+The functions ``hba_*`` mirror the C entry points one to one (argument
+marshalling only: raw device pointers are ints, streams are ``cudaStream_t``
+ints).  ``Allocator`` and ``MultiAllocator`` wrap them for torch tensors:
+PyTorch provides device memory and streams, every step of the allocator runs
+in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import HbaError, Stats, check, load
+
+HBA_FAIL = 0xFFFFFFFFFFFFFFFF
+HBA_POLICY_SEGFIT = 0
+
+
+def _lib():
+    return load()
+
+
+# ---- one-to-one wrappers ------------------------------------------------------
+
+def hba_create(arena_bytes: int, min_block: int, policy: int = HBA_POLICY_SEGFIT, max_batch: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    if max_batch is None:
+        check("hba_create", _lib().hba_create(arena_bytes, min_block, policy, ctypes.byref(h)))
+    else:
+        check("hba_create_ex", _lib().hba_create_ex(arena_bytes, min_block, policy, max_batch, ctypes.byref(h)))
+    return h.value
+
+
+def hba_destroy(h: int) -> None:
+    check("hba_destroy", _lib().hba_destroy(h))
+
+
+def hba_alloc_batch(h: int, d_sizes: int, n: int, d_out: int, stream: int = 0) -> None:
+    check("hba_alloc_batch", _lib().hba_alloc_batch(h, d_sizes, n, d_out, stream))
+
+
+def hba_free_batch(h: int, d_offsets: int, n: int, stream: int = 0) -> None:
+    check("hba_free_batch", _lib().hba_free_batch(h, d_offsets, n, stream))
+
+
+def hba_free_batch_ex(h: int, d_offsets: int, n: int, d_status: int, stream: int = 0) -> None:
+    check("hba_free_batch_ex", _lib().hba_free_batch_ex(h, d_offsets, n, d_status, stream))
+
+
+def hba_step(h: int, d_frees: int, nf: int, d_status: int, d_sizes: int, na: int, d_out: int, stream: int = 0) -> None:
+    check("hba_step", _lib().hba_step(h, d_frees, nf, d_status, d_sizes, na, d_out, stream))
+
+
+def hba_step_host(h: int, h_frees: int, nf: int, h_status: int, h_sizes: int, na: int, h_out: int, stream: int = 0) -> None:
+    check("hba_step_host", _lib().hba_step_host(h, h_frees, nf, h_status, h_sizes, na, h_out, stream))
+
+
+def hba_reset(h: int, stream: int = 0) -> None:
+    check("hba_reset", _lib().hba_reset(h, stream))
+
+
+def hba_stats(h: int) -> dict:
+    s = Stats()
+    check("hba_stats", _lib().hba_stats(h, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def hba_export_state(h: int, arena: int = 0) -> np.ndarray:
+    n = ctypes.c_size_t()
+    check("hba_export_state", _lib().hba_export_state(h, arena, None, 0, ctypes.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint64)
+    check("hba_export_state", _lib().hba_export_state(h, arena, buf.ctypes.data, n.value, ctypes.byref(n)))
+    return buf
+
+
+def hba_multi_create(arena_bytes, min_block: int, policy: int = HBA_POLICY_SEGFIT, max_total_frees: int = 1 << 22) -> int:
+    a = np.ascontiguousarray(arena_bytes, dtype=np.uint64)
+    h = ctypes.c_void_p()
+    check("hba_multi_create", _lib().hba_multi_create(a.size, a.ctypes.data, min_block, policy,
+                                                      max_total_frees, ctypes.byref(h)))
+    return h.value
+
+
+def hba_multi_step(h: int, d_free_rowptr: int, d_frees: int, nf_total: int, d_alloc_rowptr: int,
+                   d_sizes: int, na_total: int, d_out: int, d_free_status: int, stream: int = 0) -> None:
+    check("hba_multi_step", _lib().hba_multi_step(h, d_free_rowptr, d_frees, nf_total, d_alloc_rowptr,
+                                                  d_sizes, na_total, d_out, d_free_status, stream))
+
+
+def hba_multi_set_shape(h: int, threads: int, ctas: int = 0) -> None:
+    check("hba_multi_set_shape", _lib().hba_multi_set_shape(h, threads, ctas))
+
+
+def hba_version() -> str:
+    return _lib().hba_version().decode()
+
+
+# ---- torch convenience wrappers ----------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr()) if t is not None and t.numel() else 0
+
+
+class Allocator:
+    """One arena.  Inputs/outputs are uint64 (int64-typed) CUDA tensors."""
+
+    def __init__(self, arena_bytes: int, min_block: int, max_batch: int = 65536, threads: int | None = None):
+        self.h = hba_create(arena_bytes, min_block, HBA_POLICY_SEGFIT, max_batch)
+        self.arena_bytes = arena_bytes - arena_bytes % min_block
+        self.min_block = min_block
+        self.max_batch = max_batch
+        if threads is not None:
+            hba_multi_set_shape(self.h, threads, 0)
+
+    def close(self):
+        if self.h:
+            hba_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, frees=None, sizes=None, out=None, status=None, stream=None):
+        """Frees (index order), then allocations (index order), one launch."""
+        torch = _torch()
+        nf = 0 if frees is None else frees.numel()
+        na = 0 if sizes is None else sizes.numel()
+        if na and out is None:
+            out = torch.empty(na, dtype=torch.int64, device=sizes.device)
+        hba_step(self.h, _ptr(frees), nf, _ptr(status), _ptr(sizes), na, _ptr(out), _stream_ptr(stream))
+        return out
+
+    def alloc_batch(self, sizes, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(sizes.numel(), dtype=torch.int64, device=sizes.device)
+        hba_alloc_batch(self.h, _ptr(sizes), sizes.numel(), _ptr(out), _stream_ptr(stream))
+        return out
+
+    def free_batch(self, offsets, status=None, stream=None):
+        hba_free_batch_ex(self.h, _ptr(offsets), offsets.numel(), _ptr(status), _stream_ptr(stream))
+
+    def reset(self, stream=None):
+        hba_reset(self.h, _stream_ptr(stream))
+
+    def stats(self) -> dict:
+        return hba_stats(self.h)
+
+    def export_state(self) -> np.ndarray:
+        return hba_export_state(self.h, 0)
+
+
+class MultiAllocator:
+    """Many independent arenas; one launch applies one batch to all of them."""
+
+    def __init__(self, arena_bytes, min_block: int, max_total_frees: int = 1 << 22):
+        self.h = hba_multi_create(arena_bytes, min_block, HBA_POLICY_SEGFIT, max_total_frees)
+        self.n = len(arena_bytes)
+
+    def close(self):
+        if self.h:
+            hba_destroy(self.h)
+            self.h = 0
+
+    def set_shape(self, threads: int, ctas: int = 0):
+        hba_multi_set_shape(self.h, threads, ctas)
+
+    def step(self, free_rowptr, frees, alloc_rowptr, sizes, out, status=None, stream=None):
+        hba_multi_step(self.h, _ptr(free_rowptr), _ptr(frees), frees.numel(), _ptr(alloc_rowptr),
+                       _ptr(sizes), sizes.numel(), _ptr(out), _ptr(status), _stream_ptr(stream))
+
+    def stats(self) -> dict:
+        return hba_stats(self.h)
+
+    def export_state(self, arena: int) -> np.ndarray:
+        return hba_export_state(self.h, arena)
+
+
+__all__ = [n for n in dir() if n.startswith("hba_")] + ["Allocator", "MultiAllocator", "HbaError", "HBA_FAIL"]

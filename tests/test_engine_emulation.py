@@ -1,0 +1,136 @@
+"""The batch engine's logic, compiled for the host (HBA_EMULATE), against the
+oracle.  The kernel body runs phase by phase as loops over thread indices;
+small CTA widths force many chunk boundaries.  This checks the parallel
+formulation (run detection, list surgery, carve chunks) without a GPU; the
+GPU tests check the same source on the device."""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from _helpers import oracle_trace
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "paper_2405_07079_gb300", "csrc", "hba_emu.cpp")
+HDR = os.path.join(ROOT, "paper_2405_07079_gb300", "csrc", "hba_engine.cuh")
+OUT = os.path.join(ROOT, "paper_2405_07079_gb300", "_build", "libhba_emu_test.so")
+
+
+@pytest.fixture(scope="module")
+def emu():
+    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
+        tmp = OUT + f".{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, SRC])
+        os.replace(tmp, OUT)
+    lib = ctypes.CDLL(OUT)
+    vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+    lib.emu_create.restype = vp
+    lib.emu_create.argtypes = [u64, u64, ctypes.c_int]
+    lib.emu_destroy.argtypes = [vp]
+    lib.emu_step.argtypes = [vp, vp, u32, vp, vp, u32, vp]
+    lib.emu_export.restype = ctypes.c_size_t
+    lib.emu_export.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.emu_stats.argtypes = [vp, vp]
+    return lib
+
+
+class Emu:
+    def __init__(self, lib, A, mb, nt):
+        self.lib, self.h = lib, lib.emu_create(A, mb, nt)
+        assert self.h
+
+    def batch(self, f, s):
+        f = np.ascontiguousarray(f, np.uint64)
+        s = np.ascontiguousarray(s, np.uint64)
+        out = np.empty(s.size, np.uint64)
+        st = np.empty(f.size, np.uint8)
+        p = lambda a: a.ctypes.data if a.size else None
+        assert self.lib.emu_step(self.h, p(f), f.size, p(st), p(s), s.size, p(out)) == 0
+        return out, st
+
+    def export_state(self):
+        n = self.lib.emu_export(self.h, None, 0)
+        b = np.empty(n, np.uint64)
+        self.lib.emu_export(self.h, b.ctypes.data, n)
+        return b
+
+    def stats(self):
+        b = np.zeros(9, np.uint64)
+        self.lib.emu_stats(self.h, b.ctypes.data)
+        return [int(x) for x in b]
+
+    def close(self):
+        self.lib.emu_destroy(self.h)
+
+
+def _check(emu, wl, nt, every=1):
+    trace, o = oracle_trace(wl)
+    e = Emu(emu, wl.arena, wl.min_block, nt)
+    import oracle as _o
+    ref = _o.Oracle(wl.arena, wl.min_block)
+    try:
+        for b, (f, s, out, st) in enumerate(trace):
+            go, gs = e.batch(f, s)
+            ref.batch(f, s)
+            assert np.array_equal(go, out), f"batch {b} allocs"
+            assert np.array_equal(gs, st), f"batch {b} frees"
+            if b % every == 0:
+                assert np.array_equal(e.export_state(), ref.export_state()), f"batch {b} state"
+        assert np.array_equal(e.export_state(), o.export_state())
+        assert e.stats() == list(o.stats().values())
+    finally:
+        e.close()
+
+
+@pytest.mark.parametrize("nt", [4, 32, 256, 1024])
+def test_tiny(emu, nt):
+    from paper_2405_07079_gb300 import workloads as W
+    _check(emu, W.tiny(n_ops=4000 if nt == 4 else 10_000), nt)
+
+
+@pytest.mark.parametrize("nt", [4, 32, 256])
+def test_dense_random(emu, nt):
+    from paper_2405_07079_gb300 import workloads as W
+    wl = W.Workload("dense", 1 << 20, 256, lambda: W.TinyRandom(n_ops=4000, batch=400, p_free=0.5))
+    _check(emu, wl, nt)
+
+
+@pytest.mark.parametrize("nt", [32, 256])
+def test_lifetimes(emu, nt):
+    from paper_2405_07079_gb300 import workloads as W
+    wl = W.Workload("life", 1 << 30, 512, lambda: W.Lifetimes(n_ops=300_000, batch=8192, mean_life=100))
+    _check(emu, wl, nt, every=4)
+
+
+@pytest.mark.parametrize("nt", [32, 1024])
+def test_frag(emu, nt):
+    from paper_2405_07079_gb300 import workloads as W
+    _check(emu, W.frag(n_fill=30_000, n_big=3000, batch=2048, arena=1 << 27), nt, every=3)
+
+
+def test_many_small_arenas_random(emu):
+    """Tiny arenas with every op kind, including invalid and duplicate frees."""
+    import oracle
+    rng = np.random.default_rng(1)
+    for trial in range(150):
+        mb = int(rng.choice([8, 16, 256]))
+        A = mb * int(rng.integers(1, 200))
+        nt = int(rng.choice([4, 32]))
+        o, e = oracle.Oracle(A, mb), Emu(emu, A, mb, nt)
+        held = []
+        for _ in range(25):
+            fr = [held[int(rng.integers(0, len(held)))] if held and rng.random() < 0.8
+                  else int(rng.integers(0, A + mb)) for _ in range(int(rng.integers(0, 12)))]
+            sz = [int(x) for x in rng.integers(0, A + 2 * mb, int(rng.integers(0, 12)))]
+            f, s = np.array(fr, np.uint64), np.array(sz, np.uint64)
+            oo, os_ = o.batch(f, s)
+            eo, es = e.batch(f, s)
+            assert np.array_equal(oo, eo) and np.array_equal(os_, es), trial
+            assert np.array_equal(o.export_state(), e.export_state()), trial
+            held = [a for a in held if a not in set(fr)] + [int(x) for x in oo if x != 0xFFFFFFFFFFFFFFFF]
+        e.close()

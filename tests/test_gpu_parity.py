@@ -1,0 +1,245 @@
+"""GPU path vs the CPU oracle, bit-exact on every offset, every free status,
+the counters and the final canonical state (all integer work)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from _helpers import FAIL, check_invariants, first_diff, from_dev, oracle_trace, to_dev
+
+pytestmark = pytest.mark.gpu
+
+KiB, MiB, GiB = 1 << 10, 1 << 20, 1 << 30
+
+
+def _run(wl, threads=None, max_batches=None, state_every=0, canary=False):
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator
+
+    dev = torch.device("cuda")
+    trace, o = oracle_trace(wl, max_batches)
+    guard = None
+    if canary:
+        # a real arena of the managed size, filled with the canary byte; the
+        # allocator never receives its address, so it must stay untouched
+        guard = torch.full((wl.arena,), 0xA5, dtype=torch.uint8, device=dev)
+    with Allocator(wl.arena, wl.min_block, threads=threads) as a:
+        for b, (f, s, out, st) in enumerate(trace):
+            dst = torch.empty(f.size, dtype=torch.uint8, device=dev)
+            go = from_dev(a.step(to_dev(f, dev), to_dev(s, dev), status=dst)) if s.size else np.zeros(0, np.uint64)
+            if not s.size:
+                a.step(to_dev(f, dev), None, status=dst)
+            i = first_diff(go, out)
+            assert i is None, f"batch {b}: alloc {i}: gpu {go[i]:#x} oracle {out[i]:#x}"
+            j = first_diff(from_dev(dst), st)
+            assert j is None, f"batch {b}: free {j} status differs"
+            if state_every and b % state_every == 0:
+                assert np.array_equal(a.export_state(), o.export_state()), f"batch {b}: state differs"
+        gs = a.export_state()
+        assert np.array_equal(gs, o.export_state()), "final state differs"
+        check_invariants(gs)
+        ref = o.stats()
+        got = a.stats()
+        for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes", "used_blocks",
+                  "blocks", "requested_bytes", "bitmask"):
+            assert got[k] == ref[k], (k, got[k], ref[k])
+    if canary:
+        torch.cuda.synchronize()
+        assert bool((guard == 0xA5).all()), "the managed arena was written"
+    return trace
+
+
+def test_worked_examples(gpu_lib):
+    """W1-W3 (hand-derived from Algorithms 4/5, tests/golden/worked_examples.txt)."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator
+    from test_oracle_pins import load_golden
+
+    dev = torch.device("cuda")
+    for case in load_golden():
+        with Allocator(case["arena"], case["min_block"]) as a:
+            for frees, sizes, expect in case["batches"]:
+                f = to_dev(np.array(frees, np.uint64), dev)
+                s = to_dev(np.array(sizes, np.uint64), dev)
+                got = from_dev(a.step(f, s)) if sizes else np.zeros(0, np.uint64)
+                if not sizes:
+                    a.step(f, None)
+                assert [int(x) for x in got] == expect, case["name"]
+            if case.get("final") is not None:
+                assert [int(x) for x in a.export_state()] == case["final"], case["name"]
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512, 1024])
+def test_tiny_full(gpu_lib, threads):
+    """1 MiB arena, 10,000 ops in batches of 64, canary arena untouched."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    _run(W.tiny(), threads=threads, state_every=16, canary=True)
+
+
+@pytest.mark.parametrize("threads", [128, 1024])
+def test_large_reduced(gpu_lib, threads):
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.Workload("large-1GiB", 1 * GiB, 512, lambda: W.Lifetimes(n_ops=400_000, batch=8192, mean_life=300))
+    _run(wl, threads=threads, state_every=5)
+
+
+def test_large_full(gpu_lib):
+    """16 GiB arena, 10M ops in batches of 65,536: every result of every batch
+    (the launch configuration the benchmark times)."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    _run(W.large(), threads=1024, state_every=50)
+
+
+def test_frag_reduced(gpu_lib):
+    from paper_2405_07079_gb300 import workloads as W
+
+    trace = _run(W.frag(n_fill=60_000, n_big=4000, batch=4096, arena=256 * MiB), threads=512, state_every=4)
+    assert trace[-1][0].size > 0
+
+
+def test_frag_full_returns_to_one_block(gpu_lib):
+    """4 GiB, 1M x 4 KiB fill, free evens, 50k big, free all -> one block."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    trace = _run(W.frag(), threads=1024)
+    fill = np.concatenate([t[2] for t in trace[:62]])
+    assert np.array_equal(fill, np.arange(1_000_000, dtype=np.uint64) * 4096)
+
+
+def test_frag_pow2_fill_all_big_fail(gpu_lib):
+    """Fill with 2^20 x 4 KiB: the arena is exactly full with 4 KiB holes
+    after the even frees, so every later request (class >= 13) fails."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    trace = _run(W.frag(n_fill=1 << 20), threads=1024)
+    big = [t for t in trace if t[1].size and t[1][0] != 4096]
+    assert big and all((t[2] == FAIL).all() for t in big)
+
+
+def test_edge_cases(gpu_lib):
+    """Empty batches, size 0, oversize, whole-arena, invalid/duplicate frees."""
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import Allocator
+
+    dev = torch.device("cuda")
+    A, mb = 1 << 20, 256
+    o = oracle.Oracle(A, mb)
+    batches = [
+        ([], []),
+        ([], [0, A + 1, 1 << 63, FAIL, A]),          # only the whole-arena request succeeds
+        ([0, 0, 1, 256, A, FAIL], [1]),               # duplicate, misaligned, interior, out of range
+        ([0], []),                                    # double free across batches
+        ([], [255, 256, 257, 4096, 65536, 1000]),
+        ([256, 0, 512, 512, 1024], [A]),              # ragged frees incl. a free block
+        ([], [1] * 5000),                             # many tiny requests
+    ]
+    with Allocator(A, mb, threads=256) as a:
+        for f, s in batches:
+            f = np.array(f, np.uint64)
+            s = np.array(s, np.uint64)
+            ro, rs = o.batch(f, s)
+            dst = torch.empty(f.size, dtype=torch.uint8, device=dev)
+            out = a.step(to_dev(f, dev) if f.size else None, to_dev(s, dev) if s.size else None, status=dst)
+            if s.size:
+                assert np.array_equal(from_dev(out), ro)
+            assert np.array_equal(from_dev(dst), rs)
+            assert np.array_equal(a.export_state(), o.export_state())
+
+
+def test_free_slices_beyond_scratch(gpu_lib):
+    """A batch with more frees than the scratch holds is applied in slices."""
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import Allocator
+
+    dev = torch.device("cuda")
+    A, mb = 64 * MiB, 256
+    o = oracle.Oracle(A, mb)
+    rng = np.random.default_rng(7)
+    sizes = rng.integers(1, 8192, 3000).astype(np.uint64)
+    with Allocator(A, mb, max_batch=100, threads=128) as a:
+        ro, _ = o.batch(np.zeros(0, np.uint64), sizes)
+        go = from_dev(a.step(None, to_dev(sizes, dev)))
+        assert np.array_equal(go, ro)
+        frees = ro[ro != FAIL][rng.permutation(int((ro != FAIL).sum()))]
+        frees = np.concatenate([frees, frees[:50]])
+        ro2, rs2 = o.batch(frees, sizes[:500])
+        dst = torch.empty(frees.size, dtype=torch.uint8, device=dev)
+        go2 = from_dev(a.step(to_dev(frees, dev), to_dev(sizes[:500], dev), status=dst))
+        assert np.array_equal(go2, ro2) and np.array_equal(from_dev(dst), rs2)
+        assert np.array_equal(a.export_state(), o.export_state())
+
+
+def test_host_entry_point(gpu_lib):
+    """hba_step_host (host buffers, copies inside) equals the device path."""
+    import ctypes
+
+    from paper_2405_07079_gb300 import Allocator, hba_step_host
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.tiny(n_ops=2000)
+    trace, _ = oracle_trace(wl)
+    with Allocator(wl.arena, wl.min_block) as a:
+        for f, s, out, st in trace:
+            f = np.ascontiguousarray(f)
+            s = np.ascontiguousarray(s)
+            go = np.empty(s.size, np.uint64)
+            gst = np.empty(f.size, np.uint8)
+            hba_step_host(a.h, f.ctypes.data if f.size else 0, f.size, gst.ctypes.data if f.size else 0,
+                          s.ctypes.data if s.size else 0, s.size, go.ctypes.data if s.size else 0, 0)
+            assert np.array_equal(go, out) and np.array_equal(gst, st)
+
+
+def test_multi_arena_matches_per_arena_oracle(gpu_lib):
+    """Independent arenas in one launch: arena i's results equal a single-arena
+    oracle run of arena i's sub-trace."""
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import MultiAllocator
+    from paper_2405_07079_gb300 import workloads as W
+
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(11)
+    n = 37
+    sizes_a = (rng.integers(1, 64, n) * 256 * 1024 + rng.integers(0, 4, n) * 256).astype(np.uint64)
+    mb = 256
+    orcs = [oracle.Oracle(int(x), mb) for x in sizes_a]
+    clients = [W.Lifetimes(n_ops=10**9, batch=int(rng.integers(0, 700)), mean_life=200,
+                           seed=W.BASE_SEED + 100 + i, scale=float(x) / (16 * GiB), min_size=256)
+               for i, x in enumerate(sizes_a)]
+    for threads in (64, 256):
+        m = MultiAllocator(sizes_a, mb, max_total_frees=1 << 16)
+        m.set_shape(threads)
+        orcs = [oracle.Oracle(int(x), mb) for x in sizes_a]
+        clients = [W.Lifetimes(n_ops=10**9, batch=int(rng.integers(0, 700)), mean_life=200,
+                               seed=W.BASE_SEED + 100 + i, scale=float(x) / (16 * GiB), min_size=256)
+                   for i, x in enumerate(sizes_a)]
+        for b in range(12):
+            fr, sz, exp_o, exp_s = [], [], [], []
+            for i in range(n):
+                f, s = clients[i].next_batch()
+                ro, rs = orcs[i].batch(f, s)
+                clients[i].feed(ro)
+                fr.append(f); sz.append(s); exp_o.append(ro); exp_s.append(rs)
+            frow = np.concatenate([[0], np.cumsum([x.size for x in fr])]).astype(np.uint32)
+            arow = np.concatenate([[0], np.cumsum([x.size for x in sz])]).astype(np.uint32)
+            F = np.concatenate(fr).astype(np.uint64)
+            S = np.concatenate(sz).astype(np.uint64)
+            out = torch.empty(S.size, dtype=torch.int64, device=dev)
+            st = torch.empty(F.size, dtype=torch.uint8, device=dev)
+            m.step(to_dev(frow.view(np.int32), dev), to_dev(F, dev), to_dev(arow.view(np.int32), dev),
+                   to_dev(S, dev), out, st)
+            assert np.array_equal(from_dev(out), np.concatenate(exp_o)), f"threads {threads} batch {b}"
+            assert np.array_equal(from_dev(st), np.concatenate(exp_s))
+        for i in range(n):
+            assert np.array_equal(m.export_state(i), orcs[i].export_state()), i
+        m.close()
