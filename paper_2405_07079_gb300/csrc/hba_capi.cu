@@ -51,21 +51,28 @@ namespace {
         }                                          \
     } while (0)
 
+// Shared memory for pointer jumping over the applied frees of one batch:
+// batches with more applied frees use the global scratch instead.
+constexpr uint32_t RCAP_SINGLE = 16384;  // 64 KiB, one CTA per SM
+constexpr uint32_t RCAP_MULTI = 2048;    // 8 KiB, several CTAs per SM
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
                                                uint8_t* st, const uint64_t* sizes, uint32_t na,
-                                               uint64_t* out, uint32_t* scr) {
+                                               uint64_t* out, uint32_t* scr, uint32_t rcap) {
     __shared__ hba::Smem<NT> S;
+    extern __shared__ uint32_t root_sm[];
     hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr};
-    hba::arena_step<NT>(S, a);
+    hba::arena_step<NT>(S, a, root_sm, rcap);
 }
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint32_t* frow,
                                               const uint64_t* frees, uint8_t* st, const uint32_t* arow,
                                               const uint64_t* sizes, uint64_t* out, uint32_t* scr,
-                                              uint32_t n_arenas) {
+                                              uint32_t n_arenas, uint32_t rcap) {
     __shared__ hba::Smem<NT> S;
+    extern __shared__ uint32_t root_sm[];
     for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
         const uint32_t f0 = frow[a], f1 = frow[a + 1], a0 = arow[a], a1 = arow[a + 1];
         Arena* ar = ars + a;
@@ -78,8 +85,14 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            a1 - a0,
                            out + a0,
                            scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE};
-        hba::arena_step<NT>(S, args);
+        hba::arena_step<NT>(S, args, root_sm, rcap);
     }
+}
+
+template <int NT>
+void set_smem_limits() {
+    cudaFuncSetAttribute(k_single<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, RCAP_SINGLE * 4);
+    cudaFuncSetAttribute(k_multi<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, RCAP_MULTI * 4);
 }
 
 // Write the initial record of every arena (one free block spanning it).
@@ -116,11 +129,13 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
                            const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
+    const size_t dyn = RCAP_SINGLE * 4;
     switch (h->threads) {
-        case 128: k_single<128><<<1, 128, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
-        case 256: k_single<256><<<1, 256, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
-        case 512: k_single<512><<<1, 512, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
-        default: k_single<1024><<<1, 1024, 0, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr); break;
+        case 64: k_single<64><<<1, 64, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
+        case 128: k_single<128><<<1, 128, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
+        case 256: k_single<256><<<1, 256, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
+        case 512: k_single<512><<<1, 512, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
+        default: k_single<1024><<<1, 1024, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
     }
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
@@ -143,6 +158,12 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
 }
 
 hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_frees, uint32_t stage) {
+    set_smem_limits<64>();
+    set_smem_limits<128>();
+    set_smem_limits<256>();
+    set_smem_limits<512>();
+    set_smem_limits<1024>();
+    HBA_CUDA_TRY(cudaGetLastError());
     h->h_init = init;
     h->n_arenas = (uint32_t)init.size();
     HBA_CUDA_TRY(cudaGetDevice(&h->device));
@@ -364,11 +385,11 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     const uint32_t n = h->n_arenas;
     const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
     switch (h->m_threads) {
-        case 64: k_multi<64><<<grid, 64, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
-        case 128: k_multi<128><<<grid, 128, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
-        case 512: k_multi<512><<<grid, 512, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
-        case 1024: k_multi<1024><<<grid, 1024, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
-        default: k_multi<256><<<grid, 256, 0, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n); break;
+        case 64: k_multi<64><<<grid, 64, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
+        case 128: k_multi<128><<<grid, 128, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
+        case 512: k_multi<512><<<grid, 512, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
+        case 1024: k_multi<1024><<<grid, 1024, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
+        default: k_multi<256><<<grid, 256, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
     }
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }

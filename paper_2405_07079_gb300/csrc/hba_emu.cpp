@@ -30,7 +30,10 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
     Smem<NT>* S = new Smem<NT>();
     if (e->scr.size() < (size_t)SCRATCH_WORDS_PER_FREE * nf) e->scr.resize((size_t)SCRATCH_WORDS_PER_FREE * nf);
     StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data()};
-    arena_step<NT>(*S, a);
+    // a small shared-memory pointer-jumping area, so both the shared and the
+    // global variant run
+    std::vector<uint32_t> root_sm(64);
+    arena_step<NT>(*S, a, root_sm.data(), (uint32_t)root_sm.size());
     delete S;
 }
 }  // namespace

@@ -68,6 +68,14 @@
 #define HBA_SYNC() __syncthreads()
 #endif
 
+// Phase-boundary hook for timing probes; compiled out unless a probe build
+// defines it.
+#ifndef HBA_PROF
+#define HBA_PROF(slot) \
+    do {               \
+    } while (0)
+#endif
+
 namespace hba {
 
 constexpr uint32_t NIL = 0xFFFFFFFFu;
@@ -77,7 +85,7 @@ constexpr uint32_t MAX_GRANULES = SZ_MASK;  // G <= 2^29 - 1
 constexpr uint32_t ST_NONE = 0, ST_USED = 1, ST_FREE = 2, ST_NEW = 3, ST_DEL = 4;
 constexpr uint64_t FAIL64 = ~0ull;
 constexpr int NBINS = 32;  // granule classes 0..28 are reachable
-constexpr uint32_t SCRATCH_WORDS_PER_FREE = 12;
+constexpr uint32_t SCRATCH_WORDS_PER_FREE = 16;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
 constexpr uint32_t ERR_EMPTY_HEAD = 2;  // a class with its bit set had no head
@@ -149,9 +157,12 @@ HBA_DEV void at_add_i64(int64_t* p, int64_t v) {
 
 // ---- shared state of one CTA --------------------------------------------
 enum : uint8_t { CL_NONE = 0, CL_FAIL = 1, CL_CARVE = 2, CL_OTHER = 3 };
+// per-warp counter slots (summed once per batch; no contended atomics)
+enum : int { C_AOK = 0, C_AFAIL, C_FOK, C_FFAIL, C_USEDG, C_REQ, C_NOSPLIT, C_BLOCKS, NCNT };
 
 template <int NT>
 struct Smem {
+    static constexpr int NW = NT >= 32 ? NT / 32 : 1;
     uint64_t A;          // arena bytes
     uint64_t mask;       // bitmap of classes whose list is non-empty (X excluded)
     uint32_t heads[NBINS];
@@ -161,14 +172,49 @@ struct Smem {
     // loop control
     uint32_t p, ev, W, nul, nruns, flag[3];
     uint32_t err;        // first metadata error seen by this CTA (0 = none)
-    // counter deltas of this batch
-    int64_t c_aok, c_afail, c_fok, c_ffail, c_used_g, c_used_blocks, c_blocks, c_req;
+    uint32_t rcap;       // capacity of root_sm
+    uint32_t* root_sm;   // pointer-jumping array in shared memory
+    int64_t wc[NW][NCNT];
     int64_t warp_tot[32];
-    int64_t val[NT];
+    int64_t val[NT];     // carve sizes, then their inclusive prefix
+    uint64_t s64[NT];    // request sizes of the chunk
     uint32_t cnt[NT];
-    uint32_t sgr[NT];
-    uint8_t cls[NT];
+    uint32_t sgr[NT];    // rounded sizes in granules
+    uint8_t cls[NT];     // speculative class of each lane
+    uint8_t ccl[NT];     // size class c of each lane
 };
+
+// ---- warp-aggregated counters (call convergently from every thread) ------
+template <int NT>
+HBA_DEV void warp_count(Smem<NT>& S, int tid, int k, bool pred) {
+#ifdef HBA_EMULATE
+    S.wc[tid / 32][k] += pred ? 1 : 0;
+#else
+    const unsigned b = __ballot_sync(0xffffffffu, pred);
+    if ((tid & 31) == 0) S.wc[tid >> 5][k] += __popc(b);
+#endif
+}
+template <int NT>
+HBA_DEV void warp_sum(Smem<NT>& S, int tid, int k, int64_t v) {
+#ifdef HBA_EMULATE
+    S.wc[tid / 32][k] += v;
+#else
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) S.wc[tid >> 5][k] += v;
+#endif
+}
+// one thread (tid 0), in a phase where no warp_* call runs
+template <int NT>
+HBA_DEV void single_add(Smem<NT>& S, int k, int64_t v) { S.wc[0][k] += v; }
+
+HBA_DEV void prefetch_l2(const void* p) {
+#ifdef HBA_EMULATE
+    (void)p;
+#else
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#endif
+}
 
 // ---- block-wide collectives (called by all threads, outside phases) ------
 // Inclusive prefix sum of v[0..NT) in place, followed by a barrier.
@@ -276,38 +322,48 @@ template <int NT>
 HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t nf = a.nf;
     Rec* rec = a.rec;
-    uint32_t* fg = a.scr;              // [nf] by free index: granule or NIL
-    uint32_t* runAt = fg + nf;         // [nf] by free index: run leader or NIL
-    uint32_t* cg = runAt + nf;         // [W] compact: granule
-    uint32_t* cj = cg + nf;            // [W] compact: free index
-    uint32_t* root = cj + nf;          // [W] pointer-jumping root
-    uint32_t* lh = root + nf;          // [W] leftmost block of the run at my left
-    uint32_t* rend = lh + nf;          // [W] right end of my piece (max over run at root)
-    uint32_t* rmaxj = rend + nf;       // [W] largest free index (max over run at root)
-    uint32_t* fl = rmaxj + nf;         // [W] bit0: zero left old-free, bit1: zero right old-free
-    uint32_t* ul = fl + nf;            // [2 nf] free blocks absorbed by runs
+    uint32_t* fg = a.scr;              // by free index j: granule, or NIL if rejected
+    uint32_t* fsz = fg + nf;           //   size of the freed block (granules)
+    uint32_t* fy = fsz + nf;           //   its previous adjacent block
+    uint32_t* runAt = fy + nf;         //   run leader whose last free is j, or NIL
+    uint32_t* cg = runAt + nf;         // by compact index w (applied frees in order)
+    uint32_t* csz = cg + nf;
+    uint32_t* cy = csz + nf;
+    uint32_t* cj = cy + nf;            //   free index
+    uint32_t* rootg = cj + nf;         //   pointer-jumping root (when it does not fit in smem)
+    uint32_t* lh = rootg + nf;         //   leftmost block of the run at my left
+    uint32_t* rend = lh + nf;          //   right end of my piece (max over the run at the root)
+    uint32_t* rmaxj = rend + nf;       //   largest free index (max over the run at the root)
+    uint32_t* fl = rmaxj + nf;         //   bit0: erase left old-free record, bit1: erase right one
+    uint32_t* ul = fl + nf;            // [2 nf] old free blocks absorbed by runs
     uint32_t* runs = ul + 2 * nf;      // [nf] run leaders in free-index order
     const uint64_t mbm = (1ull << S.lg) - 1ull;
     const uint32_t per = (nf + NT - 1) / NT;
 
-    // F1: validate, claim (lowest index wins among duplicates).
+    // F1: validate (start of an in-use block), claim (lowest index wins).
     HBA_FOR_THREADS(tid) {
         for (uint32_t j = tid; j < nf; j += NT) {
             const uint64_t off = a.frees[j];
-            uint32_t g = NIL;
+            uint32_t g = NIL, sz = 0, y = NIL;
             if (off < S.A && (off & mbm) == 0) {
                 const uint32_t gg = (uint32_t)(off >> S.lg);
-                if (st_of(rec[gg].x) == ST_USED) {
+                const Rec r = ldr(rec, gg);
+                if (st_of(r.x) == ST_USED) {
                     g = gg;
+                    sz = sz_of(r.x);
+                    y = r.y;
                     at_min_u32(&rec[gg].z, j);
                 }
             }
             fg[j] = g;
+            fsz[j] = sz;
+            fy[j] = y;
             runAt[j] = NIL;
         }
-        if (tid == 0) { S.nul = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
+        if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
     }
     HBA_SYNC();
+    HBA_PROF(1);
     // F2: winners, statuses, per-thread counts over contiguous ranges.
     HBA_FOR_THREADS(tid) {
         const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
@@ -324,70 +380,70 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     HBA_SYNC();
     scan_excl_u32<NT>(S, S.cnt, &S.W);
     const uint32_t W = S.W;
-    // F3: compact in free-index order.
+    uint32_t* root = W <= S.rcap ? S.root_sm : rootg;
+    HBA_PROF(2);
+    // F3: compact in free-index order; mark the freed blocks NEW and map
+    // granule -> compact index.
     HBA_FOR_THREADS(tid) {
         const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
         uint32_t w = S.cnt[tid];
-        for (uint32_t j = lo; j < hi; ++j)
-            if (fg[j] != NIL) { cg[w] = fg[j]; cj[w] = j; ++w; }
-    }
-    HBA_SYNC();
-    // F3b: mark the freed blocks NEW, map granule -> compact index.
-    HBA_FOR_THREADS(tid) {
-        int64_t freed_g = 0;
-        for (uint32_t w = tid; w < W; w += NT) {
-            const uint32_t g = cg[w];
-            const uint32_t sz = sz_of(rec[g].x);
-            rec[g].x = mkx(sz, ST_NEW);
-            rec[g].z = w;
-            freed_g += sz;
+        int64_t freed = 0;
+        for (uint32_t j = lo; j < hi; ++j) {
+            const uint32_t g = fg[j];
+            if (g != NIL) {
+                const uint32_t sz = fsz[j];
+                cg[w] = g;
+                csz[w] = sz;
+                cy[w] = fy[j];
+                cj[w] = j;
+                rec[g].x = mkx(sz, ST_NEW);
+                rec[g].z = w;
+                freed += sz;
+                ++w;
+            }
         }
-        if (freed_g) at_add_i64(&S.c_used_g, -freed_g);
+        warp_sum(S, tid, C_USEDG, -freed);
         if (tid == 0) {
-            S.c_fok += W;
-            S.c_ffail += (int64_t)nf - (int64_t)W;
-            S.c_used_blocks -= W;
+            single_add(S, C_FOK, W);
+            single_add(S, C_FFAIL, (int64_t)nf - (int64_t)W);
         }
     }
     HBA_SYNC();
+    HBA_PROF(3);
     // F4: neighbours.  pred = the freed block to my left inside the same run
     // (directly adjacent, or across exactly one old free block); an old free
     // block absorbed by a run is unlinked by the freed block to its right, or
     // by the one to its left when it ends the run.
     HBA_FOR_THREADS(tid) {
         for (uint32_t w = tid; w < W; w += NT) {
-            const uint32_t g = cg[w];
-            const Rec r = ldr(rec, g);
-            const uint32_t sz = sz_of(r.x);
+            const uint32_t g = cg[w], sz = csz[w], L = cy[w];
+            uint32_t end = g + sz;
+            Rec rl{0, NIL, 0, 0};
+            uint32_t rx = 0;
+            if (L != NIL) rl = ldr(rec, L);
+            if (end < S.G) rx = rec[end].x;
             uint32_t pr = NIL, head = g, flags = 0;
-            const uint32_t L = r.y;
-            if (L != NIL) {
-                const Rec rl = ldr(rec, L);
-                const uint32_t st = st_of(rl.x);
-                if (st == ST_NEW) {
-                    pr = rl.z;
-                } else if (st == ST_FREE) {
-                    ul[at_add_u32(&S.nul, 1)] = L;
-                    const uint32_t LL = rl.y;
-                    if (LL != NIL && st_of(rec[LL].x) == ST_NEW) {
-                        pr = rec[LL].z;
-                        flags |= 1;   // L is inside the run: erase its record
-                    } else {
-                        head = L;     // L starts the run
-                    }
+            const uint32_t lst = st_of(rl.x);
+            if (lst == ST_NEW) {
+                pr = rl.z;
+            } else if (lst == ST_FREE) {
+                ul[at_add_u32(&S.nul, 1)] = L;
+                const uint32_t LL = rl.y;
+                const Rec rll = LL != NIL ? ldr(rec, LL) : Rec{0, 0, 0, 0};
+                if (st_of(rll.x) == ST_NEW) {
+                    pr = rll.z;
+                    flags |= 1;   // L is inside the run: erase its record
+                } else {
+                    head = L;     // L starts the run
                 }
             }
-            uint32_t end = g + sz;
-            if (end < S.G) {
+            if (st_of(rx) == ST_FREE) {
                 const uint32_t R = end;
-                const uint32_t rx = rec[R].x;
-                if (st_of(rx) == ST_FREE) {
-                    end = R + sz_of(rx);
-                    const bool rr_new = end < S.G && st_of(rec[end].x) == ST_NEW;
-                    if (!rr_new) {
-                        ul[at_add_u32(&S.nul, 1)] = R;
-                        flags |= 2;   // R ends the run: erase its record
-                    }
+                end = R + sz_of(rx);
+                const bool rr_new = end < S.G && st_of(rec[end].x) == ST_NEW;
+                if (!rr_new) {
+                    ul[at_add_u32(&S.nul, 1)] = R;
+                    flags |= 2;   // R ends the run: erase its record
                 }
             }
             root[w] = pr == NIL ? w : pr;
@@ -398,6 +454,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_SYNC();
+    HBA_PROF(4);
     // F5: pointer jumping to the run's leftmost freed block.
     for (int it = 0;; ++it) {
         HBA_FOR_THREADS(tid) {
@@ -413,7 +470,8 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         HBA_SYNC();
         if (!S.flag[it % 3]) break;
     }
-    // F6: per-run right end and last free index.
+    HBA_PROF(5);
+    // F6: per-run right end and last free index; F7a: mark absorbed blocks.
     HBA_FOR_THREADS(tid) {
         for (uint32_t w = tid; w < W; w += NT) {
             const uint32_t r = root[w];
@@ -422,16 +480,14 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                 at_max_u32(&rend[r], rend[w]);
             }
         }
-    }
-    // F7a: mark the absorbed old free blocks.
-    HBA_FOR_THREADS(tid) {
         for (uint32_t i = tid; i < S.nul; i += NT) {
             const uint32_t u = ul[i];
             rec[u].x = mkx(sz_of(rec[u].x), ST_DEL);
         }
     }
     HBA_SYNC();
-    // F7b: unlink maximal segments of absorbed blocks from their lists.
+    HBA_PROF(6);
+    // F7: unlink maximal segments of absorbed blocks from their lists.
     HBA_FOR_THREADS(tid) {
         for (uint32_t i = tid; i < S.nul; i += NT) {
             const uint32_t u = ul[i];
@@ -450,17 +506,15 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_SYNC();
+    HBA_PROF(7);
     // F8: write the merged blocks, erase absorbed records.
     HBA_FOR_THREADS(tid) {
         uint32_t nr = 0;
         for (uint32_t w = tid; w < W; w += NT) {
-            const uint32_t g = cg[w];
-            const Rec r = ldr(rec, g);
-            const uint32_t sz = sz_of(r.x);
-            const bool leader = root[w] == w;
-            if (fl[w] & 1) rec[r.y].x = 0;
-            if (fl[w] & 2) rec[g + sz].x = 0;
-            if (leader) {
+            const uint32_t g = cg[w], sz = csz[w], f = fl[w];
+            if (f & 1) rec[cy[w]].x = 0;
+            if (f & 2) rec[g + sz].x = 0;
+            if (root[w] == w) {
                 const uint32_t H = lh[w], end = rend[w];
                 rec[H].x = mkx(end - H, ST_FREE);
                 if (end < S.G) rec[end].y = H;
@@ -474,6 +528,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         if (nr) at_add_u32(&S.nruns, nr);
     }
     HBA_SYNC();
+    HBA_PROF(8);
     // F9: run leaders in increasing order of their last free index.
     HBA_FOR_THREADS(tid) {
         const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
@@ -482,9 +537,8 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         S.cnt[tid] = c;
     }
     HBA_SYNC();
-    uint32_t nruns_scan;
     scan_excl_u32<NT>(S, S.cnt, &S.flag[0]);
-    nruns_scan = S.flag[0];
+    const uint32_t nruns = S.flag[0];
     HBA_FOR_THREADS(tid) {
         const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
         uint32_t k = S.cnt[tid];
@@ -492,10 +546,11 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             if (runAt[j] != NIL) runs[k++] = runAt[j];
     }
     HBA_SYNC();
+    HBA_PROF(9);
     // F10: push the merged blocks (one thread, in order), rebuild the bitmap.
     HBA_FOR_THREADS(tid) {
         if (tid == 0) {
-            for (uint32_t k = 0; k < nruns_scan; ++k) {
+            for (uint32_t k = 0; k < nruns; ++k) {
                 const uint32_t w = runs[k];
                 const uint32_t H = lh[w];
                 const uint32_t b = flog2(rend[w] - H);
@@ -509,15 +564,80 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             for (int b = 0; b < NBINS; ++b)
                 if (S.heads[b] != NIL) m |= 1ull << b;
             S.mask = m;
-            S.c_blocks += (int64_t)nruns_scan - (int64_t)W - (int64_t)S.nul;
+            single_add(S, C_BLOCKS, (int64_t)nruns - (int64_t)W - (int64_t)S.nul);
         }
     }
     HBA_SYNC();
+    HBA_PROF(10);
 }
 
 // ---------------------------------------------------------------------------
 // The alloc phase (Algorithm 4 for all allocations of the batch).
 // ---------------------------------------------------------------------------
+
+// Apply request i alone against the current state (one thread): the
+// general step of Algorithm 4 -- fail, carve from X, or pop another list.
+template <int NT>
+HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s, uint32_t sg, uint32_t c) {
+    Rec* rec = a.rec;
+    const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
+    const uint64_t cand = sg ? (M >> c) << c : 0ull;
+    if (!cand) {
+        a.out[i] = FAIL64;
+        single_add(S, C_AFAIL, 1);
+        return;
+    }
+    const uint32_t k = ctz64(cand);
+    if (S.xok && k == S.xL) {
+        // carve the front of X
+        const uint32_t start = S.xg;
+        str(rec, start, Rec{mkx(sg, ST_USED), S.xprev, NIL, NIL});
+        a.out[i] = (uint64_t)start << S.lg;
+        S.xg += sg;
+        S.xsz -= sg;
+        S.xprev = start;
+        if (S.xsz == 0) {
+            S.xok = 0;
+            if (S.xright < S.G) rec[S.xright].y = start;
+            single_add(S, C_NOSPLIT, 1);
+        } else {
+            S.xL = flog2(S.xsz);
+        }
+    } else {
+        // pop the head of list k; the old X becomes a listed block first
+        if (S.xok) materialize_x<NT>(S, rec);
+        const uint32_t Y = S.heads[k];
+        if (Y >= S.G) {  // bitmap and heads disagree: record, fail the request
+            S.err = ERR_EMPTY_HEAD;
+            S.mask &= ~(1ull << k);
+            a.out[i] = FAIL64;
+            single_add(S, C_AFAIL, 1);
+            return;
+        }
+        const Rec ry = ldr(rec, Y);
+        const uint32_t nxt = ry.z;
+        S.heads[k] = nxt;
+        if (nxt == NIL) S.mask &= ~(1ull << k);
+        else rec[nxt].w = NIL;
+        const uint32_t ysz = sz_of(ry.x);
+        str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
+        a.out[i] = (uint64_t)Y << S.lg;
+        if (ysz > sg) {
+            S.xok = 1;
+            S.xg = Y + sg;
+            S.xsz = ysz - sg;
+            S.xprev = Y;
+            S.xright = Y + ysz;
+            S.xL = flog2(ysz - sg);
+        } else {
+            single_add(S, C_NOSPLIT, 1);
+        }
+    }
+    single_add(S, C_AOK, 1);
+    single_add(S, C_USEDG, sg);
+    single_add(S, C_REQ, (int64_t)s);
+}
+
 template <int NT>
 HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t na = a.na;
@@ -534,147 +654,147 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         if (!S.xok && S.mask == 0) {
             // nothing is free: every remaining request fails
             HBA_FOR_THREADS(tid) {
+#ifdef HBA_EMULATE
                 for (uint32_t i = p + tid; i < na; i += NT) a.out[i] = FAIL64;
-                if (tid == 0) S.c_afail += (int64_t)(na - p);
+#else
+                uint32_t lo = p;
+                if (((uintptr_t)(a.out + lo) & 15) && lo < na) {
+                    if (tid == 0) a.out[lo] = FAIL64;
+                    ++lo;
+                }
+                ulonglong2* o2 = reinterpret_cast<ulonglong2*>(a.out + lo);
+                const uint32_t npair = (na - lo) / 2;
+                for (uint32_t q = tid; q < npair; q += NT) o2[q] = make_ulonglong2(FAIL64, FAIL64);
+                if (((na - lo) & 1) && tid == 0) a.out[na - 1] = FAIL64;
+#endif
+                if (tid == 0) single_add(S, C_AFAIL, (int64_t)(na - p));
             }
             HBA_SYNC();
+            HBA_PROF(17);
             break;
         }
-        // classify the chunk [p, p + NT) against the current state
+        // classify the chunk [p, p + NT) against the state at its start,
+        // assuming every lane classified as a carve from X succeeds
         HBA_FOR_THREADS(tid) {
             const uint32_t i = p + tid;
             uint8_t cl = CL_NONE;
-            uint32_t sg = 0;
-            int64_t v = 0;
+            uint32_t sg = 0, c = 0;
+            uint64_t s = 0;
             if (i < na) {
-                const uint64_t s = a.sizes[i];
+                s = a.sizes[i];
+                if (i + NT < na) prefetch_l2(a.sizes + i + NT);
                 if (s == 0 || s > S.A) {
                     cl = CL_FAIL;
                 } else {
                     sg = (uint32_t)((s + mbm) >> lg);
-                    const uint32_t c = clog2(sg);
+                    c = clog2(sg);
                     const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
                     const uint64_t cand = (M >> c) << c;
                     if (!cand) cl = CL_FAIL;
                     else cl = (S.xok && ctz64(cand) == S.xL) ? CL_CARVE : CL_OTHER;
-                    if (cl == CL_CARVE) v = sg;
                 }
             }
             S.cls[tid] = cl;
             S.sgr[tid] = sg;
-            S.val[tid] = v;
+            S.ccl[tid] = (uint8_t)c;
+            S.s64[tid] = s;
+            S.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
             if (tid == 0) S.ev = NT;
         }
         HBA_SYNC();
+        HBA_PROF(12);
         scan_incl_i64<NT>(S, S.val);
-        // first event: an "other", or the carve that drops X below 2^xL
+        HBA_PROF(13);
+        // verify: the first lane whose speculated class is wrong given X's
+        // actual size in front of it (or an "other") ends the parallel part
         HBA_FOR_THREADS(tid) {
             const uint8_t cl = S.cls[tid];
             bool e = cl == CL_OTHER;
-            if (cl == CL_CARVE && (int64_t)S.xsz - S.val[tid] < ((int64_t)1 << S.xL)) e = true;
+            if (cl == CL_CARVE) {
+                const int64_t before = (int64_t)S.xsz - (S.val[tid] - (int64_t)S.sgr[tid]);
+                uint64_t M = S.mask;
+                uint32_t Lt = 64;
+                if (before > 0) {
+                    Lt = flog2((uint32_t)before);
+                    M |= 1ull << Lt;
+                }
+                const uint32_t c = S.ccl[tid];
+                const uint64_t cand = (M >> c) << c;
+                if (!(cand && ctz64(cand) == Lt)) e = true;
+            }
             if (e) at_min_u32(&S.ev, (uint32_t)tid);
         }
         HBA_SYNC();
+        HBA_PROF(14);
         const uint32_t ev = S.ev;
         const uint32_t n_here = na - p < (uint32_t)NT ? na - p : (uint32_t)NT;
-        const bool ev_carve = ev < n_here && S.cls[ev] == CL_CARVE;
-        const uint32_t nres = ev >= n_here ? n_here : ev + (ev_carve ? 1u : 0u);
+        const uint32_t nres = ev < n_here ? ev : n_here;
         const int64_t ptot = nres ? S.val[nres - 1] : 0;
         // resolve lanes [0, nres): failures and carves from X
         HBA_FOR_THREADS(tid) {
-            if ((uint32_t)tid < nres) {
-                const uint32_t i = p + tid;
-                if (S.cls[tid] == CL_FAIL) {
-                    a.out[i] = FAIL64;
-                    at_add_i64(&S.c_afail, 1);
-                } else {
-                    const uint32_t sg = S.sgr[tid];
-                    const int64_t P = S.val[tid];
-                    const uint32_t start = S.xg + (uint32_t)(P - sg);
-                    const uint32_t end = S.xg + (uint32_t)P;
-                    a.out[i] = (uint64_t)start << lg;
-                    rec[start].x = mkx(sg, ST_USED);
-                    rec[start].z = NIL;
-                    rec[start].w = NIL;
-                    if (P == (int64_t)sg) rec[start].y = S.xprev;
-                    if (end < S.G) rec[end].y = start;
-                    if (P == ptot) S.xprev_new = start;
-                    at_add_i64(&S.c_aok, 1);
-                    at_add_i64(&S.c_used_g, sg);
-                    at_add_i64(&S.c_used_blocks, 1);
-                    at_add_i64(&S.c_blocks, 1);
-                    at_add_i64(&S.c_req, (int64_t)a.sizes[i]);
-                }
+            const bool act = (uint32_t)tid < nres;
+            const uint8_t cl = S.cls[tid];
+            const bool is_fail = act && cl == CL_FAIL;
+            const bool is_carve = act && cl == CL_CARVE;
+            if (is_fail) a.out[p + tid] = FAIL64;
+            if (is_carve) {
+                const uint32_t sg = S.sgr[tid];
+                const int64_t P = S.val[tid];
+                const uint32_t start = S.xg + (uint32_t)(P - sg);
+                const uint32_t end = S.xg + (uint32_t)P;
+                a.out[p + tid] = (uint64_t)start << lg;
+                rec[start].x = mkx(sg, ST_USED);
+                rec[start].z = NIL;
+                rec[start].w = NIL;
+                if (P == (int64_t)sg) rec[start].y = S.xprev;
+                if (end < S.G) rec[end].y = start;
+                if (P == ptot) S.xprev_new = start;
             }
+            warp_count(S, tid, C_AFAIL, is_fail);
+            warp_count(S, tid, C_AOK, is_carve);
+            warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
         }
         HBA_SYNC();
-        // advance X and the cursor; apply an "other" request sequentially
+        HBA_PROF(15);
+        // advance X and the cursor; apply the event lane alone
         HBA_FOR_THREADS(tid) {
             if (tid == 0) {
                 if (ptot > 0) {
                     S.xg += (uint32_t)ptot;
                     S.xsz -= (uint32_t)ptot;
                     S.xprev = S.xprev_new;
-                }
-                if (ev_carve) {
-                    if (S.xsz == 0) { S.xok = 0; S.c_blocks -= 1; }
-                    else S.xL = flog2(S.xsz);
+                    single_add(S, C_USEDG, ptot);
+                    if (S.xsz == 0) {
+                        S.xok = 0;
+                        single_add(S, C_NOSPLIT, 1);
+                    } else {
+                        S.xL = flog2(S.xsz);
+                    }
                 }
                 S.p = p + nres;
-                if (ev < n_here && !ev_carve) {
-                    const uint32_t i = p + ev;
-                    const uint32_t sg = S.sgr[ev];
-                    const uint32_t c = clog2(sg);
-                    const uint64_t cand = (S.mask >> c) << c;  // X's class is not the winner
-                    const uint32_t k = ctz64(cand);
-                    if (S.xok) materialize_x<NT>(S, rec);
-                    const uint32_t Y = S.heads[k];
-                    if (Y >= S.G) {  // bitmap and heads disagree: record, fail the request
-                        S.err = ERR_EMPTY_HEAD;
-                        S.mask &= ~(1ull << k);
-                        a.out[i] = FAIL64;
-                        S.c_afail += 1;
-                        S.p = i + 1;
-                    } else {
-                    const Rec ry = ldr(rec, Y);
-                    const uint32_t nxt = ry.z;
-                    S.heads[k] = nxt;
-                    if (nxt == NIL) S.mask &= ~(1ull << k);
-                    else rec[nxt].w = NIL;
-                    const uint32_t ysz = sz_of(ry.x);
-                    str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
-                    a.out[i] = (uint64_t)Y << lg;
-                    S.c_aok += 1;
-                    S.c_used_g += sg;
-                    S.c_used_blocks += 1;
-                    S.c_req += (int64_t)a.sizes[i];
-                    if (ysz > sg) {
-                        S.xok = 1;
-                        S.xg = Y + sg;
-                        S.xsz = ysz - sg;
-                        S.xprev = Y;
-                        S.xright = Y + ysz;
-                        S.xL = flog2(ysz - sg);
-                        S.c_blocks += 1;
-                    }
-                    S.p = i + 1;
-                    }
+                if (nres < n_here) {
+                    seq_request<NT>(S, a, p + nres, S.s64[nres], S.sgr[nres], S.ccl[nres]);
+                    S.p = p + nres + 1;
                 }
             }
         }
         HBA_SYNC();
+        HBA_PROF(16);
     }
     HBA_FOR_THREADS(tid) {
         if (tid == 0 && S.xok) materialize_x<NT>(S, rec);
     }
     HBA_SYNC();
+    HBA_PROF(18);
 }
 
-// One batch of one arena.  All threads of the CTA call this.
+// One batch of one arena.  All threads of the CTA call this.  root_sm/rcap:
+// shared-memory space for the pointer jumping of up to rcap applied frees.
 template <int NT>
-HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a) {
+HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* root_sm, uint32_t rcap) {
     HBA_FOR_THREADS(tid) {
         for (int b = tid; b < NBINS; b += NT) S.heads[b] = a.ar->heads[b];
+        for (int q = tid; q < Smem<NT>::NW * NCNT; q += NT) (&S.wc[0][0])[q] = 0;
         if (tid == 0) {
             S.A = a.ar->arena_bytes;
             S.mask = a.ar->mask;
@@ -683,30 +803,35 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a) {
             S.xok = 0;
             S.nruns = 0;
             S.err = 0;
-            S.c_aok = S.c_afail = S.c_fok = S.c_ffail = 0;
-            S.c_used_g = S.c_used_blocks = S.c_blocks = S.c_req = 0;
+            S.root_sm = root_sm;
+            S.rcap = rcap;
         }
     }
     HBA_SYNC();
+    HBA_PROF(0);
     if (a.nf) free_phase<NT>(S, a);
     if (a.na) alloc_phase<NT>(S, a);
     HBA_FOR_THREADS(tid) {
         for (int b = tid; b < NBINS; b += NT) a.ar->heads[b] = S.heads[b];
         if (tid == 0) {
+            int64_t c[NCNT] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int w = 0; w < Smem<NT>::NW; ++w)
+                for (int k = 0; k < NCNT; ++k) c[k] += S.wc[w][k];
             Arena* ar = a.ar;
             ar->mask = S.mask;
-            ar->alloc_ok += S.c_aok;
-            ar->alloc_fail += S.c_afail;
-            ar->free_ok += S.c_fok;
-            ar->free_fail += S.c_ffail;
-            ar->used_g += S.c_used_g;
-            ar->used_blocks += S.c_used_blocks;
-            ar->blocks += S.c_blocks;
-            ar->requested += S.c_req;
+            ar->alloc_ok += c[C_AOK];
+            ar->alloc_fail += c[C_AFAIL];
+            ar->free_ok += c[C_FOK];
+            ar->free_fail += c[C_FFAIL];
+            ar->used_g += c[C_USEDG];
+            ar->used_blocks += c[C_AOK] - c[C_FOK];
+            ar->blocks += c[C_AOK] - c[C_NOSPLIT] + c[C_BLOCKS];
+            ar->requested += c[C_REQ];
             if (S.err && !ar->err) ar->err = S.err;
         }
     }
     HBA_SYNC();
+    HBA_PROF(19);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,8 +17,11 @@ def _run(wl, threads=None, max_batches=None, state_every=0, canary=False):
 
     from paper_2405_07079_gb300 import Allocator
 
+    import oracle
+
     dev = torch.device("cuda")
     trace, o = oracle_trace(wl, max_batches)
+    lock = oracle.Oracle(wl.arena, wl.min_block) if state_every else None  # replayed in lock step
     guard = None
     if canary:
         # a real arena of the managed size, filled with the canary byte; the
@@ -34,8 +37,10 @@ def _run(wl, threads=None, max_batches=None, state_every=0, canary=False):
             assert i is None, f"batch {b}: alloc {i}: gpu {go[i]:#x} oracle {out[i]:#x}"
             j = first_diff(from_dev(dst), st)
             assert j is None, f"batch {b}: free {j} status differs"
-            if state_every and b % state_every == 0:
-                assert np.array_equal(a.export_state(), o.export_state()), f"batch {b}: state differs"
+            if lock is not None:
+                lock.batch(f, s)
+                if b % state_every == 0:
+                    assert np.array_equal(a.export_state(), lock.export_state()), f"batch {b}: state differs"
         gs = a.export_state()
         assert np.array_equal(gs, o.export_state()), "final state differs"
         check_invariants(gs)
