@@ -38,6 +38,7 @@ struct hba_s {
     uint32_t threads = 1024;    // single-arena CTA width
     uint32_t m_threads = 256;   // multi-arena CTA width
     uint32_t m_ctas = 0;        // multi-arena grid (0 = one CTA per arena)
+    uint32_t m_dyn = 0;         // multi-arena dynamic shared memory per CTA (bytes)
     uint64_t* d_largest = nullptr;
 };
 
@@ -51,28 +52,29 @@ namespace {
         }                                          \
     } while (0)
 
-// Shared memory for pointer jumping over the applied frees of one batch:
-// batches with more applied frees use the global scratch instead.
-constexpr uint32_t RCAP_SINGLE = 16384;  // 64 KiB, one CTA per SM
-constexpr uint32_t RCAP_MULTI = 2048;    // 8 KiB, several CTAs per SM
+// Dynamic shared memory holds the free-phase scratch of a batch (12 words
+// per free) when it fits; otherwise the global scratch is used.  The single
+// arena kernel takes everything the SM offers one CTA; the multi-arena
+// kernel takes a per-CTA budget that leaves room for several CTAs per SM.
+constexpr uint32_t MULTI_DYN_BYTES_DEFAULT = 24 * 1024;
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
                                                uint8_t* st, const uint64_t* sizes, uint32_t na,
-                                               uint64_t* out, uint32_t* scr, uint32_t rcap) {
+                                               uint64_t* out, uint32_t* scr, uint32_t dyn_words) {
     __shared__ hba::Smem<NT> S;
-    extern __shared__ uint32_t root_sm[];
+    extern __shared__ uint32_t dyn[];
     hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr};
-    hba::arena_step<NT>(S, a, root_sm, rcap);
+    hba::arena_step<NT>(S, a, dyn, dyn_words);
 }
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint32_t* frow,
                                               const uint64_t* frees, uint8_t* st, const uint32_t* arow,
                                               const uint64_t* sizes, uint64_t* out, uint32_t* scr,
-                                              uint32_t n_arenas, uint32_t rcap) {
+                                              uint32_t n_arenas, uint32_t dyn_words) {
     __shared__ hba::Smem<NT> S;
-    extern __shared__ uint32_t root_sm[];
+    extern __shared__ uint32_t dyn[];
     for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
         const uint32_t f0 = frow[a], f1 = frow[a + 1], a0 = arow[a], a1 = arow[a + 1];
         Arena* ar = ars + a;
@@ -85,14 +87,42 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            a1 - a0,
                            out + a0,
                            scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE};
-        hba::arena_step<NT>(S, args, root_sm, rcap);
+        hba::arena_step<NT>(S, args, dyn, dyn_words);
     }
 }
 
+// Largest dynamic shared memory a CTA of k_single<NT> / k_multi<NT> can get.
+struct SmemLimits {
+    uint32_t single_dyn = 0, multi_dyn = 0;
+};
+
 template <int NT>
-void set_smem_limits() {
-    cudaFuncSetAttribute(k_single<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, RCAP_SINGLE * 4);
-    cudaFuncSetAttribute(k_multi<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, RCAP_MULTI * 4);
+SmemLimits set_smem_limits() {
+    int dev = 0, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    SmemLimits L;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_single<NT>) == cudaSuccess) {
+        L.single_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_single<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn);
+    }
+    if (cudaFuncGetAttributes(&fa, k_multi<NT>) == cudaSuccess) {
+        L.multi_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_multi<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.multi_dyn);
+    }
+    return L;
+}
+
+SmemLimits g_limits[5];  // for 64, 128, 256, 512, 1024 threads
+int limit_index(uint32_t threads) {
+    switch (threads) {
+        case 64: return 0;
+        case 128: return 1;
+        case 256: return 2;
+        case 512: return 3;
+        default: return 4;
+    }
 }
 
 // Write the initial record of every arena (one free block spanning it).
@@ -129,13 +159,14 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
                            const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
-    const size_t dyn = RCAP_SINGLE * 4;
+    const uint32_t dyn = g_limits[limit_index(h->threads)].single_dyn;
+    const uint32_t dw = dyn / 4;
     switch (h->threads) {
-        case 64: k_single<64><<<1, 64, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
-        case 128: k_single<128><<<1, 128, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
-        case 256: k_single<256><<<1, 256, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
-        case 512: k_single<512><<<1, 512, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
-        default: k_single<1024><<<1, 1024, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, RCAP_SINGLE); break;
+        case 64: k_single<64><<<1, 64, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
+        case 128: k_single<128><<<1, 128, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
+        case 256: k_single<256><<<1, 256, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
+        case 512: k_single<512><<<1, 512, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
+        default: k_single<1024><<<1, 1024, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
     }
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
@@ -158,11 +189,11 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
 }
 
 hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_frees, uint32_t stage) {
-    set_smem_limits<64>();
-    set_smem_limits<128>();
-    set_smem_limits<256>();
-    set_smem_limits<512>();
-    set_smem_limits<1024>();
+    g_limits[0] = set_smem_limits<64>();
+    g_limits[1] = set_smem_limits<128>();
+    g_limits[2] = set_smem_limits<256>();
+    g_limits[3] = set_smem_limits<512>();
+    g_limits[4] = set_smem_limits<1024>();
     HBA_CUDA_TRY(cudaGetLastError());
     h->h_init = init;
     h->n_arenas = (uint32_t)init.size();
@@ -384,12 +415,14 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = h->n_arenas;
     const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
+    const uint32_t dyn = std::min(h->m_dyn ? h->m_dyn : MULTI_DYN_BYTES_DEFAULT,
+                                  g_limits[limit_index(h->m_threads)].multi_dyn);
     switch (h->m_threads) {
-        case 64: k_multi<64><<<grid, 64, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
-        case 128: k_multi<128><<<grid, 128, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
-        case 512: k_multi<512><<<grid, 512, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
-        case 1024: k_multi<1024><<<grid, 1024, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
-        default: k_multi<256><<<grid, 256, RCAP_MULTI * 4, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, RCAP_MULTI); break;
+        case 64: k_multi<64><<<grid, 64, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
+        case 128: k_multi<128><<<grid, 128, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
+        case 512: k_multi<512><<<grid, 512, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
+        case 1024: k_multi<1024><<<grid, 1024, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
+        default: k_multi<256><<<grid, 256, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
     }
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }

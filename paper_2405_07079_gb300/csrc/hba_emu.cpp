@@ -22,6 +22,7 @@ struct Emu {
     std::vector<Rec> rec;
     std::vector<uint32_t> scr;
     int nt;
+    uint32_t dyn_words = 600;
 };
 
 template <int NT>
@@ -30,10 +31,10 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
     Smem<NT>* S = new Smem<NT>();
     if (e->scr.size() < (size_t)SCRATCH_WORDS_PER_FREE * nf) e->scr.resize((size_t)SCRATCH_WORDS_PER_FREE * nf);
     StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data()};
-    // a small shared-memory pointer-jumping area, so both the shared and the
-    // global variant run
-    std::vector<uint32_t> root_sm(64);
-    arena_step<NT>(*S, a, root_sm.data(), (uint32_t)root_sm.size());
+    // a small "shared memory" area, so that both the shared-memory and the
+    // global-scratch variants of the free phase run
+    std::vector<uint32_t> dyn(e->dyn_words + 1);
+    arena_step<NT>(*S, a, dyn.data(), e->dyn_words);
     delete S;
 }
 }  // namespace
@@ -54,6 +55,8 @@ void* emu_create(uint64_t arena_bytes, uint64_t min_block, int nt) {
 }
 
 void emu_destroy(void* h) { delete (Emu*)h; }
+
+void emu_set_dyn(void* h, uint32_t words) { ((Emu*)h)->dyn_words = words; }
 
 int emu_step(void* h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
              uint32_t na, uint64_t* out) {

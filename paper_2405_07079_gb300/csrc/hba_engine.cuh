@@ -85,7 +85,7 @@ constexpr uint32_t MAX_GRANULES = SZ_MASK;  // G <= 2^29 - 1
 constexpr uint32_t ST_NONE = 0, ST_USED = 1, ST_FREE = 2, ST_NEW = 3, ST_DEL = 4;
 constexpr uint64_t FAIL64 = ~0ull;
 constexpr int NBINS = 32;  // granule classes 0..28 are reachable
-constexpr uint32_t SCRATCH_WORDS_PER_FREE = 16;
+constexpr uint32_t SCRATCH_WORDS_PER_FREE = 12;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
 constexpr uint32_t ERR_EMPTY_HEAD = 2;  // a class with its bit set had no head
@@ -157,34 +157,45 @@ HBA_DEV void at_add_i64(int64_t* p, int64_t v) {
 
 // ---- shared state of one CTA --------------------------------------------
 enum : uint8_t { CL_NONE = 0, CL_FAIL = 1, CL_CARVE = 2, CL_OTHER = 3 };
-// per-warp counter slots (summed once per batch; no contended atomics)
+// counter slots (per warp, plus one row for single-thread updates)
 enum : int { C_AOK = 0, C_AFAIL, C_FOK, C_FFAIL, C_USEDG, C_REQ, C_NOSPLIT, C_BLOCKS, NCNT };
 
 template <int NT>
 struct Smem {
     static constexpr int NW = NT >= 32 ? NT / 32 : 1;
+    static constexpr int NSEG = NT >= 16 ? NT / 16 : 1;  // segments of the push order
     uint64_t A;          // arena bytes
     uint64_t mask;       // bitmap of classes whose list is non-empty (X excluded)
     uint32_t heads[NBINS];
     uint32_t G, lg;
-    // the most recent remainder X (virtual head of class xL while xok)
-    uint32_t xok, xg, xsz, xprev, xright, xL, xprev_new;
+    // the most recent remainder X, virtual head of class xL while xok; its
+    // prev_adj is kept in rec[xg].y at all times
+    uint32_t xok, xg, xsz, xright, xL;
+    uint32_t c0g;        // X's start when the current chunk was classified
     // loop control
     uint32_t p, ev, W, nul, nruns, flag[3];
     uint32_t err;        // first metadata error seen by this CTA (0 = none)
-    uint32_t rcap;       // capacity of root_sm
-    uint32_t* root_sm;   // pointer-jumping array in shared memory
-    int64_t wc[NW][NCNT];
+    uint32_t* dyn;       // dynamic shared memory (free-phase scratch)
+    uint32_t dyn_words;
+    int64_t wc[NW + 1][NCNT];
     int64_t warp_tot[32];
-    int64_t val[NT];     // carve sizes, then their inclusive prefix
-    uint64_t s64[NT];    // request sizes of the chunk
+    union {
+        struct {
+            int64_t val[NT];   // carve sizes, then their inclusive prefix
+            uint64_t s64[NT];  // request sizes of the chunk
+        } a;
+        struct {
+            uint32_t f[NSEG][NBINS];  // oldest run of each class per segment
+            uint32_t l[NSEG][NBINS];  // newest run of each class per segment
+        } seg;
+    } u;
     uint32_t cnt[NT];
     uint32_t sgr[NT];    // rounded sizes in granules
     uint8_t cls[NT];     // speculative class of each lane
     uint8_t ccl[NT];     // size class c of each lane
 };
 
-// ---- warp-aggregated counters (call convergently from every thread) ------
+// ---- warp-aggregated counters and votes (call convergently) --------------
 template <int NT>
 HBA_DEV void warp_count(Smem<NT>& S, int tid, int k, bool pred) {
 #ifdef HBA_EMULATE
@@ -204,9 +215,19 @@ HBA_DEV void warp_sum(Smem<NT>& S, int tid, int k, int64_t v) {
     if ((tid & 31) == 0) S.wc[tid >> 5][k] += v;
 #endif
 }
-// one thread (tid 0), in a phase where no warp_* call runs
+// S.ev = min(S.ev, first lane with e)
 template <int NT>
-HBA_DEV void single_add(Smem<NT>& S, int k, int64_t v) { S.wc[0][k] += v; }
+HBA_DEV void warp_first_min(Smem<NT>& S, int tid, bool e) {
+#ifdef HBA_EMULATE
+    if (e && (uint32_t)tid < S.ev) S.ev = (uint32_t)tid;
+#else
+    const unsigned b = __ballot_sync(0xffffffffu, e);
+    if ((tid & 31) == 0 && b) atomicMin(&S.ev, (uint32_t)(tid + __ffs(b) - 1));
+#endif
+}
+// single-thread counter update (its own row: never races with warp_*)
+template <int NT>
+HBA_DEV void single_add(Smem<NT>& S, int k, int64_t v) { S.wc[Smem<NT>::NW][k] += v; }
 
 HBA_DEV void prefetch_l2(const void* p) {
 #ifdef HBA_EMULATE
@@ -217,7 +238,8 @@ HBA_DEV void prefetch_l2(const void* p) {
 }
 
 // ---- block-wide collectives (called by all threads, outside phases) ------
-// Inclusive prefix sum of v[0..NT) in place, followed by a barrier.
+// Inclusive prefix sum of v[0..NT) in place.  On return each thread has
+// written its own v[tid]; a barrier is needed before reading other lanes.
 template <int NT>
 HBA_DEV void scan_incl_i64(Smem<NT>& S, int64_t* v) {
 #ifdef HBA_EMULATE
@@ -233,19 +255,16 @@ HBA_DEV void scan_incl_i64(Smem<NT>& S, int64_t* v) {
     }
     if (lane == 31) S.warp_tot[wid] = x;
     __syncthreads();
-    if (wid == 0) {
-        int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
+    // every warp scans the warp totals itself: no second barrier
+    int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
-        }
-        if (lane < NT / 32) S.warp_tot[lane] = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += u;
     }
-    __syncthreads();
-    if (wid > 0) x += S.warp_tot[wid - 1];
+    const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
+    if (wid > 0) x += before;
     v[tid] = x;
-    __syncthreads();
 #endif
 }
 
@@ -273,17 +292,14 @@ HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
     }
     if (lane == 31) S.warp_tot[wid] = x;
     __syncthreads();
-    if (wid == 0) {
-        int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
+    int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
-        }
-        if (lane < NT / 32) S.warp_tot[lane] = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += u;
     }
-    __syncthreads();
-    if (wid > 0) x += S.warp_tot[wid - 1];
+    const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
+    if (wid > 0) x += before;
     c[tid] = (uint32_t)(x - own);
     if (tid == NT - 1) *total = (uint32_t)x;
     __syncthreads();
@@ -299,15 +315,17 @@ struct StepArgs {
     const uint64_t* sizes;
     uint32_t na;
     uint64_t* out;
-    uint32_t* scr;   // SCRATCH_WORDS_PER_FREE * nf words
+    uint32_t* scr;   // SCRATCH_WORDS_PER_FREE * nf words of global scratch
 };
 
 // Push the virtual remainder X at the head of its list and write its record
-// (one thread).
+// (one thread).  rec[xg].y already holds X's prev_adj and is left alone.
 template <int NT>
 HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec) {
     const uint32_t b = S.xL, old = S.heads[b];
-    str(rec, S.xg, Rec{mkx(S.xsz, ST_FREE), S.xprev, old, NIL});
+    rec[S.xg].x = mkx(S.xsz, ST_FREE);
+    rec[S.xg].z = old;
+    rec[S.xg].w = NIL;
     if (old != NIL) rec[old].w = S.xg;
     S.heads[b] = S.xg;
     S.mask |= 1ull << b;
@@ -322,21 +340,26 @@ template <int NT>
 HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t nf = a.nf;
     Rec* rec = a.rec;
-    uint32_t* fg = a.scr;              // by free index j: granule, or NIL if rejected
-    uint32_t* fsz = fg + nf;           //   size of the freed block (granules)
-    uint32_t* fy = fsz + nf;           //   its previous adjacent block
-    uint32_t* runAt = fy + nf;         //   run leader whose last free is j, or NIL
-    uint32_t* cg = runAt + nf;         // by compact index w (applied frees in order)
-    uint32_t* csz = cg + nf;
-    uint32_t* cy = csz + nf;
-    uint32_t* cj = cy + nf;            //   free index
-    uint32_t* rootg = cj + nf;         //   pointer-jumping root (when it does not fit in smem)
-    uint32_t* lh = rootg + nf;         //   leftmost block of the run at my left
-    uint32_t* rend = lh + nf;          //   right end of my piece (max over the run at the root)
-    uint32_t* rmaxj = rend + nf;       //   largest free index (max over the run at the root)
-    uint32_t* fl = rmaxj + nf;         //   bit0: erase left old-free record, bit1: erase right one
-    uint32_t* ul = fl + nf;            // [2 nf] old free blocks absorbed by runs
-    uint32_t* runs = ul + 2 * nf;      // [nf] run leaders in free-index order
+    // Scratch: 12 words per free, in shared memory when they fit.  Arrays
+    // whose lifetimes do not overlap share storage.
+    const bool in_smem = (uint64_t)SCRATCH_WORDS_PER_FREE * nf <= S.dyn_words;
+    uint32_t* base = in_smem ? S.dyn : a.scr;
+    uint32_t* fg = base;               // by free index j: granule, or NIL if rejected (F1-F3)
+    uint32_t* runAt = base;            //   then: run leader whose last free is j (F4-F9)
+    uint32_t* fsz = base + nf;         //   size of the freed block (F1-F3)
+    uint32_t* lh = base + nf;          // by compact index w: leftmost block of my run's left part (F4-)
+    uint32_t* fy = base + 2 * nf;      //   prev_adj of the freed block (F1-F3)
+    uint32_t* rend = base + 2 * nf;    //   right end of my piece; max over the run at the root (F4-)
+    uint32_t* cg = base + 3 * nf;      // applied frees in order: granule
+    uint32_t* csz = base + 4 * nf;     //   size
+    uint32_t* cy = base + 5 * nf;      //   prev_adj
+    uint32_t* cj = base + 6 * nf;      //   free index (F3-F6)
+    uint32_t* runs = base + 6 * nf;    //   then: run leaders in free-index order (F9-F10)
+    uint32_t* root = base + 7 * nf;    //   pointer-jumping root
+    uint32_t* rmaxj = base + 8 * nf;   //   largest free index (max over the run at the root)
+    uint32_t* fl = base + 9 * nf;      //   bit0: erase left old-free record, bit1: erase right one
+    uint32_t* ul = base + 10 * nf;     // [2 nf] old free blocks absorbed by runs
+    if (!in_smem && nf <= S.dyn_words) root = S.dyn;
     const uint64_t mbm = (1ull << S.lg) - 1ull;
     const uint32_t per = (nf + NT - 1) / NT;
 
@@ -358,7 +381,6 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             fg[j] = g;
             fsz[j] = sz;
             fy[j] = y;
-            runAt[j] = NIL;
         }
         if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
     }
@@ -380,7 +402,6 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     HBA_SYNC();
     scan_excl_u32<NT>(S, S.cnt, &S.W);
     const uint32_t W = S.W;
-    uint32_t* root = W <= S.rcap ? S.root_sm : rootg;
     HBA_PROF(2);
     // F3: compact in free-index order; mark the freed blocks NEW and map
     // granule -> compact index.
@@ -415,6 +436,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     // block absorbed by a run is unlinked by the freed block to its right, or
     // by the one to its left when it ends the run.
     HBA_FOR_THREADS(tid) {
+        for (uint32_t j = tid; j < nf; j += NT) runAt[j] = NIL;
         for (uint32_t w = tid; w < W; w += NT) {
             const uint32_t g = cg[w], sz = csz[w], L = cy[w];
             uint32_t end = g + sz;
@@ -471,7 +493,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         if (!S.flag[it % 3]) break;
     }
     HBA_PROF(5);
-    // F6: per-run right end and last free index; F7a: mark absorbed blocks.
+    // F6: per-run right end and last free index; mark absorbed blocks.
     HBA_FOR_THREADS(tid) {
         for (uint32_t w = tid; w < W; w += NT) {
             const uint32_t r = root[w];
@@ -547,19 +569,53 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     }
     HBA_SYNC();
     HBA_PROF(9);
-    // F10: push the merged blocks (one thread, in order), rebuild the bitmap.
+    // F10a: the merged blocks are pushed in run order.  Split that order into
+    // NSEG segments; inside each, link consecutive runs of the same class.
+    constexpr int NSEG = Smem<NT>::NSEG;
     HBA_FOR_THREADS(tid) {
-        if (tid == 0) {
-            for (uint32_t k = 0; k < nruns; ++k) {
+        if (tid < NSEG) {
+            uint32_t* F = S.u.seg.f[tid];
+            uint32_t* Lw = S.u.seg.l[tid];
+            for (int b = 0; b < NBINS; ++b) F[b] = Lw[b] = NIL;
+            const uint32_t ps = (nruns + NSEG - 1) / NSEG;
+            const uint32_t lo = tid * ps, hi = lo + ps < nruns ? lo + ps : nruns;
+            for (uint32_t k = lo; k < hi; ++k) {
                 const uint32_t w = runs[k];
                 const uint32_t H = lh[w];
                 const uint32_t b = flog2(rend[w] - H);
-                const uint32_t old = S.heads[b];
-                rec[H].z = old;
-                rec[H].w = NIL;
-                if (old != NIL) rec[old].w = H;
-                S.heads[b] = H;
+                if (Lw[b] == NIL) {
+                    F[b] = H;
+                } else {
+                    rec[H].z = Lw[b];
+                    rec[Lw[b]].w = H;
+                }
+                Lw[b] = H;
             }
+        }
+    }
+    HBA_SYNC();
+    // F10b: per class, stitch the segments in order on top of the old list.
+    HBA_FOR_THREADS(tid) {
+        for (int b = tid; b < NBINS; b += NT) {
+            uint32_t below = S.heads[b];
+            bool any = false;
+            for (int sgm = 0; sgm < NSEG; ++sgm) {
+                const uint32_t f = S.u.seg.f[sgm][b];
+                if (f == NIL) continue;
+                rec[f].z = below;
+                if (below != NIL) rec[below].w = f;
+                below = S.u.seg.l[sgm][b];
+                any = true;
+            }
+            if (any) {
+                rec[below].w = NIL;
+                S.heads[b] = below;
+            }
+        }
+    }
+    HBA_SYNC();
+    HBA_FOR_THREADS(tid) {
+        if (tid == 0) {
             uint64_t m = 0;
             for (int b = 0; b < NBINS; ++b)
                 if (S.heads[b] != NIL) m |= 1ull << b;
@@ -589,16 +645,17 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
     }
     const uint32_t k = ctz64(cand);
     if (S.xok && k == S.xL) {
-        // carve the front of X
+        // carve the front of X (its prev_adj is already in rec[xg].y)
         const uint32_t start = S.xg;
-        str(rec, start, Rec{mkx(sg, ST_USED), S.xprev, NIL, NIL});
+        rec[start].x = mkx(sg, ST_USED);
+        rec[start].z = NIL;
+        rec[start].w = NIL;
         a.out[i] = (uint64_t)start << S.lg;
         S.xg += sg;
         S.xsz -= sg;
-        S.xprev = start;
+        if (S.xg < S.G) rec[S.xg].y = start;
         if (S.xsz == 0) {
             S.xok = 0;
-            if (S.xright < S.G) rec[S.xright].y = start;
             single_add(S, C_NOSPLIT, 1);
         } else {
             S.xL = flog2(S.xsz);
@@ -620,15 +677,17 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
         if (nxt == NIL) S.mask &= ~(1ull << k);
         else rec[nxt].w = NIL;
         const uint32_t ysz = sz_of(ry.x);
-        str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
+        rec[Y].x = mkx(sg, ST_USED);
+        rec[Y].z = NIL;
+        rec[Y].w = NIL;
         a.out[i] = (uint64_t)Y << S.lg;
         if (ysz > sg) {
             S.xok = 1;
             S.xg = Y + sg;
             S.xsz = ysz - sg;
-            S.xprev = Y;
             S.xright = Y + ysz;
             S.xL = flog2(ysz - sg);
+            rec[S.xg].y = Y;
         } else {
             single_add(S, C_NOSPLIT, 1);
         }
@@ -673,8 +732,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             HBA_PROF(17);
             break;
         }
-        // classify the chunk [p, p + NT) against the state at its start,
-        // assuming every lane classified as a carve from X succeeds
+        // A: classify the chunk [p, p + NT) against the state at its start
         HBA_FOR_THREADS(tid) {
             const uint32_t i = p + tid;
             uint8_t cl = CL_NONE;
@@ -697,21 +755,25 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             S.cls[tid] = cl;
             S.sgr[tid] = sg;
             S.ccl[tid] = (uint8_t)c;
-            S.s64[tid] = s;
-            S.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
-            if (tid == 0) S.ev = NT;
+            S.u.a.s64[tid] = s;
+            S.u.a.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
+            if (tid == 0) {
+                S.ev = NT;
+                S.c0g = S.xg;
+            }
         }
         HBA_SYNC();
         HBA_PROF(12);
-        scan_incl_i64<NT>(S, S.val);
+        scan_incl_i64<NT>(S, S.u.a.val);
         HBA_PROF(13);
-        // verify: the first lane whose speculated class is wrong given X's
-        // actual size in front of it (or an "other") ends the parallel part
+        // B: verify the speculation (every carve-classified lane assumed that
+        // the carves before it succeeded); the first wrong lane, or the first
+        // "other", ends the parallel part of the chunk
         HBA_FOR_THREADS(tid) {
             const uint8_t cl = S.cls[tid];
             bool e = cl == CL_OTHER;
             if (cl == CL_CARVE) {
-                const int64_t before = (int64_t)S.xsz - (S.val[tid] - (int64_t)S.sgr[tid]);
+                const int64_t before = (int64_t)S.xsz - (S.u.a.val[tid] - (int64_t)S.sgr[tid]);
                 uint64_t M = S.mask;
                 uint32_t Lt = 64;
                 if (before > 0) {
@@ -722,15 +784,16 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                 const uint64_t cand = (M >> c) << c;
                 if (!(cand && ctz64(cand) == Lt)) e = true;
             }
-            if (e) at_min_u32(&S.ev, (uint32_t)tid);
+            warp_first_min(S, tid, e);
         }
         HBA_SYNC();
         HBA_PROF(14);
         const uint32_t ev = S.ev;
         const uint32_t n_here = na - p < (uint32_t)NT ? na - p : (uint32_t)NT;
         const uint32_t nres = ev < n_here ? ev : n_here;
-        const int64_t ptot = nres ? S.val[nres - 1] : 0;
-        // resolve lanes [0, nres): failures and carves from X
+        const uint32_t upd = nres < n_here ? nres : n_here - 1;
+        // C: resolve lanes [0, nres) (failures, carves from X) in parallel;
+        // lane `upd` then advances X and applies the event lane alone
         HBA_FOR_THREADS(tid) {
             const bool act = (uint32_t)tid < nres;
             const uint8_t cl = S.cls[tid];
@@ -739,30 +802,23 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             if (is_fail) a.out[p + tid] = FAIL64;
             if (is_carve) {
                 const uint32_t sg = S.sgr[tid];
-                const int64_t P = S.val[tid];
-                const uint32_t start = S.xg + (uint32_t)(P - sg);
-                const uint32_t end = S.xg + (uint32_t)P;
+                const int64_t P = S.u.a.val[tid];
+                const uint32_t start = S.c0g + (uint32_t)(P - sg);
+                const uint32_t end = S.c0g + (uint32_t)P;
                 a.out[p + tid] = (uint64_t)start << lg;
                 rec[start].x = mkx(sg, ST_USED);
                 rec[start].z = NIL;
                 rec[start].w = NIL;
-                if (P == (int64_t)sg) rec[start].y = S.xprev;
                 if (end < S.G) rec[end].y = start;
-                if (P == ptot) S.xprev_new = start;
             }
             warp_count(S, tid, C_AFAIL, is_fail);
             warp_count(S, tid, C_AOK, is_carve);
-            warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
-        }
-        HBA_SYNC();
-        HBA_PROF(15);
-        // advance X and the cursor; apply the event lane alone
-        HBA_FOR_THREADS(tid) {
-            if (tid == 0) {
+            warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.u.a.s64[tid] : 0);
+            if ((uint32_t)tid == upd) {
+                const int64_t ptot = nres ? S.u.a.val[nres - 1] : 0;
                 if (ptot > 0) {
                     S.xg += (uint32_t)ptot;
                     S.xsz -= (uint32_t)ptot;
-                    S.xprev = S.xprev_new;
                     single_add(S, C_USEDG, ptot);
                     if (S.xsz == 0) {
                         S.xok = 0;
@@ -773,13 +829,13 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                 }
                 S.p = p + nres;
                 if (nres < n_here) {
-                    seq_request<NT>(S, a, p + nres, S.s64[nres], S.sgr[nres], S.ccl[nres]);
+                    seq_request<NT>(S, a, p + nres, S.u.a.s64[nres], S.sgr[nres], S.ccl[nres]);
                     S.p = p + nres + 1;
                 }
             }
         }
         HBA_SYNC();
-        HBA_PROF(16);
+        HBA_PROF(15);
     }
     HBA_FOR_THREADS(tid) {
         if (tid == 0 && S.xok) materialize_x<NT>(S, rec);
@@ -788,13 +844,13 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
     HBA_PROF(18);
 }
 
-// One batch of one arena.  All threads of the CTA call this.  root_sm/rcap:
-// shared-memory space for the pointer jumping of up to rcap applied frees.
+// One batch of one arena.  All threads of the CTA call this.  dyn/dyn_words:
+// dynamic shared memory for the free phase (may be 0 words).
 template <int NT>
-HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* root_sm, uint32_t rcap) {
+HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t dyn_words) {
     HBA_FOR_THREADS(tid) {
         for (int b = tid; b < NBINS; b += NT) S.heads[b] = a.ar->heads[b];
-        for (int q = tid; q < Smem<NT>::NW * NCNT; q += NT) (&S.wc[0][0])[q] = 0;
+        for (int q = tid; q < (Smem<NT>::NW + 1) * NCNT; q += NT) (&S.wc[0][0])[q] = 0;
         if (tid == 0) {
             S.A = a.ar->arena_bytes;
             S.mask = a.ar->mask;
@@ -803,8 +859,8 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* root_sm, uint3
             S.xok = 0;
             S.nruns = 0;
             S.err = 0;
-            S.root_sm = root_sm;
-            S.rcap = rcap;
+            S.dyn = dyn;
+            S.dyn_words = dyn_words;
         }
     }
     HBA_SYNC();
@@ -815,7 +871,7 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* root_sm, uint3
         for (int b = tid; b < NBINS; b += NT) a.ar->heads[b] = S.heads[b];
         if (tid == 0) {
             int64_t c[NCNT] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int w = 0; w < Smem<NT>::NW; ++w)
+            for (int w = 0; w <= Smem<NT>::NW; ++w)
                 for (int k = 0; k < NCNT; ++k) c[k] += S.wc[w][k];
             Arena* ar = a.ar;
             ar->mask = S.mask;

@@ -36,13 +36,16 @@ def emu():
     lib.emu_export.restype = ctypes.c_size_t
     lib.emu_export.argtypes = [vp, vp, ctypes.c_size_t]
     lib.emu_stats.argtypes = [vp, vp]
+    lib.emu_set_dyn.argtypes = [vp, u32]
     return lib
 
 
 class Emu:
-    def __init__(self, lib, A, mb, nt):
+    def __init__(self, lib, A, mb, nt, dyn_words=None):
         self.lib, self.h = lib, lib.emu_create(A, mb, nt)
         assert self.h
+        if dyn_words is not None:
+            lib.emu_set_dyn(self.h, dyn_words)
 
     def batch(self, f, s):
         f = np.ascontiguousarray(f, np.uint64)
@@ -68,9 +71,9 @@ class Emu:
         self.lib.emu_destroy(self.h)
 
 
-def _check(emu, wl, nt, every=1):
+def _check(emu, wl, nt, every=1, dyn_words=None):
     trace, o = oracle_trace(wl)
-    e = Emu(emu, wl.arena, wl.min_block, nt)
+    e = Emu(emu, wl.arena, wl.min_block, nt, dyn_words)
     import oracle as _o
     ref = _o.Oracle(wl.arena, wl.min_block)
     try:
@@ -98,6 +101,15 @@ def test_dense_random(emu, nt):
     from paper_2405_07079_gb300 import workloads as W
     wl = W.Workload("dense", 1 << 20, 256, lambda: W.TinyRandom(n_ops=4000, batch=400, p_free=0.5))
     _check(emu, wl, nt)
+
+
+@pytest.mark.parametrize("dyn_words", [0, 4096, 1 << 20])
+def test_scratch_placements(emu, dyn_words):
+    """Free-phase scratch all in global memory, pointer jumping only in shared
+    memory, and everything in shared memory."""
+    from paper_2405_07079_gb300 import workloads as W
+    wl = W.Workload("life", 1 << 28, 512, lambda: W.Lifetimes(n_ops=200_000, batch=4096, mean_life=60))
+    _check(emu, wl, 256, every=3, dyn_words=dyn_words)
 
 
 @pytest.mark.parametrize("nt", [32, 256])
