@@ -32,7 +32,7 @@ SIGNATURES = {
     "hba_export_state": (i32, [vp, u32, vp, sz, vp]),
     "hba_multi_create": (i32, [u32, vp, u64, i32, u32, vp]),
     "hba_multi_step": (i32, [vp, vp, vp, u32, vp, vp, u32, vp, vp, vp]),
-    "hba_multi_set_shape": (i32, [vp, u32, u32]),
+    "hba_set_shape": (i32, [vp, u32, u32, u32]),
     "hba_version": (ctypes.c_char_p, []),
 }
 

@@ -38,7 +38,7 @@ struct hba_s {
     uint32_t threads = 1024;    // single-arena CTA width
     uint32_t m_threads = 256;   // multi-arena CTA width
     uint32_t m_ctas = 0;        // multi-arena grid (0 = one CTA per arena)
-    uint32_t m_dyn = 0;         // multi-arena dynamic shared memory per CTA (bytes)
+    uint32_t smem_bytes = 0;    // dynamic shared memory per CTA (0 = automatic)
     uint64_t* d_largest = nullptr;
 };
 
@@ -61,10 +61,11 @@ constexpr uint32_t MULTI_DYN_BYTES_DEFAULT = 24 * 1024;
 template <int NT>
 __global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
                                                uint8_t* st, const uint64_t* sizes, uint32_t na,
-                                               uint64_t* out, uint32_t* scr, uint32_t dyn_words) {
+                                               uint64_t* out, uint32_t* scr, uint32_t dyn_words,
+                                               uint32_t prefilled) {
     __shared__ hba::Smem<NT> S;
     extern __shared__ uint32_t dyn[];
-    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr};
+    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, prefilled};
     hba::arena_step<NT>(S, a, dyn, dyn_words);
 }
 
@@ -72,7 +73,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint32_t* frow,
                                               const uint64_t* frees, uint8_t* st, const uint32_t* arow,
                                               const uint64_t* sizes, uint64_t* out, uint32_t* scr,
-                                              uint32_t n_arenas, uint32_t dyn_words) {
+                                              uint32_t n_arenas, uint32_t dyn_words, uint32_t prefilled) {
     __shared__ hba::Smem<NT> S;
     extern __shared__ uint32_t dyn[];
     for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
@@ -86,7 +87,8 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            sizes + a0,
                            a1 - a0,
                            out + a0,
-                           scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE};
+                           scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE,
+                           prefilled};
         hba::arena_step<NT>(S, args, dyn, dyn_words);
     }
 }
@@ -125,6 +127,49 @@ int limit_index(uint32_t threads) {
     }
 }
 
+// Pre-fill out[0..n) with HBA_FAIL on many SMs; the allocator kernel that
+// follows (programmatic dependent launch) then stores only successes.
+__global__ void k_fill_fail(uint64_t* out, uint32_t n) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    uint32_t lo = 0;
+    if (((uintptr_t)out & 15) && n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = hba::FAIL64;
+        lo = 1;
+    }
+    ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + lo);
+    const uint32_t npair = (n - lo) / 2;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < npair; q += gridDim.x * blockDim.x)
+        o2[q] = make_ulonglong2(hba::FAIL64, hba::FAIL64);
+    if (((n - lo) & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[n - 1] = hba::FAIL64;
+}
+
+// Allocation batches at least this large get their failures pre-filled.
+constexpr uint32_t PREFILL_MIN = 2048;
+
+bool prefill(uint64_t* out, uint32_t n, cudaStream_t s) {
+    if (n < PREFILL_MIN) return false;
+    const uint32_t blocks = std::min<uint32_t>((n / 2 + 255) / 256, 1024);
+    k_fill_fail<<<blocks, 256, 0, s>>>(out, n);
+    return true;
+}
+
+// Launch with a programmatic dependency on the preceding kernel of the stream.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), uint32_t grid, uint32_t block, uint32_t dyn, cudaStream_t s,
+                       bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Write the initial record of every arena (one free block spanning it).
 __global__ void k_init_records(const Arena* ars, Rec* pool, uint32_t n_arenas) {
     const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -159,16 +204,30 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
                            const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
-    const uint32_t dyn = g_limits[limit_index(h->threads)].single_dyn;
-    const uint32_t dw = dyn / 4;
-    switch (h->threads) {
-        case 64: k_single<64><<<1, 64, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
-        case 128: k_single<128><<<1, 128, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
-        case 256: k_single<256><<<1, 256, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
-        case 512: k_single<512><<<1, 512, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
-        default: k_single<1024><<<1, 1024, dyn, s>>>(ar, rec, frees, nf, st, sizes, na, out, h->d_scr, dw); break;
+    const uint32_t maxdyn = g_limits[limit_index(h->threads)].single_dyn;
+    uint32_t dyn;
+    if (h->smem_bytes) {
+        dyn = std::min(h->smem_bytes, maxdyn) & ~15u;
+    } else {
+        // just what this batch's free scratch needs, so L1 keeps the rest
+        const uint64_t full = 4ull * hba::SCRATCH_WORDS_PER_FREE * nf, root = 4ull * nf;
+        dyn = full <= maxdyn ? (uint32_t)full : root <= maxdyn ? (uint32_t)root : 0u;
+        dyn = (dyn + 15u) & ~15u;
     }
-    return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+    const uint32_t dw = dyn / 4;
+    const bool pre = na && prefill(out, na, s);
+    const uint32_t pf = pre ? 1u : 0u;
+    cudaError_t e;
+    uint32_t* scr = h->d_scr;
+    switch (h->threads) {
+        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
+        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
+        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
+        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
+        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
+    }
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
+    return HBA_OK;
 }
 
 hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
@@ -396,13 +455,14 @@ hba_status_t hba_export_state(hba_t h, uint32_t arena, uint64_t* host_buf, size_
     return HBA_OK;
 }
 
-hba_status_t hba_multi_set_shape(hba_t h, uint32_t threads, uint32_t ctas) {
+hba_status_t hba_set_shape(hba_t h, uint32_t threads, uint32_t ctas, uint32_t smem_bytes) {
     if (!h) return HBA_ERR_INVALID_ARGUMENT;
     if (threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
         return HBA_ERR_INVALID_ARGUMENT;
     if (h->n_arenas == 1) h->threads = threads;
     h->m_threads = threads;
     h->m_ctas = ctas;
+    h->smem_bytes = smem_bytes;
     return HBA_OK;
 }
 
@@ -415,15 +475,23 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = h->n_arenas;
     const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
-    const uint32_t dyn = std::min(h->m_dyn ? h->m_dyn : MULTI_DYN_BYTES_DEFAULT,
-                                  g_limits[limit_index(h->m_threads)].multi_dyn);
+    const uint32_t dyn = std::min(h->smem_bytes ? h->smem_bytes : MULTI_DYN_BYTES_DEFAULT,
+                                  g_limits[limit_index(h->m_threads)].multi_dyn) & ~15u;
+    const uint32_t dw = dyn / 4;
+    const bool pre = na_total && prefill(d_out, na_total, s);
+    const uint32_t pf = pre ? 1u : 0u;
+    Arena* ar = h->d_arenas;
+    Rec* rec = h->d_rec;
+    uint32_t* scr = h->d_scr;
+    cudaError_t e;
     switch (h->m_threads) {
-        case 64: k_multi<64><<<grid, 64, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
-        case 128: k_multi<128><<<grid, 128, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
-        case 512: k_multi<512><<<grid, 512, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
-        case 1024: k_multi<1024><<<grid, 1024, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
-        default: k_multi<256><<<grid, 256, dyn, s>>>(h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr, n, dyn / 4); break;
+        case 64: e = launch_pdl(k_multi<64>, grid, 64, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
+        case 128: e = launch_pdl(k_multi<128>, grid, 128, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
+        case 512: e = launch_pdl(k_multi<512>, grid, 512, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
+        case 1024: e = launch_pdl(k_multi<1024>, grid, 1024, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
+        default: e = launch_pdl(k_multi<256>, grid, 256, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
     }
+    if (e != cudaSuccess) return HBA_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
 

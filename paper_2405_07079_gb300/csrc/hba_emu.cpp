@@ -30,7 +30,7 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
          uint32_t na, uint64_t* out) {
     Smem<NT>* S = new Smem<NT>();
     if (e->scr.size() < (size_t)SCRATCH_WORDS_PER_FREE * nf) e->scr.resize((size_t)SCRATCH_WORDS_PER_FREE * nf);
-    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data()};
+    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), 0};
     // a small "shared memory" area, so that both the shared-memory and the
     // global-scratch variants of the free phase run
     std::vector<uint32_t> dyn(e->dyn_words + 1);

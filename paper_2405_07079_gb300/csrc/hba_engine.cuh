@@ -61,7 +61,9 @@
 #define HBA_SYNC() \
     do {           \
     } while (0)
+#define HBA_UNROLL
 #else
+#define HBA_UNROLL _Pragma("unroll")
 #define HBA_HD __host__ __device__ __forceinline__
 #define HBA_DEV __device__ __forceinline__
 #define HBA_FOR_THREADS(tid) for (int tid = (int)threadIdx.x; tid < NT; tid += NT)
@@ -171,7 +173,10 @@ struct Smem {
     // the most recent remainder X, virtual head of class xL while xok; its
     // prev_adj is kept in rec[xg].y at all times
     uint32_t xok, xg, xsz, xright, xL;
-    uint32_t c0g;        // X's start when the current chunk was classified
+    uint32_t c0g, c0sz;  // X's start and size when the current chunk was classified
+    uint32_t r, cont;    // first unresolved lane of the chunk; 1 = chunk continues
+    uint32_t evb[2];     // first event lane, double-buffered per round
+    int64_t D;           // rounded sizes of the chunk's carve-speculated lanes that failed
     // loop control
     uint32_t p, ev, W, nul, nruns, flag[3];
     uint32_t err;        // first metadata error seen by this CTA (0 = none)
@@ -316,6 +321,8 @@ struct StepArgs {
     uint32_t na;
     uint64_t* out;
     uint32_t* scr;   // SCRATCH_WORDS_PER_FREE * nf words of global scratch
+    uint32_t prefilled;  // out[] already holds HBA_FAIL everywhere (written by a
+                         // preceding grid): failures need no store
 };
 
 // Push the virtual remainder X at the head of its list and write its record
@@ -364,23 +371,31 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t per = (nf + NT - 1) / NT;
 
     // F1: validate (start of an in-use block), claim (lowest index wins).
+    // Each thread takes U frees at a time so their loads overlap.
+    constexpr int U = 4;
     HBA_FOR_THREADS(tid) {
-        for (uint32_t j = tid; j < nf; j += NT) {
-            const uint64_t off = a.frees[j];
-            uint32_t g = NIL, sz = 0, y = NIL;
-            if (off < S.A && (off & mbm) == 0) {
-                const uint32_t gg = (uint32_t)(off >> S.lg);
-                const Rec r = ldr(rec, gg);
-                if (st_of(r.x) == ST_USED) {
-                    g = gg;
-                    sz = sz_of(r.x);
-                    y = r.y;
-                    at_min_u32(&rec[gg].z, j);
+        for (uint32_t j0 = tid; j0 < nf; j0 += NT * U) {
+            uint32_t gg[U];
+            Rec r[U];
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + u * NT;
+                const uint64_t off = j < nf ? a.frees[j] : FAIL64;
+                gg[u] = (off < S.A && (off & mbm) == 0) ? (uint32_t)(off >> S.lg) : NIL;
+            }
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) r[u] = gg[u] != NIL ? ldr(rec, gg[u]) : Rec{0, NIL, 0, 0};
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + u * NT;
+                if (j < nf) {
+                    const bool used = st_of(r[u].x) == ST_USED;
+                    if (used) at_min_u32(&rec[gg[u]].z, j);
+                    fg[j] = used ? gg[u] : NIL;
+                    fsz[j] = used ? sz_of(r[u].x) : 0;
+                    fy[j] = used ? r[u].y : NIL;
                 }
             }
-            fg[j] = g;
-            fsz[j] = sz;
-            fy[j] = y;
         }
         if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
     }
@@ -390,12 +405,22 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     HBA_FOR_THREADS(tid) {
         const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
         uint32_t c = 0;
-        for (uint32_t j = lo; j < hi; ++j) {
-            const uint32_t g = fg[j];
-            const bool win = g != NIL && rec[g].z == j;
-            if (!win) fg[j] = NIL;
-            if (a.fstat) a.fstat[j] = win ? 0 : 1;
-            c += win;
+        for (uint32_t j0 = lo; j0 < hi; j0 += U) {
+            uint32_t g[U], cl[U];
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) g[u] = j0 + u < hi ? fg[j0 + u] : NIL;
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) cl[u] = g[u] != NIL ? rec[g[u]].z : NIL;
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + u;
+                if (j < hi) {
+                    const bool win = g[u] != NIL && cl[u] == j;
+                    if (!win) fg[j] = NIL;
+                    if (a.fstat) a.fstat[j] = win ? 0 : 1;
+                    c += win;
+                }
+            }
         }
         S.cnt[tid] = c;
     }
@@ -437,42 +462,64 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     // by the one to its left when it ends the run.
     HBA_FOR_THREADS(tid) {
         for (uint32_t j = tid; j < nf; j += NT) runAt[j] = NIL;
-        for (uint32_t w = tid; w < W; w += NT) {
-            const uint32_t g = cg[w], sz = csz[w], L = cy[w];
-            uint32_t end = g + sz;
-            Rec rl{0, NIL, 0, 0};
-            uint32_t rx = 0;
-            if (L != NIL) rl = ldr(rec, L);
-            if (end < S.G) rx = rec[end].x;
-            uint32_t pr = NIL, head = g, flags = 0;
-            const uint32_t lst = st_of(rl.x);
-            if (lst == ST_NEW) {
-                pr = rl.z;
-            } else if (lst == ST_FREE) {
-                ul[at_add_u32(&S.nul, 1)] = L;
-                const uint32_t LL = rl.y;
-                const Rec rll = LL != NIL ? ldr(rec, LL) : Rec{0, 0, 0, 0};
-                if (st_of(rll.x) == ST_NEW) {
-                    pr = rll.z;
-                    flags |= 1;   // L is inside the run: erase its record
-                } else {
-                    head = L;     // L starts the run
-                }
+        for (uint32_t w0 = tid; w0 < W; w0 += NT * U) {
+            uint32_t g[U], sz[U], L[U], rx[U], LL[U], E2[U], rrx[U];
+            Rec rl[U], rll[U];
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                const uint32_t w = w0 + u * NT;
+                const bool ok = w < W;
+                g[u] = ok ? cg[w] : 0;
+                sz[u] = ok ? csz[w] : 0;
+                L[u] = ok ? cy[w] : NIL;
             }
-            if (st_of(rx) == ST_FREE) {
-                const uint32_t R = end;
-                end = R + sz_of(rx);
-                const bool rr_new = end < S.G && st_of(rec[end].x) == ST_NEW;
-                if (!rr_new) {
-                    ul[at_add_u32(&S.nul, 1)] = R;
-                    flags |= 2;   // R ends the run: erase its record
-                }
+            // round 1: both neighbours
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                const uint32_t w = w0 + u * NT;
+                rl[u] = L[u] != NIL ? ldr(rec, L[u]) : Rec{0, NIL, 0, 0};
+                rx[u] = (w < W && g[u] + sz[u] < S.G) ? rec[g[u] + sz[u]].x : 0u;
             }
-            root[w] = pr == NIL ? w : pr;
-            lh[w] = head;
-            rend[w] = end;
-            rmaxj[w] = cj[w];
-            fl[w] = flags;
+            // round 2: across an old free neighbour
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                LL[u] = st_of(rl[u].x) == ST_FREE ? rl[u].y : NIL;
+                E2[u] = st_of(rx[u]) == ST_FREE ? g[u] + sz[u] + sz_of(rx[u]) : S.G;
+                rll[u] = LL[u] != NIL ? ldr(rec, LL[u]) : Rec{0, 0, 0, 0};
+                rrx[u] = E2[u] < S.G ? rec[E2[u]].x : 0u;
+            }
+HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                const uint32_t w = w0 + u * NT;
+                if (w >= W) continue;
+                uint32_t end = g[u] + sz[u];
+                uint32_t pr = NIL, head = g[u], flags = 0;
+                const uint32_t lst = st_of(rl[u].x);
+                if (lst == ST_NEW) {
+                    pr = rl[u].z;
+                } else if (lst == ST_FREE) {
+                    ul[at_add_u32(&S.nul, 1)] = L[u];
+                    if (st_of(rll[u].x) == ST_NEW) {
+                        pr = rll[u].z;
+                        flags |= 1;   // L is inside the run: erase its record
+                    } else {
+                        head = L[u];  // L starts the run
+                    }
+                }
+                if (st_of(rx[u]) == ST_FREE) {
+                    const uint32_t R = end;
+                    end = E2[u];
+                    if (st_of(rrx[u]) != ST_NEW) {
+                        ul[at_add_u32(&S.nul, 1)] = R;
+                        flags |= 2;   // R ends the run: erase its record
+                    }
+                }
+                root[w] = pr == NIL ? w : pr;
+                lh[w] = head;
+                rend[w] = end;
+                rmaxj[w] = cj[w];
+                fl[w] = flags;
+            }
         }
     }
     HBA_SYNC();
@@ -639,7 +686,7 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
     const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
     const uint64_t cand = sg ? (M >> c) << c : 0ull;
     if (!cand) {
-        a.out[i] = FAIL64;
+        if (!a.prefilled) a.out[i] = FAIL64;
         single_add(S, C_AFAIL, 1);
         return;
     }
@@ -667,7 +714,7 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
         if (Y >= S.G) {  // bitmap and heads disagree: record, fail the request
             S.err = ERR_EMPTY_HEAD;
             S.mask &= ~(1ull << k);
-            a.out[i] = FAIL64;
+            if (!a.prefilled) a.out[i] = FAIL64;
             single_add(S, C_AFAIL, 1);
             return;
         }
@@ -703,6 +750,11 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
     Rec* rec = a.rec;
     const uint32_t lg = S.lg;
     const uint64_t mbm = (1ull << lg) - 1ull;
+#ifndef HBA_EMULATE
+    // out[] may be pre-filled by the preceding grid: wait for it (no-op when
+    // the launch carries no programmatic dependency)
+    if (a.prefilled) asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
     HBA_FOR_THREADS(tid) {
         if (tid == 0) { S.p = 0; S.xok = 0; }
     }
@@ -713,19 +765,21 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         if (!S.xok && S.mask == 0) {
             // nothing is free: every remaining request fails
             HBA_FOR_THREADS(tid) {
+                if (!a.prefilled) {
 #ifdef HBA_EMULATE
-                for (uint32_t i = p + tid; i < na; i += NT) a.out[i] = FAIL64;
+                    for (uint32_t i = p + tid; i < na; i += NT) a.out[i] = FAIL64;
 #else
-                uint32_t lo = p;
-                if (((uintptr_t)(a.out + lo) & 15) && lo < na) {
-                    if (tid == 0) a.out[lo] = FAIL64;
-                    ++lo;
-                }
-                ulonglong2* o2 = reinterpret_cast<ulonglong2*>(a.out + lo);
-                const uint32_t npair = (na - lo) / 2;
-                for (uint32_t q = tid; q < npair; q += NT) o2[q] = make_ulonglong2(FAIL64, FAIL64);
-                if (((na - lo) & 1) && tid == 0) a.out[na - 1] = FAIL64;
+                    uint32_t lo = p;
+                    if (((uintptr_t)(a.out + lo) & 15) && lo < na) {
+                        if (tid == 0) a.out[lo] = FAIL64;
+                        ++lo;
+                    }
+                    ulonglong2* o2 = reinterpret_cast<ulonglong2*>(a.out + lo);
+                    const uint32_t npair = (na - lo) / 2;
+                    for (uint32_t q = tid; q < npair; q += NT) o2[q] = make_ulonglong2(FAIL64, FAIL64);
+                    if (((na - lo) & 1) && tid == 0) a.out[na - 1] = FAIL64;
 #endif
+                }
                 if (tid == 0) single_add(S, C_AFAIL, (int64_t)(na - p));
             }
             HBA_SYNC();
@@ -758,84 +812,131 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             S.u.a.s64[tid] = s;
             S.u.a.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
             if (tid == 0) {
-                S.ev = NT;
                 S.c0g = S.xg;
+                S.c0sz = S.xok ? S.xsz : 0;
+                S.r = 0;
+                S.D = 0;
+                S.evb[0] = S.evb[1] = NT;
             }
         }
         HBA_SYNC();
         HBA_PROF(12);
         scan_incl_i64<NT>(S, S.u.a.val);
         HBA_PROF(13);
-        // B: verify the speculation (every carve-classified lane assumed that
-        // the carves before it succeeded); the first wrong lane, or the first
-        // "other", ends the parallel part of the chunk
-        HBA_FOR_THREADS(tid) {
-            const uint8_t cl = S.cls[tid];
-            bool e = cl == CL_OTHER;
-            if (cl == CL_CARVE) {
-                const int64_t before = (int64_t)S.xsz - (S.u.a.val[tid] - (int64_t)S.sgr[tid]);
-                uint64_t M = S.mask;
-                uint32_t Lt = 64;
-                if (before > 0) {
-                    Lt = flog2((uint32_t)before);
-                    M |= 1ull << Lt;
-                }
-                const uint32_t c = S.ccl[tid];
-                const uint64_t cand = (M >> c) << c;
-                if (!(cand && ctz64(cand) == Lt)) e = true;
-            }
-            warp_first_min(S, tid, e);
-        }
-        HBA_SYNC();
-        HBA_PROF(14);
-        const uint32_t ev = S.ev;
         const uint32_t n_here = na - p < (uint32_t)NT ? na - p : (uint32_t)NT;
-        const uint32_t nres = ev < n_here ? ev : n_here;
-        const uint32_t upd = nres < n_here ? nres : n_here - 1;
-        // C: resolve lanes [0, nres) (failures, carves from X) in parallel;
-        // lane `upd` then advances X and applies the event lane alone
-        HBA_FOR_THREADS(tid) {
-            const bool act = (uint32_t)tid < nres;
-            const uint8_t cl = S.cls[tid];
-            const bool is_fail = act && cl == CL_FAIL;
-            const bool is_carve = act && cl == CL_CARVE;
-            if (is_fail) a.out[p + tid] = FAIL64;
-            if (is_carve) {
-                const uint32_t sg = S.sgr[tid];
-                const int64_t P = S.u.a.val[tid];
-                const uint32_t start = S.c0g + (uint32_t)(P - sg);
-                const uint32_t end = S.c0g + (uint32_t)P;
-                a.out[p + tid] = (uint64_t)start << lg;
-                rec[start].x = mkx(sg, ST_USED);
-                rec[start].z = NIL;
-                rec[start].w = NIL;
-                if (end < S.G) rec[end].y = start;
-            }
-            warp_count(S, tid, C_AFAIL, is_fail);
-            warp_count(S, tid, C_AOK, is_carve);
-            warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.u.a.s64[tid] : 0);
-            if ((uint32_t)tid == upd) {
-                const int64_t ptot = nres ? S.u.a.val[nres - 1] : 0;
-                if (ptot > 0) {
-                    S.xg += (uint32_t)ptot;
-                    S.xsz -= (uint32_t)ptot;
-                    single_add(S, C_USEDG, ptot);
-                    if (S.xsz == 0) {
-                        S.xok = 0;
-                        single_add(S, C_NOSPLIT, 1);
-                    } else {
-                        S.xL = flog2(S.xsz);
+        // Rounds over the chunk.  Every carve-classified lane assumed that the
+        // carve-classified lanes before it succeeded; a lane whose true class
+        // (given X's actual size in front of it) is different, or an "other",
+        // is an event.  Lanes before the first event are exact and resolved in
+        // parallel.  An event lane that simply fails stays inside the chunk
+        // (its size is deducted from the later prefixes, D); any other event
+        // is applied alone and ends the chunk.
+        for (int round = 0;; ++round) {
+            const uint32_t r = S.r;
+            const int64_t D = S.D;
+            uint32_t* evp = &S.evb[round & 1];
+            // B: verify lanes [r, n_here)
+            HBA_FOR_THREADS(tid) {
+                const uint8_t cl = S.cls[tid];
+                bool e = false;
+                if ((uint32_t)tid >= r) {
+                    e = cl == CL_OTHER;
+                    if (cl == CL_CARVE) {
+                        const int64_t before =
+                            (int64_t)S.c0sz - (S.u.a.val[tid] - D - (int64_t)S.sgr[tid]);
+                        uint64_t M = S.mask;
+                        uint32_t Lt = 64;
+                        if (before > 0) {
+                            Lt = flog2((uint32_t)before);
+                            M |= 1ull << Lt;
+                        }
+                        const uint32_t c = S.ccl[tid];
+                        const uint64_t cand = (M >> c) << c;
+                        if (!(cand && ctz64(cand) == Lt)) e = true;
                     }
                 }
-                S.p = p + nres;
-                if (nres < n_here) {
-                    seq_request<NT>(S, a, p + nres, S.u.a.s64[nres], S.sgr[nres], S.ccl[nres]);
-                    S.p = p + nres + 1;
+#ifdef HBA_EMULATE
+                if (e && (uint32_t)tid < *evp) *evp = (uint32_t)tid;
+#else
+                const unsigned bal = __ballot_sync(0xffffffffu, e);
+                if ((tid & 31) == 0 && bal) atomicMin(evp, (uint32_t)(tid + __ffs(bal) - 1));
+#endif
+            }
+            HBA_SYNC();
+            HBA_PROF(14);
+            const uint32_t ev = *evp;
+            const uint32_t nres = ev < n_here ? ev : n_here;   // lanes [r, nres) are exact
+            const uint32_t upd = nres < n_here ? nres : n_here - 1;
+            // C: resolve [r, nres); lane `upd` handles the event lane / chunk end
+            HBA_FOR_THREADS(tid) {
+                const bool act = (uint32_t)tid >= r && (uint32_t)tid < nres;
+                const uint8_t cl = S.cls[tid];
+                const bool is_fail = act && cl == CL_FAIL;
+                const bool is_carve = act && cl == CL_CARVE;
+                if (is_fail && !a.prefilled) a.out[p + tid] = FAIL64;
+                if (is_carve) {
+                    const uint32_t sg = S.sgr[tid];
+                    const int64_t P = S.u.a.val[tid] - D;
+                    const uint32_t start = S.c0g + (uint32_t)(P - sg);
+                    const uint32_t end = S.c0g + (uint32_t)P;
+                    a.out[p + tid] = (uint64_t)start << lg;
+                    rec[start].x = mkx(sg, ST_USED);
+                    rec[start].z = NIL;
+                    rec[start].w = NIL;
+                    if (end < S.G) rec[end].y = start;
+                }
+                warp_count(S, tid, C_AFAIL, is_fail);
+                warp_count(S, tid, C_AOK, is_carve);
+                warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.u.a.s64[tid] : 0);
+                if ((uint32_t)tid == upd) {
+                    S.evb[(round + 1) & 1] = NT;
+                    // true carve total of the chunk up to lane nres - 1
+                    const int64_t done = nres ? S.u.a.val[nres - 1] - D : 0;
+                    bool stays = false;
+                    if (nres < n_here && S.cls[nres] == CL_CARVE) {
+                        // a carve-classified lane that is wrong: does it just fail?
+                        const int64_t before = (int64_t)S.c0sz - done;
+                        const uint32_t c = S.ccl[nres];
+                        uint64_t M = S.mask;
+                        if (before > 0) M |= 1ull << flog2((uint32_t)before);
+                        stays = ((M >> c) << c) == 0;
+                    }
+                    if (stays) {
+                        if (!a.prefilled) a.out[p + nres] = FAIL64;
+                        single_add(S, C_AFAIL, 1);
+                        S.D = D + (int64_t)S.sgr[nres];
+                        S.r = nres + 1;
+                        S.cont = nres + 1 < n_here;
+                        if (!S.cont) S.p = p + n_here;
+                    } else {
+                        S.cont = 0;
+                        S.p = p + nres;
+                    }
+                    if (!S.cont) {
+                        // the chunk ends here: advance X by what it gave
+                        const int64_t gave = done;
+                        if (gave > 0) {
+                            S.xg = S.c0g + (uint32_t)gave;
+                            S.xsz = S.c0sz - (uint32_t)gave;
+                            single_add(S, C_USEDG, gave);
+                            if (S.xsz == 0) {
+                                S.xok = 0;
+                                single_add(S, C_NOSPLIT, 1);
+                            } else {
+                                S.xL = flog2(S.xsz);
+                            }
+                        }
+                        if (!stays && nres < n_here) {
+                            seq_request<NT>(S, a, p + nres, S.u.a.s64[nres], S.sgr[nres], S.ccl[nres]);
+                            S.p = p + nres + 1;
+                        }
+                    }
                 }
             }
+            HBA_SYNC();
+            HBA_PROF(15);
+            if (!S.cont) break;
         }
-        HBA_SYNC();
-        HBA_PROF(15);
     }
     HBA_FOR_THREADS(tid) {
         if (tid == 0 && S.xok) materialize_x<NT>(S, rec);

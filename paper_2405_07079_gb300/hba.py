@@ -89,8 +89,8 @@ def hba_multi_step(h: int, d_free_rowptr: int, d_frees: int, nf_total: int, d_al
                                                   d_sizes, na_total, d_out, d_free_status, stream))
 
 
-def hba_multi_set_shape(h: int, threads: int, ctas: int = 0) -> None:
-    check("hba_multi_set_shape", _lib().hba_multi_set_shape(h, threads, ctas))
+def hba_set_shape(h: int, threads: int, ctas: int = 0, smem_bytes: int = 0) -> None:
+    check("hba_set_shape", _lib().hba_set_shape(h, threads, ctas, smem_bytes))
 
 
 def hba_version() -> str:
@@ -117,13 +117,14 @@ def _ptr(t) -> int:
 class Allocator:
     """One arena.  Inputs/outputs are uint64 (int64-typed) CUDA tensors."""
 
-    def __init__(self, arena_bytes: int, min_block: int, max_batch: int = 65536, threads: int | None = None):
+    def __init__(self, arena_bytes: int, min_block: int, max_batch: int = 65536, threads: int | None = None,
+                 smem_bytes: int = 0):
         self.h = hba_create(arena_bytes, min_block, HBA_POLICY_SEGFIT, max_batch)
         self.arena_bytes = arena_bytes - arena_bytes % min_block
         self.min_block = min_block
         self.max_batch = max_batch
-        if threads is not None:
-            hba_multi_set_shape(self.h, threads, 0)
+        if threads is not None or smem_bytes:
+            hba_set_shape(self.h, threads or 1024, 0, smem_bytes)
 
     def close(self):
         if self.h:
@@ -178,8 +179,8 @@ class MultiAllocator:
             hba_destroy(self.h)
             self.h = 0
 
-    def set_shape(self, threads: int, ctas: int = 0):
-        hba_multi_set_shape(self.h, threads, ctas)
+    def set_shape(self, threads: int, ctas: int = 0, smem_bytes: int = 0):
+        hba_set_shape(self.h, threads, ctas, smem_bytes)
 
     def step(self, free_rowptr, frees, alloc_rowptr, sizes, out, status=None, stream=None):
         hba_multi_step(self.h, _ptr(free_rowptr), _ptr(frees), frees.numel(), _ptr(alloc_rowptr),
