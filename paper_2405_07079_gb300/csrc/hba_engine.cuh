@@ -176,7 +176,6 @@ struct Smem {
     uint32_t c0g, c0sz;  // X's start and size when the current chunk was classified
     uint32_t r, cont;    // first unresolved lane of the chunk; 1 = chunk continues
     uint32_t evb[2];     // first event lane, double-buffered per round
-    int64_t D;           // rounded sizes of the chunk's carve-speculated lanes that failed
     // loop control
     uint32_t p, ev, W, nul, nruns, flag[3];
     uint32_t err;        // first metadata error seen by this CTA (0 = none)
@@ -786,74 +785,82 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             HBA_PROF(17);
             break;
         }
-        // A: classify the chunk [p, p + NT) against the state at its start
+        // A0: load the chunk [p, p + NT) once
         HBA_FOR_THREADS(tid) {
             const uint32_t i = p + tid;
-            uint8_t cl = CL_NONE;
             uint32_t sg = 0, c = 0;
             uint64_t s = 0;
+            bool bad = true;
             if (i < na) {
                 s = a.sizes[i];
                 if (i + NT < na) prefetch_l2(a.sizes + i + NT);
-                if (s == 0 || s > S.A) {
-                    cl = CL_FAIL;
-                } else {
+                if (s != 0 && s <= S.A) {
+                    bad = false;
                     sg = (uint32_t)((s + mbm) >> lg);
                     c = clog2(sg);
-                    const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
-                    const uint64_t cand = (M >> c) << c;
-                    if (!cand) cl = CL_FAIL;
-                    else cl = (S.xok && ctz64(cand) == S.xL) ? CL_CARVE : CL_OTHER;
                 }
             }
-            S.cls[tid] = cl;
-            S.sgr[tid] = sg;
+            S.sgr[tid] = bad ? 0 : sg;
             S.ccl[tid] = (uint8_t)c;
             S.u.a.s64[tid] = s;
-            S.u.a.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
-            if (tid == 0) {
-                S.c0g = S.xg;
-                S.c0sz = S.xok ? S.xsz : 0;
-                S.r = 0;
-                S.D = 0;
-                S.evb[0] = S.evb[1] = NT;
-            }
+            if (tid == 0) S.r = 0;
         }
         HBA_SYNC();
-        HBA_PROF(12);
-        scan_incl_i64<NT>(S, S.u.a.val);
-        HBA_PROF(13);
+        HBA_PROF(11);
         const uint32_t n_here = na - p < (uint32_t)NT ? na - p : (uint32_t)NT;
-        // Rounds over the chunk.  Every carve-classified lane assumed that the
-        // carve-classified lanes before it succeeded; a lane whose true class
-        // (given X's actual size in front of it) is different, or an "other",
-        // is an event.  Lanes before the first event are exact and resolved in
-        // parallel.  An event lane that simply fails stays inside the chunk
-        // (its size is deducted from the later prefixes, D); any other event
-        // is applied alone and ends the chunk.
+        // Rounds over the chunk.  Each round classifies the unresolved lanes
+        // [r, n_here) against the current state, assuming that every lane
+        // classified as a carve from X succeeds; a lane whose true class
+        // (given X's actual size in front of it) differs, or an "other", is an
+        // event.  Lanes before the first event are exact and resolved in
+        // parallel; the event lane is applied alone; the next round starts
+        // after it.
         for (int round = 0;; ++round) {
             const uint32_t r = S.r;
-            const int64_t D = S.D;
             uint32_t* evp = &S.evb[round & 1];
-            // B: verify lanes [r, n_here)
+            // A1: classify
+            HBA_FOR_THREADS(tid) {
+                uint8_t cl = CL_NONE;
+                const uint32_t sg = S.sgr[tid];
+                if ((uint32_t)tid >= r && (uint32_t)tid < n_here) {
+                    if (sg == 0) {
+                        cl = CL_FAIL;
+                    } else {
+                        const uint32_t c = S.ccl[tid];
+                        const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
+                        const uint64_t cand = (M >> c) << c;
+                        if (!cand) cl = CL_FAIL;
+                        else cl = (S.xok && ctz64(cand) == S.xL) ? CL_CARVE : CL_OTHER;
+                    }
+                }
+                S.cls[tid] = cl;
+                S.u.a.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
+                if (tid == 0) {
+                    S.c0g = S.xg;
+                    S.c0sz = S.xok ? S.xsz : 0;
+                    S.evb[(round + 1) & 1] = NT;
+                    if (round == 0) S.evb[0] = NT;
+                }
+            }
+            HBA_SYNC();
+            HBA_PROF(12);
+            scan_incl_i64<NT>(S, S.u.a.val);
+            HBA_PROF(13);
+            // B: verify
             HBA_FOR_THREADS(tid) {
                 const uint8_t cl = S.cls[tid];
-                bool e = false;
-                if ((uint32_t)tid >= r) {
-                    e = cl == CL_OTHER;
-                    if (cl == CL_CARVE) {
-                        const int64_t before =
-                            (int64_t)S.c0sz - (S.u.a.val[tid] - D - (int64_t)S.sgr[tid]);
-                        uint64_t M = S.mask;
-                        uint32_t Lt = 64;
-                        if (before > 0) {
-                            Lt = flog2((uint32_t)before);
-                            M |= 1ull << Lt;
-                        }
-                        const uint32_t c = S.ccl[tid];
-                        const uint64_t cand = (M >> c) << c;
-                        if (!(cand && ctz64(cand) == Lt)) e = true;
+                bool e = cl == CL_OTHER;
+                if (cl == CL_CARVE) {
+                    const int64_t before = (int64_t)S.c0sz - (S.u.a.val[tid] - (int64_t)S.sgr[tid]);
+                    uint64_t M = S.mask;
+                    uint32_t Lt = 64;
+                    if (before > 0) {
+                        Lt = flog2((uint32_t)before);
+                        M |= 1ull << Lt;
                     }
+                    const uint32_t c = S.ccl[tid];
+                    const uint64_t cand = (M >> c) << c;
+                    if (!(cand && ctz64(cand) == Lt)) e = true;
                 }
 #ifdef HBA_EMULATE
                 if (e && (uint32_t)tid < *evp) *evp = (uint32_t)tid;
@@ -867,16 +874,16 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             const uint32_t ev = *evp;
             const uint32_t nres = ev < n_here ? ev : n_here;   // lanes [r, nres) are exact
             const uint32_t upd = nres < n_here ? nres : n_here - 1;
-            // C: resolve [r, nres); lane `upd` handles the event lane / chunk end
+            // C: resolve [r, nres); lane `upd` advances X and applies the event
             HBA_FOR_THREADS(tid) {
-                const bool act = (uint32_t)tid >= r && (uint32_t)tid < nres;
                 const uint8_t cl = S.cls[tid];
+                const bool act = (uint32_t)tid < nres;   // lanes below r have class NONE
                 const bool is_fail = act && cl == CL_FAIL;
                 const bool is_carve = act && cl == CL_CARVE;
                 if (is_fail && !a.prefilled) a.out[p + tid] = FAIL64;
                 if (is_carve) {
                     const uint32_t sg = S.sgr[tid];
-                    const int64_t P = S.u.a.val[tid] - D;
+                    const int64_t P = S.u.a.val[tid];
                     const uint32_t start = S.c0g + (uint32_t)(P - sg);
                     const uint32_t end = S.c0g + (uint32_t)P;
                     a.out[p + tid] = (uint64_t)start << lg;
@@ -889,53 +896,43 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                 warp_count(S, tid, C_AOK, is_carve);
                 warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.u.a.s64[tid] : 0);
                 if ((uint32_t)tid == upd) {
-                    S.evb[(round + 1) & 1] = NT;
-                    // true carve total of the chunk up to lane nres - 1
-                    const int64_t done = nres ? S.u.a.val[nres - 1] - D : 0;
-                    bool stays = false;
-                    if (nres < n_here && S.cls[nres] == CL_CARVE) {
-                        // a carve-classified lane that is wrong: does it just fail?
-                        const int64_t before = (int64_t)S.c0sz - done;
-                        const uint32_t c = S.ccl[nres];
-                        uint64_t M = S.mask;
-                        if (before > 0) M |= 1ull << flog2((uint32_t)before);
-                        stays = ((M >> c) << c) == 0;
-                    }
-                    if (stays) {
-                        if (!a.prefilled) a.out[p + nres] = FAIL64;
-                        single_add(S, C_AFAIL, 1);
-                        S.D = D + (int64_t)S.sgr[nres];
-                        S.r = nres + 1;
-                        S.cont = nres + 1 < n_here;
-                        if (!S.cont) S.p = p + n_here;
-                    } else {
-                        S.cont = 0;
-                        S.p = p + nres;
-                    }
-                    if (!S.cont) {
-                        // the chunk ends here: advance X by what it gave
-                        const int64_t gave = done;
-                        if (gave > 0) {
-                            S.xg = S.c0g + (uint32_t)gave;
-                            S.xsz = S.c0sz - (uint32_t)gave;
-                            single_add(S, C_USEDG, gave);
-                            if (S.xsz == 0) {
-                                S.xok = 0;
-                                single_add(S, C_NOSPLIT, 1);
-                            } else {
-                                S.xL = flog2(S.xsz);
-                            }
-                        }
-                        if (!stays && nres < n_here) {
-                            seq_request<NT>(S, a, p + nres, S.u.a.s64[nres], S.sgr[nres], S.ccl[nres]);
-                            S.p = p + nres + 1;
+                    const int64_t gave = nres ? S.u.a.val[nres - 1] : 0;
+                    if (gave > 0) {
+                        S.xg = S.c0g + (uint32_t)gave;
+                        S.xsz = S.c0sz - (uint32_t)gave;
+                        single_add(S, C_USEDG, gave);
+                        if (S.xsz == 0) {
+                            S.xok = 0;
+                            single_add(S, C_NOSPLIT, 1);
+                        } else {
+                            S.xL = flog2(S.xsz);
                         }
                     }
+                    uint32_t next = n_here;
+                    if (nres < n_here) {
+                        seq_request<NT>(S, a, p + nres, S.u.a.s64[nres], S.sgr[nres], S.ccl[nres]);
+                        next = nres + 1;
+                    }
+                    S.r = next;
+                    S.cont = next < n_here;
+                    if (!S.cont) S.p = p + n_here;
                 }
             }
             HBA_SYNC();
             HBA_PROF(15);
             if (!S.cont) break;
+            if (!S.xok && S.mask == 0) {
+                // nothing is free any more: the rest of the chunk fails
+                HBA_FOR_THREADS(tid) {
+                    const uint32_t rr = S.r;
+                    const bool f = (uint32_t)tid >= rr && (uint32_t)tid < n_here;
+                    if (f && !a.prefilled) a.out[p + tid] = FAIL64;
+                    warp_count(S, tid, C_AFAIL, f);
+                    if (tid == 0) S.p = p + n_here;
+                }
+                HBA_SYNC();
+                break;
+            }
         }
     }
     HBA_FOR_THREADS(tid) {
