@@ -209,10 +209,10 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     if (h->smem_bytes) {
         dyn = std::min(h->smem_bytes, maxdyn) & ~15u;
     } else {
-        // just what this batch's free scratch needs, so L1 keeps the rest
-        const uint64_t full = 4ull * hba::SCRATCH_WORDS_PER_FREE * nf, root = 4ull * nf;
-        dyn = full <= maxdyn ? (uint32_t)full : root <= maxdyn ? (uint32_t)root : 0u;
-        dyn = (dyn + 15u) & ~15u;
+        // just what this batch's free phase keeps in shared memory, so that
+        // L1 keeps the rest
+        const uint64_t hot = 4ull * hba::free_hot_words(std::min(nf, h->max_batch));
+        dyn = hot <= maxdyn ? (uint32_t)((hot + 15u) & ~15ull) : 0u;
     }
     const uint32_t dw = dyn / 4;
     const bool pre = na && prefill(out, na, s);

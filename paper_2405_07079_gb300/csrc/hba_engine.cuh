@@ -87,7 +87,7 @@ constexpr uint32_t MAX_GRANULES = SZ_MASK;  // G <= 2^29 - 1
 constexpr uint32_t ST_NONE = 0, ST_USED = 1, ST_FREE = 2, ST_NEW = 3, ST_DEL = 4;
 constexpr uint64_t FAIL64 = ~0ull;
 constexpr int NBINS = 32;  // granule classes 0..28 are reachable
-constexpr uint32_t SCRATCH_WORDS_PER_FREE = 12;
+constexpr uint32_t SCRATCH_WORDS_PER_FREE = 28;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
 constexpr uint32_t ERR_EMPTY_HEAD = 2;  // a class with its bit set had no head
@@ -143,6 +143,7 @@ HBA_DEV uint32_t at_min_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; if (v < 
 HBA_DEV uint32_t at_max_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; if (v > o) *p = v; return o; }
 HBA_DEV uint32_t at_add_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; *p = o + v; return o; }
 HBA_DEV void at_add_i64(int64_t* p, int64_t v) { *p += v; }
+HBA_DEV uint32_t at_cas_u32(uint32_t* p, uint32_t cmp, uint32_t v) { uint32_t o = *p; if (o == cmp) *p = v; return o; }
 #else
 HBA_DEV Rec ldr(const Rec* r, uint32_t g) {
     uint4 v = *reinterpret_cast<const uint4*>(r + g);
@@ -152,6 +153,7 @@ HBA_DEV void str(Rec* r, uint32_t g, Rec v) { *reinterpret_cast<uint4*>(r + g) =
 HBA_DEV uint32_t at_min_u32(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
 HBA_DEV uint32_t at_max_u32(uint32_t* p, uint32_t v) { return atomicMax(p, v); }
 HBA_DEV uint32_t at_add_u32(uint32_t* p, uint32_t v) { return atomicAdd(p, v); }
+HBA_DEV uint32_t at_cas_u32(uint32_t* p, uint32_t cmp, uint32_t v) { return atomicCAS(p, cmp, v); }
 HBA_DEV void at_add_i64(int64_t* p, int64_t v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
@@ -342,195 +344,207 @@ HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec) {
 // ---------------------------------------------------------------------------
 // The free phase (Algorithm 5 for all frees of the batch).
 // ---------------------------------------------------------------------------
+
+// Open-addressing table in (shared) memory: granule -> lowest free index
+// that names it.  Only in-use block starts are inserted.
+struct GTable {
+    uint32_t* key;
+    uint32_t* val;
+    uint32_t mask;  // capacity - 1 (capacity: power of two >= 2 * keys)
+};
+HBA_DEV uint32_t gt_hash(uint32_t g, uint32_t mask) { return (g * 0x9E3779B1u >> 7) & mask; }
+HBA_DEV void gt_insert_min(const GTable& t, uint32_t g, uint32_t j) {
+    uint32_t s = gt_hash(g, t.mask);
+    while (true) {
+        const uint32_t k = at_cas_u32(&t.key[s], NIL, g);
+        if (k == NIL || k == g) {
+            at_min_u32(&t.val[s], j);
+            return;
+        }
+        s = (s + 1) & t.mask;
+    }
+}
+// Lowest free index naming granule g, or NIL when g was not freed.
+HBA_DEV uint32_t gt_find(const GTable& t, uint32_t g) {
+    uint32_t s = gt_hash(g, t.mask);
+    while (true) {
+        const uint32_t k = t.key[s];
+        if (k == g) return t.val[s];
+        if (k == NIL) return NIL;
+        s = (s + 1) & t.mask;
+    }
+}
+
+// Capacity of the granule table for nf frees, and the words of the free
+// phase's hot arrays (table, roots, per-run maxima) that go to shared memory
+// when they fit.
+HBA_HD uint32_t gt_capacity(uint32_t nf) {
+    uint32_t c = 2;
+    while (c < 2 * nf) c <<= 1;
+    return c;
+}
+HBA_HD uint32_t free_hot_words(uint32_t nf) { return 2 * gt_capacity(nf) + 3 * nf; }
+
 template <int NT>
 HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t nf = a.nf;
     Rec* rec = a.rec;
-    // Scratch: 12 words per free, in shared memory when they fit.  Arrays
-    // whose lifetimes do not overlap share storage.
-    const bool in_smem = (uint64_t)SCRATCH_WORDS_PER_FREE * nf <= S.dyn_words;
-    uint32_t* base = in_smem ? S.dyn : a.scr;
-    uint32_t* fg = base;               // by free index j: granule, or NIL if rejected (F1-F3)
-    uint32_t* runAt = base;            //   then: run leader whose last free is j (F4-F9)
-    uint32_t* fsz = base + nf;         //   size of the freed block (F1-F3)
-    uint32_t* lh = base + nf;          // by compact index w: leftmost block of my run's left part (F4-)
-    uint32_t* fy = base + 2 * nf;      //   prev_adj of the freed block (F1-F3)
-    uint32_t* rend = base + 2 * nf;    //   right end of my piece; max over the run at the root (F4-)
-    uint32_t* cg = base + 3 * nf;      // applied frees in order: granule
-    uint32_t* csz = base + 4 * nf;     //   size
-    uint32_t* cy = base + 5 * nf;      //   prev_adj
-    uint32_t* cj = base + 6 * nf;      //   free index (F3-F6)
-    uint32_t* runs = base + 6 * nf;    //   then: run leaders in free-index order (F9-F10)
-    uint32_t* root = base + 7 * nf;    //   pointer-jumping root
-    uint32_t* rmaxj = base + 8 * nf;   //   largest free index (max over the run at the root)
-    uint32_t* fl = base + 9 * nf;      //   bit0: erase left old-free record, bit1: erase right one
-    uint32_t* ul = base + 10 * nf;     // [2 nf] old free blocks absorbed by runs
-    if (!in_smem && nf <= S.dyn_words) root = S.dyn;
+    // Everything is indexed by free index j; a rejected free has g[j] = NIL.
+    // Global scratch (28 words per free): the records read up front, the
+    // per-run results, the lists of absorbed blocks and runs; the hot arrays
+    // (granule table, pointer-jumping roots, per-run maxima) go to shared
+    // memory when they fit.
+    const uint32_t hcap = gt_capacity(nf);
+    uint32_t* sc = a.scr;
+    uint32_t* fgr = sc;                 // granule of the freed block, NIL if rejected
+    uint32_t* fsz = sc + nf;            // its size
+    uint32_t* fy = sc + 2 * nf;         // its prev_adj (L)
+    uint32_t* Lx = sc + 3 * nf;         // record of L (x, y, z, w)
+    uint32_t* Ly = sc + 4 * nf;
+    uint32_t* Lz = sc + 5 * nf;
+    uint32_t* Lw = sc + 6 * nf;
+    uint32_t* Rx = sc + 7 * nf;         // record of R = g + size (x, z, w)
+    uint32_t* Rz = sc + 8 * nf;
+    uint32_t* Rw = sc + 9 * nf;
+    uint32_t* lh = sc + 10 * nf;        // leftmost block of the run's left part
+    uint32_t* fl = sc + 11 * nf;        // bit0: erase L's record, bit1: erase R's record
+    uint32_t* runAt = sc + 12 * nf;     // run leader whose last free is j, or NIL
+    uint32_t* runs = sc + 13 * nf;      // run leaders in order of their last free
+    uint32_t* ul = sc + 14 * nf;        // [2 nf] old free blocks absorbed by runs
+    uint32_t* hb = free_hot_words(nf) <= S.dyn_words ? S.dyn : sc + 16 * nf;
+    GTable T{hb, hb + hcap, hcap - 1};
+    uint32_t* root = hb + 2 * hcap;     // pointer-jumping root (a free index)
+    uint32_t* rmaxj = root + nf;        // largest free index of the run (at the root)
+    uint32_t* rend = rmaxj + nf;        // right end of the run (at the root)
     const uint64_t mbm = (1ull << S.lg) - 1ull;
-    const uint32_t per = (nf + NT - 1) / NT;
-
-    // F1: validate (start of an in-use block), claim (lowest index wins).
-    // Each thread takes U frees at a time so their loads overlap.
     constexpr int U = 4;
+
+    // F0: clear the granule table.
+    HBA_FOR_THREADS(tid) {
+        for (uint32_t q = tid; q < hcap; q += NT) {
+            T.key[q] = NIL;
+            T.val[q] = NIL;
+        }
+        if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
+    }
+    HBA_SYNC();
+    // F1: every record the phase needs, U frees per thread at a time so the
+    // loads overlap: the freed block (must be the start of an in-use block),
+    // then both address neighbours.  Candidates go into the granule table.
     HBA_FOR_THREADS(tid) {
         for (uint32_t j0 = tid; j0 < nf; j0 += NT * U) {
             uint32_t gg[U];
-            Rec r[U];
-HBA_UNROLL
+            Rec r[U], rl[U], rr[U];
+            HBA_UNROLL
             for (int u = 0; u < U; ++u) {
                 const uint32_t j = j0 + u * NT;
                 const uint64_t off = j < nf ? a.frees[j] : FAIL64;
                 gg[u] = (off < S.A && (off & mbm) == 0) ? (uint32_t)(off >> S.lg) : NIL;
             }
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) r[u] = gg[u] != NIL ? ldr(rec, gg[u]) : Rec{0, NIL, 0, 0};
-HBA_UNROLL
+            HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                r[u] = gg[u] != NIL ? ldr(rec, gg[u]) : Rec{0, NIL, 0, 0};
+                if (st_of(r[u].x) != ST_USED) gg[u] = NIL;
+            }
+            HBA_UNROLL
+            for (int u = 0; u < U; ++u) {
+                const uint32_t R = gg[u] != NIL ? gg[u] + sz_of(r[u].x) : S.G;
+                rl[u] = (gg[u] != NIL && r[u].y != NIL) ? ldr(rec, r[u].y) : Rec{0, NIL, NIL, NIL};
+                rr[u] = R < S.G ? ldr(rec, R) : Rec{0, NIL, NIL, NIL};
+            }
+            HBA_UNROLL
             for (int u = 0; u < U; ++u) {
                 const uint32_t j = j0 + u * NT;
-                if (j < nf) {
-                    const bool used = st_of(r[u].x) == ST_USED;
-                    if (used) at_min_u32(&rec[gg[u]].z, j);
-                    fg[j] = used ? gg[u] : NIL;
-                    fsz[j] = used ? sz_of(r[u].x) : 0;
-                    fy[j] = used ? r[u].y : NIL;
-                }
+                if (j >= nf) continue;
+                fgr[j] = gg[u];
+                fsz[j] = sz_of(r[u].x);
+                fy[j] = r[u].y;
+                Lx[j] = rl[u].x;
+                Ly[j] = rl[u].y;
+                Lz[j] = rl[u].z;
+                Lw[j] = rl[u].w;
+                Rx[j] = rr[u].x;
+                Rz[j] = rr[u].z;
+                Rw[j] = rr[u].w;
+                if (gg[u] != NIL) gt_insert_min(T, gg[u], j);
             }
         }
-        if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
     }
     HBA_SYNC();
     HBA_PROF(1);
-    // F2: winners, statuses, per-thread counts over contiguous ranges.
+    // F2: the lowest index naming a block wins; statuses; counters.
     HBA_FOR_THREADS(tid) {
-        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
-        uint32_t c = 0;
-        for (uint32_t j0 = lo; j0 < hi; j0 += U) {
-            uint32_t g[U], cl[U];
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) g[u] = j0 + u < hi ? fg[j0 + u] : NIL;
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) cl[u] = g[u] != NIL ? rec[g[u]].z : NIL;
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                const uint32_t j = j0 + u;
-                if (j < hi) {
-                    const bool win = g[u] != NIL && cl[u] == j;
-                    if (!win) fg[j] = NIL;
-                    if (a.fstat) a.fstat[j] = win ? 0 : 1;
-                    c += win;
-                }
-            }
-        }
-        S.cnt[tid] = c;
-    }
-    HBA_SYNC();
-    scan_excl_u32<NT>(S, S.cnt, &S.W);
-    const uint32_t W = S.W;
-    HBA_PROF(2);
-    // F3: compact in free-index order; mark the freed blocks NEW and map
-    // granule -> compact index.
-    HBA_FOR_THREADS(tid) {
-        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
-        uint32_t w = S.cnt[tid];
         int64_t freed = 0;
-        for (uint32_t j = lo; j < hi; ++j) {
-            const uint32_t g = fg[j];
-            if (g != NIL) {
-                const uint32_t sz = fsz[j];
-                cg[w] = g;
-                csz[w] = sz;
-                cy[w] = fy[j];
-                cj[w] = j;
-                rec[g].x = mkx(sz, ST_NEW);
-                rec[g].z = w;
-                freed += sz;
-                ++w;
-            }
+        uint32_t won = 0;
+        for (uint32_t j = tid; j < nf; j += NT) {
+            const uint32_t g = fgr[j];
+            const bool win = g != NIL && gt_find(T, g) == j;
+            if (!win && g != NIL) fgr[j] = NIL;
+            if (a.fstat) a.fstat[j] = win ? 0 : 1;
+            if (win) { freed += fsz[j]; ++won; }
         }
         warp_sum(S, tid, C_USEDG, -freed);
-        if (tid == 0) {
-            single_add(S, C_FOK, W);
-            single_add(S, C_FFAIL, (int64_t)nf - (int64_t)W);
+        warp_sum(S, tid, C_FOK, won);
+    }
+    HBA_SYNC();
+    HBA_PROF(2);
+    // F3: pred = the freed block to my left inside the same run (directly
+    // adjacent, or across exactly one old free block); an old free block
+    // absorbed by a run is unlinked by the freed block to its right, or by
+    // the one to its left when it ends the run.
+    HBA_FOR_THREADS(tid) {
+        for (uint32_t j = tid; j < nf; j += NT) {
+            const uint32_t g = fgr[j];
+            runAt[j] = NIL;
+            if (g == NIL) {
+                root[j] = j;
+                rmaxj[j] = 0;
+                rend[j] = 0;
+                continue;
+            }
+            const uint32_t L = fy[j];
+            uint32_t pr = NIL, head = g, flags = 0;
+            if (L != NIL) {
+                const uint32_t wl = gt_find(T, L);
+                if (wl != NIL) {
+                    pr = wl;
+                } else if (st_of(Lx[j]) == ST_FREE) {
+                    ul[at_add_u32(&S.nul, 1)] = L;
+                    const uint32_t wll = Ly[j] != NIL ? gt_find(T, Ly[j]) : NIL;
+                    if (wll != NIL) {
+                        pr = wll;
+                        flags |= 1;   // L is inside the run: erase its record
+                    } else {
+                        head = L;     // L starts the run
+                    }
+                }
+            }
+            uint32_t end = g + fsz[j];
+            if (st_of(Rx[j]) == ST_FREE) {
+                const uint32_t R = end;
+                end = R + sz_of(Rx[j]);
+                if (end >= S.G || gt_find(T, end) == NIL) {
+                    ul[at_add_u32(&S.nul, 1)] = R;
+                    flags |= 2;       // R ends the run: erase its record
+                }
+            }
+            root[j] = pr == NIL ? j : pr;
+            rmaxj[j] = j;
+            rend[j] = end;
+            lh[j] = head;
+            fl[j] = flags;
         }
     }
     HBA_SYNC();
     HBA_PROF(3);
-    // F4: neighbours.  pred = the freed block to my left inside the same run
-    // (directly adjacent, or across exactly one old free block); an old free
-    // block absorbed by a run is unlinked by the freed block to its right, or
-    // by the one to its left when it ends the run.
-    HBA_FOR_THREADS(tid) {
-        for (uint32_t j = tid; j < nf; j += NT) runAt[j] = NIL;
-        for (uint32_t w0 = tid; w0 < W; w0 += NT * U) {
-            uint32_t g[U], sz[U], L[U], rx[U], LL[U], E2[U], rrx[U];
-            Rec rl[U], rll[U];
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                const uint32_t w = w0 + u * NT;
-                const bool ok = w < W;
-                g[u] = ok ? cg[w] : 0;
-                sz[u] = ok ? csz[w] : 0;
-                L[u] = ok ? cy[w] : NIL;
-            }
-            // round 1: both neighbours
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                const uint32_t w = w0 + u * NT;
-                rl[u] = L[u] != NIL ? ldr(rec, L[u]) : Rec{0, NIL, 0, 0};
-                rx[u] = (w < W && g[u] + sz[u] < S.G) ? rec[g[u] + sz[u]].x : 0u;
-            }
-            // round 2: across an old free neighbour
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                LL[u] = st_of(rl[u].x) == ST_FREE ? rl[u].y : NIL;
-                E2[u] = st_of(rx[u]) == ST_FREE ? g[u] + sz[u] + sz_of(rx[u]) : S.G;
-                rll[u] = LL[u] != NIL ? ldr(rec, LL[u]) : Rec{0, 0, 0, 0};
-                rrx[u] = E2[u] < S.G ? rec[E2[u]].x : 0u;
-            }
-HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                const uint32_t w = w0 + u * NT;
-                if (w >= W) continue;
-                uint32_t end = g[u] + sz[u];
-                uint32_t pr = NIL, head = g[u], flags = 0;
-                const uint32_t lst = st_of(rl[u].x);
-                if (lst == ST_NEW) {
-                    pr = rl[u].z;
-                } else if (lst == ST_FREE) {
-                    ul[at_add_u32(&S.nul, 1)] = L[u];
-                    if (st_of(rll[u].x) == ST_NEW) {
-                        pr = rll[u].z;
-                        flags |= 1;   // L is inside the run: erase its record
-                    } else {
-                        head = L[u];  // L starts the run
-                    }
-                }
-                if (st_of(rx[u]) == ST_FREE) {
-                    const uint32_t R = end;
-                    end = E2[u];
-                    if (st_of(rrx[u]) != ST_NEW) {
-                        ul[at_add_u32(&S.nul, 1)] = R;
-                        flags |= 2;   // R ends the run: erase its record
-                    }
-                }
-                root[w] = pr == NIL ? w : pr;
-                lh[w] = head;
-                rend[w] = end;
-                rmaxj[w] = cj[w];
-                fl[w] = flags;
-            }
-        }
-    }
-    HBA_SYNC();
-    HBA_PROF(4);
-    // F5: pointer jumping to the run's leftmost freed block.
+    // F4: pointer jumping to the run's leftmost freed block.
     for (int it = 0;; ++it) {
         HBA_FOR_THREADS(tid) {
             bool ch = false;
-            for (uint32_t w = tid; w < W; w += NT) {
-                const uint32_t r = root[w];
+            for (uint32_t j = tid; j < nf; j += NT) {
+                const uint32_t r = root[j];
                 const uint32_t rr = root[r];
-                if (rr != r) { root[w] = rr; ch = true; }
+                if (rr != r) { root[j] = rr; ch = true; }
             }
             if (ch) S.flag[it % 3] = 1;
             if (tid == 0) S.flag[(it + 1) % 3] = 0;
@@ -538,14 +552,14 @@ HBA_UNROLL
         HBA_SYNC();
         if (!S.flag[it % 3]) break;
     }
-    HBA_PROF(5);
-    // F6: per-run right end and last free index; mark absorbed blocks.
+    HBA_PROF(4);
+    // F5: per-run right end and last free index; mark absorbed blocks.
     HBA_FOR_THREADS(tid) {
-        for (uint32_t w = tid; w < W; w += NT) {
-            const uint32_t r = root[w];
-            if (r != w) {
-                at_max_u32(&rmaxj[r], cj[w]);
-                at_max_u32(&rend[r], rend[w]);
+        for (uint32_t j = tid; j < nf; j += NT) {
+            const uint32_t r = root[j];
+            if (r != j) {
+                at_max_u32(&rmaxj[r], rmaxj[j]);
+                at_max_u32(&rend[r], rend[j]);
             }
         }
         for (uint32_t i = tid; i < S.nul; i += NT) {
@@ -554,8 +568,8 @@ HBA_UNROLL
         }
     }
     HBA_SYNC();
-    HBA_PROF(6);
-    // F7: unlink maximal segments of absorbed blocks from their lists.
+    HBA_PROF(5);
+    // F6: unlink maximal segments of absorbed blocks from their lists.
     HBA_FOR_THREADS(tid) {
         for (uint32_t i = tid; i < S.nul; i += NT) {
             const uint32_t u = ul[i];
@@ -574,19 +588,21 @@ HBA_UNROLL
         }
     }
     HBA_SYNC();
-    HBA_PROF(7);
-    // F8: write the merged blocks, erase absorbed records.
+    HBA_PROF(6);
+    // F7: write the merged blocks, erase absorbed records.
     HBA_FOR_THREADS(tid) {
         uint32_t nr = 0;
-        for (uint32_t w = tid; w < W; w += NT) {
-            const uint32_t g = cg[w], sz = csz[w], f = fl[w];
-            if (f & 1) rec[cy[w]].x = 0;
-            if (f & 2) rec[g + sz].x = 0;
-            if (root[w] == w) {
-                const uint32_t H = lh[w], end = rend[w];
+        for (uint32_t j = tid; j < nf; j += NT) {
+            const uint32_t g = fgr[j];
+            if (g == NIL) continue;
+            const uint32_t f = fl[j];
+            if (f & 1) rec[fy[j]].x = 0;
+            if (f & 2) rec[g + fsz[j]].x = 0;
+            if (root[j] == j) {
+                const uint32_t H = lh[j], end = rend[j];
                 rec[H].x = mkx(end - H, ST_FREE);
                 if (end < S.G) rec[end].y = H;
-                runAt[rmaxj[w]] = w;
+                runAt[rmaxj[j]] = j;
                 ++nr;
                 if (H != g) rec[g].x = 0;
             } else {
@@ -596,8 +612,9 @@ HBA_UNROLL
         if (nr) at_add_u32(&S.nruns, nr);
     }
     HBA_SYNC();
-    HBA_PROF(8);
-    // F9: run leaders in increasing order of their last free index.
+    HBA_PROF(7);
+    // F8: run leaders in increasing order of their last free index.
+    const uint32_t per = (nf + NT - 1) / NT;
     HBA_FOR_THREADS(tid) {
         const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
         uint32_t c = 0;
@@ -614,33 +631,33 @@ HBA_UNROLL
             if (runAt[j] != NIL) runs[k++] = runAt[j];
     }
     HBA_SYNC();
-    HBA_PROF(9);
-    // F10a: the merged blocks are pushed in run order.  Split that order into
+    HBA_PROF(8);
+    // F9a: the merged blocks are pushed in run order.  Split that order into
     // NSEG segments; inside each, link consecutive runs of the same class.
     constexpr int NSEG = Smem<NT>::NSEG;
     HBA_FOR_THREADS(tid) {
         if (tid < NSEG) {
             uint32_t* F = S.u.seg.f[tid];
-            uint32_t* Lw = S.u.seg.l[tid];
-            for (int b = 0; b < NBINS; ++b) F[b] = Lw[b] = NIL;
+            uint32_t* Lt = S.u.seg.l[tid];
+            for (int b = 0; b < NBINS; ++b) F[b] = Lt[b] = NIL;
             const uint32_t ps = (nruns + NSEG - 1) / NSEG;
             const uint32_t lo = tid * ps, hi = lo + ps < nruns ? lo + ps : nruns;
             for (uint32_t k = lo; k < hi; ++k) {
-                const uint32_t w = runs[k];
-                const uint32_t H = lh[w];
-                const uint32_t b = flog2(rend[w] - H);
-                if (Lw[b] == NIL) {
+                const uint32_t j = runs[k];
+                const uint32_t H = lh[j];
+                const uint32_t b = flog2(rend[j] - H);
+                if (Lt[b] == NIL) {
                     F[b] = H;
                 } else {
-                    rec[H].z = Lw[b];
-                    rec[Lw[b]].w = H;
+                    rec[H].z = Lt[b];
+                    rec[Lt[b]].w = H;
                 }
-                Lw[b] = H;
+                Lt[b] = H;
             }
         }
     }
     HBA_SYNC();
-    // F10b: per class, stitch the segments in order on top of the old list.
+    // F9b: per class, stitch the segments in order on top of the old list.
     HBA_FOR_THREADS(tid) {
         for (int b = tid; b < NBINS; b += NT) {
             uint32_t below = S.heads[b];
@@ -666,11 +683,15 @@ HBA_UNROLL
             for (int b = 0; b < NBINS; ++b)
                 if (S.heads[b] != NIL) m |= 1ull << b;
             S.mask = m;
-            single_add(S, C_BLOCKS, (int64_t)nruns - (int64_t)W - (int64_t)S.nul);
+            // applied frees = runs' new members; blocks: every run becomes one
+            int64_t fok = 0;
+            for (int w = 0; w <= Smem<NT>::NW; ++w) fok += S.wc[w][C_FOK];
+            single_add(S, C_FFAIL, (int64_t)nf - fok);
+            single_add(S, C_BLOCKS, (int64_t)nruns - fok - (int64_t)S.nul);
         }
     }
     HBA_SYNC();
-    HBA_PROF(10);
+    HBA_PROF(9);
 }
 
 // ---------------------------------------------------------------------------
