@@ -26,6 +26,7 @@ struct hba_s {
     Arena* d_arenas = nullptr;
     Rec* d_rec = nullptr;
     uint32_t* d_scr = nullptr;
+    uint32_t* d_gi = nullptr;   // gathered records of a batch's frees (5 words each)
     uint64_t scr_frees = 0;     // scratch capacity in frees
     uint32_t max_batch = 0;     // single arena: frees per launch slice
     std::vector<Arena> h_init;  // initial headers (for reset)
@@ -61,11 +62,13 @@ constexpr uint32_t MULTI_DYN_BYTES_DEFAULT = 24 * 1024;
 template <int NT>
 __global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
                                                uint8_t* st, const uint64_t* sizes, uint32_t na,
-                                               uint64_t* out, uint32_t* scr, uint32_t dyn_words,
-                                               uint32_t prefilled) {
+                                               uint64_t* out, uint32_t* scr, const uint32_t* gi,
+                                               uint32_t dyn_words, uint32_t prefilled) {
     __shared__ hba::Smem<NT> S;
-    extern __shared__ uint32_t dyn[];
-    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, prefilled};
+    extern __shared__ __align__(16) uint32_t dyn[];
+    // the preceding prep grid (gathered records, pre-filled failures)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled};
     hba::arena_step<NT>(S, a, dyn, dyn_words);
 }
 
@@ -73,9 +76,11 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint32_t* frow,
                                               const uint64_t* frees, uint8_t* st, const uint32_t* arow,
                                               const uint64_t* sizes, uint64_t* out, uint32_t* scr,
-                                              uint32_t n_arenas, uint32_t dyn_words, uint32_t prefilled) {
+                                              const uint32_t* gi, uint32_t nf_total, uint32_t n_arenas,
+                                              uint32_t dyn_words, uint32_t prefilled) {
     __shared__ hba::Smem<NT> S;
-    extern __shared__ uint32_t dyn[];
+    extern __shared__ __align__(16) uint32_t dyn[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
         const uint32_t f0 = frow[a], f1 = frow[a + 1], a0 = arow[a], a1 = arow[a + 1];
         Arena* ar = ars + a;
@@ -88,6 +93,8 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            a1 - a0,
                            out + a0,
                            scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE,
+                           gi + f0,
+                           nf_total,
                            prefilled};
         hba::arena_step<NT>(S, args, dyn, dyn_words);
     }
@@ -95,7 +102,8 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
 
 // Largest dynamic shared memory a CTA of k_single<NT> / k_multi<NT> can get.
 struct SmemLimits {
-    uint32_t single_dyn = 0, multi_dyn = 0;
+    uint32_t single_dyn = 0, multi_dyn = 0;  // bytes
+    uint32_t alloc_words = 0;                 // minimum dynamic words (alloc phase)
 };
 
 template <int NT>
@@ -104,6 +112,7 @@ SmemLimits set_smem_limits() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     SmemLimits L;
+    L.alloc_words = hba::alloc_dyn_words<NT>();
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_single<NT>) == cudaSuccess) {
         L.single_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
@@ -127,31 +136,49 @@ int limit_index(uint32_t threads) {
     }
 }
 
-// Pre-fill out[0..n) with HBA_FAIL on many SMs; the allocator kernel that
-// follows (programmatic dependent launch) then stores only successes.
-__global__ void k_fill_fail(uint64_t* out, uint32_t n) {
+// The prep grid of a batch, on many SMs: gathers the records every free
+// needs (hba::gather_free, one thread per free; one SM alone could keep too
+// few random loads in flight) and pre-fills out[0..na) with HBA_FAIL, so that
+// the allocator kernel that follows (programmatic dependent launch) stores
+// only successes.  frow (multi-arena) maps a free to its arena.
+__global__ void k_prep(const Arena* ars, const Rec* pool, const uint32_t* frow, uint32_t n_arenas,
+                       const uint64_t* frees, uint32_t nf, uint32_t* gi, uint64_t* out, uint32_t na) {
     asm volatile("griddepcontrol.launch_dependents;");
-    uint32_t lo = 0;
-    if (((uintptr_t)out & 15) && n) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = hba::FAIL64;
-        lo = 1;
+    const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (uint32_t j = t0; j < nf; j += nth) {
+        uint32_t a = 0;
+        if (frow) {  // last arena whose first free is <= j
+            uint32_t lo = 0, hi = n_arenas;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) / 2;
+                if (frow[mid] <= j) lo = mid;
+                else hi = mid;
+            }
+            a = lo;
+        }
+        const Arena& ar = ars[a];
+        hba::gather_free(pool + ar.rec_base, ar.arena_bytes, ar.G, ar.lg, frees[j], gi, nf, j);
     }
-    ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + lo);
-    const uint32_t npair = (n - lo) / 2;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < npair; q += gridDim.x * blockDim.x)
-        o2[q] = make_ulonglong2(hba::FAIL64, hba::FAIL64);
-    if (((n - lo) & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[n - 1] = hba::FAIL64;
+    if (out && na) {
+        uint32_t lo = 0;
+        if ((uintptr_t)out & 15) {
+            if (t0 == 0) out[0] = hba::FAIL64;
+            lo = 1;
+        }
+        ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + lo);
+        const uint32_t npair = (na - lo) / 2;
+        for (uint32_t q = t0; q < npair; q += nth) o2[q] = make_ulonglong2(hba::FAIL64, hba::FAIL64);
+        if (((na - lo) & 1) && t0 == 0) out[na - 1] = hba::FAIL64;
+    }
 }
 
 // Allocation batches at least this large get their failures pre-filled.
 constexpr uint32_t PREFILL_MIN = 2048;
 
-bool prefill(uint64_t* out, uint32_t n, cudaStream_t s) {
-    if (n < PREFILL_MIN) return false;
-    const uint32_t blocks = std::min<uint32_t>((n / 2 + 255) / 256, 1024);
-    k_fill_fail<<<blocks, 256, 0, s>>>(out, n);
-    return true;
-}
+// Launch the prep grid if the batch needs one; returns whether out[] is
+// pre-filled.  *pdl is set when the next launch may depend on it.
+bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint64_t* out, uint32_t na,
+                 cudaStream_t s, bool* pdl);
 
 // Launch with a programmatic dependency on the preceding kernel of the stream.
 template <typename... KArgs, typename... Args>
@@ -200,31 +227,50 @@ __global__ void k_largest(const Arena* ars, const Rec* pool, uint32_t n_arenas, 
     out[a] = best << ar.lg;
 }
 
+bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint64_t* out, uint32_t na,
+                 cudaStream_t s, bool* pdl) {
+    const bool fill = na >= PREFILL_MIN;
+    *pdl = false;
+    if (!nf && !fill) return false;
+    const uint32_t work = std::max(nf, fill ? na / 2 : 0u);
+    const uint32_t blocks = std::max(1u, std::min<uint32_t>((work + 127) / 128, 2048));
+    k_prep<<<blocks, 128, 0, s>>>(h->d_arenas, h->d_rec, frow, h->n_arenas, frees, nf, h->d_gi,
+                                  fill ? out : nullptr, fill ? na : 0);
+    *pdl = true;
+    return fill;
+}
+
 hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
                            const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
-    const uint32_t maxdyn = g_limits[limit_index(h->threads)].single_dyn;
+    const int li = limit_index(h->threads);
+    const uint32_t maxdyn = g_limits[li].single_dyn;
+    const uint32_t base = 4 * g_limits[li].alloc_words;
     uint32_t dyn;
     if (h->smem_bytes) {
-        dyn = std::min(h->smem_bytes, maxdyn) & ~15u;
+        dyn = std::max(base, std::min(h->smem_bytes, maxdyn));
     } else {
-        // just what this batch's free phase keeps in shared memory, so that
-        // L1 keeps the rest
-        const uint64_t hot = 4ull * hba::free_hot_words(std::min(nf, h->max_batch));
-        dyn = hot <= maxdyn ? (uint32_t)((hot + 15u) & ~15ull) : 0u;
+        // what this batch's free phase keeps in shared memory (if it fits),
+        // so that L1 keeps the rest
+        const uint64_t hot = 4ull * hba::free_hot_words(nf);
+        dyn = hot <= maxdyn ? (uint32_t)std::max<uint64_t>(hot, base) : base;
     }
+    dyn = (dyn + 15u) & ~15u;
     const uint32_t dw = dyn / 4;
-    const bool pre = na && prefill(out, na, s);
+    bool pdl = false;
+    const bool pre = launch_prep(h, nullptr, frees, nf, out, na, s, &pdl);
+    if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     const uint32_t pf = pre ? 1u : 0u;
-    cudaError_t e;
+    const uint32_t* gi = h->d_gi;
     uint32_t* scr = h->d_scr;
+    cudaError_t e;
     switch (h->threads) {
-        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
-        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
-        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
-        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
-        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pre, ar, rec, frees, nf, st, sizes, na, out, scr, dw, pf); break;
+        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
+        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
+        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
+        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
+        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
     }
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     return HBA_OK;
@@ -262,6 +308,8 @@ hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_fr
     h->scr_frees = scr_frees;
     if (cudaMalloc(&h->d_scr, 4ull * hba::SCRATCH_WORDS_PER_FREE * std::max<uint64_t>(scr_frees, 1)) != cudaSuccess)
         return HBA_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc(&h->d_gi, 4ull * hba::GATHER_WORDS * std::max<uint64_t>(scr_frees, 1)) != cudaSuccess)
+        return HBA_ERR_OUT_OF_MEMORY;
     if (cudaMalloc(&h->d_largest, sizeof(uint64_t) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
     if (stage) {
         if (cudaMalloc(&h->d_stage_f, 8ull * stage) != cudaSuccess ||
@@ -286,6 +334,7 @@ void free_all(hba_t h) {
     cudaFree(h->d_arenas);
     cudaFree(h->d_rec);
     cudaFree(h->d_scr);
+    cudaFree(h->d_gi);
     cudaFree(h->d_largest);
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_s);
@@ -475,21 +524,26 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = h->n_arenas;
     const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
-    const uint32_t dyn = std::min(h->smem_bytes ? h->smem_bytes : MULTI_DYN_BYTES_DEFAULT,
-                                  g_limits[limit_index(h->m_threads)].multi_dyn) & ~15u;
+    const int li = limit_index(h->m_threads);
+    const uint32_t base = 4 * g_limits[li].alloc_words;
+    uint32_t dyn = std::min(h->smem_bytes ? h->smem_bytes : MULTI_DYN_BYTES_DEFAULT, g_limits[li].multi_dyn);
+    dyn = (std::max(dyn, base) + 15u) & ~15u;
     const uint32_t dw = dyn / 4;
-    const bool pre = na_total && prefill(d_out, na_total, s);
+    bool pdl = false;
+    const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, d_out, na_total, s, &pdl);
+    if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     const uint32_t pf = pre ? 1u : 0u;
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
     uint32_t* scr = h->d_scr;
+    const uint32_t* gi = h->d_gi;
     cudaError_t e;
     switch (h->m_threads) {
-        case 64: e = launch_pdl(k_multi<64>, grid, 64, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
-        case 128: e = launch_pdl(k_multi<128>, grid, 128, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
-        case 512: e = launch_pdl(k_multi<512>, grid, 512, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
-        case 1024: e = launch_pdl(k_multi<1024>, grid, 1024, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
-        default: e = launch_pdl(k_multi<256>, grid, 256, dyn, s, pre, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, n, dw, pf); break;
+        case 64: e = launch_pdl(k_multi<64>, grid, 64, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
+        case 128: e = launch_pdl(k_multi<128>, grid, 128, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
+        case 512: e = launch_pdl(k_multi<512>, grid, 512, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
+        case 1024: e = launch_pdl(k_multi<1024>, grid, 1024, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
+        default: e = launch_pdl(k_multi<256>, grid, 256, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
     }
     if (e != cudaSuccess) return HBA_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;

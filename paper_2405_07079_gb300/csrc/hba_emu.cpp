@@ -10,6 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "hba_engine.cuh"
@@ -30,11 +31,16 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
          uint32_t na, uint64_t* out) {
     Smem<NT>* S = new Smem<NT>();
     if (e->scr.size() < (size_t)SCRATCH_WORDS_PER_FREE * nf) e->scr.resize((size_t)SCRATCH_WORDS_PER_FREE * nf);
-    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), 0};
-    // a small "shared memory" area, so that both the shared-memory and the
-    // global-scratch variants of the free phase run
-    std::vector<uint32_t> dyn(e->dyn_words + 1);
-    arena_step<NT>(*S, a, dyn.data(), e->dyn_words);
+    // the gather that a separate grid does on the GPU
+    std::vector<uint32_t> gi((size_t)GATHER_WORDS * nf + 1);
+    for (uint32_t j = 0; j < nf; ++j)
+        gather_free(e->rec.data(), e->ar.arena_bytes, e->ar.G, e->ar.lg, frees[j], gi.data(), nf, j);
+    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0};
+    // "shared memory": at least what the alloc phase needs, plus a test knob so
+    // that both placements of the free-phase arrays run
+    const uint32_t words = std::max(alloc_dyn_words<NT>(), e->dyn_words);
+    std::vector<uint64_t> dyn(words / 2 + 1);
+    arena_step<NT>(*S, a, reinterpret_cast<uint32_t*>(dyn.data()), words);
     delete S;
 }
 }  // namespace

@@ -42,6 +42,10 @@
 //   when another remainder replaces it or the phase ends -- the
 //   intermediate push/pop pairs of the sequential algorithm cancel out.
 //
+// Record reads for the frees are gathered before the engine runs, on many
+// SMs (gather_free, one thread per free): one SM alone can keep only so many
+// random loads in flight.
+//
 // The same source compiles for the GPU and, with HBA_EMULATE, for a
 // host-only emulation used by the test suite: each HBA_FOR_THREADS body is a
 // phase run by every thread, HBA_SYNC is the barrier between phases.  Inside
@@ -87,7 +91,11 @@ constexpr uint32_t MAX_GRANULES = SZ_MASK;  // G <= 2^29 - 1
 constexpr uint32_t ST_NONE = 0, ST_USED = 1, ST_FREE = 2, ST_NEW = 3, ST_DEL = 4;
 constexpr uint64_t FAIL64 = ~0ull;
 constexpr int NBINS = 32;  // granule classes 0..28 are reachable
-constexpr uint32_t SCRATCH_WORDS_PER_FREE = 28;
+// global scratch per free: the gathered records (5 words), per-run data,
+// absorbed blocks (2), runs, and the granule table / pointer-jumping arrays
+// when they do not fit in shared memory
+constexpr uint32_t SCRATCH_WORDS_PER_FREE = 24;
+constexpr uint32_t GATHER_WORDS = 5;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
 constexpr uint32_t ERR_EMPTY_HEAD = 2;  // a class with its bit set had no head
@@ -159,6 +167,48 @@ HBA_DEV void at_add_i64(int64_t* p, int64_t v) {
 }
 #endif
 
+// ---- gathering the records a free needs (one thread per free) ------------
+// For a free of byte offset `off`: the block it names (if it is the start of
+// an in-use block), and the two address neighbours' facts that coalescing
+// needs.  Written as five words per free (structure of arrays, stride n):
+//   g     the block's first granule, NIL if the free is not valid
+//   szf   its size in granules | Lfree << 29 | Rfree << 30
+//   L     its left neighbour (prev_adj), NIL at offset 0
+//   LL    the left neighbour's own left neighbour when the left one is free
+//   Rend  end of the right neighbour when that one is free, else end of the block
+constexpr uint32_t F_LFREE = 1u << 29, F_RFREE = 1u << 30;
+HBA_HD void gather_free(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, uint64_t off, uint32_t* gi,
+                        uint32_t n, uint32_t j) {
+    uint32_t g = NIL, szf = 0, L = NIL, LL = NIL, Rend = 0;
+    if (off < A && (off & ((1ull << lg) - 1ull)) == 0) {
+        const uint32_t gg = (uint32_t)(off >> lg);
+        const Rec r = rec[gg];
+        if (st_of(r.x) == ST_USED) {
+            g = gg;
+            const uint32_t sz = sz_of(r.x);
+            szf = sz;
+            L = r.y;
+            Rend = gg + sz;
+            // both neighbours are independent loads
+            const Rec rl = L != NIL ? rec[L] : Rec{0, NIL, 0, 0};
+            const uint32_t rx = Rend < G ? rec[Rend].x : 0u;
+            if (st_of(rl.x) == ST_FREE) {
+                szf |= F_LFREE;
+                LL = rl.y;
+            }
+            if (st_of(rx) == ST_FREE) {
+                szf |= F_RFREE;
+                Rend += sz_of(rx);
+            }
+        }
+    }
+    gi[j] = g;
+    gi[n + j] = szf;
+    gi[2 * n + j] = L;
+    gi[3 * n + j] = LL;
+    gi[4 * n + j] = Rend;
+}
+
 // ---- shared state of one CTA --------------------------------------------
 enum : uint8_t { CL_NONE = 0, CL_FAIL = 1, CL_CARVE = 2, CL_OTHER = 3 };
 // counter slots (per warp, plus one row for single-thread updates)
@@ -172,34 +222,32 @@ struct Smem {
     uint64_t mask;       // bitmap of classes whose list is non-empty (X excluded)
     uint32_t heads[NBINS];
     uint32_t G, lg;
-    // the most recent remainder X, virtual head of class xL while xok; its
-    // prev_adj is kept in rec[xg].y at all times
-    uint32_t xok, xg, xsz, xright, xL;
-    uint32_t c0g, c0sz;  // X's start and size when the current chunk was classified
-    uint32_t r, cont;    // first unresolved lane of the chunk; 1 = chunk continues
-    uint32_t evb[2];     // first event lane, double-buffered per round
+    // the most recent remainder X: virtual head of class xL while xok
+    uint32_t xok, xg, xsz, xright, xL, xprev;
+    uint32_t c0g, c0sz, c0prev;  // X when the current round classified its lanes
     // loop control
-    uint32_t p, ev, W, nul, nruns, flag[3];
+    uint32_t p, r, cont, evb[2], nul, nruns, flag[3];
     uint32_t err;        // first metadata error seen by this CTA (0 = none)
-    uint32_t* dyn;       // dynamic shared memory (free-phase scratch)
+    uint32_t* dyn;       // dynamic shared memory
     uint32_t dyn_words;
+    // alloc-phase arrays (carved from dyn)
+    int64_t* val;        // carve sizes, then their inclusive prefix
+    uint64_t* s64;       // request sizes of the chunk
+    uint32_t* cst;       // start granule of each carve lane
+    uint32_t* sgr;       // rounded sizes in granules (0: invalid request)
+    uint8_t* cls;        // class of each lane in the current round
+    uint8_t* ccl;        // size class c of each lane
     int64_t wc[NW + 1][NCNT];
     int64_t warp_tot[32];
-    union {
-        struct {
-            int64_t val[NT];   // carve sizes, then their inclusive prefix
-            uint64_t s64[NT];  // request sizes of the chunk
-        } a;
-        struct {
-            uint32_t f[NSEG][NBINS];  // oldest run of each class per segment
-            uint32_t l[NSEG][NBINS];  // newest run of each class per segment
-        } seg;
-    } u;
+    uint32_t wlast[32];  // start of the highest carve lane of each warp
+    uint32_t segf[NSEG][NBINS];  // oldest run of each class per push segment
+    uint32_t segl[NSEG][NBINS];  // newest run of each class per push segment
     uint32_t cnt[NT];
-    uint32_t sgr[NT];    // rounded sizes in granules
-    uint8_t cls[NT];     // speculative class of each lane
-    uint8_t ccl[NT];     // size class c of each lane
 };
+
+// words of dynamic shared memory the alloc phase carves for NT lanes
+template <int NT>
+HBA_HD uint32_t alloc_dyn_words() { return 2 * NT + 2 * NT + NT + NT + NT / 4 + NT / 4 + 8; }
 
 // ---- warp-aggregated counters and votes (call convergently) --------------
 template <int NT>
@@ -221,16 +269,6 @@ HBA_DEV void warp_sum(Smem<NT>& S, int tid, int k, int64_t v) {
     if ((tid & 31) == 0) S.wc[tid >> 5][k] += v;
 #endif
 }
-// S.ev = min(S.ev, first lane with e)
-template <int NT>
-HBA_DEV void warp_first_min(Smem<NT>& S, int tid, bool e) {
-#ifdef HBA_EMULATE
-    if (e && (uint32_t)tid < S.ev) S.ev = (uint32_t)tid;
-#else
-    const unsigned b = __ballot_sync(0xffffffffu, e);
-    if ((tid & 31) == 0 && b) atomicMin(&S.ev, (uint32_t)(tid + __ffs(b) - 1));
-#endif
-}
 // single-thread counter update (its own row: never races with warp_*)
 template <int NT>
 HBA_DEV void single_add(Smem<NT>& S, int k, int64_t v) { S.wc[Smem<NT>::NW][k] += v; }
@@ -244,14 +282,18 @@ HBA_DEV void prefetch_l2(const void* p) {
 }
 
 // ---- block-wide collectives (called by all threads, outside phases) ------
-// Inclusive prefix sum of v[0..NT) in place.  On return each thread has
-// written its own v[tid]; a barrier is needed before reading other lanes.
+// Inclusive prefix sum over the lanes: thread tid passes x and gets its
+// inclusive prefix back (also stored in v[tid]).  One barrier inside; on
+// return only the caller's own v[tid] may be read without another barrier.
 template <int NT>
-HBA_DEV void scan_incl_i64(Smem<NT>& S, int64_t* v) {
+HBA_DEV int64_t scan_incl_i64(Smem<NT>& S, int64_t* v, int tid_emu = 0) {
 #ifdef HBA_EMULATE
     for (int i = 1; i < NT; ++i) v[i] += v[i - 1];
     (void)S;
+    (void)tid_emu;
+    return 0;
 #else
+    (void)tid_emu;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int64_t x = v[tid];
 #pragma unroll
@@ -271,6 +313,7 @@ HBA_DEV void scan_incl_i64(Smem<NT>& S, int64_t* v) {
     const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
     if (wid > 0) x += before;
     v[tid] = x;
+    return x;
 #endif
 }
 
@@ -314,7 +357,7 @@ HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
 
 struct StepArgs {
     Arena* ar;
-    Rec* rec;  // the arena's records (already offset by rec_base)
+    Rec* rec;        // the arena's records (already offset by rec_base)
     const uint64_t* frees;
     uint32_t nf;
     uint8_t* fstat;  // may be null
@@ -322,18 +365,18 @@ struct StepArgs {
     uint32_t na;
     uint64_t* out;
     uint32_t* scr;   // SCRATCH_WORDS_PER_FREE * nf words of global scratch
+    const uint32_t* gi;  // gathered records of the frees (5 arrays of stride gstride)
+    uint32_t gstride;
     uint32_t prefilled;  // out[] already holds HBA_FAIL everywhere (written by a
                          // preceding grid): failures need no store
 };
 
 // Push the virtual remainder X at the head of its list and write its record
-// (one thread).  rec[xg].y already holds X's prev_adj and is left alone.
+// (one thread).
 template <int NT>
 HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec) {
     const uint32_t b = S.xL, old = S.heads[b];
-    rec[S.xg].x = mkx(S.xsz, ST_FREE);
-    rec[S.xg].z = old;
-    rec[S.xg].w = NIL;
+    str(rec, S.xg, Rec{mkx(S.xsz, ST_FREE), S.xprev, old, NIL});
     if (old != NIL) rec[old].w = S.xg;
     S.heads[b] = S.xg;
     S.mask |= 1ull << b;
@@ -345,8 +388,8 @@ HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec) {
 // The free phase (Algorithm 5 for all frees of the batch).
 // ---------------------------------------------------------------------------
 
-// Open-addressing table in (shared) memory: granule -> lowest free index
-// that names it.  Only in-use block starts are inserted.
+// Open-addressing table: granule -> lowest free index that names it.  Only
+// valid frees (starts of in-use blocks) are inserted.
 struct GTable {
     uint32_t* key;
     uint32_t* val;
@@ -364,7 +407,7 @@ HBA_DEV void gt_insert_min(const GTable& t, uint32_t g, uint32_t j) {
         s = (s + 1) & t.mask;
     }
 }
-// Lowest free index naming granule g, or NIL when g was not freed.
+// Lowest free index naming granule g, or NIL when g was not validly freed.
 HBA_DEV uint32_t gt_find(const GTable& t, uint32_t g) {
     uint32_t s = gt_hash(g, t.mask);
     while (true) {
@@ -374,50 +417,40 @@ HBA_DEV uint32_t gt_find(const GTable& t, uint32_t g) {
         s = (s + 1) & t.mask;
     }
 }
-
 // Capacity of the granule table for nf frees, and the words of the free
-// phase's hot arrays (table, roots, per-run maxima) that go to shared memory
-// when they fit.
+// phase's hot arrays (table, roots, per-run maxima, run slots) that go to
+// shared memory when they fit.
 HBA_HD uint32_t gt_capacity(uint32_t nf) {
     uint32_t c = 2;
     while (c < 2 * nf) c <<= 1;
     return c;
 }
-HBA_HD uint32_t free_hot_words(uint32_t nf) { return 2 * gt_capacity(nf) + 3 * nf; }
+HBA_HD uint32_t free_hot_words(uint32_t nf) { return 2 * gt_capacity(nf) + 4 * nf; }
+
+constexpr uint32_t FL_WIN = 4;  // flag: this free is applied
 
 template <int NT>
 HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t nf = a.nf;
     Rec* rec = a.rec;
-    // Everything is indexed by free index j; a rejected free has g[j] = NIL.
-    // Global scratch (28 words per free): the records read up front, the
-    // per-run results, the lists of absorbed blocks and runs; the hot arrays
-    // (granule table, pointer-jumping roots, per-run maxima) go to shared
-    // memory when they fit.
+    const uint32_t gs = a.gstride;
+    const uint32_t* gG = a.gi;          // gathered: block granule or NIL
+    const uint32_t* gSZ = a.gi + gs;    //   size | neighbour flags
+    const uint32_t* gL = a.gi + 2 * gs; //   left neighbour
+    const uint32_t* gLL = a.gi + 3 * gs;
+    const uint32_t* gRE = a.gi + 4 * gs;
     const uint32_t hcap = gt_capacity(nf);
     uint32_t* sc = a.scr;
-    uint32_t* fgr = sc;                 // granule of the freed block, NIL if rejected
-    uint32_t* fsz = sc + nf;            // its size
-    uint32_t* fy = sc + 2 * nf;         // its prev_adj (L)
-    uint32_t* Lx = sc + 3 * nf;         // record of L (x, y, z, w)
-    uint32_t* Ly = sc + 4 * nf;
-    uint32_t* Lz = sc + 5 * nf;
-    uint32_t* Lw = sc + 6 * nf;
-    uint32_t* Rx = sc + 7 * nf;         // record of R = g + size (x, z, w)
-    uint32_t* Rz = sc + 8 * nf;
-    uint32_t* Rw = sc + 9 * nf;
-    uint32_t* lh = sc + 10 * nf;        // leftmost block of the run's left part
-    uint32_t* fl = sc + 11 * nf;        // bit0: erase L's record, bit1: erase R's record
-    uint32_t* runAt = sc + 12 * nf;     // run leader whose last free is j, or NIL
-    uint32_t* runs = sc + 13 * nf;      // run leaders in order of their last free
-    uint32_t* ul = sc + 14 * nf;        // [2 nf] old free blocks absorbed by runs
-    uint32_t* hb = free_hot_words(nf) <= S.dyn_words ? S.dyn : sc + 16 * nf;
+    uint32_t* lh = sc;                  // leftmost block of the run's left part
+    uint32_t* fl = sc + nf;             // bit0: erase L, bit1: erase R, FL_WIN
+    uint32_t* runs = sc + 2 * nf;       // run leaders in order of their last free
+    uint32_t* ul = sc + 3 * nf;         // [2 nf] old free blocks absorbed by runs
+    uint32_t* hb = free_hot_words(nf) <= S.dyn_words ? S.dyn : sc + 5 * nf;
     GTable T{hb, hb + hcap, hcap - 1};
     uint32_t* root = hb + 2 * hcap;     // pointer-jumping root (a free index)
     uint32_t* rmaxj = root + nf;        // largest free index of the run (at the root)
     uint32_t* rend = rmaxj + nf;        // right end of the run (at the root)
-    const uint64_t mbm = (1ull << S.lg) - 1ull;
-    constexpr int U = 4;
+    uint32_t* runAt = rend + nf;        // run leader whose last free is j, or NIL
 
     // F0: clear the granule table.
     HBA_FOR_THREADS(tid) {
@@ -428,89 +461,44 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
     }
     HBA_SYNC();
-    // F1: every record the phase needs, U frees per thread at a time so the
-    // loads overlap: the freed block (must be the start of an in-use block),
-    // then both address neighbours.  Candidates go into the granule table.
+    // F1: valid frees go into the granule table (lowest index wins).
     HBA_FOR_THREADS(tid) {
-        for (uint32_t j0 = tid; j0 < nf; j0 += NT * U) {
-            uint32_t gg[U];
-            Rec r[U], rl[U], rr[U];
-            HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                const uint32_t j = j0 + u * NT;
-                const uint64_t off = j < nf ? a.frees[j] : FAIL64;
-                gg[u] = (off < S.A && (off & mbm) == 0) ? (uint32_t)(off >> S.lg) : NIL;
-            }
-            HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                r[u] = gg[u] != NIL ? ldr(rec, gg[u]) : Rec{0, NIL, 0, 0};
-                if (st_of(r[u].x) != ST_USED) gg[u] = NIL;
-            }
-            HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                const uint32_t R = gg[u] != NIL ? gg[u] + sz_of(r[u].x) : S.G;
-                rl[u] = (gg[u] != NIL && r[u].y != NIL) ? ldr(rec, r[u].y) : Rec{0, NIL, NIL, NIL};
-                rr[u] = R < S.G ? ldr(rec, R) : Rec{0, NIL, NIL, NIL};
-            }
-            HBA_UNROLL
-            for (int u = 0; u < U; ++u) {
-                const uint32_t j = j0 + u * NT;
-                if (j >= nf) continue;
-                fgr[j] = gg[u];
-                fsz[j] = sz_of(r[u].x);
-                fy[j] = r[u].y;
-                Lx[j] = rl[u].x;
-                Ly[j] = rl[u].y;
-                Lz[j] = rl[u].z;
-                Lw[j] = rl[u].w;
-                Rx[j] = rr[u].x;
-                Rz[j] = rr[u].z;
-                Rw[j] = rr[u].w;
-                if (gg[u] != NIL) gt_insert_min(T, gg[u], j);
-            }
+        for (uint32_t j = tid; j < nf; j += NT) {
+            const uint32_t g = gG[j];
+            if (g != NIL) gt_insert_min(T, g, j);
         }
     }
     HBA_SYNC();
     HBA_PROF(1);
-    // F2: the lowest index naming a block wins; statuses; counters.
+    // F2: winners and statuses; pred = the applied free to my left inside the
+    // same run (directly adjacent, or across exactly one old free block); an
+    // old free block absorbed by a run is unlinked by the applied free to its
+    // right, or by the one to its left when it ends the run.
     HBA_FOR_THREADS(tid) {
         int64_t freed = 0;
         uint32_t won = 0;
         for (uint32_t j = tid; j < nf; j += NT) {
-            const uint32_t g = fgr[j];
+            const uint32_t g = gG[j];
             const bool win = g != NIL && gt_find(T, g) == j;
-            if (!win && g != NIL) fgr[j] = NIL;
             if (a.fstat) a.fstat[j] = win ? 0 : 1;
-            if (win) { freed += fsz[j]; ++won; }
-        }
-        warp_sum(S, tid, C_USEDG, -freed);
-        warp_sum(S, tid, C_FOK, won);
-    }
-    HBA_SYNC();
-    HBA_PROF(2);
-    // F3: pred = the freed block to my left inside the same run (directly
-    // adjacent, or across exactly one old free block); an old free block
-    // absorbed by a run is unlinked by the freed block to its right, or by
-    // the one to its left when it ends the run.
-    HBA_FOR_THREADS(tid) {
-        for (uint32_t j = tid; j < nf; j += NT) {
-            const uint32_t g = fgr[j];
             runAt[j] = NIL;
-            if (g == NIL) {
+            if (!win) {
                 root[j] = j;
                 rmaxj[j] = 0;
                 rend[j] = 0;
+                fl[j] = 0;
                 continue;
             }
-            const uint32_t L = fy[j];
-            uint32_t pr = NIL, head = g, flags = 0;
+            const uint32_t szf = gSZ[j], sz = sz_of(szf), L = gL[j];
+            uint32_t pr = NIL, head = g, flags = FL_WIN;
             if (L != NIL) {
                 const uint32_t wl = gt_find(T, L);
                 if (wl != NIL) {
                     pr = wl;
-                } else if (st_of(Lx[j]) == ST_FREE) {
+                } else if (szf & F_LFREE) {
                     ul[at_add_u32(&S.nul, 1)] = L;
-                    const uint32_t wll = Ly[j] != NIL ? gt_find(T, Ly[j]) : NIL;
+                    const uint32_t LL = gLL[j];
+                    const uint32_t wll = LL != NIL ? gt_find(T, LL) : NIL;
                     if (wll != NIL) {
                         pr = wll;
                         flags |= 1;   // L is inside the run: erase its record
@@ -519,10 +507,10 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                     }
                 }
             }
-            uint32_t end = g + fsz[j];
-            if (st_of(Rx[j]) == ST_FREE) {
+            uint32_t end = g + sz;
+            if (szf & F_RFREE) {
                 const uint32_t R = end;
-                end = R + sz_of(Rx[j]);
+                end = gRE[j];
                 if (end >= S.G || gt_find(T, end) == NIL) {
                     ul[at_add_u32(&S.nul, 1)] = R;
                     flags |= 2;       // R ends the run: erase its record
@@ -533,11 +521,15 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             rend[j] = end;
             lh[j] = head;
             fl[j] = flags;
+            freed += sz;
+            ++won;
         }
+        warp_sum(S, tid, C_USEDG, -freed);
+        warp_sum(S, tid, C_FOK, won);
     }
     HBA_SYNC();
-    HBA_PROF(3);
-    // F4: pointer jumping to the run's leftmost freed block.
+    HBA_PROF(2);
+    // F3: pointer jumping to the run's leftmost applied free.
     for (int it = 0;; ++it) {
         HBA_FOR_THREADS(tid) {
             bool ch = false;
@@ -552,8 +544,8 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         HBA_SYNC();
         if (!S.flag[it % 3]) break;
     }
-    HBA_PROF(4);
-    // F5: per-run right end and last free index; mark absorbed blocks.
+    HBA_PROF(3);
+    // F4: per-run right end and last free index; mark absorbed blocks.
     HBA_FOR_THREADS(tid) {
         for (uint32_t j = tid; j < nf; j += NT) {
             const uint32_t r = root[j];
@@ -568,36 +560,38 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_SYNC();
-    HBA_PROF(5);
-    // F6: unlink maximal segments of absorbed blocks from their lists.
-    HBA_FOR_THREADS(tid) {
-        for (uint32_t i = tid; i < S.nul; i += NT) {
-            const uint32_t u = ul[i];
-            const Rec r = ldr(rec, u);
-            const uint32_t pv = r.w;
-            if (pv != NIL && st_of(rec[pv].x) == ST_DEL) continue;  // not a segment start
-            uint32_t n = r.z;
-            uint32_t guard = 0;
-            while (n != NIL && st_of(rec[n].x) == ST_DEL) {
-                n = rec[n].z;
-                if (++guard > S.G) { S.err = ERR_LIST_WALK; n = NIL; break; }
+    HBA_PROF(4);
+    // F5: unlink maximal segments of absorbed blocks from their lists.
+    if (S.nul) {
+        HBA_FOR_THREADS(tid) {
+            for (uint32_t i = tid; i < S.nul; i += NT) {
+                const uint32_t u = ul[i];
+                const Rec r = ldr(rec, u);
+                const uint32_t pv = r.w;
+                if (pv != NIL && st_of(rec[pv].x) == ST_DEL) continue;  // not a segment start
+                uint32_t n = r.z;
+                uint32_t guard = 0;
+                while (n != NIL && st_of(rec[n].x) == ST_DEL) {
+                    n = rec[n].z;
+                    if (++guard > S.G) { S.err = ERR_LIST_WALK; n = NIL; break; }
+                }
+                if (pv == NIL) S.heads[flog2(sz_of(r.x))] = n;
+                else rec[pv].z = n;
+                if (n != NIL) rec[n].w = pv;
             }
-            if (pv == NIL) S.heads[flog2(sz_of(r.x))] = n;
-            else rec[pv].z = n;
-            if (n != NIL) rec[n].w = pv;
         }
+        HBA_SYNC();
     }
-    HBA_SYNC();
-    HBA_PROF(6);
-    // F7: write the merged blocks, erase absorbed records.
+    HBA_PROF(5);
+    // F6: write the merged blocks, erase absorbed records.
     HBA_FOR_THREADS(tid) {
         uint32_t nr = 0;
         for (uint32_t j = tid; j < nf; j += NT) {
-            const uint32_t g = fgr[j];
-            if (g == NIL) continue;
             const uint32_t f = fl[j];
-            if (f & 1) rec[fy[j]].x = 0;
-            if (f & 2) rec[g + fsz[j]].x = 0;
+            if (!(f & FL_WIN)) continue;
+            const uint32_t g = gG[j];
+            if (f & 1) rec[gL[j]].x = 0;
+            if (f & 2) rec[g + sz_of(gSZ[j])].x = 0;
             if (root[j] == j) {
                 const uint32_t H = lh[j], end = rend[j];
                 rec[H].x = mkx(end - H, ST_FREE);
@@ -612,8 +606,8 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         if (nr) at_add_u32(&S.nruns, nr);
     }
     HBA_SYNC();
-    HBA_PROF(7);
-    // F8: run leaders in increasing order of their last free index.
+    HBA_PROF(6);
+    // F7: run leaders in increasing order of their last free index.
     const uint32_t per = (nf + NT - 1) / NT;
     HBA_FOR_THREADS(tid) {
         const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
@@ -631,14 +625,14 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             if (runAt[j] != NIL) runs[k++] = runAt[j];
     }
     HBA_SYNC();
-    HBA_PROF(8);
-    // F9a: the merged blocks are pushed in run order.  Split that order into
+    HBA_PROF(7);
+    // F8a: the merged blocks are pushed in run order.  Split that order into
     // NSEG segments; inside each, link consecutive runs of the same class.
     constexpr int NSEG = Smem<NT>::NSEG;
     HBA_FOR_THREADS(tid) {
         if (tid < NSEG) {
-            uint32_t* F = S.u.seg.f[tid];
-            uint32_t* Lt = S.u.seg.l[tid];
+            uint32_t* F = S.segf[tid];
+            uint32_t* Lt = S.segl[tid];
             for (int b = 0; b < NBINS; ++b) F[b] = Lt[b] = NIL;
             const uint32_t ps = (nruns + NSEG - 1) / NSEG;
             const uint32_t lo = tid * ps, hi = lo + ps < nruns ? lo + ps : nruns;
@@ -657,17 +651,17 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_SYNC();
-    // F9b: per class, stitch the segments in order on top of the old list.
+    // F8b: per class, stitch the segments in order on top of the old list.
     HBA_FOR_THREADS(tid) {
         for (int b = tid; b < NBINS; b += NT) {
             uint32_t below = S.heads[b];
             bool any = false;
             for (int sgm = 0; sgm < NSEG; ++sgm) {
-                const uint32_t f = S.u.seg.f[sgm][b];
+                const uint32_t f = S.segf[sgm][b];
                 if (f == NIL) continue;
                 rec[f].z = below;
                 if (below != NIL) rec[below].w = f;
-                below = S.u.seg.l[sgm][b];
+                below = S.segl[sgm][b];
                 any = true;
             }
             if (any) {
@@ -683,15 +677,15 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             for (int b = 0; b < NBINS; ++b)
                 if (S.heads[b] != NIL) m |= 1ull << b;
             S.mask = m;
-            // applied frees = runs' new members; blocks: every run becomes one
             int64_t fok = 0;
             for (int w = 0; w <= Smem<NT>::NW; ++w) fok += S.wc[w][C_FOK];
             single_add(S, C_FFAIL, (int64_t)nf - fok);
+            // every run becomes one block
             single_add(S, C_BLOCKS, (int64_t)nruns - fok - (int64_t)S.nul);
         }
     }
     HBA_SYNC();
-    HBA_PROF(9);
+    HBA_PROF(8);
 }
 
 // ---------------------------------------------------------------------------
@@ -712,17 +706,16 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
     }
     const uint32_t k = ctz64(cand);
     if (S.xok && k == S.xL) {
-        // carve the front of X (its prev_adj is already in rec[xg].y)
+        // carve the front of X
         const uint32_t start = S.xg;
-        rec[start].x = mkx(sg, ST_USED);
-        rec[start].z = NIL;
-        rec[start].w = NIL;
+        str(rec, start, Rec{mkx(sg, ST_USED), S.xprev, NIL, NIL});
         a.out[i] = (uint64_t)start << S.lg;
         S.xg += sg;
         S.xsz -= sg;
-        if (S.xg < S.G) rec[S.xg].y = start;
+        S.xprev = start;
         if (S.xsz == 0) {
             S.xok = 0;
+            if (S.xright < S.G) rec[S.xright].y = start;
             single_add(S, C_NOSPLIT, 1);
         } else {
             S.xL = flog2(S.xsz);
@@ -744,17 +737,15 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
         if (nxt == NIL) S.mask &= ~(1ull << k);
         else rec[nxt].w = NIL;
         const uint32_t ysz = sz_of(ry.x);
-        rec[Y].x = mkx(sg, ST_USED);
-        rec[Y].z = NIL;
-        rec[Y].w = NIL;
+        str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
         a.out[i] = (uint64_t)Y << S.lg;
         if (ysz > sg) {
             S.xok = 1;
             S.xg = Y + sg;
             S.xsz = ysz - sg;
+            S.xprev = Y;
             S.xright = Y + ysz;
             S.xL = flog2(ysz - sg);
-            rec[S.xg].y = Y;
         } else {
             single_add(S, C_NOSPLIT, 1);
         }
@@ -764,19 +755,50 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
     single_add(S, C_REQ, (int64_t)s);
 }
 
+// Start granule of the nearest carve lane below `tid` in this round (lanes
+// are carves iff S.cls == CL_CARVE; their starts are in S.cst), or X's
+// prev_adj at the start of the round when there is none.  GPU: ballot and
+// shuffle inside the warp, per-warp last carves (S.wlast) across warps.
+// Call convergently.
+template <int NT>
+HBA_DEV uint32_t prev_carve_start(Smem<NT>& S, int tid, bool carve, uint32_t start) {
+#ifdef HBA_EMULATE
+    (void)carve;
+    (void)start;
+    for (int t = tid - 1; t >= 0; --t)
+        if (S.cls[t] == CL_CARVE) return S.cst[t];
+    return S.c0prev;
+#else
+    const int lane = tid & 31, wid = tid >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, carve) & ((1u << lane) - 1u);
+    const int src = m ? 31 - __clz(m) : lane;
+    const uint32_t v = __shfl_sync(0xffffffffu, start, src);
+    if (m) return v;
+    for (int w = wid - 1; w >= 0; --w)
+        if (S.wlast[w] != NIL) return S.wlast[w];
+    return S.c0prev;
+#endif
+}
+
 template <int NT>
 HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t na = a.na;
     Rec* rec = a.rec;
     const uint32_t lg = S.lg;
     const uint64_t mbm = (1ull << lg) - 1ull;
-#ifndef HBA_EMULATE
-    // out[] may be pre-filled by the preceding grid: wait for it (no-op when
-    // the launch carries no programmatic dependency)
-    if (a.prefilled) asm volatile("griddepcontrol.wait;" ::: "memory");
-#endif
+    // alloc arrays live in the dynamic shared memory (the free phase is over)
     HBA_FOR_THREADS(tid) {
-        if (tid == 0) { S.p = 0; S.xok = 0; }
+        if (tid == 0) {
+            uint32_t* d = S.dyn;
+            S.val = reinterpret_cast<int64_t*>(d);
+            S.s64 = reinterpret_cast<uint64_t*>(d + 2 * NT);
+            S.cst = d + 4 * NT;
+            S.sgr = d + 5 * NT;
+            S.cls = reinterpret_cast<uint8_t*>(d + 6 * NT);
+            S.ccl = reinterpret_cast<uint8_t*>(d + 6 * NT + NT / 4 + 4);
+            S.p = 0;
+            S.xok = 0;
+        }
     }
     HBA_SYNC();
     while (true) {
@@ -811,20 +833,21 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             const uint32_t i = p + tid;
             uint32_t sg = 0, c = 0;
             uint64_t s = 0;
-            bool bad = true;
             if (i < na) {
                 s = a.sizes[i];
                 if (i + NT < na) prefetch_l2(a.sizes + i + NT);
                 if (s != 0 && s <= S.A) {
-                    bad = false;
                     sg = (uint32_t)((s + mbm) >> lg);
                     c = clog2(sg);
                 }
             }
-            S.sgr[tid] = bad ? 0 : sg;
+            S.sgr[tid] = sg;
             S.ccl[tid] = (uint8_t)c;
-            S.u.a.s64[tid] = s;
-            if (tid == 0) S.r = 0;
+            S.s64[tid] = s;
+            if (tid == 0) {
+                S.r = 0;
+                S.evb[0] = S.evb[1] = NT;
+            }
         }
         HBA_SYNC();
         HBA_PROF(11);
@@ -839,7 +862,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         for (int round = 0;; ++round) {
             const uint32_t r = S.r;
             uint32_t* evp = &S.evb[round & 1];
-            // A1: classify
+            // A1: classify (own lane only: no barrier before the scan)
             HBA_FOR_THREADS(tid) {
                 uint8_t cl = CL_NONE;
                 const uint32_t sg = S.sgr[tid];
@@ -855,24 +878,28 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     }
                 }
                 S.cls[tid] = cl;
-                S.u.a.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
+                S.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
                 if (tid == 0) {
                     S.c0g = S.xg;
                     S.c0sz = S.xok ? S.xsz : 0;
+                    S.c0prev = S.xprev;
                     S.evb[(round + 1) & 1] = NT;
-                    if (round == 0) S.evb[0] = NT;
                 }
             }
-            HBA_SYNC();
             HBA_PROF(12);
-            scan_incl_i64<NT>(S, S.u.a.val);
+            scan_incl_i64<NT>(S, S.val);
             HBA_PROF(13);
-            // B: verify
+            // B: verify; carve lanes record their start; per-warp last carve
             HBA_FOR_THREADS(tid) {
                 const uint8_t cl = S.cls[tid];
+                const bool carve = cl == CL_CARVE;
                 bool e = cl == CL_OTHER;
-                if (cl == CL_CARVE) {
-                    const int64_t before = (int64_t)S.c0sz - (S.u.a.val[tid] - (int64_t)S.sgr[tid]);
+                uint32_t start = NIL;
+                if (carve) {
+                    const int64_t P = S.val[tid];
+                    const uint32_t sg = S.sgr[tid];
+                    start = S.c0g + (uint32_t)(P - sg);
+                    const int64_t before = (int64_t)S.c0sz - (P - (int64_t)sg);
                     uint64_t M = S.mask;
                     uint32_t Lt = 64;
                     if (before > 0) {
@@ -883,11 +910,15 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     const uint64_t cand = (M >> c) << c;
                     if (!(cand && ctz64(cand) == Lt)) e = true;
                 }
+                S.cst[tid] = start;
 #ifdef HBA_EMULATE
                 if (e && (uint32_t)tid < *evp) *evp = (uint32_t)tid;
 #else
                 const unsigned bal = __ballot_sync(0xffffffffu, e);
                 if ((tid & 31) == 0 && bal) atomicMin(evp, (uint32_t)(tid + __ffs(bal) - 1));
+                const unsigned cb = __ballot_sync(0xffffffffu, carve);
+                const uint32_t top = __shfl_sync(0xffffffffu, start, cb ? 31 - __clz(cb) : 0);
+                if ((tid & 31) == 0) S.wlast[tid >> 5] = cb ? top : NIL;
 #endif
             }
             HBA_SYNC();
@@ -901,29 +932,29 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                 const bool act = (uint32_t)tid < nres;   // lanes below r have class NONE
                 const bool is_fail = act && cl == CL_FAIL;
                 const bool is_carve = act && cl == CL_CARVE;
+                const uint32_t start = S.cst[tid];
+                const uint32_t prev = prev_carve_start<NT>(S, tid, cl == CL_CARVE, start);
                 if (is_fail && !a.prefilled) a.out[p + tid] = FAIL64;
                 if (is_carve) {
                     const uint32_t sg = S.sgr[tid];
-                    const int64_t P = S.u.a.val[tid];
-                    const uint32_t start = S.c0g + (uint32_t)(P - sg);
-                    const uint32_t end = S.c0g + (uint32_t)P;
                     a.out[p + tid] = (uint64_t)start << lg;
-                    rec[start].x = mkx(sg, ST_USED);
-                    rec[start].z = NIL;
-                    rec[start].w = NIL;
-                    if (end < S.G) rec[end].y = start;
+                    str(rec, start, Rec{mkx(sg, ST_USED), prev, NIL, NIL});
                 }
                 warp_count(S, tid, C_AFAIL, is_fail);
                 warp_count(S, tid, C_AOK, is_carve);
-                warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.u.a.s64[tid] : 0);
+                warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
                 if ((uint32_t)tid == upd) {
-                    const int64_t gave = nres ? S.u.a.val[nres - 1] : 0;
+                    const int64_t gave = nres ? S.val[nres - 1] : 0;
                     if (gave > 0) {
+                        // the last carve of the round: this lane, or the one before it
+                        const uint32_t last = (nres == n_here && is_carve) ? start : prev;
                         S.xg = S.c0g + (uint32_t)gave;
                         S.xsz = S.c0sz - (uint32_t)gave;
+                        S.xprev = last;
                         single_add(S, C_USEDG, gave);
                         if (S.xsz == 0) {
                             S.xok = 0;
+                            if (S.xright < S.G) rec[S.xright].y = last;
                             single_add(S, C_NOSPLIT, 1);
                         } else {
                             S.xL = flog2(S.xsz);
@@ -931,7 +962,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     }
                     uint32_t next = n_here;
                     if (nres < n_here) {
-                        seq_request<NT>(S, a, p + nres, S.u.a.s64[nres], S.sgr[nres], S.ccl[nres]);
+                        seq_request<NT>(S, a, p + nres, S.s64[nres], S.sgr[nres], S.ccl[nres]);
                         next = nres + 1;
                     }
                     S.r = next;
@@ -964,7 +995,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
 }
 
 // One batch of one arena.  All threads of the CTA call this.  dyn/dyn_words:
-// dynamic shared memory for the free phase (may be 0 words).
+// dynamic shared memory (at least alloc_dyn_words<NT>() words).
 template <int NT>
 HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t dyn_words) {
     HBA_FOR_THREADS(tid) {
@@ -976,6 +1007,7 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t 
             S.G = a.ar->G;
             S.lg = a.ar->lg;
             S.xok = 0;
+            S.xprev = NIL;
             S.nruns = 0;
             S.err = 0;
             S.dyn = dyn;
