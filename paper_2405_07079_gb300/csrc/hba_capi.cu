@@ -253,7 +253,7 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     } else {
         // what this batch's free phase keeps in shared memory (if it fits),
         // so that L1 keeps the rest
-        const uint64_t hot = 4ull * hba::free_hot_words(nf);
+        const uint64_t hot = 4ull * hba::free_smem_words(nf);
         dyn = hot <= maxdyn ? (uint32_t)std::max<uint64_t>(hot, base) : base;
     }
     dyn = (dyn + 15u) & ~15u;

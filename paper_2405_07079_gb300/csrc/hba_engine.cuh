@@ -91,10 +91,10 @@ constexpr uint32_t MAX_GRANULES = SZ_MASK;  // G <= 2^29 - 1
 constexpr uint32_t ST_NONE = 0, ST_USED = 1, ST_FREE = 2, ST_NEW = 3, ST_DEL = 4;
 constexpr uint64_t FAIL64 = ~0ull;
 constexpr int NBINS = 32;  // granule classes 0..28 are reachable
-// global scratch per free: the gathered records (5 words), per-run data,
-// absorbed blocks (2), runs, and the granule table / pointer-jumping arrays
-// when they do not fit in shared memory
-constexpr uint32_t SCRATCH_WORDS_PER_FREE = 24;
+// global scratch per free: absorbed blocks (2 words) always; the free
+// phase's working arrays (table < 4, 7 per-free arrays, 2 absorbed) when
+// they do not fit in shared memory
+constexpr uint32_t SCRATCH_WORDS_PER_FREE = 16;
 constexpr uint32_t GATHER_WORDS = 5;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
@@ -388,20 +388,22 @@ HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec) {
 // The free phase (Algorithm 5 for all frees of the batch).
 // ---------------------------------------------------------------------------
 
-// Open-addressing table: granule -> lowest free index that names it.  Only
+// Open-addressing table: granule -> lowest free index that names it.  A slot
+// holds a free index j; its key is the granule gG[j] of that free.  Only
 // valid frees (starts of in-use blocks) are inserted.
 struct GTable {
-    uint32_t* key;
-    uint32_t* val;
+    uint32_t* slot;
+    const uint32_t* gG;
     uint32_t mask;  // capacity - 1 (capacity: power of two >= 2 * keys)
 };
 HBA_DEV uint32_t gt_hash(uint32_t g, uint32_t mask) { return (g * 0x9E3779B1u >> 7) & mask; }
 HBA_DEV void gt_insert_min(const GTable& t, uint32_t g, uint32_t j) {
     uint32_t s = gt_hash(g, t.mask);
     while (true) {
-        const uint32_t k = at_cas_u32(&t.key[s], NIL, g);
-        if (k == NIL || k == g) {
-            at_min_u32(&t.val[s], j);
+        const uint32_t k = at_cas_u32(&t.slot[s], NIL, j);
+        if (k == NIL) return;
+        if (t.gG[k] == g) {
+            at_min_u32(&t.slot[s], j);
             return;
         }
         s = (s + 1) & t.mask;
@@ -411,21 +413,21 @@ HBA_DEV void gt_insert_min(const GTable& t, uint32_t g, uint32_t j) {
 HBA_DEV uint32_t gt_find(const GTable& t, uint32_t g) {
     uint32_t s = gt_hash(g, t.mask);
     while (true) {
-        const uint32_t k = t.key[s];
-        if (k == g) return t.val[s];
+        const uint32_t k = t.slot[s];
         if (k == NIL) return NIL;
+        if (t.gG[k] == g) return k;
         s = (s + 1) & t.mask;
     }
 }
-// Capacity of the granule table for nf frees, and the words of the free
-// phase's hot arrays (table, roots, per-run maxima, run slots) that go to
-// shared memory when they fit.
+// Capacity of the granule table for nf frees, and the shared-memory words of
+// the free phase (gathered records 5 nf, table, roots, per-run maxima, run
+// slots, run heads and flags 6 nf).
 HBA_HD uint32_t gt_capacity(uint32_t nf) {
     uint32_t c = 2;
     while (c < 2 * nf) c <<= 1;
     return c;
 }
-HBA_HD uint32_t free_hot_words(uint32_t nf) { return 2 * gt_capacity(nf) + 4 * nf; }
+HBA_HD uint32_t free_smem_words(uint32_t nf) { return 11 * nf + gt_capacity(nf) + 4; }
 
 constexpr uint32_t FL_WIN = 4;  // flag: this free is applied
 
@@ -433,31 +435,50 @@ template <int NT>
 HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t nf = a.nf;
     Rec* rec = a.rec;
-    const uint32_t gs = a.gstride;
-    const uint32_t* gG = a.gi;          // gathered: block granule or NIL
-    const uint32_t* gSZ = a.gi + gs;    //   size | neighbour flags
-    const uint32_t* gL = a.gi + 2 * gs; //   left neighbour
-    const uint32_t* gLL = a.gi + 3 * gs;
-    const uint32_t* gRE = a.gi + 4 * gs;
     const uint32_t hcap = gt_capacity(nf);
-    uint32_t* sc = a.scr;
-    uint32_t* lh = sc;                  // leftmost block of the run's left part
-    uint32_t* fl = sc + nf;             // bit0: erase L, bit1: erase R, FL_WIN
-    uint32_t* runs = sc + 2 * nf;       // run leaders in order of their last free
-    uint32_t* ul = sc + 3 * nf;         // [2 nf] old free blocks absorbed by runs
-    uint32_t* hb = free_hot_words(nf) <= S.dyn_words ? S.dyn : sc + 5 * nf;
-    GTable T{hb, hb + hcap, hcap - 1};
-    uint32_t* root = hb + 2 * hcap;     // pointer-jumping root (a free index)
+    // All working arrays in shared memory when they fit (the gathered records
+    // are staged there first); otherwise in global memory, reading the
+    // gathered records where the prep grid left them.
+    const bool sm = free_smem_words(nf) <= S.dyn_words;
+    uint32_t* w = sm ? S.dyn : a.scr;
+    const uint32_t* gG;
+    const uint32_t* gSZ;
+    const uint32_t* gL;
+    const uint32_t* gLL;
+    const uint32_t* gRE;
+    if (sm) {
+        gG = w; gSZ = w + nf; gL = w + 2 * nf; gLL = w + 3 * nf; gRE = w + 4 * nf;
+        w += 5 * nf;
+    } else {
+        const uint32_t gs = a.gstride;
+        gG = a.gi; gSZ = a.gi + gs; gL = a.gi + 2 * gs; gLL = a.gi + 3 * gs; gRE = a.gi + 4 * gs;
+    }
+    GTable T{w, gG, hcap - 1};
+    uint32_t* root = w + hcap;          // pointer-jumping root (a free index)
     uint32_t* rmaxj = root + nf;        // largest free index of the run (at the root)
     uint32_t* rend = rmaxj + nf;        // right end of the run (at the root)
     uint32_t* runAt = rend + nf;        // run leader whose last free is j, or NIL
+    uint32_t* lh = runAt + nf;          // leftmost block of the run's left part
+    uint32_t* fl = lh + nf;             // bit0: erase L, bit1: erase R, FL_WIN
+    uint32_t* runs = sm ? const_cast<uint32_t*>(gLL) : fl + nf;  // run leaders in order
+    uint32_t* ul = sm ? a.scr : fl + 2 * nf;                     // [2 nf] absorbed old free blocks
 
-    // F0: clear the granule table.
+    // F0: stage the gathered records, clear the granule table.
     HBA_FOR_THREADS(tid) {
-        for (uint32_t q = tid; q < hcap; q += NT) {
-            T.key[q] = NIL;
-            T.val[q] = NIL;
+        if (sm) {
+            const uint32_t gs = a.gstride;
+            uint32_t* d = S.dyn;
+            for (uint32_t j = tid; j < nf; j += NT) {
+                const uint32_t v0 = a.gi[j], v1 = a.gi[gs + j], v2 = a.gi[2 * gs + j];
+                const uint32_t v3 = a.gi[3 * gs + j], v4 = a.gi[4 * gs + j];
+                d[j] = v0;
+                d[nf + j] = v1;
+                d[2 * nf + j] = v2;
+                d[3 * nf + j] = v3;
+                d[4 * nf + j] = v4;
+            }
         }
+        for (uint32_t q = tid; q < hcap; q += NT) T.slot[q] = NIL;
         if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
     }
     HBA_SYNC();
@@ -678,7 +699,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                 if (S.heads[b] != NIL) m |= 1ull << b;
             S.mask = m;
             int64_t fok = 0;
-            for (int w = 0; w <= Smem<NT>::NW; ++w) fok += S.wc[w][C_FOK];
+            for (int w2 = 0; w2 <= Smem<NT>::NW; ++w2) fok += S.wc[w2][C_FOK];
             single_add(S, C_FFAIL, (int64_t)nf - fok);
             // every run becomes one block
             single_add(S, C_BLOCKS, (int64_t)nruns - fok - (int64_t)S.nul);
