@@ -39,8 +39,13 @@ sys.path.insert(0, ROOT)
 METRIC = "alloc+free ops/s on 1 GB300 (batched/serving vs plain GPU); p50/p99 latency; bit-exact"
 UNIT = "ops/s"
 FAIL = np.uint64(0xFFFFFFFFFFFFFFFF)
-# Algorithmic metadata bytes per request (the paper's six-word, 48-byte
-# address-keyed record, §3.3; see the design doc for the derivation).
+# Algorithmic metadata bytes per request, counted with the paper's six-word
+# (48-byte) address-keyed record (§3.3): a served allocation reads the list
+# head and the head's record, writes it back, writes the remainder's record,
+# fixes three links and the right neighbour's prev_adj (168 B with request and
+# result); a failed one only reads its request and writes its result (16 B);
+# an applied free reads three neighbour records and writes one plus a list
+# head (216 B); a rejected free reads its request and writes a status (9 B).
 BYTES_ALLOC_OK = 168
 BYTES_ALLOC_FAIL = 16
 BYTES_FREE_OK = 216
