@@ -136,6 +136,38 @@ hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_
                            const uint64_t* h_sizes, uint32_t na, uint64_t* h_out_offsets,
                            hba_stream_t stream);
 
+/* ---- batches that allocate nothing ------------------------------------- */
+
+/* Maximum number of frees per hba_step_static call. */
+#define HBA_STATIC_MAX_FREES 4096u
+
+/* hba_step without the handle's scratch.  The paper has no counterpart: it
+ * is a packaging choice of this library.
+ *
+ * Every handle normally carries its own device scratch for batch work,
+ * allocated by hba_create* and proportional to max_batch (about 84 bytes per
+ * free).  Some callers cannot afford that allocation: a process that keeps
+ * many small handles under a fixed device-memory budget, or one whose device
+ * memory is reserved up front by another pool, so that cudaMalloc would fail
+ * or would have to be avoided.  Such callers can create their handles with
+ * max_batch = 1 and run their batches here.  This call makes no allocation
+ * at all: its kernels use one static device array compiled into the library
+ * (room for HBA_STATIC_MAX_FREES frees, 336 KiB, held by every device
+ * that loads the library until the process exits).
+ *
+ * Same arguments, results and stream semantics as hba_step.  nf above
+ * HBA_STATIC_MAX_FREES returns HBA_ERR_INVALID_ARGUMENT and enqueues nothing.
+ * The array is shared by every call on a device, whatever the handle:
+ * calls whose work overlaps on the GPU (different streams without ordering
+ * between them) race on it and corrupt each other's results, so order them.
+ * Nothing in the array needs clearing between calls: each call writes every
+ * word it reads.  The first call on a device looks up the array's device
+ * address with that device current (HBA_ERR_CUDA if that fails); make that
+ * first call before any stream capture. */
+hba_status_t hba_step_static(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status,
+                             const uint64_t* d_sizes, uint32_t na, uint64_t* d_out_offsets,
+                             hba_stream_t stream);
+
 /* Return the arena to its initial state (one free block) and zero the
  * counters.  Asynchronous on stream. */
 hba_status_t hba_reset(hba_t h, hba_stream_t stream);

@@ -27,6 +27,7 @@ SIGNATURES = {
     "hba_free_batch_ex": (i32, [vp, vp, u32, vp, vp]),
     "hba_step": (i32, [vp, vp, u32, vp, vp, u32, vp, vp]),
     "hba_step_host": (i32, [vp, vp, u32, vp, vp, u32, vp, vp]),
+    "hba_step_static": (i32, [vp, vp, u32, vp, vp, u32, vp, vp]),
     "hba_reset": (i32, [vp, vp]),
     "hba_stats": (i32, [vp, vp]),
     "hba_export_state": (i32, [vp, u32, vp, sz, vp]),

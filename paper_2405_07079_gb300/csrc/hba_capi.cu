@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "hba.h"
@@ -350,9 +351,92 @@ bool check_geometry(uint64_t arena_bytes, uint64_t min_block, uint32_t* lg, uint
     return G >= 1 && G <= hba::MAX_GRANULES;
 }
 
+// ---- batches that allocate nothing (hba_step_static) ----------------------
+// Scratch for HBA_STATIC_MAX_FREES frees: the gathered records, then the
+// free phase's global working arrays.  One array per device, shared by all
+// calls; nothing in it needs clearing (a call writes every word it reads).
+constexpr uint32_t STATIC_GI_WORDS = hba::GATHER_WORDS * HBA_STATIC_MAX_FREES;
+constexpr uint32_t STATIC_WORDS = (hba::GATHER_WORDS + hba::SCRATCH_WORDS_PER_FREE) * HBA_STATIC_MAX_FREES;
+static __device__ __align__(256) uint32_t g_static_scratch[STATIC_WORDS];
+
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex g_static_mu;
+uint32_t* g_static_addr[STATIC_MAX_DEVICES] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device with that device current (host code cannot use the symbol's
+// name as a device pointer).  nullptr on failure.
+uint32_t* static_scratch_address() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= STATIC_MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        g_static_addr[dev] = static_cast<uint32_t*>(p);
+    }
+    return g_static_addr[dev];
+}
+
+hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
+                              uint32_t na, uint64_t* out, cudaStream_t s) {
+    if (!h || h->n_arenas != 1) return HBA_ERR_INVALID_ARGUMENT;
+    if ((nf && !frees) || (na && (!sizes || !out))) return HBA_ERR_INVALID_ARGUMENT;
+    if (nf > HBA_STATIC_MAX_FREES) return HBA_ERR_INVALID_ARGUMENT;
+    if (nf == 0 && na == 0) return HBA_OK;
+    uint32_t* base = static_scratch_address();
+    if (!base) return HBA_ERR_CUDA;
+    uint32_t* gi = base;
+    uint32_t* scr = base + STATIC_GI_WORDS;
+    Arena* ar = h->d_arenas;
+    Rec* rec = h->d_rec;
+    const int li = limit_index(h->threads);
+    const uint32_t maxdyn = g_limits[li].single_dyn;
+    const uint32_t minb = 4 * g_limits[li].alloc_words;
+    uint32_t dyn;
+    if (h->smem_bytes) {
+        dyn = std::max(minb, std::min(h->smem_bytes, maxdyn));
+    } else {
+        const uint64_t hot = 4ull * hba::free_smem_words(nf);
+        dyn = hot <= maxdyn ? (uint32_t)std::max<uint64_t>(hot, minb) : minb;
+    }
+    dyn = (dyn + 15u) & ~15u;
+    const uint32_t dw = dyn / 4;
+    // the prep grid: gather into the static array, pre-fill failures
+    const bool fill = na >= PREFILL_MIN;
+    bool pdl = false;
+    if (nf || fill) {
+        const uint32_t work = std::max(nf, fill ? na / 2 : 0u);
+        const uint32_t blocks = std::max(1u, std::min<uint32_t>((work + 127) / 128, 2048));
+        k_prep<<<blocks, 128, 0, s>>>(ar, rec, nullptr, 1, frees, nf, gi, fill ? out : nullptr, fill ? na : 0);
+        if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
+        pdl = true;
+    }
+    const uint32_t pf = fill ? 1u : 0u;
+    cudaError_t e;
+    switch (h->threads) {
+        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
+        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
+        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
+        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
+        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
+    }
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
+    return HBA_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+hba_status_t hba_step_static(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status,
+                             const uint64_t* d_sizes, uint32_t na, uint64_t* d_out_offsets, hba_stream_t stream) {
+    return step_static_impl(h, d_frees, nf, d_status, d_sizes, na, d_out_offsets, (cudaStream_t)stream);
+}
+
 
 const char* hba_version(void) { return "hba 0.1 (sm_103a)"; }
 

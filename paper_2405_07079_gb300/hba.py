@@ -57,6 +57,15 @@ def hba_step_host(h: int, h_frees: int, nf: int, h_status: int, h_sizes: int, na
     check("hba_step_host", _lib().hba_step_host(h, h_frees, nf, h_status, h_sizes, na, h_out, stream))
 
 
+HBA_STATIC_MAX_FREES = 4096
+
+
+def hba_step_static(h: int, d_frees: int, nf: int, d_status: int, d_sizes: int, na: int, d_out: int,
+                    stream: int = 0) -> None:
+    """hba_step with scratch from the library's static device array (no allocation)."""
+    check("hba_step_static", _lib().hba_step_static(h, d_frees, nf, d_status, d_sizes, na, d_out, stream))
+
+
 def hba_reset(h: int, stream: int = 0) -> None:
     check("hba_reset", _lib().hba_reset(h, stream))
 
@@ -193,4 +202,5 @@ class MultiAllocator:
         return hba_export_state(self.h, arena)
 
 
-__all__ = [n for n in dir() if n.startswith("hba_")] + ["Allocator", "MultiAllocator", "HbaError", "HBA_FAIL"]
+__all__ = [n for n in dir() if n.startswith("hba_")] + ["Allocator", "MultiAllocator", "HbaError", "HBA_FAIL",
+                                                          "HBA_STATIC_MAX_FREES"]
