@@ -139,6 +139,8 @@ def record_trace(wl, alloc, dev):
                   + BYTES_FREE_OK * n_fok + BYTES_FREE_REJECTED * (f.size - n_fok))
         batches.append({"f": df, "s": ds, "out": out, "st": st, "nf": f.size, "na": s.size,
                         "ops": f.size + s.size, "bytes": nbytes,
+                        # engine launch, plus the prep grid when there are frees or many allocations
+                        "launches": 1 + int(f.size > 0 or s.size >= 2048),
                         "hf": torch.from_numpy(f.view(np.int64).copy()).pin_memory(),
                         "hs": torch.from_numpy(s.view(np.int64).copy()).pin_memory()})
     return batches
@@ -192,6 +194,7 @@ def run_gpu(args, rank, world, local_rank):
     busy_s = sum(step_ms) / 1e3
     ops = sum(batches[i]["ops"] for i in idx)
     nbytes = sum(batches[i]["bytes"] for i in idx)
+    launches = sum(batches[i]["launches"] for i in idx)
 
     # e2e through the public host-buffer entry point, from a fresh state
     alloc.reset()
@@ -234,18 +237,138 @@ def run_gpu(args, rank, world, local_rank):
                    "ops_per_step_mean": ops / max(1, args.steps)},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak, "traffic": None,
-                     "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_single<1024>",
+                     "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_prep + k_single<1024>",
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "unit": "per batch of one step"},
         "e2e": {"value": e2e_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d // max(1, args.steps),
                 "d2h_bytes_per_step": e2e_d2h // max(1, args.steps), "api": "hba_step_host"},
-        "gpu_launches": args.steps,
+        "gpu_launches": launches,
         "clocks": clocks.summary(),
         "final_stats": {k: stats[k] for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail")},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+    return line
+
+
+def run_multi(args, rank, world, local_rank):
+    """The batched form: thousands of independent arenas, one batch of all of
+    them per step (prep grid + one multi-arena launch)."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator, MultiAllocator, hba_step, workloads
+    from paper_2405_07079_gb300.hba import _ptr
+    from paper_2405_07079_gb300.tune import autotune_multi
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    A = workloads.multi_arena_sizes(args.arenas)
+    gen = workloads.MultiLifetimes(A, n_batches=args.batches)
+    ma = MultiAllocator(A, 256, max_total_frees=args.arenas * 2048 + 1)
+    t_rec = time.time()
+    batches = []
+    while (b := gen.next_batch()) is not None:
+        frow, f, arow, s = b
+        d = {"frow": torch.from_numpy(frow.view(np.int32)).to(dev), "f": torch.from_numpy(f.view(np.int64)).to(dev),
+             "arow": torch.from_numpy(arow.view(np.int32)).to(dev), "s": torch.from_numpy(s.view(np.int64)).to(dev),
+             "nf": f.size, "na": s.size, "ops": f.size + s.size, "hfrow": frow, "harow": arow}
+        d["out"] = torch.empty(s.size, dtype=torch.int64, device=dev)
+        d["st"] = torch.empty(f.size, dtype=torch.uint8, device=dev)
+        ma.step(d["frow"], d["f"], d["arow"], d["s"], d["out"], d["st"])
+        o = d["out"].cpu().numpy().view(np.uint64)
+        gen.feed(o)
+        stat = d["st"].cpu().numpy()
+        n_ok, n_fok = int((o != FAIL).sum()), int((stat == 0).sum())
+        d["bytes"] = (BYTES_ALLOC_OK * n_ok + BYTES_ALLOC_FAIL * (s.size - n_ok)
+                      + BYTES_FREE_OK * n_fok + BYTES_FREE_REJECTED * (f.size - n_fok))
+        d["ref_out"] = o.copy()
+        batches.append(d)
+    t_rec = time.time() - t_rec
+    best, table = autotune_multi(ma, batches, n_probe=3)
+    nb = len(batches)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def launch(b):
+        ma.step(b["frow"], b["f"], b["arow"], b["s"], b["out"], b["st"], stream=stream)
+
+    ma_reset = lambda: __import__("paper_2405_07079_gb300").hba_reset(ma.h, int(stream.cuda_stream))
+    ma_reset()
+    pos = 0
+    for _ in range(args.warmup):
+        if pos == nb:
+            ma_reset(); pos = 0
+        flush.zero_()
+        launch(batches[pos]); pos += 1
+    steps = args.steps if args.steps else nb
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    idx = []
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        for k in range(steps):
+            if pos == nb:
+                ma_reset(); pos = 0
+            flush.zero_()
+            ev[k][0].record(stream)
+            launch(batches[pos])
+            ev[k][1].record(stream)
+            idx.append(pos); pos += 1
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    busy_s = sum(step_ms) / 1e3
+    ops = sum(batches[i]["ops"] for i in idx)
+    nbytes = sum(batches[i]["bytes"] for i in idx)
+
+    # the plain form on the same requests: the first P arenas, one handle and
+    # one launch per arena per batch; results must equal the batched form's
+    P = min(args.plain_arenas, args.arenas)
+    plain = [Allocator(int(A[i]), 256, max_batch=2048) for i in range(P)]
+    plain_ops, plain_ms, nb_plain = 0, 0.0, min(nb, 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for bi in range(nb_plain):
+        b = batches[bi]
+        outs = []
+        e0.record(stream)
+        for i in range(P):
+            f0, f1, a0, a1 = int(b["hfrow"][i]), int(b["hfrow"][i + 1]), int(b["harow"][i]), int(b["harow"][i + 1])
+            o = b["out"][a0:a1]
+            hba_step(plain[i].h, _ptr(b["f"][f0:f1]), f1 - f0, 0, _ptr(b["s"][a0:a1]), a1 - a0, _ptr(o),
+                     int(stream.cuda_stream))
+            plain_ops += (f1 - f0) + (a1 - a0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        got = b["out"][: int(b["harow"][P])].cpu().numpy().view(np.uint64)
+        if not np.array_equal(got, b["ref_out"][: int(b["harow"][P])]):
+            raise AssertionError(f"plain form differs from the batched form in batch {bi}")
+    for a in plain:
+        a.close()
+    ma.close()
+    peak, peak_src = _peaks()
+    achieved = nbytes / busy_s / 1e9
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": ops / busy_s, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * busy_s / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
+                               f"min block 256 B, U{{0..2048}} requests per arena per batch, {nb} batches",
+                   "form": "batched: prep grid + one multi-arena launch per batch",
+                   "shape": {"threads": best[0], "ctas": best[1], "smem_bytes": best[2]},
+                   "l2": "flushed between steps (256 MiB write, untimed)", "ops_per_step_mean": ops / steps,
+                   "record_s": round(t_rec, 1)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_multi",
+                     "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
+        "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "unit": "per batch of all arenas"},
+        "plain_form_same_requests": {"arenas": P, "batches": nb_plain, "value": plain_ops / (plain_ms / 1e3),
+                                     "unit": UNIT, "results_equal": True},
+        "autotune_ms": {f"t{t}_c{c}_s{m}": round(v, 3) for (t, c, m), v in sorted(table.items())},
+        "gpu_launches": 2 * steps,
+        "clocks": clocks.summary(),
+    }
     return line
 
 
@@ -316,7 +439,10 @@ def main():
     ap.add_argument("--steps", type=int, default=1530)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["large", "tiny", "frag"], default="large")
+    ap.add_argument("--workload", choices=["large", "tiny", "frag", "multi"], default="large")
+    ap.add_argument("--arenas", type=int, default=4096)
+    ap.add_argument("--batches", type=int, default=200)
+    ap.add_argument("--plain-arenas", type=int, default=64)
     ap.add_argument("--threads", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -330,7 +456,12 @@ def main():
             import torch
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        line = run_gpu(args, rank, world, local_rank)
+        if args.workload == "multi":
+            if args.steps == 1530:
+                args.steps = 0  # one pass over the recorded batches
+            line = run_multi(args, rank, world, local_rank)
+        else:
+            line = run_gpu(args, rank, world, local_rank)
         if world > 1:
             import torch
             torch.distributed.destroy_process_group()

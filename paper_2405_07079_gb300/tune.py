@@ -1,0 +1,58 @@
+"""Autotuner for the multi-arena batch kernel.
+
+The batch kernel applies one arena's batch per CTA.  Its launch shape is a
+trade-off: wider CTAs resolve bigger chunks of an arena's requests per round
+but pay more per barrier; more CTAs per SM hide each other's latencies but
+share the SM's issue slots and shared memory; a grid smaller than the number
+of arenas makes CTAs loop over arenas (fewer, longer-lived CTAs).  Results
+never depend on the shape, so the tuner simply times candidate shapes on the
+first batches of a recorded trace, from the same starting state, and keeps
+the fastest.
+"""
+from __future__ import annotations
+
+import itertools
+
+from .hba import MultiAllocator, hba_reset, hba_set_shape
+
+THREADS = (64, 128, 256, 512)
+GRID_WAVES = (0, 4, 8)          # 0 = one CTA per arena; k = k CTAs per SM
+SMEM_BYTES = (0, 48 * 1024)     # 0 = default per-CTA budget
+
+
+def _sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def autotune_multi(ma: MultiAllocator, batches, n_probe: int = 3, threads=THREADS, waves=GRID_WAVES,
+                   smem=SMEM_BYTES, verbose: bool = False):
+    """Time every (threads, grid, smem) candidate on the first ``n_probe``
+    batches (each candidate from the reset state) and set the best shape on
+    ``ma``.  ``batches``: list of dicts with device tensors ``frow, f, arow, s,
+    out, st``.  Returns ``(best_shape, table)`` where table maps shapes to
+    milliseconds."""
+    import torch
+
+    sms = _sm_count()
+    stream = torch.cuda.current_stream()
+    table = {}
+    for t, w, sm in itertools.product(threads, waves, smem):
+        ctas = 0 if w == 0 else w * sms
+        hba_set_shape(ma.h, t, ctas, sm)
+        hba_reset(ma.h, int(stream.cuda_stream))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for b in batches[:n_probe]:
+            e0.record(stream)
+            ma.step(b["frow"], b["f"], b["arow"], b["s"], b["out"], b["st"], stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        table[(t, ctas, sm)] = ms
+        if verbose:
+            print(f"  threads={t:4d} ctas={ctas:6d} smem={sm:6d}: {ms:.3f} ms")
+    best = min(table, key=table.get)
+    hba_set_shape(ma.h, *best)
+    hba_reset(ma.h, int(stream.cuda_stream))
+    return best, table

@@ -255,6 +255,90 @@ class FragStress:
             self.big_out.append(np.asarray(out, np.uint64).copy())
 
 
+class MultiLifetimes:
+    """Many independent arenas, one batch for all of them per step (CSR).
+
+    Per arena and batch: n ~ U{0..max_ops} request slots; the frees due by the
+    end of the slots come first (earliest due first, at most n), the remaining
+    slots are mallocs with the large-trace size mix scaled by the arena's size
+    (clamped to >= min_size); lifetimes are geometric in the arena's own op
+    count.  A free falling due inside its allocation's own batch waits for the
+    next batch.  Vectorised over arenas: the pending frees of all arenas live
+    in one sorted array of keys ``arena << 49 | due << 30 | seq``.
+    """
+
+    def __init__(self, arena_bytes, n_batches=200, max_ops=2048, mean_life=1000.0, min_size=256,
+                 seed=BASE_SEED + 4, ref_bytes=16 * GiB):
+        self.A = np.asarray(arena_bytes, dtype=np.uint64)
+        self.na = self.A.size
+        assert self.na < (1 << 15)
+        self.nb, self.max_ops, self.mean_life, self.min_size = n_batches, max_ops, mean_life, min_size
+        self.scale = self.A.astype(np.float64) / float(ref_bytes)
+        self.s_n, self.s_mix, self.s_size, self.s_life = (Stream(seed, f) for f in ("n", "mix", "size", "life"))
+        self.b = 0
+        self.t = np.zeros(self.na, np.int64)          # per-arena op clock
+        self.keys = np.zeros(0, np.uint64)             # pending frees, sorted
+        self.offs = np.zeros(0, np.uint64)
+        self.seq = 0
+        self._last = None
+        self._ids = np.arange(self.na, dtype=np.uint64)
+
+    def next_batch(self):
+        """Returns (free_rowptr uint32[n+1], frees uint64[], alloc_rowptr uint32[n+1], sizes uint64[])."""
+        if self.b >= self.nb:
+            return None
+        ids = self._ids
+        n = np.floor(self.s_n.unif(np.uint64(self.b) * np.uint64(self.na) + ids) * (self.max_ops + 1)).astype(np.int64)
+        hi = (ids << np.uint64(49)) | ((self.t + n).astype(np.uint64) << np.uint64(30))
+        seg = np.searchsorted(self.keys, ids << np.uint64(49))
+        elig = np.searchsorted(self.keys, hi) - seg
+        f = np.minimum(elig, n)
+        fsum = int(f.sum())
+        first = np.cumsum(f) - f
+        idx = np.repeat(seg, f) + (np.arange(fsum) - np.repeat(first, f))
+        frees = self.offs[idx]
+        keep = np.ones(self.keys.size, bool)
+        keep[idx] = False
+        self.keys, self.offs = self.keys[keep], self.offs[keep]
+        m = n - f
+        msum = int(m.sum())
+        marena = np.repeat(np.arange(self.na), m)
+        mstart = np.cumsum(m) - m
+        k = np.arange(msum) - np.repeat(mstart, m)
+        slot = np.repeat(self.t + f, m) + k                       # arena op index of each malloc
+        draw = marena.astype(np.uint64) * np.uint64(1 << 24) + slot.astype(np.uint64)
+        sz = tensor_mix(self.s_mix.unif(draw), self.s_size.unif(draw)).astype(np.float64)
+        sz = np.maximum(np.floor(sz * self.scale[marena]), self.min_size).astype(np.uint64)
+        life = geometric(self.s_life.unif(draw), self.mean_life)
+        self._last = (marena, slot, life, self.t + n)
+        self.t = self.t + n
+        self.b += 1
+        frow = np.concatenate([[0], np.cumsum(f)]).astype(np.uint32)
+        arow = np.concatenate([[0], np.cumsum(m)]).astype(np.uint32)
+        return frow, frees.astype(np.uint64), arow, sz
+
+    def feed(self, out):
+        marena, slot, life, end = self._last
+        out = np.asarray(out, np.uint64)
+        ok = out != np.uint64(FAIL)
+        a = marena[ok]
+        due = np.maximum(slot[ok] + life[ok], end[a])
+        seq = self.seq + np.arange(a.size, dtype=np.int64)
+        self.seq += a.size
+        nk = (a.astype(np.uint64) << np.uint64(49)) | (due.astype(np.uint64) << np.uint64(30)) | seq.astype(np.uint64)
+        order = np.argsort(nk, kind="stable")
+        nk, no = nk[order], out[ok][order]
+        pos = np.searchsorted(self.keys, nk)
+        self.keys = np.insert(self.keys, pos, nk)
+        self.offs = np.insert(self.offs, pos, no)
+
+
+def multi_arena_sizes(n_arenas=4096, lo=64 * MiB, hi=1 * GiB, granule=256, seed=BASE_SEED + 4):
+    """Arena sizes log-uniform in [lo, hi], rounded down to the granule."""
+    s = log_uniform(Stream(seed, "arena").unif(np.arange(n_arenas)), lo, hi)
+    return (s // np.uint64(granule)) * np.uint64(granule)
+
+
 # --------------------------------------------------------------------------
 # Named workloads (sizes of the five synthetic configurations)
 # --------------------------------------------------------------------------

@@ -248,3 +248,41 @@ def test_multi_arena_matches_per_arena_oracle(gpu_lib):
         for i in range(n):
             assert np.array_equal(m.export_state(i), orcs[i].export_state()), i
         m.close()
+
+
+def test_batched_generator_matches_per_arena_oracles(gpu_lib):
+    """The batched workload (uneven arenas, U{0..2048} requests per arena per
+    batch) in one multi-arena launch per batch equals, arena by arena, the
+    oracle applied to that arena's sub-trace."""
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import MultiAllocator
+    from paper_2405_07079_gb300 import workloads as W
+
+    dev = torch.device("cuda")
+    A = W.multi_arena_sizes(48, lo=1 << 20, hi=16 << 20)
+    gen = W.MultiLifetimes(A, n_batches=12, mean_life=300)
+    orcs = [oracle.Oracle(int(a), 256) for a in A]
+    ma = MultiAllocator(A, 256, max_total_frees=48 * 2048 + 1)
+    ma.set_shape(128, 0, 0)
+    try:
+        for b in range(12):
+            frow, f, arow, s = gen.next_batch()
+            exp_o, exp_s = [], []
+            for i in range(A.size):
+                o, st = orcs[i].batch(f[frow[i]:frow[i + 1]], s[arow[i]:arow[i + 1]])
+                exp_o.append(o)
+                exp_s.append(st)
+            out = torch.empty(s.size, dtype=torch.int64, device=dev)
+            st = torch.empty(f.size, dtype=torch.uint8, device=dev)
+            ma.step(to_dev(frow.view(np.int32), dev), to_dev(f, dev), to_dev(arow.view(np.int32), dev),
+                    to_dev(s, dev), out, st)
+            got = from_dev(out)
+            assert np.array_equal(got, np.concatenate(exp_o)), f"batch {b}"
+            assert np.array_equal(from_dev(st), np.concatenate(exp_s)), f"batch {b}"
+            gen.feed(got)
+        for i in range(A.size):
+            assert np.array_equal(ma.export_state(i), orcs[i].export_state()), i
+    finally:
+        ma.close()
