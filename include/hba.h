@@ -206,12 +206,14 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
                             uint8_t* d_free_status, hba_stream_t stream);
 
 /* Launch shape of the handle's batch kernel: threads per CTA (one of 64,
- * 128, 256, 512, 1024; a CTA applies one arena's batch), number of CTAs for
- * a multi-arena handle (0 = one CTA per arena; fewer CTAs loop over the
- * arenas), and dynamic shared memory per CTA in bytes (0 = automatic: for a
- * single arena, what the batch's free phase needs; capped at the device
- * limit; a batch whose scratch does not fit uses global scratch instead).
- * Results do not depend on the shape.  Set by the autotuner or by hand. */
+ * 128, 256, 512, 1024: a CTA applies one arena's batch; or 32: warp mode,
+ * every warp applies its own arena's batch, 8 arenas per CTA), number of
+ * CTAs for a multi-arena handle (0 = enough for every arena; fewer CTAs loop
+ * over the arenas), and dynamic shared memory per CTA (per warp in warp mode)
+ * in bytes (0 = automatic: for a single arena, what the batch's free phase
+ * needs; capped at the device limit; a batch whose scratch does not fit uses
+ * global scratch instead).  Results do not depend on the shape.  Set by the
+ * autotuner or by hand. */
 hba_status_t hba_set_shape(hba_t h, uint32_t threads, uint32_t ctas, uint32_t smem_bytes);
 
 /* Version string of the library. */

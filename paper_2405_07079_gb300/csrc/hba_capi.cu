@@ -101,6 +101,39 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
     }
 }
 
+// Warp mode: every warp of a CTA runs its own arenas (arena_step<32>, whose
+// barriers are __syncwarp), WPC arenas per CTA at a time.  For many small
+// arena batches, where a CTA per arena would spend its time in barriers.
+constexpr int WPC = 8;
+__global__ void __launch_bounds__(WPC * 32) k_multi_warp(Arena* ars, Rec* pool, const uint32_t* frow,
+                                                          const uint64_t* frees, uint8_t* st, const uint32_t* arow,
+                                                          const uint64_t* sizes, uint64_t* out, uint32_t* scr,
+                                                          const uint32_t* gi, uint32_t nf_total, uint32_t n_arenas,
+                                                          uint32_t warp_dyn_words, uint32_t prefilled) {
+    __shared__ hba::Smem<32> S[WPC];
+    extern __shared__ __align__(16) uint32_t dyn[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const uint32_t w = threadIdx.x >> 5;
+    uint32_t* mine = dyn + (size_t)w * warp_dyn_words;
+    for (uint32_t a = blockIdx.x * WPC + w; a < n_arenas; a += gridDim.x * WPC) {
+        const uint32_t f0 = frow[a], f1 = frow[a + 1], a0 = arow[a], a1 = arow[a + 1];
+        Arena* ar = ars + a;
+        hba::StepArgs args{ar,
+                           pool + ar->rec_base,
+                           frees + f0,
+                           f1 - f0,
+                           st ? st + f0 : nullptr,
+                           sizes + a0,
+                           a1 - a0,
+                           out + a0,
+                           scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE,
+                           gi + f0,
+                           nf_total,
+                           prefilled};
+        hba::arena_step<32>(S[w], args, mine, warp_dyn_words);
+    }
+}
+
 // Largest dynamic shared memory a CTA of k_single<NT> / k_multi<NT> can get.
 struct SmemLimits {
     uint32_t single_dyn = 0, multi_dyn = 0;  // bytes
@@ -126,15 +159,36 @@ SmemLimits set_smem_limits() {
     return L;
 }
 
-SmemLimits g_limits[5];  // for 64, 128, 256, 512, 1024 threads
+SmemLimits g_limits[6];  // for 64, 128, 256, 512, 1024 threads; [5]: warp mode (32)
 int limit_index(uint32_t threads) {
     switch (threads) {
+        case 32: return 5;
         case 64: return 0;
         case 128: return 1;
         case 256: return 2;
         case 512: return 3;
         default: return 4;
     }
+}
+
+// warp mode: k_single<32> for one arena; k_multi_warp for many (per-warp budget)
+SmemLimits set_smem_limits_warp() {
+    int dev = 0, optin = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    SmemLimits L;
+    L.alloc_words = hba::alloc_dyn_words<32>();
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_single<32>) == cudaSuccess) {
+        L.single_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_single<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn);
+    }
+    if (cudaFuncGetAttributes(&fa, k_multi_warp) == cudaSuccess) {
+        const uint32_t total = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_multi_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
+        L.multi_dyn = (total / WPC) & ~15u;  // per warp
+    }
+    return L;
 }
 
 // The prep grid of a batch, on many SMs: gathers the records every free
@@ -267,6 +321,7 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     uint32_t* scr = h->d_scr;
     cudaError_t e;
     switch (h->threads) {
+        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
         case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
         case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
         case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
@@ -300,6 +355,7 @@ hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_fr
     g_limits[2] = set_smem_limits<256>();
     g_limits[3] = set_smem_limits<512>();
     g_limits[4] = set_smem_limits<1024>();
+    g_limits[5] = set_smem_limits_warp();
     HBA_CUDA_TRY(cudaGetLastError());
     h->h_init = init;
     h->n_arenas = (uint32_t)init.size();
@@ -418,6 +474,7 @@ hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8
     const uint32_t pf = fill ? 1u : 0u;
     cudaError_t e;
     switch (h->threads) {
+        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
         case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
         case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
         case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
@@ -590,7 +647,7 @@ hba_status_t hba_export_state(hba_t h, uint32_t arena, uint64_t* host_buf, size_
 
 hba_status_t hba_set_shape(hba_t h, uint32_t threads, uint32_t ctas, uint32_t smem_bytes) {
     if (!h) return HBA_ERR_INVALID_ARGUMENT;
-    if (threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
         return HBA_ERR_INVALID_ARGUMENT;
     if (h->n_arenas == 1) h->threads = threads;
     h->m_threads = threads;
@@ -607,6 +664,22 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     if ((nf_total && !d_frees) || (na_total && (!d_sizes || !d_out))) return HBA_ERR_INVALID_ARGUMENT;
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = h->n_arenas;
+    if (h->m_threads == 32) {
+        // warp mode: WPC arenas per CTA, per-warp dynamic shared memory
+        const SmemLimits& L = g_limits[5];
+        uint32_t per = std::min(h->smem_bytes ? h->smem_bytes : 4u * L.alloc_words + 2048u, L.multi_dyn);
+        per = (std::max(per, 4u * L.alloc_words) + 15u) & ~15u;
+        const uint32_t need = (n + WPC - 1) / WPC;
+        const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, need) : need;
+        bool pdl = false;
+        const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, d_out, na_total, s, &pdl);
+        if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
+        cudaError_t e = launch_pdl(k_multi_warp, grid, WPC * 32, per * WPC, s, pdl, h->d_arenas, h->d_rec, d_free_rowptr,
+                                   d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr,
+                                   (const uint32_t*)h->d_gi, nf_total, n, per / 4, pre ? 1u : 0u);
+        if (e != cudaSuccess) return HBA_ERR_CUDA;
+        return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+    }
     const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
     const int li = limit_index(h->m_threads);
     const uint32_t base = 4 * g_limits[li].alloc_words;

@@ -70,8 +70,19 @@
 #define HBA_UNROLL _Pragma("unroll")
 #define HBA_HD __host__ __device__ __forceinline__
 #define HBA_DEV __device__ __forceinline__
-#define HBA_FOR_THREADS(tid) for (int tid = (int)threadIdx.x; tid < NT; tid += NT)
-#define HBA_SYNC() __syncthreads()
+// NT == 32 is the warp mode: each warp of a CTA runs its own arena, the
+// "barrier" is the warp's own __syncwarp and the thread index is the lane.
+#define HBA_FOR_THREADS(tid) for (int tid = hba_tid<NT>(); tid < NT; tid += NT)
+#define HBA_SYNC() hba_sync<NT>()
+template <int NT>
+__device__ __forceinline__ int hba_tid() {
+    return NT == 32 ? (int)(threadIdx.x & 31u) : (int)threadIdx.x;
+}
+template <int NT>
+__device__ __forceinline__ void hba_sync() {
+    if (NT == 32) __syncwarp();
+    else __syncthreads();
+}
 #endif
 
 // Phase-boundary hook for timing probes; compiled out unless a probe build
@@ -294,24 +305,28 @@ HBA_DEV int64_t scan_incl_i64(Smem<NT>& S, int64_t* v, int tid_emu = 0) {
     return 0;
 #else
     (void)tid_emu;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = hba_tid<NT>(), lane = tid & 31, wid = tid >> 5;
     int64_t x = v[tid];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         int64_t t = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += t;
     }
-    if (lane == 31) S.warp_tot[wid] = x;
-    __syncthreads();
-    // every warp scans the warp totals itself: no second barrier
-    int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
+    if (NT == 32) {
+        __syncwarp();
+    } else {
+        if (lane == 31) S.warp_tot[wid] = x;
+        __syncthreads();
+        // every warp scans the warp totals itself: no second barrier
+        int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int64_t u = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += u;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
+        if (wid > 0) x += before;
     }
-    const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
-    if (wid > 0) x += before;
     v[tid] = x;
     return x;
 #endif
@@ -331,7 +346,7 @@ HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
     *total = run;
     (void)S;
 #else
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = hba_tid<NT>(), lane = tid & 31, wid = tid >> 5;
     int64_t own = c[tid];
     int64_t x = own;
 #pragma unroll
@@ -339,19 +354,21 @@ HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
         int64_t t = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += t;
     }
-    if (lane == 31) S.warp_tot[wid] = x;
-    __syncthreads();
-    int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
+    if (NT > 32) {
+        if (lane == 31) S.warp_tot[wid] = x;
+        __syncthreads();
+        int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int64_t u = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += u;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
+        if (wid > 0) x += before;
     }
-    const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
-    if (wid > 0) x += before;
     c[tid] = (uint32_t)(x - own);
     if (tid == NT - 1) *total = (uint32_t)x;
-    __syncthreads();
+    hba_sync<NT>();
 #endif
 }
 

@@ -15,9 +15,9 @@ import itertools
 
 from .hba import MultiAllocator, hba_reset, hba_set_shape
 
-THREADS = (64, 128, 256, 512)
+THREADS = (32, 64, 128, 256)
 GRID_WAVES = (0, 4, 8)          # 0 = one CTA per arena; k = k CTAs per SM
-SMEM_BYTES = (0, 48 * 1024)     # 0 = default per-CTA budget
+SMEM_BYTES = (0, 24 * 1024)     # 0 = default per-CTA (per-warp in warp mode) budget
 
 
 def _sm_count():

@@ -76,7 +76,7 @@ def test_worked_examples(gpu_lib):
                 assert [int(x) for x in a.export_state()] == case["final"], case["name"]
 
 
-@pytest.mark.parametrize("threads", [128, 256, 512, 1024])
+@pytest.mark.parametrize("threads", [32, 128, 256, 512, 1024])
 def test_tiny_full(gpu_lib, threads):
     """1 MiB arena, 10,000 ops in batches of 64, canary arena untouched."""
     from paper_2405_07079_gb300 import workloads as W
@@ -221,7 +221,7 @@ def test_multi_arena_matches_per_arena_oracle(gpu_lib):
     clients = [W.Lifetimes(n_ops=10**9, batch=int(rng.integers(0, 700)), mean_life=200,
                            seed=W.BASE_SEED + 100 + i, scale=float(x) / (16 * GiB), min_size=256)
                for i, x in enumerate(sizes_a)]
-    for threads in (64, 256):
+    for threads in (32, 64, 256):
         m = MultiAllocator(sizes_a, mb, max_total_frees=1 << 16)
         m.set_shape(threads)
         orcs = [oracle.Oracle(int(x), mb) for x in sizes_a]
@@ -250,7 +250,8 @@ def test_multi_arena_matches_per_arena_oracle(gpu_lib):
         m.close()
 
 
-def test_batched_generator_matches_per_arena_oracles(gpu_lib):
+@pytest.mark.parametrize("threads", [32, 128])
+def test_batched_generator_matches_per_arena_oracles(gpu_lib, threads):
     """The batched workload (uneven arenas, U{0..2048} requests per arena per
     batch) in one multi-arena launch per batch equals, arena by arena, the
     oracle applied to that arena's sub-trace."""
@@ -265,7 +266,7 @@ def test_batched_generator_matches_per_arena_oracles(gpu_lib):
     gen = W.MultiLifetimes(A, n_batches=12, mean_life=300)
     orcs = [oracle.Oracle(int(a), 256) for a in A]
     ma = MultiAllocator(A, 256, max_total_frees=48 * 2048 + 1)
-    ma.set_shape(128, 0, 0)
+    ma.set_shape(threads, 0, 0)
     try:
         for b in range(12):
             frow, f, arow, s = gen.next_batch()
