@@ -107,6 +107,10 @@ constexpr int NBINS = 32;  // granule classes 0..28 are reachable
 // they do not fit in shared memory
 constexpr uint32_t SCRATCH_WORDS_PER_FREE = 16;
 constexpr uint32_t GATHER_WORDS = 5;
+// alloc phase: after a round that resolved at most RUN_AHEAD_DENSE lanes in
+// parallel before its event, the next RUN_AHEAD_LANES lanes go one by one
+constexpr uint32_t RUN_AHEAD_DENSE = 2;
+constexpr uint32_t RUN_AHEAD_LANES = 16;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
 constexpr uint32_t ERR_EMPTY_HEAD = 2;  // a class with its bit set had no head
@@ -236,6 +240,8 @@ struct Smem {
     // the most recent remainder X: virtual head of class xL while xok
     uint32_t xok, xg, xsz, xright, xL, xprev;
     uint32_t c0g, c0sz, c0prev;  // X when the current round classified its lanes
+    uint32_t xprev_new;  // start of the last carve resolved in parallel this round
+    Rec hc[NBINS];       // record of each list head (alloc phase), refilled asynchronously
     // loop control
     uint32_t p, r, cont, evb[2], nul, nruns, flag[3];
     uint32_t err;        // first metadata error seen by this CTA (0 = none)
@@ -289,6 +295,22 @@ HBA_DEV void prefetch_l2(const void* p) {
     (void)p;
 #else
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#endif
+}
+
+// 16-byte asynchronous copy of a record into shared memory, and the wait for
+// all of the calling thread's outstanding copies (one thread owns them).
+HBA_DEV void rec_copy_async(Rec* dst_smem, const Rec* src) {
+#ifdef HBA_EMULATE
+    *dst_smem = *src;
+#else
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+#endif
+}
+HBA_DEV void rec_copy_wait() {
+#ifndef HBA_EMULATE
+    asm volatile("cp.async.wait_all;" ::: "memory");
 #endif
 }
 
@@ -391,9 +413,14 @@ struct StepArgs {
 // Push the virtual remainder X at the head of its list and write its record
 // (one thread).
 template <int NT>
-HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec) {
+HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec, bool cache = false) {
     const uint32_t b = S.xL, old = S.heads[b];
-    str(rec, S.xg, Rec{mkx(S.xsz, ST_FREE), S.xprev, old, NIL});
+    const Rec r{mkx(S.xsz, ST_FREE), S.xprev, old, NIL};
+    str(rec, S.xg, r);
+    if (cache) {
+        rec_copy_wait();  // no copy may still be landing in the slot
+        S.hc[b] = r;
+    }
     if (old != NIL) rec[old].w = S.xg;
     S.heads[b] = S.xg;
     S.mask |= 1ull << b;
@@ -759,8 +786,9 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
             S.xL = flog2(S.xsz);
         }
     } else {
-        // pop the head of list k; the old X becomes a listed block first
-        if (S.xok) materialize_x<NT>(S, rec);
+        // pop the head of list k (its record is cached); the old X becomes a
+        // listed block first
+        if (S.xok) materialize_x<NT>(S, rec, true);
         const uint32_t Y = S.heads[k];
         if (Y >= S.G) {  // bitmap and heads disagree: record, fail the request
             S.err = ERR_EMPTY_HEAD;
@@ -769,11 +797,16 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
             single_add(S, C_AFAIL, 1);
             return;
         }
-        const Rec ry = ldr(rec, Y);
+        rec_copy_wait();
+        const Rec ry = S.hc[k];
         const uint32_t nxt = ry.z;
         S.heads[k] = nxt;
-        if (nxt == NIL) S.mask &= ~(1ull << k);
-        else rec[nxt].w = NIL;
+        if (nxt == NIL) {
+            S.mask &= ~(1ull << k);
+        } else {
+            rec[nxt].w = NIL;
+            rec_copy_async(&S.hc[k], rec + nxt);  // the new head, for a later pop
+        }
         const uint32_t ysz = sz_of(ry.x);
         str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
         a.out[i] = (uint64_t)Y << S.lg;
@@ -836,6 +869,9 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             S.ccl = reinterpret_cast<uint8_t*>(d + 6 * NT + NT / 4 + 4);
             S.p = 0;
             S.xok = 0;
+            // the record of every list head, for the pops of this phase
+            for (int b = 0; b < NBINS; ++b)
+                if (S.heads[b] != NIL) rec_copy_async(&S.hc[b], rec + S.heads[b]);
         }
     }
     HBA_SYNC();
@@ -963,8 +999,10 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             HBA_PROF(14);
             const uint32_t ev = *evp;
             const uint32_t nres = ev < n_here ? ev : n_here;   // lanes [r, nres) are exact
-            const uint32_t upd = nres < n_here ? nres : n_here - 1;
-            // C: resolve [r, nres); lane `upd` advances X and applies the event
+            // the lane that reports the last carve resolved in parallel: the
+            // event lane (nearest carve below it), or the last lane
+            const uint32_t wl = nres < (uint32_t)NT ? nres : (uint32_t)NT - 1;
+            // C: resolve [r, nres) in parallel (failures, carves from X)
             HBA_FOR_THREADS(tid) {
                 const uint8_t cl = S.cls[tid];
                 const bool act = (uint32_t)tid < nres;   // lanes below r have class NONE
@@ -981,18 +1019,23 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                 warp_count(S, tid, C_AFAIL, is_fail);
                 warp_count(S, tid, C_AOK, is_carve);
                 warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
-                if ((uint32_t)tid == upd) {
+                if ((uint32_t)tid == wl) S.xprev_new = (wl < nres && is_carve) ? start : prev;
+            }
+            HBA_SYNC();
+            // D: one thread advances X, applies the event lane alone and, when
+            // this round resolved (almost) nothing in parallel, runs ahead
+            // through the next lanes one by one (cheaper than rounds there)
+            HBA_FOR_THREADS(tid) {
+                if (tid == 0) {
                     const int64_t gave = nres ? S.val[nres - 1] : 0;
                     if (gave > 0) {
-                        // the last carve of the round: this lane, or the one before it
-                        const uint32_t last = (nres == n_here && is_carve) ? start : prev;
                         S.xg = S.c0g + (uint32_t)gave;
                         S.xsz = S.c0sz - (uint32_t)gave;
-                        S.xprev = last;
+                        S.xprev = S.xprev_new;
                         single_add(S, C_USEDG, gave);
                         if (S.xsz == 0) {
                             S.xok = 0;
-                            if (S.xright < S.G) rec[S.xright].y = last;
+                            if (S.xright < S.G) rec[S.xright].y = S.xprev;
                             single_add(S, C_NOSPLIT, 1);
                         } else {
                             S.xL = flog2(S.xsz);
@@ -1002,6 +1045,11 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     if (nres < n_here) {
                         seq_request<NT>(S, a, p + nres, S.s64[nres], S.sgr[nres], S.ccl[nres]);
                         next = nres + 1;
+                        if (nres - r <= RUN_AHEAD_DENSE) {
+                            const uint32_t stop = next + RUN_AHEAD_LANES < n_here ? next + RUN_AHEAD_LANES : n_here;
+                            for (; next < stop; ++next)
+                                seq_request<NT>(S, a, p + next, S.s64[next], S.sgr[next], S.ccl[next]);
+                        }
                     }
                     S.r = next;
                     S.cont = next < n_here;
@@ -1026,7 +1074,10 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_FOR_THREADS(tid) {
-        if (tid == 0 && S.xok) materialize_x<NT>(S, rec);
+        if (tid == 0) {
+            if (S.xok) materialize_x<NT>(S, rec);
+            rec_copy_wait();  // no copy may land in shared memory after this arena
+        }
     }
     HBA_SYNC();
     HBA_PROF(18);
