@@ -372,6 +372,69 @@ def run_multi(args, rank, world, local_rank):
     return line
 
 
+def run_serve(args, rank, world, local_rank):
+    """The serving form: one 80 GiB arena of 16 KiB pages, Poisson arrivals
+    (sweep of rates), malloc of U{1..512} pages held Exp(20 ms), admission by
+    free memory with a 1M-deep queue; the loop runs on the device."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator, hba_step, log_batches, serve, workloads
+    from paper_2405_07079_gb300.hba import _ptr
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    arena, page = 80 << 30, 16 << 10
+    sweep = []
+    plain = None
+    lams = [float(x) * 1e6 for x in args.lams.split(",")]
+    for li, lam in enumerate(lams):
+        arr = workloads.serving_arrivals(lam, args.serve_seconds)
+        with Allocator(arena, page, threads=256) as a:
+            served, log, rep = serve(a, arr)
+        adm = served[:, 0] != np.uint64(0xFFFFFFFFFFFFFFFE)
+        lat = (served[adm, 1] - arr[adm, 0]).astype(np.float64) / 1e3
+        ops = rep["alloc_ok"] + rep["alloc_fail"] + rep["frees"]
+        sec = rep["elapsed_ns"] / 1e9
+        sweep.append({"lambda_req_s": lam, "arrivals": rep["arrivals"], "admitted": rep["admitted"],
+                      "rejected": rep["rejected"], "alloc_ok": rep["alloc_ok"], "alloc_fail": rep["alloc_fail"],
+                      "frees": rep["frees"], "ticks": rep["ticks"], "max_queue": rep["max_queue"],
+                      "elapsed_s": sec, "ops_per_s": ops / sec, "admitted_per_s": rep["admitted"] / sec,
+                      "p50_us": float(np.percentile(lat, 50)) if lat.size else None,
+                      "p99_us": float(np.percentile(lat, 99)) if lat.size else None, "status": rep["status"]})
+        if li == 0:
+            # the plain form on the same batches: one launch per logged tick
+            ticks = log_batches(log)
+            dt = []
+            for fid, aid in ticks:
+                f = torch.from_numpy(served[fid, 0].view(np.int64)).to(dev)
+                s_ = torch.from_numpy(arr[aid, 1].view(np.int64)).to(dev)
+                dt.append((f, s_, torch.empty(max(aid.size, 1), dtype=torch.int64, device=dev), aid))
+            stream = torch.cuda.current_stream()
+            with Allocator(arena, page, threads=256) as pa:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for f, s_, o, aid in dt:
+                    hba_step(pa.h, _ptr(f), f.numel(), 0, _ptr(s_), s_.numel(), _ptr(o), int(stream.cuda_stream))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                pms = e0.elapsed_time(e1)
+                equal = all(np.array_equal(o[:aid.size].cpu().numpy().view(np.uint64), served[aid, 0]) for f, s_, o, aid in dt)
+            plain = {"lambda_req_s": lam, "ticks": len(dt), "ops_per_s": ops / (pms / 1e3), "elapsed_s": pms / 1e3,
+                     "results_equal": bool(equal)}
+    best = max(sweep, key=lambda r: r["ops_per_s"])
+    return {
+        "metric": METRIC, "value": best["ops_per_s"], "unit": UNIT, "n_gpus": world, "steps": len(sweep),
+        "warmup": 0, "ms_per_step": 1e3 * best["elapsed_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"serving: 80 GiB arena of 16 KiB pages, Poisson arrivals {args.lams} M req/s for "
+                               f"{args.serve_seconds} s each, U{{1..512}} pages held Exp(20 ms), queue 1M",
+                   "form": "serving loop: one persistent CTA, device-resident queue and timing wheel"},
+        "latency_us": {"p50": best["p50_us"], "p99": best["p99_us"], "unit": "arrival to result, admitted requests",
+                       "at_lambda": best["lambda_req_s"]},
+        "sweep": sweep, "plain_form_same_batches": plain, "gpu_launches": len(sweep),
+    }
+
+
 def alloc_threads(args):
     return args.threads or 1024
 
@@ -439,7 +502,9 @@ def main():
     ap.add_argument("--steps", type=int, default=1530)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["large", "tiny", "frag", "multi"], default="large")
+    ap.add_argument("--workload", choices=["large", "tiny", "frag", "multi", "serve"], default="large")
+    ap.add_argument("--lams", default="1,2,5,10,20,50")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--arenas", type=int, default=4096)
     ap.add_argument("--batches", type=int, default=200)
     ap.add_argument("--plain-arenas", type=int, default=64)
@@ -456,7 +521,9 @@ def main():
             import torch
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        if args.workload == "multi":
+        if args.workload == "serve":
+            line = run_serve(args, rank, world, local_rank)
+        elif args.workload == "multi":
             if args.steps == 1530:
                 args.steps = 0  # one pass over the recorded batches
             line = run_multi(args, rank, world, local_rank)

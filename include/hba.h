@@ -216,6 +216,66 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
  * autotuner or by hand. */
 hba_status_t hba_set_shape(hba_t h, uint32_t threads, uint32_t ctas, uint32_t smem_bytes);
 
+/* ---- the serving loop --------------------------------------------------- */
+
+/* One request of an open-loop stream. */
+typedef struct {
+    uint64_t t_arrive_ns; /* arrival time from the start of the run; non-decreasing */
+    uint64_t bytes;       /* size to allocate */
+    uint64_t hold_ns;     /* how long the block is held before it is freed */
+} hba_arrival_t;
+
+/* What happened to one request. */
+typedef struct {
+    uint64_t offset;    /* the block, HBA_FAIL (allocation failed) or HBA_REJECTED (queue full) */
+    uint64_t t_done_ns; /* device time of the result; 0 = never reached (run stopped first) */
+    uint64_t t_free_ns; /* device time of its free; 0 = still held when the run ended */
+} hba_served_t;
+
+#define HBA_REJECTED ((uint64_t)~1ull)
+
+typedef struct {
+    uint32_t queue_depth;  /* admission queue capacity; 0 = 1,048,576 */
+    uint32_t max_batch;    /* most frees and most allocations per tick; 0 = 4,096 */
+    uint64_t bucket_ns;    /* width of a free-timing bucket; 0 = 262,144 ns */
+    uint64_t time_limit_ns;/* stop after this much device time; 0 = 60 s */
+    uint64_t max_ticks;    /* and after this many ticks; 0 = no limit */
+} hba_serve_config_t;
+
+typedef struct {
+    uint64_t arrivals, admitted, rejected;  /* requests taken, admitted, rejected (queue full) */
+    uint64_t alloc_ok, alloc_fail, frees;   /* allocator operations applied */
+    uint64_t ticks, idle_ticks, max_queue;  /* loop iterations; the deepest queue */
+    uint64_t elapsed_ns;                    /* device time of the run */
+    uint64_t status;      /* 0 done, 1 time limit, 2 free-timing wheel full, 3 tick limit */
+    uint64_t log_words;   /* words of the tick log (more than log_cap: the log is incomplete) */
+} hba_serve_report_t;
+
+/* Serve an open-loop request stream on a single-arena handle with all
+ * allocator state on the device.  No counterpart in the paper (§6 runs one
+ * request at a time from the host); the allocation policy is the same
+ * (§5.1 Algorithms 4 and 5, through the same batch engine as hba_step).
+ *
+ * One persistent CTA runs ticks: it takes every request whose arrival time
+ * has come (device %globaltimer) into a ring-buffer queue of queue_depth,
+ * rejecting those that find it full; frees every block whose hold has ended
+ * (timing by buckets of bucket_ns: a free happens at the first tick after
+ * its bucket has ended); admits requests from the queue head while their
+ * rounded sizes fit in the free memory; applies the tick's frees then its
+ * allocations as one batch.  A request that arrives while a tick runs joins
+ * the next one.
+ *
+ * d_arrivals: device hba_arrival_t[n].  d_served: device hba_served_t[n],
+ * written by the call.  d_log (device uint32, log_cap words, may be NULL
+ * with log_cap 0): per tick [nf, na, nf request ids freed, na ids admitted],
+ * so that the run can be replayed exactly.  Allocates its working buffers
+ * (queue, timing wheel, tick buffers: about 90 MB at the defaults) at the
+ * start and frees them at the end; synchronous.  Returns HBA_ERR_STATE if
+ * the timing wheel overflowed (report.status 2). */
+hba_status_t hba_serve_run(hba_t h, const hba_arrival_t* d_arrivals, uint64_t n, hba_served_t* d_served,
+                           uint32_t* d_log, uint64_t log_cap, const hba_serve_config_t* cfg,
+                           hba_serve_report_t* report, hba_stream_t stream);
+
 /* Version string of the library. */
 const char* hba_version(void);
 

@@ -34,6 +34,7 @@ SIGNATURES = {
     "hba_multi_create": (i32, [u32, vp, u64, i32, u32, vp]),
     "hba_multi_step": (i32, [vp, vp, vp, u32, vp, vp, u32, vp, vp, vp]),
     "hba_set_shape": (i32, [vp, u32, u32, u32]),
+    "hba_serve_run": (i32, [vp, vp, u64, vp, vp, u64, vp, vp, vp]),
     "hba_version": (ctypes.c_char_p, []),
 }
 
@@ -49,6 +50,20 @@ class Stats(ctypes.Structure):
         "alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes", "used_blocks", "blocks",
         "requested_bytes", "free_bytes", "largest_free", "bitmask", "arena_bytes")] + [
         ("n_arenas", ctypes.c_uint32), ("device_error", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("queue_depth", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("bucket_ns", ctypes.c_uint64),
+                ("time_limit_ns", ctypes.c_uint64), ("max_ticks", ctypes.c_uint64)]
+
+
+class ServeReport(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "arrivals", "admitted", "rejected", "alloc_ok", "alloc_fail", "frees", "ticks", "idle_ticks",
+        "max_queue", "elapsed_ns", "status", "log_words")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

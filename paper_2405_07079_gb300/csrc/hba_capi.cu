@@ -14,6 +14,7 @@
 
 #include "hba.h"
 #include "hba_engine.cuh"
+#include "hba_serve.cuh"
 
 using hba::Arena;
 using hba::Rec;
@@ -407,6 +408,98 @@ bool check_geometry(uint64_t arena_bytes, uint64_t min_block, uint32_t* lg, uint
     return G >= 1 && G <= hba::MAX_GRANULES;
 }
 
+// ---- the serving loop ----------------------------------------------------
+constexpr int SERVE_NT = 256;
+__global__ void __launch_bounds__(SERVE_NT) k_serve(hba::ServeArgs g, uint32_t dyn_words) {
+    __shared__ hba::Smem<SERVE_NT> S;
+    __shared__ hba::ServeSmem<SERVE_NT> Q;
+    extern __shared__ __align__(16) uint32_t dyn[];
+    hba::serve_loop<SERVE_NT>(S, Q, g, dyn, dyn_words);
+}
+
+static_assert(sizeof(hba_arrival_t) == sizeof(hba::Arrival), "arrival layout");
+static_assert(sizeof(hba_served_t) == sizeof(hba::Served), "served layout");
+static_assert(sizeof(hba_serve_report_t) == sizeof(hba::ServeCtl), "report layout");
+static_assert(HBA_REJECTED == hba::REJECTED64, "rejected marker");
+
+hba_status_t serve_impl(hba_t h, const hba_arrival_t* arr, uint64_t n, hba_served_t* served, uint32_t* log,
+                        uint64_t log_cap, const hba_serve_config_t* cfg, hba_serve_report_t* rep, cudaStream_t s) {
+    if (!h || h->n_arenas != 1 || !rep || (n && (!arr || !served)) || n >= 0xFFFFFFFFull || (log_cap && !log))
+        return HBA_ERR_INVALID_ARGUMENT;
+    hba_serve_config_t c = cfg ? *cfg : hba_serve_config_t{};
+    if (!c.queue_depth) c.queue_depth = 1u << 20;
+    if (!c.max_batch) c.max_batch = 4096;
+    if (!c.bucket_ns) c.bucket_ns = 262144;
+    if (!c.time_limit_ns) c.time_limit_ns = 60ull * 1000000000ull;
+    const uint32_t W = 4096, C = c.max_batch;
+    hba::ServeArgs g{};
+    g.ar = h->d_arenas;
+    g.rec = h->d_rec;
+    g.arr = reinterpret_cast<const hba::Arrival*>(arr);
+    g.n = n;
+    g.served = reinterpret_cast<hba::Served*>(served);
+    g.log = log;
+    g.log_cap = log_cap;
+    g.qcap = c.queue_depth;
+    g.W = W;
+    g.C = C;
+    g.bucket_ns = c.bucket_ns;
+    g.max_batch = c.max_batch;
+    g.time_limit_ns = c.time_limit_ns;
+    g.max_ticks = c.max_ticks;
+    std::vector<void*> bufs;
+    auto get = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        bufs.push_back(p);
+        return p;
+    };
+    const size_t mb = c.max_batch;
+    g.queue = (uint32_t*)get(4ull * g.qcap);
+    g.wheel = (uint32_t*)get(4ull * W * C);
+    g.wheel_cnt = (uint32_t*)get(4ull * W);
+    g.t_frees = (uint64_t*)get(8 * mb);
+    g.t_fid = (uint32_t*)get(4 * mb);
+    g.t_sizes = (uint64_t*)get(8 * mb);
+    g.t_aid = (uint32_t*)get(4 * mb);
+    g.t_out = (uint64_t*)get(8 * mb);
+    g.gi = (uint32_t*)get(4 * hba::GATHER_WORDS * mb);
+    g.scr = (uint32_t*)get(4 * hba::SCRATCH_WORDS_PER_FREE * mb);
+    g.ctl = (hba::ServeCtl*)get(sizeof(hba::ServeCtl));
+    hba_status_t r = HBA_OK;
+    for (void* p : bufs) if (!p) r = HBA_ERR_OUT_OF_MEMORY;
+    if (bufs.size() != 11) r = HBA_ERR_OUT_OF_MEMORY;
+    if (r == HBA_OK) {
+        static SmemLimits L{};
+        static bool have = false;
+        if (!have) {
+            int dev = 0, optin = 48 * 1024;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, k_serve) == cudaSuccess) {
+                L.single_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+                cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn);
+            }
+            have = true;
+        }
+        const uint32_t dyn = std::max<uint32_t>(L.single_dyn, 4 * hba::alloc_dyn_words<SERVE_NT>());
+        if (cudaMemsetAsync(g.wheel_cnt, 0, 4ull * W, s) != cudaSuccess ||
+            cudaMemsetAsync(g.ctl, 0, sizeof(hba::ServeCtl), s) != cudaSuccess ||
+            (n && cudaMemsetAsync(served, 0, sizeof(hba_served_t) * n, s) != cudaSuccess))
+            r = HBA_ERR_CUDA;
+        if (r == HBA_OK) {
+            k_serve<<<1, SERVE_NT, dyn, s>>>(g, dyn / 4);
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) r = HBA_ERR_CUDA;
+        }
+        if (r == HBA_OK && cudaMemcpy(rep, g.ctl, sizeof(hba::ServeCtl), cudaMemcpyDeviceToHost) != cudaSuccess)
+            r = HBA_ERR_CUDA;
+        if (r == HBA_OK && rep->status == hba::SERVE_WHEEL_FULL) r = HBA_ERR_STATE;
+    }
+    for (void* p : bufs) cudaFree(p);
+    return r;
+}
+
 // ---- batches that allocate nothing (hba_step_static) ----------------------
 // Scratch for HBA_STATIC_MAX_FREES frees: the gathered records, then the
 // free phase's global working arrays.  One array per device, shared by all
@@ -488,6 +581,12 @@ hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8
 }  // namespace
 
 extern "C" {
+
+hba_status_t hba_serve_run(hba_t h, const hba_arrival_t* d_arrivals, uint64_t n, hba_served_t* d_served,
+                           uint32_t* d_log, uint64_t log_cap, const hba_serve_config_t* cfg,
+                           hba_serve_report_t* report, hba_stream_t stream) {
+    return serve_impl(h, d_arrivals, n, d_served, d_log, log_cap, cfg, report, (cudaStream_t)stream);
+}
 
 hba_status_t hba_step_static(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status,
                              const uint64_t* d_sizes, uint32_t na, uint64_t* d_out_offsets, hba_stream_t stream) {

@@ -12,7 +12,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import HbaError, Stats, check, load
+from ._lib import HbaError, ServeConfig, ServeReport, Stats, check, load
 
 HBA_FAIL = 0xFFFFFFFFFFFFFFFF
 HBA_POLICY_SEGFIT = 0
@@ -100,6 +100,47 @@ def hba_multi_step(h: int, d_free_rowptr: int, d_frees: int, nf_total: int, d_al
 
 def hba_set_shape(h: int, threads: int, ctas: int = 0, smem_bytes: int = 0) -> None:
     check("hba_set_shape", _lib().hba_set_shape(h, threads, ctas, smem_bytes))
+
+
+HBA_REJECTED = 0xFFFFFFFFFFFFFFFE
+
+
+def hba_serve_run(h: int, d_arrivals: int, n: int, d_served: int, d_log: int, log_cap: int,
+                  queue_depth: int = 0, max_batch: int = 0, bucket_ns: int = 0, time_limit_ns: int = 0,
+                  max_ticks: int = 0, stream: int = 0) -> dict:
+    cfg = ServeConfig(queue_depth, max_batch, bucket_ns, time_limit_ns, max_ticks)
+    rep = ServeReport()
+    check("hba_serve_run", _lib().hba_serve_run(h, d_arrivals, n, d_served, d_log, log_cap, ctypes.byref(cfg),
+                                                ctypes.byref(rep), stream))
+    return rep.as_dict()
+
+
+def serve(alloc: "Allocator", arrivals: np.ndarray, log_cap: int | None = None, **cfg):
+    """Run the serving loop on ``arrivals`` (uint64[n, 3]: arrival ns, bytes,
+    hold ns).  Returns ``(served uint64[n, 3], log uint32[], report)``."""
+    torch = _torch()
+    arr = np.ascontiguousarray(arrivals, dtype=np.uint64).reshape(-1, 3)
+    n = arr.shape[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_arr = torch.from_numpy(arr.view(np.int64)).to(dev)
+    d_served = torch.empty((max(n, 1), 3), dtype=torch.int64, device=dev)
+    cap = log_cap if log_cap is not None else 4 * n + 1024
+    d_log = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    rep = hba_serve_run(alloc.h, _ptr(d_arr), n, _ptr(d_served), _ptr(d_log), cap, **cfg,
+                        stream=_stream_ptr(None))
+    served = d_served[:n].cpu().numpy().view(np.uint64)
+    log = d_log[:min(cap, rep["log_words"])].cpu().numpy().view(np.uint32)
+    return served, log, rep
+
+
+def log_batches(log: np.ndarray):
+    """Split a serving tick log into (free ids, alloc ids) per tick."""
+    out, i = [], 0
+    while i + 2 <= log.size:
+        nf, na = int(log[i]), int(log[i + 1])
+        out.append((log[i + 2:i + 2 + nf], log[i + 2 + nf:i + 2 + nf + na]))
+        i += 2 + nf + na
+    return out
 
 
 def hba_version() -> str:
@@ -203,4 +244,5 @@ class MultiAllocator:
 
 
 __all__ = [n for n in dir() if n.startswith("hba_")] + ["Allocator", "MultiAllocator", "HbaError", "HBA_FAIL",
-                                                          "HBA_STATIC_MAX_FREES"]
+                                                          "HBA_STATIC_MAX_FREES", "HBA_REJECTED", "serve",
+                                                          "log_batches"]

@@ -333,6 +333,24 @@ class MultiLifetimes:
         self.offs = np.insert(self.offs, pos, no)
 
 
+def serving_arrivals(lam: float, seconds: float, page=16 * KiB, max_pages=512, hold_mean_ns=20e6,
+                     seed=BASE_SEED + 5):
+    """Open-loop requests: Poisson arrivals at ``lam`` per second for
+    ``seconds``; each a malloc of U{1..max_pages} pages held for an
+    exponential time (mean ``hold_mean_ns``), then freed.  uint64[n, 3]:
+    arrival ns, bytes, hold ns."""
+    n = int(lam * seconds * 1.1) + 16
+    idx = np.arange(n)
+    gaps = -np.log1p(-Stream(seed, "gap").unif(idx)) / lam * 1e9
+    t = np.floor(np.cumsum(gaps)).astype(np.uint64)
+    keep = t < np.uint64(seconds * 1e9)
+    t = t[keep]
+    m = t.size
+    pages = 1 + np.floor(Stream(seed, "pages").unif(idx[:m]) * max_pages).astype(np.uint64)
+    hold = np.floor(-np.log1p(-Stream(seed, "hold").unif(idx[:m])) * hold_mean_ns).astype(np.uint64)
+    return np.stack([t, pages * np.uint64(page), np.maximum(hold, 1)], axis=1).astype(np.uint64)
+
+
 def multi_arena_sizes(n_arenas=4096, lo=64 * MiB, hi=1 * GiB, granule=256, seed=BASE_SEED + 4):
     """Arena sizes log-uniform in [lo, hi], rounded down to the granule."""
     s = log_uniform(Stream(seed, "arena").unif(np.arange(n_arenas)), lo, hi)
