@@ -394,7 +394,7 @@ def run_serve(args, rank, world, local_rank):
         adm = served[:, 0] != np.uint64(0xFFFFFFFFFFFFFFFE)
         lat = (served[adm, 1] - arr[adm, 0]).astype(np.float64) / 1e3
         ops = rep["alloc_ok"] + rep["alloc_fail"] + rep["frees"]
-        sec = rep["elapsed_ns"] / 1e9
+        sec = max(rep["elapsed_ns"], 1) / 1e9
         sweep.append({"lambda_req_s": lam, "arrivals": rep["arrivals"], "admitted": rep["admitted"],
                       "rejected": rep["rejected"], "alloc_ok": rep["alloc_ok"], "alloc_fail": rep["alloc_fail"],
                       "frees": rep["frees"], "ticks": rep["ticks"], "max_queue": rep["max_queue"],

@@ -4,6 +4,7 @@
 // engine of hba_engine.cuh: one CTA per arena per batch.  No call here ever
 // receives, reads or writes the managed arena itself.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -420,6 +421,13 @@ __global__ void __launch_bounds__(SERVE_NT) k_serve(hba::ServeArgs g, uint32_t d
 static_assert(sizeof(hba_arrival_t) == sizeof(hba::Arrival), "arrival layout");
 static_assert(sizeof(hba_served_t) == sizeof(hba::Served), "served layout");
 static_assert(sizeof(hba_serve_report_t) == sizeof(hba::ServeCtl), "report layout");
+static_assert(offsetof(hba_serve_report_t, idle_ticks) == offsetof(hba::ServeCtl, idle_ticks) &&
+                  offsetof(hba_serve_report_t, status) == offsetof(hba::ServeCtl, status) &&
+                  offsetof(hba_serve_report_t, log_words) == offsetof(hba::ServeCtl, log_words),
+              "report field order");
+static_assert(offsetof(hba_arrival_t, hold_ns) == offsetof(hba::Arrival, hold_ns) &&
+                  offsetof(hba_served_t, t_free_ns) == offsetof(hba::Served, t_free_ns),
+              "arrival / served field order");
 static_assert(HBA_REJECTED == hba::REJECTED64, "rejected marker");
 
 hba_status_t serve_impl(hba_t h, const hba_arrival_t* arr, uint64_t n, hba_served_t* served, uint32_t* log,

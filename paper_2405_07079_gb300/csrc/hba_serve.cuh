@@ -36,9 +36,12 @@ struct Served {
 };
 constexpr uint64_t REJECTED64 = ~1ull;
 
+// same layout as hba_serve_report_t
 struct ServeCtl {
-    uint64_t arrivals, admitted, rejected, alloc_ok, alloc_fail, frees, ticks, max_queue;
-    uint64_t elapsed_ns, status, log_words, idle_ticks;
+    uint64_t arrivals, admitted, rejected;
+    uint64_t alloc_ok, alloc_fail, frees;
+    uint64_t ticks, idle_ticks, max_queue;
+    uint64_t elapsed_ns, status, log_words;
 };
 constexpr uint64_t SERVE_OK = 0, SERVE_TIMEOUT = 1, SERVE_WHEEL_FULL = 2, SERVE_TICK_LIMIT = 3;
 
