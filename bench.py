@@ -51,6 +51,10 @@ BYTES_ALLOC_FAIL = 16
 BYTES_FREE_OK = 216
 BYTES_FREE_REJECTED = 9
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per k_single<1024> launch on the large workload,
+# from an ncu capture of this kernel (profiles/k_single_large16GiB.txt); to
+# be retaken whenever the kernel changes.
+K_SINGLE_LARGE_DRAM_BYTES = 154_112
 
 
 def _peaks():
@@ -236,7 +240,8 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
                    "ops_per_step_mean": ops / max(1, args.steps)},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": achieved_gbs / peak, "traffic": None,
+                     "frac": achieved_gbs / peak,
+                     "traffic": K_SINGLE_LARGE_DRAM_BYTES if args.workload == "large" and alloc_threads(args) == 1024 else None,
                      "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_prep + k_single<1024>",
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
