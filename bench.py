@@ -142,12 +142,73 @@ def record_trace(wl, alloc, dev):
         nbytes = (BYTES_ALLOC_OK * n_ok + BYTES_ALLOC_FAIL * (s.size - n_ok)
                   + BYTES_FREE_OK * n_fok + BYTES_FREE_REJECTED * (f.size - n_fok))
         batches.append({"f": df, "s": ds, "out": out, "st": st, "nf": f.size, "na": s.size,
+                        "host": (f, stat, s, o),
                         "ops": f.size + s.size, "bytes": nbytes,
                         # engine launch, plus the prep grid when there are frees or many allocations
                         "launches": 1 + int(f.size > 0 or s.size >= 2048),
                         "hf": torch.from_numpy(f.view(np.int64).copy()).pin_memory(),
                         "hs": torch.from_numpy(s.view(np.int64).copy()).pin_memory()})
     return batches
+
+
+def reduce_over_ranks(maxes, sums, world: int, device=None):
+    """Whole-job figures of independent replicas: the MAX over ranks of each
+    time in ``maxes`` and the SUM of each count in ``sums`` (all_reduce on the
+    default process group; identity for one rank).  Returns two float lists."""
+    if world <= 1:
+        return [float(x) for x in maxes], [float(x) for x in sums]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x) for x in maxes], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
+
+
+def cuda_allocator_comparison(batches, alloc, flush, stream, max_ops: int = 60_000) -> dict:
+    """The same operations through cudaMalloc/cudaFree and cudaMallocAsync/
+    cudaFreeAsync (host-timed per call), beside this allocator on the same
+    batches (device-timed per batch).  Sample: the longest prefix of the trace
+    whose served allocations plus applied frees stay within ``max_ops``."""
+    import torch
+
+    from paper_2405_07079_gb300 import cuda_replay
+
+    nb, served = 0, 0
+    for b in batches:
+        f, st, s, o = b["host"]
+        k = int((st == 0).sum()) + int((o != FAIL).sum())
+        if nb and served + k > max_ops:
+            break
+        nb += 1; served += k
+    ops = cuda_replay.trace_ops(b["host"] for b in batches[:nb])
+    res = {"sample": f"batches 0..{nb - 1} of the trace from an empty arena: their applied frees and "
+                     f"served allocations in batch order ({ops.size} ops); failed allocations and "
+                     "rejected frees are not replayed", "unit": UNIT}
+    sptr = int(stream.cuda_stream)
+    for mode in ("cudaMalloc", "cudaMallocAsync"):
+        torch.cuda.synchronize()
+        res[mode] = cuda_replay.replay(ops, mode, sptr)
+    alloc.reset()
+    ms = []
+    for b in batches[:nb]:
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        alloc.step(b["f"] if b["nf"] else None, b["s"] if b["na"] else None, out=b["out"], status=b["st"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = sum(ms) / 1e3
+    reqs = sum(b["ops"] for b in batches[:nb])
+    res["this_allocator"] = {"value": ops.size / t, "unit": UNIT, "ops": int(ops.size), "requests": reqs,
+                             "requests_per_s": reqs / t, "ms_per_batch": 1e3 * t / nb,
+                             "note": "device time of the batches that served these ops, failed requests included"}
+    res["ratio_vs_cudaMalloc"] = res["this_allocator"]["value"] / res["cudaMalloc"]["value"]
+    res["ratio_vs_cudaMallocAsync"] = res["this_allocator"]["value"] / res["cudaMallocAsync"]["value"]
+    return res
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -215,16 +276,11 @@ def run_gpu(args, rank, world, local_rank):
         e2e_ops += b["ops"]; e2e_h2d += 8 * (b["nf"] + b["na"]); e2e_d2h += 8 * b["na"]
     e2e_s = time.perf_counter() - t0
 
-    if world > 1:
-        t = torch.tensor([busy_s, e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        busy_s, e2e_s = float(t[0]), float(t[1])
-        o = torch.tensor([ops, e2e_ops], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(o, op=torch.distributed.ReduceOp.SUM)
-        ops_all, e2e_all = float(o[0]), float(o[1])
-    else:
-        ops_all, e2e_all = float(ops), float(e2e_ops)
+    (busy_s, e2e_s), (ops_all, e2e_all) = reduce_over_ranks([busy_s, e2e_s], [ops, e2e_ops], world, dev)
     stats = alloc.stats()
+    cuda_cmp = None
+    if rank == 0 and not args.no_cuda_baseline:
+        cuda_cmp = cuda_allocator_comparison(batches, alloc, flush, stream)
     alloc.close()
     if rank != 0:
         return None
@@ -252,6 +308,8 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks.summary(),
         "final_stats": {k: stats[k] for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail")},
     }
+    if cuda_cmp is not None:
+        line["cuda_allocators"] = cuda_cmp
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     return line
@@ -309,6 +367,8 @@ def run_multi(args, rank, world, local_rank):
     steps = args.steps if args.steps else nb
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     idx = []
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clocks:
         for k in range(steps):
@@ -320,10 +380,13 @@ def run_multi(args, rank, world, local_rank):
             ev[k][1].record(stream)
             idx.append(pos); pos += 1
         torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     busy_s = sum(step_ms) / 1e3
     ops = sum(batches[i]["ops"] for i in idx)
     nbytes = sum(batches[i]["bytes"] for i in idx)
+    (busy_all,), (ops_all,) = reduce_over_ranks([busy_s], [ops], world, dev)
 
     # the plain form on the same requests: the first P arenas, one handle and
     # one launch per arena per batch; results must equal the batched form's
@@ -350,16 +413,18 @@ def run_multi(args, rank, world, local_rank):
     for a in plain:
         a.close()
     ma.close()
+    if rank != 0:
+        return None
     peak, peak_src = _peaks()
     achieved = nbytes / busy_s / 1e9
     lat = sorted(step_ms)
     line = {
-        "metric": METRIC, "value": ops / busy_s, "unit": UNIT, "n_gpus": world, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * busy_s / steps, "higher_is_better": True,
+        "metric": METRIC, "value": ops_all / busy_all, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * busy_all / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
                                f"min block 256 B, U{{0..2048}} requests per arena per batch, {nb} batches",
-                   "form": "batched: prep grid + one multi-arena launch per batch",
+                   "form": "batched: prep grid + one multi-arena launch per batch", "parallelism": f"replicas x{world}",
                    "shape": {"threads": best[0], "ctas": best[1], "smem_bytes": best[2]},
                    "l2": "flushed between steps (256 MiB write, untimed)", "ops_per_step_mean": ops / steps,
                    "record_s": round(t_rec, 1)},
@@ -427,13 +492,18 @@ def run_serve(args, rank, world, local_rank):
             plain = {"lambda_req_s": lam, "ticks": len(dt), "ops_per_s": ops / (pms / 1e3), "elapsed_s": pms / 1e3,
                      "results_equal": bool(equal)}
     best = max(sweep, key=lambda r: r["ops_per_s"])
+    (sec_all,), (ops_all,) = reduce_over_ranks([best["elapsed_s"]], [best["ops_per_s"] * best["elapsed_s"]], world,
+                                               torch.device("cuda", local_rank))
+    if rank != 0:
+        return None
     return {
-        "metric": METRIC, "value": best["ops_per_s"], "unit": UNIT, "n_gpus": world, "steps": len(sweep),
-        "warmup": 0, "ms_per_step": 1e3 * best["elapsed_s"], "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": ops_all / sec_all, "unit": UNIT, "n_gpus": world, "steps": len(sweep),
+        "warmup": 0, "ms_per_step": 1e3 * sec_all, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"serving: 80 GiB arena of 16 KiB pages, Poisson arrivals {args.lams} M req/s for "
                                f"{args.serve_seconds} s each, U{{1..512}} pages held Exp(20 ms), queue 1M",
-                   "form": "serving loop: one persistent CTA, device-resident queue and timing wheel"},
+                   "form": "serving loop: one persistent CTA, device-resident queue and timing wheel",
+                   "parallelism": f"replicas x{world}"},
         "latency_us": {"p50": best["p50_us"], "p99": best["p99_us"], "unit": "arrival to result, admitted requests",
                        "at_lambda": best["lambda_req_s"]},
         "sweep": sweep, "plain_form_same_batches": plain, "gpu_launches": len(sweep),
@@ -515,6 +585,7 @@ def main():
     ap.add_argument("--plain-arenas", type=int, default=64)
     ap.add_argument("--threads", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cuda-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -2,7 +2,9 @@
 
 The library is compiled in-tree (never installed) from ``csrc/hba_capi.cu``
 and ``csrc/hba_engine.cuh``; the public header is ``include/hba.h`` at the
-repository root.
+repository root.  ``_build/libcuda_replay.so`` (host code only, from
+``csrc/cuda_replay.cu``) replays traces through the CUDA runtime's own
+allocators for the benchmark's comparison; it is compiled alongside.
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhba.so")
 SOURCES = [os.path.join(CSRC, "hba_capi.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "hba_engine.cuh"), os.path.join(ROOT, "include", "hba.h")]
+REPLAY_LIB = os.path.join(BUILD, "libcuda_replay.so")
+REPLAY_SOURCES = [os.path.join(CSRC, "cuda_replay.cu")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -36,14 +40,20 @@ def stale(target: str, deps) -> bool:
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
+    """Compile both libraries (in parallel) when stale; returns the path of libhba.so."""
     os.makedirs(BUILD, exist_ok=True)
-    if force or stale(LIB, DEPS):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
+    jobs = []
+    for target, sources, deps in ((LIB, SOURCES, DEPS), (REPLAY_LIB, REPLAY_SOURCES, REPLAY_SOURCES)):
+        if force or stale(target, deps):
+            tmp = target + f".tmp{os.getpid()}"
+            cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, *sources]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            jobs.append((subprocess.Popen(cmd), tmp, target, cmd))
+    for proc, tmp, target, cmd in jobs:
+        if proc.wait() != 0:
+            raise subprocess.CalledProcessError(proc.returncode, cmd)
+        os.replace(tmp, target)
     return LIB
 
 
