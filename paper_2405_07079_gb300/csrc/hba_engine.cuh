@@ -111,6 +111,11 @@ constexpr uint32_t GATHER_WORDS = 5;
 // parallel before its event, the next RUN_AHEAD_LANES lanes go one by one
 constexpr uint32_t RUN_AHEAD_DENSE = 2;
 constexpr uint32_t RUN_AHEAD_LANES = 16;
+// free phase: with at most LEAD_MAX runs, every free finds its run by a
+// search among the runs' leaders (in address order); otherwise by pointer
+// jumping, following JUMP_HOPS links per pass
+constexpr uint32_t LEAD_MAX = 64;
+constexpr int JUMP_HOPS = 2;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
 constexpr uint32_t ERR_EMPTY_HEAD = 2;  // a class with its bit set had no head
@@ -240,23 +245,27 @@ struct Smem {
     // the most recent remainder X: virtual head of class xL while xok
     uint32_t xok, xg, xsz, xright, xL, xprev;
     uint32_t c0g, c0sz, c0prev;  // X when the current round classified its lanes
-    uint32_t xprev_new;  // start of the last carve resolved in parallel this round
     Rec hc[NBINS];       // record of each list head (alloc phase), refilled asynchronously
     // loop control
     uint32_t p, r, cont, evb[2], nul, nruns, flag[3];
+    // free phase: run leaders (applied frees with nothing applied to their
+    // left in the run) in address order, when there are at most LEAD_MAX
+    uint32_t nlead, lead[LEAD_MAX], lkey[LEAD_MAX], lsort[LEAD_MAX];
     uint32_t err;        // first metadata error seen by this CTA (0 = none)
     uint32_t* dyn;       // dynamic shared memory
     uint32_t dyn_words;
     // alloc-phase arrays (carved from dyn)
     int64_t* val;        // carve sizes, then their inclusive prefix
     uint64_t* s64;       // request sizes of the chunk
+    uint64_t* stg;       // [2][NT] request sizes of the next chunk, copied in ahead
     uint32_t* cst;       // start granule of each carve lane
     uint32_t* sgr;       // rounded sizes in granules (0: invalid request)
     uint8_t* cls;        // class of each lane in the current round
     uint8_t* ccl;        // size class c of each lane
     int64_t wc[NW + 1][NCNT];
     int64_t warp_tot[32];
-    uint32_t wlast[32];  // start of the highest carve lane of each warp
+    uint32_t wlast[32];  // start of the highest carve lane of each warp (NIL: none)
+    uint32_t wcm[32];    // carve lanes of each warp in the current round
     uint32_t segf[NSEG][NBINS];  // oldest run of each class per push segment
     uint32_t segl[NSEG][NBINS];  // newest run of each class per push segment
     uint32_t cnt[NT];
@@ -264,7 +273,7 @@ struct Smem {
 
 // words of dynamic shared memory the alloc phase carves for NT lanes
 template <int NT>
-HBA_HD uint32_t alloc_dyn_words() { return 2 * NT + 2 * NT + NT + NT + NT / 4 + NT / 4 + 8; }
+HBA_HD uint32_t alloc_dyn_words() { return 2 * NT + 2 * NT + 4 * NT + NT + NT + NT / 4 + NT / 4 + 8; }
 
 // ---- warp-aggregated counters and votes (call convergently) --------------
 template <int NT>
@@ -298,14 +307,22 @@ HBA_DEV void prefetch_l2(const void* p) {
 #endif
 }
 
-// 16-byte asynchronous copy of a record into shared memory, and the wait for
-// all of the calling thread's outstanding copies (one thread owns them).
+// Asynchronous copies into shared memory (a 16-byte record, an 8-byte request
+// size), and the wait for all of the calling thread's outstanding copies.
 HBA_DEV void rec_copy_async(Rec* dst_smem, const Rec* src) {
 #ifdef HBA_EMULATE
     *dst_smem = *src;
 #else
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+#endif
+}
+HBA_DEV void u64_copy_async(uint64_t* dst_smem, const uint64_t* src) {
+#ifdef HBA_EMULATE
+    *dst_smem = *src;
+#else
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
 #endif
 }
 HBA_DEV void rec_copy_wait() {
@@ -315,41 +332,54 @@ HBA_DEV void rec_copy_wait() {
 }
 
 // ---- block-wide collectives (called by all threads, outside phases) ------
-// Inclusive prefix sum over the lanes: thread tid passes x and gets its
-// inclusive prefix back (also stored in v[tid]).  One barrier inside; on
-// return only the caller's own v[tid] may be read without another barrier.
+// Inclusive prefix sum over the lanes of the warps that intersect the lane
+// window [lo, hi): thread tid of such a warp gets its inclusive prefix back
+// (also stored in v[tid]); warps outside the window contribute nothing, do
+// no shuffles and leave their v[] untouched.  One barrier inside; on return
+// only the caller's own v[tid] may be read without another barrier.
 template <int NT>
-HBA_DEV int64_t scan_incl_i64(Smem<NT>& S, int64_t* v, int tid_emu = 0) {
+HBA_DEV bool warp_in_window(int wid, uint32_t lo, uint32_t hi) {
+    const uint32_t w0 = (uint32_t)wid * 32u, w1 = w0 + 32u;
+    return w0 < hi && lo < w1;
+}
+template <int NT>
+HBA_DEV int64_t scan_incl_i64(Smem<NT>& S, int64_t* v, uint32_t lo, uint32_t hi) {
 #ifdef HBA_EMULATE
-    for (int i = 1; i < NT; ++i) v[i] += v[i - 1];
+    int64_t run = 0;
+    for (int i = 0; i < NT; ++i)
+        if (warp_in_window<NT>(i / 32, lo, hi)) {
+            run += v[i];
+            v[i] = run;
+        }
     (void)S;
-    (void)tid_emu;
     return 0;
 #else
-    (void)tid_emu;
     const int tid = hba_tid<NT>(), lane = tid & 31, wid = tid >> 5;
-    int64_t x = v[tid];
+    const bool act = warp_in_window<NT>(wid, lo, hi);
+    int64_t x = act ? v[tid] : 0;
+    if (act) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int64_t t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += t;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
     }
     if (NT == 32) {
         __syncwarp();
     } else {
         if (lane == 31) S.warp_tot[wid] = x;
         __syncthreads();
-        // every warp scans the warp totals itself: no second barrier
-        int64_t t = lane < NT / 32 ? S.warp_tot[lane] : 0;
+        if (act) {
+            // every active warp sums the totals of the warps below it itself:
+            // no second barrier
+            const int w0 = (int)(lo >> 5);
+            int64_t t = lane >= w0 && lane < wid ? S.warp_tot[lane] : 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
+            for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            x += t;
         }
-        const int64_t before = __shfl_sync(0xffffffffu, t, (wid + 31) & 31);
-        if (wid > 0) x += before;
     }
-    v[tid] = x;
+    if (act) v[tid] = x;
     return x;
 #endif
 }
@@ -512,20 +542,30 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         if (sm) {
             const uint32_t gs = a.gstride;
             uint32_t* d = S.dyn;
-            for (uint32_t j = tid; j < nf; j += NT) {
-                const uint32_t v0 = a.gi[j], v1 = a.gi[gs + j], v2 = a.gi[2 * gs + j];
-                const uint32_t v3 = a.gi[3 * gs + j], v4 = a.gi[4 * gs + j];
-                d[j] = v0;
-                d[nf + j] = v1;
-                d[2 * nf + j] = v2;
-                d[3 * nf + j] = v3;
-                d[4 * nf + j] = v4;
+            // four frees of a thread at a time: their 20 loads in flight together
+            for (uint32_t j0 = tid; j0 < nf; j0 += 4 * NT) {
+                uint32_t v[4][GATHER_WORDS];
+                HBA_UNROLL
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t j = j0 + (uint32_t)e * NT;
+                    HBA_UNROLL
+                    for (uint32_t q = 0; q < GATHER_WORDS; ++q) v[e][q] = j < nf ? a.gi[q * gs + j] : 0u;
+                }
+                HBA_UNROLL
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t j = j0 + (uint32_t)e * NT;
+                    if (j < nf) {
+                        HBA_UNROLL
+                        for (uint32_t q = 0; q < GATHER_WORDS; ++q) d[q * nf + j] = v[e][q];
+                    }
+                }
             }
         }
         for (uint32_t q = tid; q < hcap; q += NT) T.slot[q] = NIL;
-        if (tid == 0) { S.nul = 0; S.nruns = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
+        if (tid == 0) { S.nul = 0; S.nruns = 0; S.nlead = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
     }
     HBA_SYNC();
+    HBA_PROF(9);
     // F1: valid frees go into the granule table (lowest index wins).
     HBA_FOR_THREADS(tid) {
         for (uint32_t j = tid; j < nf; j += NT) {
@@ -582,6 +622,10 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                 }
             }
             root[j] = pr == NIL ? j : pr;
+            if (pr == NIL) {
+                const uint32_t k = at_add_u32(&S.nlead, 1);
+                if (k < LEAD_MAX) S.lead[k] = j;
+            }
             rmaxj[j] = j;
             rend[j] = end;
             lh[j] = head;
@@ -594,24 +638,78 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     }
     HBA_SYNC();
     HBA_PROF(2);
-    // F3: pointer jumping to the run's leftmost applied free.
-    for (int it = 0;; ++it) {
+    // F3: every applied free finds its run's leader (leftmost applied free).
+    // Runs are disjoint address ranges, so the leader of a free at granule g
+    // is the leader with the largest granule <= g.
+    const uint32_t nlead = S.nlead;
+    if (nlead <= LEAD_MAX) {
+        // few runs: rank the leaders by granule, then each free searches them
         HBA_FOR_THREADS(tid) {
-            bool ch = false;
-            for (uint32_t j = tid; j < nf; j += NT) {
-                const uint32_t r = root[j];
-                const uint32_t rr = root[r];
-                if (rr != r) { root[j] = rr; ch = true; }
+            for (uint32_t t = tid; t < nlead; t += NT) {
+                const uint32_t j = S.lead[t], g = gG[j];
+                uint32_t rank = 0;
+                for (uint32_t u = 0; u < nlead; ++u) rank += gG[S.lead[u]] < g;
+                S.lkey[rank] = g;
+                S.lsort[rank] = j;
             }
-            if (ch) S.flag[it % 3] = 1;
-            if (tid == 0) S.flag[(it + 1) % 3] = 0;
         }
         HBA_SYNC();
-        if (!S.flag[it % 3]) break;
+        HBA_FOR_THREADS(tid) {
+            for (uint32_t j = tid; j < nf; j += NT) {
+                if (!(fl[j] & FL_WIN)) continue;
+                const uint32_t g = gG[j];
+                uint32_t lo = 0, n = nlead;  // largest k with lkey[k] <= g
+                while (n > 1) {
+                    const uint32_t h = n / 2;
+                    if (S.lkey[lo + h] <= g) lo += h;
+                    n -= h;
+                }
+                root[j] = S.lsort[lo];
+            }
+        }
+        HBA_SYNC();
+    } else {
+        // many runs: pointer jumping over the pred links.  Each pass
+        // follows JUMP_HOPS links from every free before the barrier (four
+        // frees of a thread at a time, so that their loads overlap).
+        for (int it = 0;; ++it) {
+            HBA_FOR_THREADS(tid) {
+                bool ch = false;
+                for (uint32_t j0 = tid; j0 < nf; j0 += 4 * NT) {
+                    uint32_t r[4], r0[4];
+                    HBA_UNROLL
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t j = j0 + (uint32_t)e * NT;
+                        r[e] = r0[e] = root[j < nf ? j : j0];
+                    }
+                    HBA_UNROLL
+                    for (int h = 0; h < JUMP_HOPS; ++h) {
+                        HBA_UNROLL
+                        for (int e = 0; e < 4; ++e) r[e] = root[r[e]];
+                    }
+                    HBA_UNROLL
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t j = j0 + (uint32_t)e * NT;
+                        if (j < nf && r[e] != r0[e]) {
+                            root[j] = r[e];
+                            ch = true;
+                        }
+                    }
+                }
+                if (ch) S.flag[it % 3] = 1;
+                if (tid == 0) S.flag[(it + 1) % 3] = 0;
+            }
+            HBA_SYNC();
+            HBA_PROF(10);
+            if (!S.flag[it % 3]) break;
+        }
     }
     HBA_PROF(3);
-    // F4: per-run right end and last free index; mark absorbed blocks.
+    // F4: per-run right end and last free index; mark absorbed blocks.  A
+    // warp whose frees all belong to one run reduces them first and updates
+    // the run once (long runs would otherwise serialise on one address).
     HBA_FOR_THREADS(tid) {
+#ifdef HBA_EMULATE
         for (uint32_t j = tid; j < nf; j += NT) {
             const uint32_t r = root[j];
             if (r != j) {
@@ -619,6 +717,37 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                 at_max_u32(&rend[r], rend[j]);
             }
         }
+#else
+        for (uint32_t base = 0; base < nf; base += NT) {  // same trip count in the warp
+            const uint32_t j = base + (uint32_t)tid;
+            uint32_t r = NIL, mj = 0, me = 0;
+            if (j < nf) {
+                const uint32_t rt = root[j];
+                if (rt != j) {
+                    r = rt;
+                    mj = rmaxj[j];
+                    me = rend[j];
+                }
+            }
+            const unsigned any = __ballot_sync(0xffffffffu, r != NIL);
+            if (!any) continue;
+            const uint32_t rw = __shfl_sync(0xffffffffu, r, __ffs(any) - 1);
+            if (__all_sync(0xffffffffu, r == NIL || r == rw)) {
+                HBA_UNROLL
+                for (int o = 16; o; o >>= 1) {
+                    mj = max(mj, __shfl_xor_sync(0xffffffffu, mj, o));
+                    me = max(me, __shfl_xor_sync(0xffffffffu, me, o));
+                }
+                if ((tid & 31) == 0) {
+                    at_max_u32(&rmaxj[rw], mj);
+                    at_max_u32(&rend[rw], me);
+                }
+            } else if (r != NIL) {
+                at_max_u32(&rmaxj[r], mj);
+                at_max_u32(&rend[r], me);
+            }
+        }
+#endif
         for (uint32_t i = tid; i < S.nul; i += NT) {
             const uint32_t u = ul[i];
             rec[u].x = mkx(sz_of(rec[u].x), ST_DEL);
@@ -828,15 +957,15 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s,
 
 // Start granule of the nearest carve lane below `tid` in this round (lanes
 // are carves iff S.cls == CL_CARVE; their starts are in S.cst), or X's
-// prev_adj at the start of the round when there is none.  GPU: ballot and
-// shuffle inside the warp, per-warp last carves (S.wlast) across warps.
-// Call convergently.
+// prev_adj at the start of the round when there is none.  Lanes below r are
+// never carves.  GPU: ballot and shuffle inside the warp, per-warp last
+// carves (S.wlast) across warps.  Call convergently.
 template <int NT>
-HBA_DEV uint32_t prev_carve_start(Smem<NT>& S, int tid, bool carve, uint32_t start) {
+HBA_DEV uint32_t prev_carve_start(Smem<NT>& S, int tid, uint32_t r, bool carve, uint32_t start) {
 #ifdef HBA_EMULATE
     (void)carve;
     (void)start;
-    for (int t = tid - 1; t >= 0; --t)
+    for (int t = tid - 1; t >= (int)r; --t)
         if (S.cls[t] == CL_CARVE) return S.cst[t];
     return S.c0prev;
 #else
@@ -845,10 +974,26 @@ HBA_DEV uint32_t prev_carve_start(Smem<NT>& S, int tid, bool carve, uint32_t sta
     const int src = m ? 31 - __clz(m) : lane;
     const uint32_t v = __shfl_sync(0xffffffffu, start, src);
     if (m) return v;
-    for (int w = wid - 1; w >= 0; --w)
+    for (int w = wid - 1; w >= (int)(r >> 5); --w)
         if (S.wlast[w] != NIL) return S.wlast[w];
     return S.c0prev;
 #endif
+}
+
+// Start granule of the last carve lane in [r, e), or X's prev_adj at the
+// start of the round when there is none (one thread, after the verify
+// barrier: per-warp carve masks in S.wcm).
+template <int NT>
+HBA_DEV uint32_t last_carve_below(Smem<NT>& S, uint32_t r, uint32_t e) {
+    if (e <= r) return S.c0prev;
+    const uint32_t hi = e - 1;
+    int w = (int)(hi >> 5);
+    const uint32_t keep = (hi & 31) == 31 ? 0xffffffffu : ((2u << (hi & 31)) - 1u);
+    const uint32_t m = S.wcm[w] & keep;
+    if (m) return S.cst[w * 32 + (int)flog2(m)];
+    for (--w; w >= (int)(r >> 5); --w)
+        if (S.wlast[w] != NIL) return S.wlast[w];
+    return S.c0prev;
 }
 
 template <int NT>
@@ -863,10 +1008,11 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             uint32_t* d = S.dyn;
             S.val = reinterpret_cast<int64_t*>(d);
             S.s64 = reinterpret_cast<uint64_t*>(d + 2 * NT);
-            S.cst = d + 4 * NT;
-            S.sgr = d + 5 * NT;
-            S.cls = reinterpret_cast<uint8_t*>(d + 6 * NT);
-            S.ccl = reinterpret_cast<uint8_t*>(d + 6 * NT + NT / 4 + 4);
+            S.stg = reinterpret_cast<uint64_t*>(d + 4 * NT);
+            S.cst = d + 8 * NT;
+            S.sgr = d + 9 * NT;
+            S.cls = reinterpret_cast<uint8_t*>(d + 10 * NT);
+            S.ccl = reinterpret_cast<uint8_t*>(d + 10 * NT + NT / 4 + 4);
             S.p = 0;
             S.xok = 0;
             // the record of every list head, for the pops of this phase
@@ -875,6 +1021,10 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_SYNC();
+    // the first chunk's request sizes, copied in while the loop starts
+    HBA_FOR_THREADS(tid) {
+        if ((uint32_t)tid < na) u64_copy_async(&S.stg[tid], a.sizes + tid);
+    }
     while (true) {
         const uint32_t p = S.p;
         if (p >= na) break;
@@ -902,14 +1052,18 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             HBA_PROF(17);
             break;
         }
-        // A0: load the chunk [p, p + NT) once
+        // A0: load the chunk [p, p + NT) once (each thread its own lane,
+        // copied in ahead into S.stg[chunk parity]) and start copying the
+        // next chunk into the other half
         HBA_FOR_THREADS(tid) {
             const uint32_t i = p + tid;
+            const uint32_t par = (p / NT) & 1u;
             uint32_t sg = 0, c = 0;
             uint64_t s = 0;
+            rec_copy_wait();
             if (i < na) {
-                s = a.sizes[i];
-                if (i + NT < na) prefetch_l2(a.sizes + i + NT);
+                s = S.stg[par * NT + tid];
+                if (i + NT < na) u64_copy_async(&S.stg[(par ^ 1u) * NT + tid], a.sizes + i + NT);
                 if (s != 0 && s <= S.A) {
                     sg = (uint32_t)((s + mbm) >> lg);
                     c = clog2(sg);
@@ -936,23 +1090,27 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         for (int round = 0;; ++round) {
             const uint32_t r = S.r;
             uint32_t* evp = &S.evb[round & 1];
-            // A1: classify (own lane only: no barrier before the scan)
+            // A: classify the lanes of the warps that hold unresolved lanes
+            // (own lane only: no barrier before the scan); warps wholly
+            // outside [r, n_here) sit the round out
             HBA_FOR_THREADS(tid) {
-                uint8_t cl = CL_NONE;
-                const uint32_t sg = S.sgr[tid];
-                if ((uint32_t)tid >= r && (uint32_t)tid < n_here) {
-                    if (sg == 0) {
-                        cl = CL_FAIL;
-                    } else {
-                        const uint32_t c = S.ccl[tid];
-                        const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
-                        const uint64_t cand = (M >> c) << c;
-                        if (!cand) cl = CL_FAIL;
-                        else cl = (S.xok && ctz64(cand) == S.xL) ? CL_CARVE : CL_OTHER;
+                if (warp_in_window<NT>(tid >> 5, r, n_here)) {
+                    uint8_t cl = CL_NONE;
+                    const uint32_t sg = S.sgr[tid];
+                    if ((uint32_t)tid >= r && (uint32_t)tid < n_here) {
+                        if (sg == 0) {
+                            cl = CL_FAIL;
+                        } else {
+                            const uint32_t c = S.ccl[tid];
+                            const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
+                            const uint64_t cand = (M >> c) << c;
+                            if (!cand) cl = CL_FAIL;
+                            else cl = (S.xok && ctz64(cand) == S.xL) ? CL_CARVE : CL_OTHER;
+                        }
                     }
+                    S.cls[tid] = cl;
+                    S.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
                 }
-                S.cls[tid] = cl;
-                S.val[tid] = cl == CL_CARVE ? (int64_t)sg : 0;
                 if (tid == 0) {
                     S.c0g = S.xg;
                     S.c0sz = S.xok ? S.xsz : 0;
@@ -961,77 +1119,93 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                 }
             }
             HBA_PROF(12);
-            scan_incl_i64<NT>(S, S.val);
+            scan_incl_i64<NT>(S, S.val, r, n_here);
             HBA_PROF(13);
-            // B: verify; carve lanes record their start; per-warp last carve
+            // B: verify; carve lanes record their start; per-warp carve
+            // lanes and last carve
             HBA_FOR_THREADS(tid) {
-                const uint8_t cl = S.cls[tid];
-                const bool carve = cl == CL_CARVE;
-                bool e = cl == CL_OTHER;
-                uint32_t start = NIL;
-                if (carve) {
-                    const int64_t P = S.val[tid];
-                    const uint32_t sg = S.sgr[tid];
-                    start = S.c0g + (uint32_t)(P - sg);
-                    const int64_t before = (int64_t)S.c0sz - (P - (int64_t)sg);
-                    uint64_t M = S.mask;
-                    uint32_t Lt = 64;
-                    if (before > 0) {
-                        Lt = flog2((uint32_t)before);
-                        M |= 1ull << Lt;
+                const bool wact = warp_in_window<NT>(tid >> 5, r, n_here);
+                if (wact) {
+                    const uint8_t cl = S.cls[tid];
+                    const bool carve = cl == CL_CARVE;
+                    bool e = cl == CL_OTHER;
+                    uint32_t start = NIL;
+                    if (carve) {
+                        const int64_t P = S.val[tid];
+                        const uint32_t sg = S.sgr[tid];
+                        start = S.c0g + (uint32_t)(P - sg);
+                        const int64_t before = (int64_t)S.c0sz - (P - (int64_t)sg);
+                        uint64_t M = S.mask;
+                        uint32_t Lt = 64;
+                        if (before > 0) {
+                            Lt = flog2((uint32_t)before);
+                            M |= 1ull << Lt;
+                        }
+                        const uint32_t c = S.ccl[tid];
+                        const uint64_t cand = (M >> c) << c;
+                        if (!(cand && ctz64(cand) == Lt)) e = true;
                     }
-                    const uint32_t c = S.ccl[tid];
-                    const uint64_t cand = (M >> c) << c;
-                    if (!(cand && ctz64(cand) == Lt)) e = true;
-                }
-                S.cst[tid] = start;
+                    S.cst[tid] = start;
 #ifdef HBA_EMULATE
-                if (e && (uint32_t)tid < *evp) *evp = (uint32_t)tid;
+                    if (e && (uint32_t)tid < *evp) *evp = (uint32_t)tid;
+                    if ((tid & 31) == 0) {
+                        S.wcm[tid >> 5] = 0;
+                        S.wlast[tid >> 5] = NIL;
+                    }
+                    if (carve) {
+                        S.wcm[tid >> 5] |= 1u << (tid & 31);
+                        S.wlast[tid >> 5] = start;
+                    }
 #else
-                const unsigned bal = __ballot_sync(0xffffffffu, e);
-                if ((tid & 31) == 0 && bal) atomicMin(evp, (uint32_t)(tid + __ffs(bal) - 1));
-                const unsigned cb = __ballot_sync(0xffffffffu, carve);
-                const uint32_t top = __shfl_sync(0xffffffffu, start, cb ? 31 - __clz(cb) : 0);
-                if ((tid & 31) == 0) S.wlast[tid >> 5] = cb ? top : NIL;
+                    const unsigned bal = __ballot_sync(0xffffffffu, e);
+                    if ((tid & 31) == 0 && bal) atomicMin(evp, (uint32_t)(tid + __ffs(bal) - 1));
+                    const unsigned cb = __ballot_sync(0xffffffffu, carve);
+                    const uint32_t top = __shfl_sync(0xffffffffu, start, cb ? 31 - __clz(cb) : 0);
+                    if ((tid & 31) == 0) {
+                        S.wcm[tid >> 5] = cb;
+                        S.wlast[tid >> 5] = cb ? top : NIL;
+                    }
 #endif
+                } else if ((tid & 31) == 0) {
+                    S.wcm[tid >> 5] = 0;
+                    S.wlast[tid >> 5] = NIL;
+                }
             }
             HBA_SYNC();
             HBA_PROF(14);
             const uint32_t ev = *evp;
             const uint32_t nres = ev < n_here ? ev : n_here;   // lanes [r, nres) are exact
-            // the lane that reports the last carve resolved in parallel: the
-            // event lane (nearest carve below it), or the last lane
-            const uint32_t wl = nres < (uint32_t)NT ? nres : (uint32_t)NT - 1;
-            // C: resolve [r, nres) in parallel (failures, carves from X)
+            // C: resolve [r, nres) in parallel (failures, carves from X); then
+            // one thread advances X past those carves, applies the event lane
+            // alone and, when this round resolved (almost) nothing in
+            // parallel, runs ahead through the next lanes one by one.  The
+            // event only touches records outside the carved range and
+            // results of lanes >= nres, so it runs beside the resolve.
             HBA_FOR_THREADS(tid) {
-                const uint8_t cl = S.cls[tid];
-                const bool act = (uint32_t)tid < nres;   // lanes below r have class NONE
-                const bool is_fail = act && cl == CL_FAIL;
-                const bool is_carve = act && cl == CL_CARVE;
-                const uint32_t start = S.cst[tid];
-                const uint32_t prev = prev_carve_start<NT>(S, tid, cl == CL_CARVE, start);
-                if (is_fail && !a.prefilled) a.out[p + tid] = FAIL64;
-                if (is_carve) {
-                    const uint32_t sg = S.sgr[tid];
-                    a.out[p + tid] = (uint64_t)start << lg;
-                    str(rec, start, Rec{mkx(sg, ST_USED), prev, NIL, NIL});
+                if (warp_in_window<NT>(tid >> 5, r, nres)) {
+                    const uint8_t cl = S.cls[tid];
+                    const bool act = (uint32_t)tid >= r && (uint32_t)tid < nres;
+                    const bool is_fail = act && cl == CL_FAIL;
+                    const bool is_carve = act && cl == CL_CARVE;
+                    const uint32_t start = S.cst[tid];
+                    const uint32_t prev = prev_carve_start<NT>(S, tid, r, cl == CL_CARVE, start);
+                    if (is_fail && !a.prefilled) a.out[p + tid] = FAIL64;
+                    if (is_carve) {
+                        const uint32_t sg = S.sgr[tid];
+                        a.out[p + tid] = (uint64_t)start << lg;
+                        str(rec, start, Rec{mkx(sg, ST_USED), prev, NIL, NIL});
+                    }
+                    warp_count(S, tid, C_AFAIL, is_fail);
+                    warp_count(S, tid, C_AOK, is_carve);
+                    warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
                 }
-                warp_count(S, tid, C_AFAIL, is_fail);
-                warp_count(S, tid, C_AOK, is_carve);
-                warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
-                if ((uint32_t)tid == wl) S.xprev_new = (wl < nres && is_carve) ? start : prev;
-            }
-            HBA_SYNC();
-            // D: one thread advances X, applies the event lane alone and, when
-            // this round resolved (almost) nothing in parallel, runs ahead
-            // through the next lanes one by one (cheaper than rounds there)
-            HBA_FOR_THREADS(tid) {
                 if (tid == 0) {
-                    const int64_t gave = nres ? S.val[nres - 1] : 0;
+                    HBA_PROF(16);
+                    const int64_t gave = nres > r ? S.val[nres - 1] : 0;
                     if (gave > 0) {
                         S.xg = S.c0g + (uint32_t)gave;
                         S.xsz = S.c0sz - (uint32_t)gave;
-                        S.xprev = S.xprev_new;
+                        S.xprev = last_carve_below<NT>(S, r, nres);
                         single_add(S, C_USEDG, gave);
                         if (S.xsz == 0) {
                             S.xok = 0;
@@ -1049,8 +1223,10 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                             const uint32_t stop = next + RUN_AHEAD_LANES < n_here ? next + RUN_AHEAD_LANES : n_here;
                             for (; next < stop; ++next)
                                 seq_request<NT>(S, a, p + next, S.s64[next], S.sgr[next], S.ccl[next]);
+                            HBA_PROF(21);
                         }
                     }
+                    HBA_PROF(20);
                     S.r = next;
                     S.cont = next < n_here;
                     if (!S.cont) S.p = p + n_here;
@@ -1074,10 +1250,8 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_FOR_THREADS(tid) {
-        if (tid == 0) {
-            if (S.xok) materialize_x<NT>(S, rec);
-            rec_copy_wait();  // no copy may land in shared memory after this arena
-        }
+        if (tid == 0 && S.xok) materialize_x<NT>(S, rec);
+        rec_copy_wait();  // no copy may land in shared memory after this arena
     }
     HBA_SYNC();
     HBA_PROF(18);
