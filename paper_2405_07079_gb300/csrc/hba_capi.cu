@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64
                                                uint32_t dyn_words, uint32_t prefilled) {
     __shared__ hba::Smem<NT> S;
     extern __shared__ __align__(16) uint32_t dyn[];
-    // the preceding prep grid (gathered records, pre-filled failures)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled};
+    // waits for the preceding prep grid (gathered records, pre-filled
+    // failures) once it has read the arena header
+    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled, 1};
     hba::arena_step<NT>(S, a, dyn, dyn_words);
 }
 
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                                               uint32_t dyn_words, uint32_t prefilled) {
     __shared__ hba::Smem<NT> S;
     extern __shared__ __align__(16) uint32_t dyn[];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    bool first = true;  // the first arena waits for the prep grid (after its header)
     for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
         const uint32_t f0 = frow[a], f1 = frow[a + 1], a0 = arow[a], a1 = arow[a + 1];
         Arena* ar = ars + a;
@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE,
                            gi + f0,
                            nf_total,
-                           prefilled};
+                           prefilled,
+                           first ? 1u : 0u};
+        first = false;
         hba::arena_step<NT>(S, args, dyn, dyn_words);
     }
 }
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(WPC * 32) k_multi_warp(Arena* ars, Rec* pool, 
                                                           uint32_t warp_dyn_words, uint32_t prefilled) {
     __shared__ hba::Smem<32> S[WPC];
     extern __shared__ __align__(16) uint32_t dyn[];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    bool first = true;  // the first arena waits for the prep grid (after its header)
     const uint32_t w = threadIdx.x >> 5;
     uint32_t* mine = dyn + (size_t)w * warp_dyn_words;
     for (uint32_t a = blockIdx.x * WPC + w; a < n_arenas; a += gridDim.x * WPC) {
@@ -131,7 +133,9 @@ __global__ void __launch_bounds__(WPC * 32) k_multi_warp(Arena* ars, Rec* pool, 
                            scr + (uint64_t)f0 * hba::SCRATCH_WORDS_PER_FREE,
                            gi + f0,
                            nf_total,
-                           prefilled};
+                           prefilled,
+                           first ? 1u : 0u};
+        first = false;
         hba::arena_step<32>(S[w], args, mine, warp_dyn_words);
     }
 }

@@ -35,7 +35,7 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
     std::vector<uint32_t> gi((size_t)GATHER_WORDS * nf + 1);
     for (uint32_t j = 0; j < nf; ++j)
         gather_free(e->rec.data(), e->ar.arena_bytes, e->ar.G, e->ar.lg, frees[j], gi.data(), nf, j);
-    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0};
+    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0, 0};
     // "shared memory": at least what the alloc phase needs, plus a test knob so
     // that both placements of the free-phase arrays run
     const uint32_t words = std::max(alloc_dyn_words<NT>(), e->dyn_words);

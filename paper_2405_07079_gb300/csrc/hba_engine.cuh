@@ -107,10 +107,12 @@ constexpr int NBINS = 32;  // granule classes 0..28 are reachable
 // they do not fit in shared memory
 constexpr uint32_t SCRATCH_WORDS_PER_FREE = 16;
 constexpr uint32_t GATHER_WORDS = 5;
-// alloc phase: after a round that resolved at most RUN_AHEAD_DENSE lanes in
-// parallel before its event, the next RUN_AHEAD_LANES lanes go one by one
-constexpr uint32_t RUN_AHEAD_DENSE = 2;
-constexpr uint32_t RUN_AHEAD_LANES = 16;
+// alloc phase: after a block-wide round that resolved fewer than
+// STRETCH_BELOW lanes before its event, one warp goes on through up to
+// STRETCH_LANES lanes with warp-wide rounds (no block barrier), until a
+// window of 32 lanes holds no event
+constexpr uint32_t STRETCH_BELOW = 256;
+constexpr uint32_t STRETCH_LANES = 512;
 // free phase: with at most LEAD_MAX runs, every free finds its run by a
 // search among the runs' leaders (in address order); otherwise by pointer
 // jumping, following JUMP_HOPS links per pass
@@ -246,6 +248,8 @@ struct Smem {
     uint32_t xok, xg, xsz, xright, xL, xprev;
     uint32_t c0g, c0sz, c0prev;  // X when the current round classified its lanes
     Rec hc[NBINS];       // record of each list head (alloc phase), refilled asynchronously
+    uint32_t hseq[NBINS];  // copy group of each slot's pending refill (NIL: none)
+    uint32_t hissued;      // copy groups issued so far
     // loop control
     uint32_t p, r, cont, evb[2], nul, nruns, flag[3];
     // free phase: run leaders (applied frees with nothing applied to their
@@ -323,6 +327,36 @@ HBA_DEV void u64_copy_async(uint64_t* dst_smem, const uint64_t* src) {
 #else
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+#endif
+}
+// Copy the record of list k's head into the cache slot S.hc[k] as its own
+// copy group, and wait for that slot's copy only (groups complete in order:
+// wait until at most the number of groups issued after it are pending).  One
+// thread owns the slots.
+HBA_DEV void head_copy_async(Rec* slot, uint32_t* seq, uint32_t& issued, const Rec* src) {
+    rec_copy_async(slot, src);
+#ifndef HBA_EMULATE
+    asm volatile("cp.async.commit_group;" ::: "memory");
+#endif
+    *seq = issued++;
+}
+HBA_DEV void head_copy_wait(uint32_t seq, uint32_t issued) {
+#ifdef HBA_EMULATE
+    (void)seq;
+    (void)issued;
+#else
+    if (seq == NIL) return;
+    const uint32_t after = issued - 1u - seq;  // groups issued after this one
+    switch (after < 7u ? after : 7u) {
+        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+    }
 #endif
 }
 HBA_DEV void rec_copy_wait() {
@@ -438,24 +472,68 @@ struct StepArgs {
     uint32_t gstride;
     uint32_t prefilled;  // out[] already holds HBA_FAIL everywhere (written by a
                          // preceding grid): failures need no store
+    uint32_t wait_prep;  // wait for the preceding grid (programmatic dependent
+                         // launch) after reading the arena header, before
+                         // touching what that grid writes (gathered records, out[])
 };
+
+HBA_DEV void fence_block() {
+#ifndef HBA_EMULATE
+    __threadfence_block();
+#endif
+}
+HBA_DEV void grid_dep_wait() {
+#ifndef HBA_EMULATE
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+// The virtual remainder X, the bitmap and the counters of the one thread that
+// applies requests one by one, held in registers while it does (loaded from
+// and stored back to shared memory around each serial stretch).
+struct XReg {
+    uint64_t mask;
+    uint32_t xok, xg, xsz, xL, xprev, xright, lg, G;
+    int64_t aok, afail, usedg, req, nosplit;
+};
+template <int NT>
+HBA_DEV XReg x_load(const Smem<NT>& S) {
+    return XReg{S.mask, S.xok, S.xg, S.xsz, S.xL, S.xprev, S.xright, S.lg, S.G, 0, 0, 0, 0, 0};
+}
+template <int NT>
+HBA_DEV void x_store(Smem<NT>& S, const XReg& X) {
+    S.mask = X.mask;
+    S.xok = X.xok;
+    S.xg = X.xg;
+    S.xsz = X.xsz;
+    S.xL = X.xL;
+    S.xprev = X.xprev;
+    S.xright = X.xright;
+    int64_t* c = S.wc[Smem<NT>::NW];
+    c[C_AOK] += X.aok;
+    c[C_AFAIL] += X.afail;
+    c[C_USEDG] += X.usedg;
+    c[C_REQ] += X.req;
+    c[C_NOSPLIT] += X.nosplit;
+}
 
 // Push the virtual remainder X at the head of its list and write its record
 // (one thread).
 template <int NT>
-HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec, bool cache = false) {
-    const uint32_t b = S.xL, old = S.heads[b];
-    const Rec r{mkx(S.xsz, ST_FREE), S.xprev, old, NIL};
-    str(rec, S.xg, r);
+HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec, XReg& X, bool cache = false) {
+    const uint32_t b = X.xL, old = S.heads[b];
+    const Rec r{mkx(X.xsz, ST_FREE), X.xprev, old, NIL};
+    str(rec, X.xg, r);
     if (cache) {
-        rec_copy_wait();  // no copy may still be landing in the slot
+        head_copy_wait(S.hseq[b], S.hissued);  // no copy may still be landing in the slot
+        S.hseq[b] = NIL;
         S.hc[b] = r;
     }
-    if (old != NIL) rec[old].w = S.xg;
-    S.heads[b] = S.xg;
-    S.mask |= 1ull << b;
-    if (S.xright < S.G) rec[S.xright].y = S.xg;
-    S.xok = 0;
+    if (old != NIL) rec[old].w = X.xg;
+    S.heads[b] = X.xg;
+    X.mask |= 1ull << b;
+    if (X.xright < X.G) rec[X.xright].y = X.xg;
+    X.xok = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -502,6 +580,12 @@ HBA_HD uint32_t gt_capacity(uint32_t nf) {
     return c;
 }
 HBA_HD uint32_t free_smem_words(uint32_t nf) { return 11 * nf + gt_capacity(nf) + 4; }
+// Where the granule table of nf frees lives: in shared memory after the five
+// staged words per free when the free phase fits there, else at the start of
+// the global scratch.
+HBA_HD uint32_t* gt_slots(uint32_t nf, uint32_t* dyn, uint32_t dyn_words, uint32_t* scr) {
+    return free_smem_words(nf) <= dyn_words ? dyn + GATHER_WORDS * nf : scr;
+}
 
 constexpr uint32_t FL_WIN = 4;  // flag: this free is applied
 
@@ -527,7 +611,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         const uint32_t gs = a.gstride;
         gG = a.gi; gSZ = a.gi + gs; gL = a.gi + 2 * gs; gLL = a.gi + 3 * gs; gRE = a.gi + 4 * gs;
     }
-    GTable T{w, gG, hcap - 1};
+    GTable T{w, gG, hcap - 1};  // w == gt_slots(nf, ...): cleared by arena_step
     uint32_t* root = w + hcap;          // pointer-jumping root (a free index)
     uint32_t* rmaxj = root + nf;        // largest free index of the run (at the root)
     uint32_t* rend = rmaxj + nf;        // right end of the run (at the root)
@@ -537,7 +621,11 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     uint32_t* runs = sm ? const_cast<uint32_t*>(gLL) : fl + nf;  // run leaders in order
     uint32_t* ul = sm ? a.scr : fl + 2 * nf;                     // [2 nf] absorbed old free blocks
 
-    // F0: stage the gathered records, clear the granule table.
+    // F1: stage the gathered records (shared-memory layout), and put the
+    // valid frees into the granule table (lowest index wins).  The table was
+    // cleared before the prep grid finished; a free's granule is staged
+    // before the free is inserted, so that whoever finds it in the table
+    // reads its key.
     HBA_FOR_THREADS(tid) {
         if (sm) {
             const uint32_t gs = a.gstride;
@@ -559,18 +647,18 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                         for (uint32_t q = 0; q < GATHER_WORDS; ++q) d[q * nf + j] = v[e][q];
                     }
                 }
+                fence_block();
+                HBA_UNROLL
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t j = j0 + (uint32_t)e * NT;
+                    if (j < nf && v[e][0] != NIL) gt_insert_min(T, v[e][0], j);
+                }
             }
-        }
-        for (uint32_t q = tid; q < hcap; q += NT) T.slot[q] = NIL;
-        if (tid == 0) { S.nul = 0; S.nruns = 0; S.nlead = 0; S.flag[0] = S.flag[1] = S.flag[2] = 0; }
-    }
-    HBA_SYNC();
-    HBA_PROF(9);
-    // F1: valid frees go into the granule table (lowest index wins).
-    HBA_FOR_THREADS(tid) {
-        for (uint32_t j = tid; j < nf; j += NT) {
-            const uint32_t g = gG[j];
-            if (g != NIL) gt_insert_min(T, g, j);
+        } else {
+            for (uint32_t j = tid; j < nf; j += NT) {
+                const uint32_t g = gG[j];
+                if (g != NIL) gt_insert_min(T, g, j);
+            }
         }
     }
     HBA_SYNC();
@@ -801,70 +889,101 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     }
     HBA_SYNC();
     HBA_PROF(6);
-    // F7: run leaders in increasing order of their last free index.
-    const uint32_t per = (nf + NT - 1) / NT;
-    HBA_FOR_THREADS(tid) {
-        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
-        uint32_t c = 0;
-        for (uint32_t j = lo; j < hi; ++j) c += runAt[j] != NIL;
-        S.cnt[tid] = c;
-    }
-    HBA_SYNC();
-    scan_excl_u32<NT>(S, S.cnt, &S.flag[0]);
-    const uint32_t nruns = S.flag[0];
-    HBA_FOR_THREADS(tid) {
-        const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
-        uint32_t k = S.cnt[tid];
-        for (uint32_t j = lo; j < hi; ++j)
-            if (runAt[j] != NIL) runs[k++] = runAt[j];
-    }
-    HBA_SYNC();
-    HBA_PROF(7);
-    // F8a: the merged blocks are pushed in run order.  Split that order into
-    // NSEG segments; inside each, link consecutive runs of the same class.
-    constexpr int NSEG = Smem<NT>::NSEG;
-    HBA_FOR_THREADS(tid) {
-        if (tid < NSEG) {
-            uint32_t* F = S.segf[tid];
-            uint32_t* Lt = S.segl[tid];
-            for (int b = 0; b < NBINS; ++b) F[b] = Lt[b] = NIL;
-            const uint32_t ps = (nruns + NSEG - 1) / NSEG;
-            const uint32_t lo = tid * ps, hi = lo + ps < nruns ? lo + ps : nruns;
-            for (uint32_t k = lo; k < hi; ++k) {
-                const uint32_t j = runs[k];
-                const uint32_t H = lh[j];
-                const uint32_t b = flog2(rend[j] - H);
-                if (Lt[b] == NIL) {
-                    F[b] = H;
-                } else {
-                    rec[H].z = Lt[b];
-                    rec[Lt[b]].w = H;
+    uint32_t nruns;
+    if (nlead <= LEAD_MAX) {
+        // F7/F8, few runs: rank the runs by their last free index, then one
+        // thread pushes the merged blocks in that order
+        nruns = nlead;
+        HBA_FOR_THREADS(tid) {
+            for (uint32_t t = tid; t < nlead; t += NT) {
+                const uint32_t j = S.lsort[t], key = rmaxj[j];
+                uint32_t rank = 0;
+                for (uint32_t u = 0; u < nlead; ++u) rank += rmaxj[S.lsort[u]] < key;
+                S.lead[rank] = j;
+            }
+        }
+        HBA_SYNC();
+        HBA_FOR_THREADS(tid) {
+            if (tid == 0) {
+                for (uint32_t k = 0; k < nlead; ++k) {
+                    const uint32_t j = S.lead[k];
+                    const uint32_t H = lh[j];
+                    const uint32_t b = flog2(rend[j] - H);
+                    const uint32_t old = S.heads[b];
+                    rec[H].z = old;
+                    rec[H].w = NIL;
+                    if (old != NIL) rec[old].w = H;
+                    S.heads[b] = H;
                 }
-                Lt[b] = H;
             }
         }
-    }
-    HBA_SYNC();
-    // F8b: per class, stitch the segments in order on top of the old list.
-    HBA_FOR_THREADS(tid) {
-        for (int b = tid; b < NBINS; b += NT) {
-            uint32_t below = S.heads[b];
-            bool any = false;
-            for (int sgm = 0; sgm < NSEG; ++sgm) {
-                const uint32_t f = S.segf[sgm][b];
-                if (f == NIL) continue;
-                rec[f].z = below;
-                if (below != NIL) rec[below].w = f;
-                below = S.segl[sgm][b];
-                any = true;
-            }
-            if (any) {
-                rec[below].w = NIL;
-                S.heads[b] = below;
+        HBA_SYNC();
+    } else {
+        // F7: run leaders in increasing order of their last free index.
+        const uint32_t per = (nf + NT - 1) / NT;
+        HBA_FOR_THREADS(tid) {
+            const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
+            uint32_t c = 0;
+            for (uint32_t j = lo; j < hi; ++j) c += runAt[j] != NIL;
+            S.cnt[tid] = c;
+        }
+        HBA_SYNC();
+        scan_excl_u32<NT>(S, S.cnt, &S.flag[0]);
+        nruns = S.flag[0];
+        HBA_FOR_THREADS(tid) {
+            const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
+            uint32_t k = S.cnt[tid];
+            for (uint32_t j = lo; j < hi; ++j)
+                if (runAt[j] != NIL) runs[k++] = runAt[j];
+        }
+        HBA_SYNC();
+        HBA_PROF(7);
+        // F8a: the merged blocks are pushed in run order.  Split that order into
+        // NSEG segments; inside each, link consecutive runs of the same class.
+        constexpr int NSEG = Smem<NT>::NSEG;
+        HBA_FOR_THREADS(tid) {
+            if (tid < NSEG) {
+                uint32_t* F = S.segf[tid];
+                uint32_t* Lt = S.segl[tid];
+                for (int b = 0; b < NBINS; ++b) F[b] = Lt[b] = NIL;
+                const uint32_t ps = (nruns + NSEG - 1) / NSEG;
+                const uint32_t lo = tid * ps, hi = lo + ps < nruns ? lo + ps : nruns;
+                for (uint32_t k = lo; k < hi; ++k) {
+                    const uint32_t j = runs[k];
+                    const uint32_t H = lh[j];
+                    const uint32_t b = flog2(rend[j] - H);
+                    if (Lt[b] == NIL) {
+                        F[b] = H;
+                    } else {
+                        rec[H].z = Lt[b];
+                        rec[Lt[b]].w = H;
+                    }
+                    Lt[b] = H;
+                }
             }
         }
+        HBA_SYNC();
+        // F8b: per class, stitch the segments in order on top of the old list.
+        HBA_FOR_THREADS(tid) {
+            for (int b = tid; b < NBINS; b += NT) {
+                uint32_t below = S.heads[b];
+                bool any = false;
+                for (int sgm = 0; sgm < NSEG; ++sgm) {
+                    const uint32_t f = S.segf[sgm][b];
+                    if (f == NIL) continue;
+                    rec[f].z = below;
+                    if (below != NIL) rec[below].w = f;
+                    below = S.segl[sgm][b];
+                    any = true;
+                }
+                if (any) {
+                    rec[below].w = NIL;
+                    S.heads[b] = below;
+                }
+            }
+        }
+        HBA_SYNC();
     }
-    HBA_SYNC();
     HBA_FOR_THREADS(tid) {
         if (tid == 0) {
             uint64_t m = 0;
@@ -886,73 +1005,79 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
 // The alloc phase (Algorithm 4 for all allocations of the batch).
 // ---------------------------------------------------------------------------
 
-// Apply request i alone against the current state (one thread): the
-// general step of Algorithm 4 -- fail, carve from X, or pop another list.
+// Apply request i alone against the current state (one thread, X in
+// registers): the general step of Algorithm 4 -- fail, carve from X, or pop
+// another list.
 template <int NT>
-HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, uint32_t i, uint64_t s, uint32_t sg, uint32_t c) {
+HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, uint64_t s, uint32_t sg,
+                         uint32_t c) {
     Rec* rec = a.rec;
-    const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
+    const uint64_t M = X.mask | (X.xok ? (1ull << X.xL) : 0ull);
     const uint64_t cand = sg ? (M >> c) << c : 0ull;
     if (!cand) {
         if (!a.prefilled) a.out[i] = FAIL64;
-        single_add(S, C_AFAIL, 1);
+        ++X.afail;
+        HBA_PROF(24);
         return;
     }
     const uint32_t k = ctz64(cand);
-    if (S.xok && k == S.xL) {
+    if (X.xok && k == X.xL) {
         // carve the front of X
-        const uint32_t start = S.xg;
-        str(rec, start, Rec{mkx(sg, ST_USED), S.xprev, NIL, NIL});
-        a.out[i] = (uint64_t)start << S.lg;
-        S.xg += sg;
-        S.xsz -= sg;
-        S.xprev = start;
-        if (S.xsz == 0) {
-            S.xok = 0;
-            if (S.xright < S.G) rec[S.xright].y = start;
-            single_add(S, C_NOSPLIT, 1);
+        const uint32_t start = X.xg;
+        str(rec, start, Rec{mkx(sg, ST_USED), X.xprev, NIL, NIL});
+        a.out[i] = (uint64_t)start << X.lg;
+        X.xg += sg;
+        X.xsz -= sg;
+        X.xprev = start;
+        if (X.xsz == 0) {
+            X.xok = 0;
+            if (X.xright < X.G) rec[X.xright].y = start;
+            ++X.nosplit;
         } else {
-            S.xL = flog2(S.xsz);
+            X.xL = flog2(X.xsz);
         }
+        HBA_PROF(22);
     } else {
         // pop the head of list k (its record is cached); the old X becomes a
         // listed block first
-        if (S.xok) materialize_x<NT>(S, rec, true);
+        if (X.xok) materialize_x<NT>(S, rec, X, true);
         const uint32_t Y = S.heads[k];
-        if (Y >= S.G) {  // bitmap and heads disagree: record, fail the request
+        if (Y >= X.G) {  // bitmap and heads disagree: record, fail the request
             S.err = ERR_EMPTY_HEAD;
-            S.mask &= ~(1ull << k);
+            X.mask &= ~(1ull << k);
             if (!a.prefilled) a.out[i] = FAIL64;
-            single_add(S, C_AFAIL, 1);
+            ++X.afail;
             return;
         }
-        rec_copy_wait();
+        head_copy_wait(S.hseq[k], S.hissued);
         const Rec ry = S.hc[k];
         const uint32_t nxt = ry.z;
         S.heads[k] = nxt;
+        S.hseq[k] = NIL;
         if (nxt == NIL) {
-            S.mask &= ~(1ull << k);
+            X.mask &= ~(1ull << k);
         } else {
             rec[nxt].w = NIL;
-            rec_copy_async(&S.hc[k], rec + nxt);  // the new head, for a later pop
+            head_copy_async(&S.hc[k], &S.hseq[k], S.hissued, rec + nxt);  // the new head, for a later pop
         }
         const uint32_t ysz = sz_of(ry.x);
         str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
-        a.out[i] = (uint64_t)Y << S.lg;
+        a.out[i] = (uint64_t)Y << X.lg;
         if (ysz > sg) {
-            S.xok = 1;
-            S.xg = Y + sg;
-            S.xsz = ysz - sg;
-            S.xprev = Y;
-            S.xright = Y + ysz;
-            S.xL = flog2(ysz - sg);
+            X.xok = 1;
+            X.xg = Y + sg;
+            X.xsz = ysz - sg;
+            X.xprev = Y;
+            X.xright = Y + ysz;
+            X.xL = flog2(ysz - sg);
         } else {
-            single_add(S, C_NOSPLIT, 1);
+            ++X.nosplit;
         }
+        HBA_PROF(23);
     }
-    single_add(S, C_AOK, 1);
-    single_add(S, C_USEDG, sg);
-    single_add(S, C_REQ, (int64_t)s);
+    ++X.aok;
+    X.usedg += sg;
+    X.req += (int64_t)s;
 }
 
 // Start granule of the nearest carve lane below `tid` in this round (lanes
@@ -996,6 +1121,240 @@ HBA_DEV uint32_t last_carve_below(Smem<NT>& S, uint32_t r, uint32_t e) {
     return S.c0prev;
 }
 
+// X's fields from lane 0 to the whole warp (after lane 0 applied a request
+// alone); the counters stay with lane 0, which stores them.
+HBA_DEV void x_bcast(XReg& X) {
+#ifndef HBA_EMULATE
+    X.mask = __shfl_sync(0xffffffffu, X.mask, 0);
+    X.xok = __shfl_sync(0xffffffffu, X.xok, 0);
+    X.xg = __shfl_sync(0xffffffffu, X.xg, 0);
+    X.xsz = __shfl_sync(0xffffffffu, X.xsz, 0);
+    X.xL = __shfl_sync(0xffffffffu, X.xL, 0);
+    X.xprev = __shfl_sync(0xffffffffu, X.xprev, 0);
+    X.xright = __shfl_sync(0xffffffffu, X.xright, 0);
+#else
+    (void)X;
+#endif
+}
+
+// Lanes [q, stop) of the chunk, applied by one warp in windows of 32 lanes:
+// each window is classified against X, its carve sizes scanned, and the lanes
+// before its first event resolved at once; lane 0 applies the event alone.
+// The same rule as the block-wide rounds, with shuffles instead of barriers.
+// Stops after a window without an event (events are sparse there: the
+// block-wide rounds take over).  X is replicated in the warp's registers.
+// Returns the first lane not applied.
+#ifdef HBA_EMULATE
+template <int NT>
+HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
+                              uint32_t lane) {
+    (void)lane;
+    Rec* rec = a.rec;
+    while (q < stop) {
+        const uint32_t nl = stop - q < 32u ? stop - q : 32u;
+        uint8_t cl[32];
+        uint64_t P[32];
+        uint32_t start[32];
+        uint64_t run = 0;
+        for (uint32_t l = 0; l < nl; ++l) {
+            const uint32_t i = q + l, sg = S.sgr[i], c = S.ccl[i];
+            cl[l] = CL_FAIL;
+            if (sg) {
+                const uint64_t M = X.mask | (X.xok ? (1ull << X.xL) : 0ull);
+                const uint64_t cand = (M >> c) << c;
+                if (cand) cl[l] = (X.xok && ctz64(cand) == X.xL) ? CL_CARVE : CL_OTHER;
+            }
+            run += cl[l] == CL_CARVE ? sg : 0;
+            P[l] = run;
+        }
+        uint32_t ev = nl;
+        for (uint32_t l = 0; l < nl && ev == nl; ++l) {
+            const uint32_t i = q + l, sg = S.sgr[i], c = S.ccl[i];
+            bool e = cl[l] == CL_OTHER;
+            start[l] = NIL;
+            if (cl[l] == CL_CARVE) {
+                const uint64_t bc = P[l] - sg;
+                start[l] = X.xg + (uint32_t)bc;
+                const int64_t before = (int64_t)X.xsz - (int64_t)bc;
+                uint64_t M = X.mask;
+                uint32_t Lt = 64;
+                if (before > 0) {
+                    Lt = flog2((uint32_t)before);
+                    M |= 1ull << Lt;
+                }
+                const uint64_t cand = (M >> c) << c;
+                if (!(cand && ctz64(cand) == Lt)) e = true;
+            }
+            if (e) ev = l;
+        }
+        uint32_t prev = X.xprev;
+        uint64_t gave = 0;
+        for (uint32_t l = 0; l < ev; ++l) {
+            const uint32_t i = q + l;
+            if (cl[l] == CL_CARVE) {
+                a.out[p + i] = (uint64_t)start[l] << X.lg;
+                str(rec, start[l], Rec{mkx(S.sgr[i], ST_USED), prev, NIL, NIL});
+                prev = start[l];
+                gave = P[l];
+                ++X.aok;
+                X.req += (int64_t)S.s64[i];
+            } else {
+                if (!a.prefilled) a.out[p + i] = FAIL64;
+                ++X.afail;
+            }
+        }
+        if (gave) {
+            X.xg += (uint32_t)gave;
+            X.xsz -= (uint32_t)gave;
+            X.xprev = prev;
+            X.usedg += (int64_t)gave;
+            if (X.xsz == 0) {
+                X.xok = 0;
+                if (X.xright < X.G) rec[X.xright].y = X.xprev;
+                ++X.nosplit;
+            } else {
+                X.xL = flog2(X.xsz);
+            }
+        }
+        q += ev;
+        if (ev == nl) break;
+        seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
+        ++q;
+    }
+    return q;
+}
+#else
+template <int NT>
+HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
+                              uint32_t lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    Rec* rec = a.rec;
+    while (q < stop) {
+        const uint32_t nl = stop - q < 32u ? stop - q : 32u;
+        const uint32_t i = q + lane;
+        const bool in = lane < nl;
+        uint32_t sg = 0, c = 0;
+        uint64_t s = 0;
+        uint8_t cl = CL_NONE;
+        if (in) {
+            sg = S.sgr[i];
+            c = S.ccl[i];
+            s = S.s64[i];
+            cl = CL_FAIL;
+            if (sg) {
+                const uint64_t M = X.mask | (X.xok ? (1ull << X.xL) : 0ull);
+                const uint64_t cand = (M >> c) << c;
+                if (cand) cl = (X.xok && ctz64(cand) == X.xL) ? CL_CARVE : CL_OTHER;
+            }
+        }
+        uint64_t P = cl == CL_CARVE ? sg : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(FULL, P, o);
+            if (lane >= (uint32_t)o) P += t;
+        }
+        bool e = cl == CL_OTHER;
+        uint32_t start = NIL;
+        if (cl == CL_CARVE) {
+            const uint64_t bc = P - sg;
+            start = X.xg + (uint32_t)bc;
+            const int64_t before = (int64_t)X.xsz - (int64_t)bc;
+            uint64_t M = X.mask;
+            uint32_t Lt = 64;
+            if (before > 0) {
+                Lt = flog2((uint32_t)before);
+                M |= 1ull << Lt;
+            }
+            const uint64_t cand = (M >> c) << c;
+            if (!(cand && ctz64(cand) == Lt)) e = true;
+        }
+        const unsigned eb = __ballot_sync(FULL, e);
+        const uint32_t ev = eb ? (uint32_t)(__ffs(eb) - 1) : nl;
+        const bool act = lane < ev;
+        const bool carve = act && cl == CL_CARVE;
+        const bool fail = act && cl == CL_FAIL;
+        const unsigned cb = __ballot_sync(FULL, carve);
+        const unsigned below = cb & ((1u << lane) - 1u);
+        const uint32_t pv = __shfl_sync(FULL, start, below ? 31 - __clz(below) : 0);
+        if (carve) {
+            a.out[p + i] = (uint64_t)start << X.lg;
+            str(rec, start, Rec{mkx(sg, ST_USED), below ? pv : X.xprev, NIL, NIL});
+        }
+        if (fail && !a.prefilled) a.out[p + i] = FAIL64;
+        const unsigned fb = __ballot_sync(FULL, fail);
+        uint64_t rq = carve ? s : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) rq += __shfl_xor_sync(FULL, rq, o);
+        X.aok += __popc(cb);
+        X.afail += __popc(fb);
+        X.req += (int64_t)rq;
+        if (cb) {
+            const int top = 31 - __clz(cb);
+            const uint64_t gave = __shfl_sync(FULL, P, top);
+            const uint32_t last = __shfl_sync(FULL, start, top);
+            X.xg += (uint32_t)gave;
+            X.xsz -= (uint32_t)gave;
+            X.xprev = last;
+            X.usedg += (int64_t)gave;
+            if (X.xsz == 0) {
+                X.xok = 0;
+                if (lane == 0 && X.xright < X.G) rec[X.xright].y = X.xprev;
+                ++X.nosplit;
+            } else {
+                X.xL = flog2(X.xsz);
+            }
+        }
+        q += ev;
+        if (ev == nl) break;
+        if (lane == 0) seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
+        x_bcast(X);
+        ++q;
+    }
+    return q;
+}
+#endif
+
+// The end of a block-wide round, by warp 0 (lane 0 alone in the host
+// emulation): advance X past the carves resolved in parallel, apply the event
+// lane alone, go on with warp-wide rounds when events are dense, and publish
+// where the next round starts.
+template <int NT>
+HBA_DEV void round_tail(Smem<NT>& S, const StepArgs& a, uint32_t p, uint32_t r, uint32_t nres, uint32_t n_here,
+                        uint32_t lane) {
+    Rec* rec = a.rec;
+    XReg X = x_load<NT>(S);
+    const int64_t gave = nres > r ? S.val[nres - 1] : 0;
+    if (gave > 0) {
+        X.xg = S.c0g + (uint32_t)gave;
+        X.xsz = S.c0sz - (uint32_t)gave;
+        X.xprev = last_carve_below<NT>(S, r, nres);
+        X.usedg += gave;
+        if (X.xsz == 0) {
+            X.xok = 0;
+            if (lane == 0 && X.xright < X.G) rec[X.xright].y = X.xprev;
+            ++X.nosplit;
+        } else {
+            X.xL = flog2(X.xsz);
+        }
+    }
+    uint32_t next = n_here;
+    if (nres < n_here) {
+        if (lane == 0) seq_request<NT>(S, a, X, p + nres, S.s64[nres], S.sgr[nres], S.ccl[nres]);
+        x_bcast(X);
+        next = nres + 1;
+        if (nres - r < STRETCH_BELOW) {
+            const uint32_t stop = next + STRETCH_LANES < n_here ? next + STRETCH_LANES : n_here;
+            next = warp_stretch<NT>(S, a, X, p, next, stop, lane);
+        }
+    }
+    if (lane == 0) {
+        x_store<NT>(S, X);
+        S.r = next;
+        S.cont = next < n_here;
+        if (!S.cont) S.p = p + n_here;
+    }
+}
+
 template <int NT>
 HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t na = a.na;
@@ -1016,8 +1375,13 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             S.p = 0;
             S.xok = 0;
             // the record of every list head, for the pops of this phase
-            for (int b = 0; b < NBINS; ++b)
-                if (S.heads[b] != NIL) rec_copy_async(&S.hc[b], rec + S.heads[b]);
+            {
+                S.hissued = 0;
+                for (int b = 0; b < NBINS; ++b) {
+                    S.hseq[b] = NIL;
+                    if (S.heads[b] != NIL) head_copy_async(&S.hc[b], &S.hseq[b], S.hissued, rec + S.heads[b]);
+                }
+            }
         }
     }
     HBA_SYNC();
@@ -1176,11 +1540,10 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             const uint32_t ev = *evp;
             const uint32_t nres = ev < n_here ? ev : n_here;   // lanes [r, nres) are exact
             // C: resolve [r, nres) in parallel (failures, carves from X); then
-            // one thread advances X past those carves, applies the event lane
-            // alone and, when this round resolved (almost) nothing in
-            // parallel, runs ahead through the next lanes one by one.  The
-            // event only touches records outside the carved range and
-            // results of lanes >= nres, so it runs beside the resolve.
+            // warp 0 advances X past those carves, applies the event lane
+            // and, when events are dense, goes on with warp-wide rounds.  The
+            // events only touch records outside the carved range and results
+            // of lanes >= nres, so they run beside the resolve.
             HBA_FOR_THREADS(tid) {
                 if (warp_in_window<NT>(tid >> 5, r, nres)) {
                     const uint8_t cl = S.cls[tid];
@@ -1199,38 +1562,15 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     warp_count(S, tid, C_AOK, is_carve);
                     warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
                 }
-                if (tid == 0) {
+#ifdef HBA_EMULATE
+                if (tid == 0) round_tail<NT>(S, a, p, r, nres, n_here, 0);
+#else
+                if ((tid >> 5) == 0) {
                     HBA_PROF(16);
-                    const int64_t gave = nres > r ? S.val[nres - 1] : 0;
-                    if (gave > 0) {
-                        S.xg = S.c0g + (uint32_t)gave;
-                        S.xsz = S.c0sz - (uint32_t)gave;
-                        S.xprev = last_carve_below<NT>(S, r, nres);
-                        single_add(S, C_USEDG, gave);
-                        if (S.xsz == 0) {
-                            S.xok = 0;
-                            if (S.xright < S.G) rec[S.xright].y = S.xprev;
-                            single_add(S, C_NOSPLIT, 1);
-                        } else {
-                            S.xL = flog2(S.xsz);
-                        }
-                    }
-                    uint32_t next = n_here;
-                    if (nres < n_here) {
-                        seq_request<NT>(S, a, p + nres, S.s64[nres], S.sgr[nres], S.ccl[nres]);
-                        next = nres + 1;
-                        if (nres - r <= RUN_AHEAD_DENSE) {
-                            const uint32_t stop = next + RUN_AHEAD_LANES < n_here ? next + RUN_AHEAD_LANES : n_here;
-                            for (; next < stop; ++next)
-                                seq_request<NT>(S, a, p + next, S.s64[next], S.sgr[next], S.ccl[next]);
-                            HBA_PROF(21);
-                        }
-                    }
+                    round_tail<NT>(S, a, p, r, nres, n_here, (uint32_t)(tid & 31));
                     HBA_PROF(20);
-                    S.r = next;
-                    S.cont = next < n_here;
-                    if (!S.cont) S.p = p + n_here;
                 }
+#endif
             }
             HBA_SYNC();
             HBA_PROF(15);
@@ -1250,7 +1590,11 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         }
     }
     HBA_FOR_THREADS(tid) {
-        if (tid == 0 && S.xok) materialize_x<NT>(S, rec);
+        if (tid == 0 && S.xok) {
+            XReg X = x_load<NT>(S);
+            materialize_x<NT>(S, rec, X);
+            x_store<NT>(S, X);
+        }
         rec_copy_wait();  // no copy may land in shared memory after this arena
     }
     HBA_SYNC();
@@ -1272,12 +1616,28 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t 
             S.xok = 0;
             S.xprev = NIL;
             S.nruns = 0;
+            S.nul = 0;
+            S.nlead = 0;
+            S.flag[0] = S.flag[1] = S.flag[2] = 0;
             S.err = 0;
             S.dyn = dyn;
             S.dyn_words = dyn_words;
         }
+        if (a.nf) {
+            // the free phase's granule table, cleared ahead
+            uint32_t* slot = gt_slots(a.nf, dyn, dyn_words, a.scr);
+            const uint32_t cap = gt_capacity(a.nf);
+            for (uint32_t q = tid; q < cap; q += NT) slot[q] = NIL;
+        }
     }
     HBA_SYNC();
+    HBA_FOR_THREADS(tid) {
+        // the first chunk's request sizes on their way to L2 (inputs: not
+        // written by the preceding grid)
+        const uint32_t n0 = a.na < (uint32_t)NT ? a.na : (uint32_t)NT;
+        for (uint32_t q = (uint32_t)tid * 16u; q < n0; q += 16u * NT) prefetch_l2(a.sizes + q);
+        if (a.wait_prep) grid_dep_wait();
+    }
     HBA_PROF(0);
     if (a.nf) free_phase<NT>(S, a);
     if (a.na) alloc_phase<NT>(S, a);
