@@ -250,6 +250,7 @@ struct Smem {
     Rec hc[NBINS];       // record of each list head (alloc phase), refilled asynchronously
     uint32_t hseq[NBINS];  // copy group of each slot's pending refill (NIL: none)
     uint32_t hissued;      // copy groups issued so far
+    uint32_t szseq;        // thread 0's copy group of the next chunk's request sizes
     // loop control
     uint32_t p, r, cont, evb[2], nul, nruns, flag[3];
     // free phase: run leaders (applied frees with nothing applied to their
@@ -357,6 +358,25 @@ HBA_DEV void head_copy_wait(uint32_t seq, uint32_t issued) {
         case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
         default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
     }
+#endif
+}
+// The request sizes of a chunk are copied in as one copy group per thread;
+// thread 0, which also owns the head refills, numbers it among those.
+template <int NT>
+HBA_DEV void size_copy_commit(Smem<NT>& S, int tid) {
+#ifndef HBA_EMULATE
+    asm volatile("cp.async.commit_group;" ::: "memory");
+#endif
+    if (tid == 0) S.szseq = S.hissued++;
+}
+template <int NT>
+HBA_DEV void size_copy_wait(Smem<NT>& S, int tid) {
+#ifndef HBA_EMULATE
+    if (tid == 0) head_copy_wait(S.szseq, S.hissued);
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+#else
+    (void)S;
+    (void)tid;
 #endif
 }
 HBA_DEV void rec_copy_wait() {
@@ -648,6 +668,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                     }
                 }
                 fence_block();
+                HBA_PROF(9);
                 HBA_UNROLL
                 for (int e = 0; e < 4; ++e) {
                     const uint32_t j = j0 + (uint32_t)e * NT;
@@ -1388,6 +1409,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
     // the first chunk's request sizes, copied in while the loop starts
     HBA_FOR_THREADS(tid) {
         if ((uint32_t)tid < na) u64_copy_async(&S.stg[tid], a.sizes + tid);
+        size_copy_commit<NT>(S, tid);
     }
     while (true) {
         const uint32_t p = S.p;
@@ -1424,7 +1446,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             const uint32_t par = (p / NT) & 1u;
             uint32_t sg = 0, c = 0;
             uint64_t s = 0;
-            rec_copy_wait();
+            size_copy_wait<NT>(S, tid);
             if (i < na) {
                 s = S.stg[par * NT + tid];
                 if (i + NT < na) u64_copy_async(&S.stg[(par ^ 1u) * NT + tid], a.sizes + i + NT);
@@ -1433,6 +1455,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     c = clog2(sg);
                 }
             }
+            size_copy_commit<NT>(S, tid);
             S.sgr[tid] = sg;
             S.ccl[tid] = (uint8_t)c;
             S.s64[tid] = s;
