@@ -51,10 +51,10 @@ BYTES_ALLOC_FAIL = 16
 BYTES_FREE_OK = 216
 BYTES_FREE_REJECTED = 9
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per k_single<1024> launch on the large workload,
-# from an ncu capture of this kernel (profiles/k_single_large16GiB.txt); to
-# be retaken whenever the kernel changes.
-K_SINGLE_LARGE_DRAM_BYTES = 179_584
+# DRAM bytes (read + write) per engine launch on the large workload, from an
+# ncu capture of that kernel (profiles/); None until the current kernel has
+# been captured.
+K_SINGLE_LARGE_DRAM_BYTES = None
 
 
 def _peaks():
@@ -144,8 +144,6 @@ def record_trace(wl, alloc, dev):
         batches.append({"f": df, "s": ds, "out": out, "st": st, "nf": f.size, "na": s.size,
                         "host": (f, stat, s, o),
                         "ops": f.size + s.size, "bytes": nbytes,
-                        # engine launch, plus the prep grid when there are frees or many allocations
-                        "launches": 1 + int(f.size > 0 or s.size >= 2048),
                         "hf": torch.from_numpy(f.view(np.int64).copy()).pin_memory(),
                         "hs": torch.from_numpy(s.view(np.int64).copy()).pin_memory()})
     return batches
@@ -220,7 +218,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag}[args.workload]()
-    alloc = Allocator(wl.arena, wl.min_block, threads=args.threads)
+    alloc = Allocator(wl.arena, wl.min_block, threads=args.threads, ctas=args.ctas)
     batches = record_trace(wl, alloc, dev)
     nb = len(batches)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -240,6 +238,7 @@ def run_gpu(args, rank, world, local_rank):
         launch(batches[pos]); pos += 1
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     idx = []
+    launches = 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -248,9 +247,11 @@ def run_gpu(args, rank, world, local_rank):
             if pos == nb:
                 alloc.reset(); pos = 0
             flush.zero_()
+            c0 = alloc.launches()
             ev[k][0].record(stream)
             launch(batches[pos])
             ev[k][1].record(stream)
+            launches += alloc.launches() - c0
             idx.append(pos); pos += 1
         torch.cuda.synchronize()
     if world > 1:
@@ -259,7 +260,6 @@ def run_gpu(args, rank, world, local_rank):
     busy_s = sum(step_ms) / 1e3
     ops = sum(batches[i]["ops"] for i in idx)
     nbytes = sum(batches[i]["bytes"] for i in idx)
-    launches = sum(batches[i]["launches"] for i in idx)
 
     # e2e through the public host-buffer entry point, from a fresh state
     alloc.reset()
@@ -292,13 +292,19 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": 1e3 * busy_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.name + ": " + wl.note, "parallelism": f"replicas x{world}",
-                   "form": "plain single arena, one launch per batch", "threads_per_cta": alloc_threads(args),
+                   "form": ("plain single arena: one thread-block cluster per batch (engine CTA + CTAs that "
+                            "gather the frees' records into its shared memory and pre-fill failures)"
+                            if args.ctas >= 2 else "plain single arena: prep grid + engine kernel per batch"),
+                   "threads_per_cta": alloc_threads(args),
                    "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
                    "ops_per_step_mean": ops / max(1, args.steps)},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak,
-                     "traffic": K_SINGLE_LARGE_DRAM_BYTES if args.workload == "large" and alloc_threads(args) == 1024 else None,
-                     "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_prep + k_single<1024>",
+                     "traffic": (K_SINGLE_LARGE_DRAM_BYTES
+                                 if args.workload == "large" and alloc_threads(args) == 1024 and args.ctas < 2 else None),
+                     "peak_source": f"{peak_src} hbm_gbs",
+                     "kernel": (f"k_single_cl<{alloc_threads(args)}>" if args.ctas >= 2
+                                else f"k_prep + k_single<{alloc_threads(args)}>"),
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "unit": "per batch of one step"},
@@ -584,6 +590,8 @@ def main():
     ap.add_argument("--batches", type=int, default=200)
     ap.add_argument("--plain-arenas", type=int, default=64)
     ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--ctas", type=int, default=0,
+                    help="single arena: batch cluster size (0 or 1 = prep grid + engine; 2..8 = engine CTA + gathering CTAs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cuda-baseline", action="store_true")
     args = ap.parse_args()

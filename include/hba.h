@@ -207,13 +207,18 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
 
 /* Launch shape of the handle's batch kernel: threads per CTA (one of 64,
  * 128, 256, 512, 1024: a CTA applies one arena's batch; or 32: warp mode,
- * every warp applies its own arena's batch, 8 arenas per CTA), number of
- * CTAs for a multi-arena handle (0 = enough for every arena; fewer CTAs loop
- * over the arenas), and dynamic shared memory per CTA (per warp in warp mode)
- * in bytes (0 = automatic: for a single arena, what the batch's free phase
- * needs; capped at the device limit; a batch whose scratch does not fit uses
- * global scratch instead).  Results do not depend on the shape.  Set by the
- * autotuner or by hand. */
+ * every warp applies its own arena's batch, 8 arenas per CTA); number of
+ * CTAs: for a multi-arena handle, the grid (0 = enough for every arena;
+ * fewer CTAs loop over the arenas); for a single-arena handle with 256 or
+ * more threads, the size of the batch's thread-block cluster (0 or 1 = no
+ * cluster: a separate grid gathers the frees' records and pre-fills
+ * failures, then the engine runs; 2..8 = the engine CTA plus CTAs that
+ * gather the records straight into its shared memory and pre-fill failures,
+ * capped at the cluster size the device holds); and dynamic
+ * shared memory per CTA (per warp in warp mode) in bytes (0 = automatic: for
+ * a single arena, what the batch's free phase needs; capped at the device
+ * limit; a batch whose scratch does not fit uses global scratch instead).
+ * Results do not depend on the shape.  Set by the autotuner or by hand. */
 hba_status_t hba_set_shape(hba_t h, uint32_t threads, uint32_t ctas, uint32_t smem_bytes);
 
 /* ---- the serving loop --------------------------------------------------- */
@@ -278,6 +283,11 @@ hba_status_t hba_serve_run(hba_t h, const hba_arrival_t* d_arrivals, uint64_t n,
 
 /* Version string of the library. */
 const char* hba_version(void);
+
+/* Number of kernels this handle has launched so far (batches, resets,
+ * statistics, serving runs): for accounting what a timed region ran.  No
+ * device work. */
+hba_status_t hba_launch_count(hba_t h, uint64_t* count);
 
 #ifdef __cplusplus
 }

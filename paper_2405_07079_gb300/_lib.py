@@ -36,6 +36,7 @@ SIGNATURES = {
     "hba_set_shape": (i32, [vp, u32, u32, u32]),
     "hba_serve_run": (i32, [vp, vp, u64, vp, vp, u64, vp, vp, vp]),
     "hba_version": (ctypes.c_char_p, []),
+    "hba_launch_count": (i32, [vp, vp]),
 }
 
 

@@ -43,6 +43,8 @@ struct hba_s {
     uint32_t m_threads = 256;   // multi-arena CTA width
     uint32_t m_ctas = 0;        // multi-arena grid (0 = one CTA per arena)
     uint32_t smem_bytes = 0;    // dynamic shared memory per CTA (0 = automatic)
+    uint32_t single_ctas = 0;   // single arena: CTAs of the batch cluster (0, 1 = prep grid + engine)
+    uint64_t launches = 0;      // kernels this handle has launched
     uint64_t* d_largest = nullptr;
 };
 
@@ -63,7 +65,7 @@ namespace {
 constexpr uint32_t MULTI_DYN_BYTES_DEFAULT = 24 * 1024;
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
+__global__ void __launch_bounds__(NT, 1) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
                                                uint8_t* st, const uint64_t* sizes, uint32_t na,
                                                uint64_t* out, uint32_t* scr, const uint32_t* gi,
                                                uint32_t dyn_words, uint32_t prefilled) {
@@ -71,8 +73,62 @@ __global__ void __launch_bounds__(NT) k_single(Arena* ar, Rec* rec, const uint64
     extern __shared__ __align__(16) uint32_t dyn[];
     // waits for the preceding prep grid (gathered records, pre-filled
     // failures) once it has read the arena header
-    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled, 1};
+    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled, hba::WAIT_GRID, 0};
     hba::arena_step<NT>(S, a, dyn, dyn_words);
+}
+
+// Single arena as one thread-block cluster: CTA 0 runs the engine; CTAs
+// 1..n-1 gather the records the frees need (hba::gather_words) straight into
+// CTA 0's shared memory -- or into the global gather buffer when the free
+// phase does not fit there -- and pre-fill out[] with HBA_FAIL, then arrive
+// on the cluster barrier that CTA 0 waits on after reading the arena header.
+// One launch per batch, and the gathered records need no second copy.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_single_cl(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
+                                                  uint8_t* st, const uint64_t* sizes, uint32_t na,
+                                                  uint64_t* out, uint32_t* scr, uint32_t* gi,
+                                                  uint32_t dyn_words, uint32_t prefill, uint32_t staged) {
+    __shared__ hba::Smem<NT> S;
+    extern __shared__ __align__(16) uint32_t dyn[];
+    uint32_t rank, nrank;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(nrank));
+    if (rank == 0) {
+        hba::cluster_arrive_relaxed();
+        hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefill, hba::WAIT_CLUSTER, staged};
+        hba::arena_step<NT>(S, a, dyn, dyn_words);
+        return;
+    }
+    const uint32_t t = (rank - 1) * NT + threadIdx.x, nth = (nrank - 1) * NT;
+    const uint64_t A = ar->arena_bytes;
+    const uint32_t G = ar->G, lg = ar->lg;
+    // CTA 0's dynamic shared memory, in the cluster's shared window
+    uint32_t eng;
+    asm("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(eng) : "r"((uint32_t)__cvta_generic_to_shared(dyn)));
+    for (uint32_t j = t; j < nf; j += nth) {
+        uint32_t w[hba::GATHER_WORDS];
+        hba::gather_words(rec, A, G, lg, frees[j], w);
+#pragma unroll
+        for (uint32_t q = 0; q < hba::GATHER_WORDS; ++q) {
+            if (staged)
+                asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(eng + 4u * (q * nf + j)), "r"(w[q]) : "memory");
+            else
+                gi[q * nf + j] = w[q];
+        }
+    }
+    if (prefill && na) {
+        uint32_t lo = 0;
+        if ((uintptr_t)out & 15) {
+            if (t == 0) out[0] = hba::FAIL64;
+            lo = 1;
+        }
+        ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + lo);
+        const uint32_t npair = (na - lo) / 2;
+        for (uint32_t q = t; q < npair; q += nth) o2[q] = make_ulonglong2(hba::FAIL64, hba::FAIL64);
+        if (((na - lo) & 1) && t == 0) out[na - 1] = hba::FAIL64;
+    }
+    hba::cluster_arrive_release();
+    hba::cluster_wait();
 }
 
 template <int NT>
@@ -99,7 +155,8 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            gi + f0,
                            nf_total,
                            prefilled,
-                           first ? 1u : 0u};
+                           first ? hba::WAIT_GRID : hba::WAIT_NONE,
+                           0};
         first = false;
         hba::arena_step<NT>(S, args, dyn, dyn_words);
     }
@@ -109,7 +166,11 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
 // barriers are __syncwarp), WPC arenas per CTA at a time.  For many small
 // arena batches, where a CTA per arena would spend its time in barriers.
 constexpr int WPC = 8;
-__global__ void __launch_bounds__(WPC * 32) k_multi_warp(Arena* ars, Rec* pool, const uint32_t* frow,
+// at least this many CTAs per SM (a register budget for ptxas; 0 = its choice)
+#ifndef HBA_MULTI_WARP_MINB
+#define HBA_MULTI_WARP_MINB 2
+#endif
+__global__ void __launch_bounds__(WPC * 32, HBA_MULTI_WARP_MINB) k_multi_warp(Arena* ars, Rec* pool, const uint32_t* frow,
                                                           const uint64_t* frees, uint8_t* st, const uint32_t* arow,
                                                           const uint64_t* sizes, uint64_t* out, uint32_t* scr,
                                                           const uint32_t* gi, uint32_t nf_total, uint32_t n_arenas,
@@ -134,7 +195,8 @@ __global__ void __launch_bounds__(WPC * 32) k_multi_warp(Arena* ars, Rec* pool, 
                            gi + f0,
                            nf_total,
                            prefilled,
-                           first ? 1u : 0u};
+                           first ? hba::WAIT_GRID : hba::WAIT_NONE,
+                           0};
         first = false;
         hba::arena_step<32>(S[w], args, mine, warp_dyn_words);
     }
@@ -144,6 +206,7 @@ __global__ void __launch_bounds__(WPC * 32) k_multi_warp(Arena* ars, Rec* pool, 
 struct SmemLimits {
     uint32_t single_dyn = 0, multi_dyn = 0;  // bytes
     uint32_t alloc_words = 0;                 // minimum dynamic words (alloc phase)
+    uint32_t cluster_max = 0;                 // largest batch cluster that fits (0: none)
 };
 
 template <int NT>
@@ -161,6 +224,28 @@ SmemLimits set_smem_limits() {
     if (cudaFuncGetAttributes(&fa, k_multi<NT>) == cudaSuccess) {
         L.multi_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
         cudaFuncSetAttribute(k_multi<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.multi_dyn);
+    }
+    if (NT >= 256 && cudaFuncGetAttributes(&fa, k_single_cl<NT>) == cudaSuccess) {
+        const uint32_t dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_single_cl<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        L.single_dyn = std::min(L.single_dyn, dyn);
+        // the largest portable cluster of such CTAs that the device can hold
+        for (uint32_t n = 8; n >= 2 && !L.cluster_max; n /= 2) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(n);
+            cfg.blockDim = dim3(NT);
+            cfg.dynamicSmemBytes = L.single_dyn;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = n;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, k_single_cl<NT>, &cfg) == cudaSuccess && nc > 0) L.cluster_max = n;
+        }
+        (void)cudaGetLastError();
     }
     return L;
 }
@@ -238,8 +323,8 @@ constexpr uint32_t PREFILL_MIN = 2048;
 
 // Launch the prep grid if the batch needs one; returns whether out[] is
 // pre-filled.  *pdl is set when the next launch may depend on it.
-bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint64_t* out, uint32_t na,
-                 cudaStream_t s, bool* pdl);
+bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint32_t* gi, uint64_t* out,
+                 uint32_t na, cudaStream_t s, bool* pdl);
 
 // Launch with a programmatic dependency on the preceding kernel of the stream.
 template <typename... KArgs, typename... Args>
@@ -288,26 +373,51 @@ __global__ void k_largest(const Arena* ars, const Rec* pool, uint32_t n_arenas, 
     out[a] = best << ar.lg;
 }
 
-bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint64_t* out, uint32_t na,
-                 cudaStream_t s, bool* pdl) {
+bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint32_t* gi, uint64_t* out,
+                 uint32_t na, cudaStream_t s, bool* pdl) {
     const bool fill = na >= PREFILL_MIN;
     *pdl = false;
     if (!nf && !fill) return false;
     const uint32_t work = std::max(nf, fill ? na / 2 : 0u);
     const uint32_t blocks = std::max(1u, std::min<uint32_t>((work + 127) / 128, 2048));
-    k_prep<<<blocks, 128, 0, s>>>(h->d_arenas, h->d_rec, frow, h->n_arenas, frees, nf, h->d_gi,
+    k_prep<<<blocks, 128, 0, s>>>(h->d_arenas, h->d_rec, frow, h->n_arenas, frees, nf, gi,
                                   fill ? out : nullptr, fill ? na : 0);
+    ++h->launches;
     *pdl = true;
     return fill;
 }
 
-hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
-                           const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
+// Launch a batch cluster of n CTAs (one cluster).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster(void (*k)(KArgs...), uint32_t n, uint32_t block, uint32_t dyn, cudaStream_t s,
+                           Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = n;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// One batch of a single arena: the prep grid and the engine kernel, or, when
+// the handle asks for a cluster of 2..8 CTAs and the device holds one, a
+// batch cluster (engine + gathering CTAs).  gi / scr: the gather buffer and
+// the free-phase scratch to use.
+hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
+                           uint32_t na, uint64_t* out, cudaStream_t s, uint32_t* gi, uint32_t* scr) {
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
     const int li = limit_index(h->threads);
-    const uint32_t maxdyn = g_limits[li].single_dyn;
-    const uint32_t base = 4 * g_limits[li].alloc_words;
+    const SmemLimits& L = g_limits[li];
+    const uint32_t maxdyn = L.single_dyn;
+    const uint32_t base = 4 * L.alloc_words;
     uint32_t dyn;
     if (h->smem_bytes) {
         dyn = std::max(base, std::min(h->smem_bytes, maxdyn));
@@ -319,22 +429,36 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     }
     dyn = (dyn + 15u) & ~15u;
     const uint32_t dw = dyn / 4;
+    const bool fill = na >= PREFILL_MIN;
+    cudaError_t e;
+    if (h->threads >= 256 && h->single_ctas >= 2 && L.cluster_max >= 2 && (nf || fill)) {
+        const uint32_t ncl = std::min(h->single_ctas, L.cluster_max);
+        const uint32_t staged = nf && hba::free_smem_words(nf) <= dw ? 1u : 0u;
+        const uint32_t pf = fill ? 1u : 0u;
+        switch (h->threads) {
+            case 256: e = launch_cluster(k_single_cl<256>, ncl, 256, dyn, s, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf, staged); break;
+            case 512: e = launch_cluster(k_single_cl<512>, ncl, 512, dyn, s, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf, staged); break;
+            default: e = launch_cluster(k_single_cl<1024>, ncl, 1024, dyn, s, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf, staged); break;
+        }
+        if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
+        ++h->launches;
+        return HBA_OK;
+    }
     bool pdl = false;
-    const bool pre = launch_prep(h, nullptr, frees, nf, out, na, s, &pdl);
+    const bool pre = launch_prep(h, nullptr, frees, nf, gi, out, na, s, &pdl);
     if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     const uint32_t pf = pre ? 1u : 0u;
-    const uint32_t* gi = h->d_gi;
-    uint32_t* scr = h->d_scr;
-    cudaError_t e;
+    const uint32_t* g = gi;
     switch (h->threads) {
-        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
-        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
-        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
-        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
-        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
-        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf); break;
+        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
+        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
+        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
+        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
+        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
+        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
     }
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
+    ++h->launches;
     return HBA_OK;
 }
 
@@ -345,14 +469,14 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
     // frees beyond the scratch capacity go in consecutive slices (exact:
     // frees apply one by one in index order)
     while (nf > h->max_batch) {
-        hba_status_t r = launch_single(h, frees, h->max_batch, st, nullptr, 0, nullptr, s);
+        hba_status_t r = launch_single(h, frees, h->max_batch, st, nullptr, 0, nullptr, s, h->d_gi, h->d_scr);
         if (r != HBA_OK) return r;
         frees += h->max_batch;
         if (st) st += h->max_batch;
         nf -= h->max_batch;
     }
     if (nf == 0 && na == 0) return HBA_OK;
-    return launch_single(h, frees, nf, st, sizes, na, out, s);
+    return launch_single(h, frees, nf, st, sizes, na, out, s, h->d_gi, h->d_scr);
 }
 
 hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_frees, uint32_t stage) {
@@ -389,6 +513,7 @@ hba_status_t reset_impl(hba_t h, cudaStream_t s) {
     HBA_CUDA_TRY(cudaMemcpyAsync(h->d_arenas, h->h_init.data(), sizeof(Arena) * h->n_arenas,
                                  cudaMemcpyHostToDevice, s));
     k_init_records<<<(h->n_arenas + 255) / 256, 256, 0, s>>>(h->d_arenas, h->d_rec, h->n_arenas);
+    ++h->launches;
     HBA_CUDA_TRY(cudaGetLastError());
     return HBA_OK;
 }
@@ -415,7 +540,7 @@ bool check_geometry(uint64_t arena_bytes, uint64_t min_block, uint32_t* lg, uint
 
 // ---- the serving loop ----------------------------------------------------
 constexpr int SERVE_NT = 256;
-__global__ void __launch_bounds__(SERVE_NT) k_serve(hba::ServeArgs g, uint32_t dyn_words) {
+__global__ void __launch_bounds__(SERVE_NT, 1) k_serve(hba::ServeArgs g, uint32_t dyn_words) {
     __shared__ hba::Smem<SERVE_NT> S;
     __shared__ hba::ServeSmem<SERVE_NT> Q;
     extern __shared__ __align__(16) uint32_t dyn[];
@@ -502,6 +627,7 @@ hba_status_t serve_impl(hba_t h, const hba_arrival_t* arr, uint64_t n, hba_serve
             r = HBA_ERR_CUDA;
         if (r == HBA_OK) {
             k_serve<<<1, SERVE_NT, dyn, s>>>(g, dyn / 4);
+            ++h->launches;
             if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) r = HBA_ERR_CUDA;
         }
         if (r == HBA_OK && cudaMemcpy(rep, g.ctl, sizeof(hba::ServeCtl), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -552,42 +678,7 @@ hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8
     if (!base) return HBA_ERR_CUDA;
     uint32_t* gi = base;
     uint32_t* scr = base + STATIC_GI_WORDS;
-    Arena* ar = h->d_arenas;
-    Rec* rec = h->d_rec;
-    const int li = limit_index(h->threads);
-    const uint32_t maxdyn = g_limits[li].single_dyn;
-    const uint32_t minb = 4 * g_limits[li].alloc_words;
-    uint32_t dyn;
-    if (h->smem_bytes) {
-        dyn = std::max(minb, std::min(h->smem_bytes, maxdyn));
-    } else {
-        const uint64_t hot = 4ull * hba::free_smem_words(nf);
-        dyn = hot <= maxdyn ? (uint32_t)std::max<uint64_t>(hot, minb) : minb;
-    }
-    dyn = (dyn + 15u) & ~15u;
-    const uint32_t dw = dyn / 4;
-    // the prep grid: gather into the static array, pre-fill failures
-    const bool fill = na >= PREFILL_MIN;
-    bool pdl = false;
-    if (nf || fill) {
-        const uint32_t work = std::max(nf, fill ? na / 2 : 0u);
-        const uint32_t blocks = std::max(1u, std::min<uint32_t>((work + 127) / 128, 2048));
-        k_prep<<<blocks, 128, 0, s>>>(ar, rec, nullptr, 1, frees, nf, gi, fill ? out : nullptr, fill ? na : 0);
-        if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
-        pdl = true;
-    }
-    const uint32_t pf = fill ? 1u : 0u;
-    cudaError_t e;
-    switch (h->threads) {
-        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
-        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
-        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
-        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
-        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
-        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, (const uint32_t*)gi, dw, pf); break;
-    }
-    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
-    return HBA_OK;
+    return launch_single(h, frees, nf, st, sizes, na, out, s, gi, scr);
 }
 
 }  // namespace
@@ -607,6 +698,12 @@ hba_status_t hba_step_static(hba_t h, const uint64_t* d_frees, uint32_t nf, uint
 
 
 const char* hba_version(void) { return "hba 0.1 (sm_103a)"; }
+
+hba_status_t hba_launch_count(hba_t h, uint64_t* count) {
+    if (!h || !count) return HBA_ERR_INVALID_ARGUMENT;
+    *count = h->launches;
+    return HBA_OK;
+}
 
 hba_status_t hba_create_ex(uint64_t arena_bytes, uint64_t min_block, int policy, uint32_t max_batch,
                            hba_t* out) {
@@ -719,6 +816,7 @@ hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
     if (!h || !out) return HBA_ERR_INVALID_ARGUMENT;
     HBA_CUDA_TRY(cudaDeviceSynchronize());
     k_largest<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->d_largest);
+    ++h->launches;
     HBA_CUDA_TRY(cudaGetLastError());
     std::vector<Arena> ar(h->n_arenas);
     std::vector<uint64_t> largest(h->n_arenas);
@@ -760,7 +858,10 @@ hba_status_t hba_set_shape(hba_t h, uint32_t threads, uint32_t ctas, uint32_t sm
     if (!h) return HBA_ERR_INVALID_ARGUMENT;
     if (threads != 32 && threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 1024)
         return HBA_ERR_INVALID_ARGUMENT;
-    if (h->n_arenas == 1) h->threads = threads;
+    if (h->n_arenas == 1) {
+        h->threads = threads;
+        h->single_ctas = ctas;
+    }
     h->m_threads = threads;
     h->m_ctas = ctas;
     h->smem_bytes = smem_bytes;
@@ -783,12 +884,13 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
         const uint32_t need = (n + WPC - 1) / WPC;
         const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, need) : need;
         bool pdl = false;
-        const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, d_out, na_total, s, &pdl);
+        const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, h->d_gi, d_out, na_total, s, &pdl);
         if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
         cudaError_t e = launch_pdl(k_multi_warp, grid, WPC * 32, per * WPC, s, pdl, h->d_arenas, h->d_rec, d_free_rowptr,
                                    d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr,
                                    (const uint32_t*)h->d_gi, nf_total, n, per / 4, pre ? 1u : 0u);
         if (e != cudaSuccess) return HBA_ERR_CUDA;
+        ++h->launches;
         return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
     }
     const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
@@ -798,7 +900,7 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     dyn = (std::max(dyn, base) + 15u) & ~15u;
     const uint32_t dw = dyn / 4;
     bool pdl = false;
-    const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, d_out, na_total, s, &pdl);
+    const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, h->d_gi, d_out, na_total, s, &pdl);
     if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     const uint32_t pf = pre ? 1u : 0u;
     Arena* ar = h->d_arenas;
@@ -814,6 +916,7 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
         default: e = launch_pdl(k_multi<256>, grid, 256, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
     }
     if (e != cudaSuccess) return HBA_ERR_CUDA;
+    ++h->launches;
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
 

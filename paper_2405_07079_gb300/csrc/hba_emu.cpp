@@ -24,6 +24,7 @@ struct Emu {
     std::vector<uint32_t> scr;
     int nt;
     uint32_t dyn_words = 600;
+    int staged = 0;  // write the gathered records straight into the shared-memory layout
 };
 
 template <int NT>
@@ -35,12 +36,18 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
     std::vector<uint32_t> gi((size_t)GATHER_WORDS * nf + 1);
     for (uint32_t j = 0; j < nf; ++j)
         gather_free(e->rec.data(), e->ar.arena_bytes, e->ar.G, e->ar.lg, frees[j], gi.data(), nf, j);
-    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0, 0};
+    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0, WAIT_NONE, 0};
     // "shared memory": at least what the alloc phase needs, plus a test knob so
     // that both placements of the free-phase arrays run
     const uint32_t words = std::max(alloc_dyn_words<NT>(), e->dyn_words);
     std::vector<uint64_t> dyn(words / 2 + 1);
-    arena_step<NT>(*S, a, reinterpret_cast<uint32_t*>(dyn.data()), words);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dyn.data());
+    if (e->staged && nf && free_smem_words(nf) <= words) {
+        // what the gathering CTAs of a cluster do on the GPU
+        memcpy(d, gi.data(), sizeof(uint32_t) * GATHER_WORDS * nf);
+        a.staged = 1;
+    }
+    arena_step<NT>(*S, a, d, words);
     delete S;
 }
 }  // namespace
@@ -63,6 +70,7 @@ void* emu_create(uint64_t arena_bytes, uint64_t min_block, int nt) {
 void emu_destroy(void* h) { delete (Emu*)h; }
 
 void emu_set_dyn(void* h, uint32_t words) { ((Emu*)h)->dyn_words = words; }
+void emu_set_staged(void* h, int staged) { ((Emu*)h)->staged = staged; }
 
 int emu_step(void* h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
              uint32_t na, uint64_t* out) {

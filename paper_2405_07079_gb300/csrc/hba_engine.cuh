@@ -111,12 +111,45 @@ constexpr uint32_t GATHER_WORDS = 5;
 // STRETCH_BELOW lanes before its event, one warp goes on through up to
 // STRETCH_LANES lanes with warp-wide rounds (no block barrier), until a
 // window of 32 lanes holds no event
-constexpr uint32_t STRETCH_BELOW = 256;
-constexpr uint32_t STRETCH_LANES = 512;
+#ifndef HBA_STRETCH_BELOW
+#define HBA_STRETCH_BELOW 256
+#endif
+#ifndef HBA_STRETCH_LANES
+#define HBA_STRETCH_LANES 512
+#endif
+// Where events come one after another (the event is the first unresolved
+// lane), speculation resolves nothing: one thread applies the next
+// SERIAL_LANES lanes one by one instead.
+#ifndef HBA_SERIAL_LANES
+#define HBA_SERIAL_LANES 64
+#endif
+constexpr uint32_t STRETCH_BELOW = HBA_STRETCH_BELOW;
+constexpr uint32_t STRETCH_LANES = HBA_STRETCH_LANES;
+constexpr uint32_t SERIAL_LANES = HBA_SERIAL_LANES;
+#ifndef HBA_CARVE_RUN
+#define HBA_CARVE_RUN 4
+#endif
+constexpr uint32_t CARVE_RUN = HBA_CARVE_RUN;
+// a block-wide round that resolved at most SERIAL_AFTER lanes before its
+// event counts as "events one after another"
+#ifndef HBA_SERIAL_AFTER
+#define HBA_SERIAL_AFTER 2
+#endif
+constexpr uint32_t SERIAL_AFTER = HBA_SERIAL_AFTER;
 // free phase: with at most LEAD_MAX runs, every free finds its run by a
 // search among the runs' leaders (in address order); otherwise by pointer
-// jumping, following JUMP_HOPS links per pass
-constexpr uint32_t LEAD_MAX = 64;
+// jumping, following JUMP_HOPS links per pass.  With at most SERIAL_PUSH_MAX
+// runs, one thread pushes the merged blocks; otherwise segments of the push
+// order are linked in parallel.
+#ifndef HBA_LEAD_MAX
+#define HBA_LEAD_MAX 64
+#endif
+#ifndef HBA_SERIAL_PUSH_MAX
+#define HBA_SERIAL_PUSH_MAX 8
+#endif
+constexpr uint32_t LEAD_MAX = HBA_LEAD_MAX;
+constexpr uint32_t SERIAL_PUSH_MAX = HBA_SERIAL_PUSH_MAX;
+static_assert(SERIAL_PUSH_MAX <= LEAD_MAX, "the serial push uses the leader search's order");
 constexpr int JUMP_HOPS = 2;
 // device error codes (Arena::err); any of them means corrupted metadata
 constexpr uint32_t ERR_LIST_WALK = 1;   // an unlink walk ran past the block count
@@ -199,8 +232,8 @@ HBA_DEV void at_add_i64(int64_t* p, int64_t v) {
 //   LL    the left neighbour's own left neighbour when the left one is free
 //   Rend  end of the right neighbour when that one is free, else end of the block
 constexpr uint32_t F_LFREE = 1u << 29, F_RFREE = 1u << 30;
-HBA_HD void gather_free(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, uint64_t off, uint32_t* gi,
-                        uint32_t n, uint32_t j) {
+HBA_HD void gather_words(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, uint64_t off,
+                         uint32_t w[GATHER_WORDS]) {
     uint32_t g = NIL, szf = 0, L = NIL, LL = NIL, Rend = 0;
     if (off < A && (off & ((1ull << lg) - 1ull)) == 0) {
         const uint32_t gg = (uint32_t)(off >> lg);
@@ -224,11 +257,17 @@ HBA_HD void gather_free(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, uin
             }
         }
     }
-    gi[j] = g;
-    gi[n + j] = szf;
-    gi[2 * n + j] = L;
-    gi[3 * n + j] = LL;
-    gi[4 * n + j] = Rend;
+    w[0] = g;
+    w[1] = szf;
+    w[2] = L;
+    w[3] = LL;
+    w[4] = Rend;
+}
+HBA_HD void gather_free(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, uint64_t off, uint32_t* gi,
+                        uint32_t n, uint32_t j) {
+    uint32_t w[GATHER_WORDS];
+    gather_words(rec, A, G, lg, off, w);
+    for (uint32_t q = 0; q < GATHER_WORDS; ++q) gi[q * n + j] = w[q];
 }
 
 // ---- shared state of one CTA --------------------------------------------
@@ -248,9 +287,6 @@ struct Smem {
     uint32_t xok, xg, xsz, xright, xL, xprev;
     uint32_t c0g, c0sz, c0prev;  // X when the current round classified its lanes
     Rec hc[NBINS];       // record of each list head (alloc phase), refilled asynchronously
-    uint32_t hseq[NBINS];  // copy group of each slot's pending refill (NIL: none)
-    uint32_t hissued;      // copy groups issued so far
-    uint32_t szseq;        // thread 0's copy group of the next chunk's request sizes
     // loop control
     uint32_t p, r, cont, evb[2], nul, nruns, flag[3];
     // free phase: run leaders (applied frees with nothing applied to their
@@ -328,55 +364,6 @@ HBA_DEV void u64_copy_async(uint64_t* dst_smem, const uint64_t* src) {
 #else
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-#endif
-}
-// Copy the record of list k's head into the cache slot S.hc[k] as its own
-// copy group, and wait for that slot's copy only (groups complete in order:
-// wait until at most the number of groups issued after it are pending).  One
-// thread owns the slots.
-HBA_DEV void head_copy_async(Rec* slot, uint32_t* seq, uint32_t& issued, const Rec* src) {
-    rec_copy_async(slot, src);
-#ifndef HBA_EMULATE
-    asm volatile("cp.async.commit_group;" ::: "memory");
-#endif
-    *seq = issued++;
-}
-HBA_DEV void head_copy_wait(uint32_t seq, uint32_t issued) {
-#ifdef HBA_EMULATE
-    (void)seq;
-    (void)issued;
-#else
-    if (seq == NIL) return;
-    const uint32_t after = issued - 1u - seq;  // groups issued after this one
-    switch (after < 7u ? after : 7u) {
-        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
-        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
-        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
-        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
-    }
-#endif
-}
-// The request sizes of a chunk are copied in as one copy group per thread;
-// thread 0, which also owns the head refills, numbers it among those.
-template <int NT>
-HBA_DEV void size_copy_commit(Smem<NT>& S, int tid) {
-#ifndef HBA_EMULATE
-    asm volatile("cp.async.commit_group;" ::: "memory");
-#endif
-    if (tid == 0) S.szseq = S.hissued++;
-}
-template <int NT>
-HBA_DEV void size_copy_wait(Smem<NT>& S, int tid) {
-#ifndef HBA_EMULATE
-    if (tid == 0) head_copy_wait(S.szseq, S.hissued);
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-#else
-    (void)S;
-    (void)tid;
 #endif
 }
 HBA_DEV void rec_copy_wait() {
@@ -492,10 +479,15 @@ struct StepArgs {
     uint32_t gstride;
     uint32_t prefilled;  // out[] already holds HBA_FAIL everywhere (written by a
                          // preceding grid): failures need no store
-    uint32_t wait_prep;  // wait for the preceding grid (programmatic dependent
-                         // launch) after reading the arena header, before
-                         // touching what that grid writes (gathered records, out[])
+    uint32_t wait_prep;  // after reading the arena header, before touching what
+                         // the gathering threads write (gathered records, out[]):
+                         // WAIT_NONE, WAIT_GRID (preceding grid, programmatic
+                         // dependent launch) or WAIT_CLUSTER (the other CTAs of
+                         // this cluster)
+    uint32_t staged;     // the gathered records are already in the free phase's
+                         // shared-memory layout (written there by the cluster)
 };
+constexpr uint32_t WAIT_NONE = 0, WAIT_GRID = 1, WAIT_CLUSTER = 2;
 
 HBA_DEV void fence_block() {
 #ifndef HBA_EMULATE
@@ -505,6 +497,24 @@ HBA_DEV void fence_block() {
 HBA_DEV void grid_dep_wait() {
 #ifndef HBA_EMULATE
     asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+// Cluster barrier halves: the engine CTA arrives early (it publishes nothing)
+// and waits when it needs what the other CTAs wrote; they arrive with release
+// semantics once their writes are done.
+HBA_DEV void cluster_arrive_relaxed() {
+#ifndef HBA_EMULATE
+    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+#endif
+}
+HBA_DEV void cluster_arrive_release() {
+#ifndef HBA_EMULATE
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+#endif
+}
+HBA_DEV void cluster_wait() {
+#ifndef HBA_EMULATE
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 #endif
 }
 
@@ -545,8 +555,7 @@ HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec, XReg& X, bool cache = false) {
     const Rec r{mkx(X.xsz, ST_FREE), X.xprev, old, NIL};
     str(rec, X.xg, r);
     if (cache) {
-        head_copy_wait(S.hseq[b], S.hissued);  // no copy may still be landing in the slot
-        S.hseq[b] = NIL;
+        rec_copy_wait();  // no copy may still be landing in the slot
         S.hc[b] = r;
     }
     if (old != NIL) rec[old].w = X.xg;
@@ -647,7 +656,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     // before the free is inserted, so that whoever finds it in the table
     // reads its key.
     HBA_FOR_THREADS(tid) {
-        if (sm) {
+        if (sm && !a.staged) {
             const uint32_t gs = a.gstride;
             uint32_t* d = S.dyn;
             // four frees of a thread at a time: their 20 loads in flight together
@@ -911,7 +920,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     HBA_SYNC();
     HBA_PROF(6);
     uint32_t nruns;
-    if (nlead <= LEAD_MAX) {
+    if (nlead <= SERIAL_PUSH_MAX) {
         // F7/F8, few runs: rank the runs by their last free index, then one
         // thread pushes the merged blocks in that order
         nruns = nlead;
@@ -1038,7 +1047,6 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
     if (!cand) {
         if (!a.prefilled) a.out[i] = FAIL64;
         ++X.afail;
-        HBA_PROF(24);
         return;
     }
     const uint32_t k = ctz64(cand);
@@ -1057,7 +1065,6 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
         } else {
             X.xL = flog2(X.xsz);
         }
-        HBA_PROF(22);
     } else {
         // pop the head of list k (its record is cached); the old X becomes a
         // listed block first
@@ -1070,16 +1077,15 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
             ++X.afail;
             return;
         }
-        head_copy_wait(S.hseq[k], S.hissued);
+        rec_copy_wait();
         const Rec ry = S.hc[k];
         const uint32_t nxt = ry.z;
         S.heads[k] = nxt;
-        S.hseq[k] = NIL;
         if (nxt == NIL) {
             X.mask &= ~(1ull << k);
         } else {
             rec[nxt].w = NIL;
-            head_copy_async(&S.hc[k], &S.hseq[k], S.hissued, rec + nxt);  // the new head, for a later pop
+            rec_copy_async(&S.hc[k], rec + nxt);  // the new head, for a later pop
         }
         const uint32_t ysz = sz_of(ry.x);
         str(rec, Y, Rec{mkx(sg, ST_USED), ry.y, NIL, NIL});
@@ -1094,7 +1100,6 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
         } else {
             ++X.nosplit;
         }
-        HBA_PROF(23);
     }
     ++X.aok;
     X.usedg += sg;
@@ -1156,6 +1161,31 @@ HBA_DEV void x_bcast(XReg& X) {
 #else
     (void)X;
 #endif
+}
+
+// Lane q (an event) alone, then up to `more` further lanes one by one (one
+// thread), stopping before the lane that would make more than CARVE_RUN
+// carves from X in a row (long stretches of carves go faster in parallel);
+// returns the first lane not applied.
+template <int NT>
+HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
+                         uint32_t more) {
+    seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
+    ++q;
+    const uint32_t end = q + more < stop ? q + more : stop;
+    uint32_t carves = 0;
+    for (; q < end; ++q) {
+        const uint32_t sg = S.sgr[q], c = S.ccl[q];
+        bool carve = false;
+        if (sg && X.xok) {
+            const uint64_t cand = ((X.mask | (1ull << X.xL)) >> c) << c;
+            carve = cand && ctz64(cand) == X.xL;
+        }
+        carves = carve ? carves + 1 : 0;
+        if (carves > CARVE_RUN) break;
+        seq_request<NT>(S, a, X, p + q, S.s64[q], sg, c);
+    }
+    return q;
 }
 
 // Lanes [q, stop) of the chunk, applied by one warp in windows of 32 lanes:
@@ -1239,8 +1269,7 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
         }
         q += ev;
         if (ev == nl) break;
-        seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
-        ++q;
+        q = seq_run<NT>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
     }
     return q;
 }
@@ -1327,9 +1356,10 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
         }
         q += ev;
         if (ev == nl) break;
-        if (lane == 0) seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
+        uint32_t qn = 0;
+        if (lane == 0) qn = seq_run<NT>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
+        q = __shfl_sync(FULL, qn, 0);
         x_bcast(X);
-        ++q;
     }
     return q;
 }
@@ -1360,10 +1390,17 @@ HBA_DEV void round_tail(Smem<NT>& S, const StepArgs& a, uint32_t p, uint32_t r, 
     }
     uint32_t next = n_here;
     if (nres < n_here) {
-        if (lane == 0) seq_request<NT>(S, a, X, p + nres, S.s64[nres], S.sgr[nres], S.ccl[nres]);
+        // the event lane, and when (almost) nothing came before it, the next
+        // few one by one
+        uint32_t qn = 0;
+        if (lane == 0) qn = seq_run<NT>(S, a, X, p, nres, n_here, nres - r <= SERIAL_AFTER ? SERIAL_LANES : 0);
+#ifdef HBA_EMULATE
+        next = qn;
+#else
+        next = __shfl_sync(0xffffffffu, qn, 0);
+#endif
         x_bcast(X);
-        next = nres + 1;
-        if (nres - r < STRETCH_BELOW) {
+        if (next < n_here && nres - r < STRETCH_BELOW) {
             const uint32_t stop = next + STRETCH_LANES < n_here ? next + STRETCH_LANES : n_here;
             next = warp_stretch<NT>(S, a, X, p, next, stop, lane);
         }
@@ -1396,20 +1433,14 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             S.p = 0;
             S.xok = 0;
             // the record of every list head, for the pops of this phase
-            {
-                S.hissued = 0;
-                for (int b = 0; b < NBINS; ++b) {
-                    S.hseq[b] = NIL;
-                    if (S.heads[b] != NIL) head_copy_async(&S.hc[b], &S.hseq[b], S.hissued, rec + S.heads[b]);
-                }
-            }
+            for (int b = 0; b < NBINS; ++b)
+                if (S.heads[b] != NIL) rec_copy_async(&S.hc[b], rec + S.heads[b]);
         }
     }
     HBA_SYNC();
     // the first chunk's request sizes, copied in while the loop starts
     HBA_FOR_THREADS(tid) {
         if ((uint32_t)tid < na) u64_copy_async(&S.stg[tid], a.sizes + tid);
-        size_copy_commit<NT>(S, tid);
     }
     while (true) {
         const uint32_t p = S.p;
@@ -1446,7 +1477,7 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             const uint32_t par = (p / NT) & 1u;
             uint32_t sg = 0, c = 0;
             uint64_t s = 0;
-            size_copy_wait<NT>(S, tid);
+            rec_copy_wait();
             if (i < na) {
                 s = S.stg[par * NT + tid];
                 if (i + NT < na) u64_copy_async(&S.stg[(par ^ 1u) * NT + tid], a.sizes + i + NT);
@@ -1455,7 +1486,6 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     c = clog2(sg);
                 }
             }
-            size_copy_commit<NT>(S, tid);
             S.sgr[tid] = sg;
             S.ccl[tid] = (uint8_t)c;
             S.s64[tid] = s;
@@ -1659,7 +1689,8 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t 
         // written by the preceding grid)
         const uint32_t n0 = a.na < (uint32_t)NT ? a.na : (uint32_t)NT;
         for (uint32_t q = (uint32_t)tid * 16u; q < n0; q += 16u * NT) prefetch_l2(a.sizes + q);
-        if (a.wait_prep) grid_dep_wait();
+        if (a.wait_prep == WAIT_GRID) grid_dep_wait();
+        else if (a.wait_prep == WAIT_CLUSTER) cluster_wait();
     }
     HBA_PROF(0);
     if (a.nf) free_phase<NT>(S, a);

@@ -253,7 +253,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
         for (uint32_t j = tid; j < nf; j += NT)
             gather_free(g.rec, A, g.ar->G, lg, g.t_frees[j], g.gi, nf, j);
         __syncthreads();
-        StepArgs a{g.ar, g.rec, g.t_frees, nf, nullptr, g.t_sizes, na, g.t_out, g.scr, g.gi, nf, 0, 0};
+        StepArgs a{g.ar, g.rec, g.t_frees, nf, nullptr, g.t_sizes, na, g.t_out, g.scr, g.gi, nf, 0, WAIT_NONE, 0};
         arena_step<NT>(S, a, dyn, dyn_words);
         if (tid == 0) Q.now = globaltimer_ns() - Q.t0;
         __syncthreads();

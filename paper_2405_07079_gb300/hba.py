@@ -147,6 +147,13 @@ def hba_version() -> str:
     return _lib().hba_version().decode()
 
 
+def hba_launch_count(h: int) -> int:
+    """Kernels the handle has launched so far."""
+    c = ctypes.c_uint64(0)
+    check("hba_launch_count", _lib().hba_launch_count(h, ctypes.byref(c)))
+    return c.value
+
+
 # ---- torch convenience wrappers ----------------------------------------------
 
 def _torch():
@@ -168,13 +175,16 @@ class Allocator:
     """One arena.  Inputs/outputs are uint64 (int64-typed) CUDA tensors."""
 
     def __init__(self, arena_bytes: int, min_block: int, max_batch: int = 65536, threads: int | None = None,
-                 smem_bytes: int = 0):
+                 smem_bytes: int = 0, ctas: int = 0):
+        """``ctas``: size of the batch's thread-block cluster (0 or 1: a
+        separate gathering grid, then the engine; 2..8: the engine CTA plus
+        gathering CTAs; see hba_set_shape)."""
         self.h = hba_create(arena_bytes, min_block, HBA_POLICY_SEGFIT, max_batch)
         self.arena_bytes = arena_bytes - arena_bytes % min_block
         self.min_block = min_block
         self.max_batch = max_batch
-        if threads is not None or smem_bytes:
-            hba_set_shape(self.h, threads or 1024, 0, smem_bytes)
+        if threads is not None or smem_bytes or ctas:
+            hba_set_shape(self.h, threads or 1024, ctas, smem_bytes)
 
     def close(self):
         if self.h:
@@ -212,6 +222,9 @@ class Allocator:
 
     def stats(self) -> dict:
         return hba_stats(self.h)
+
+    def launches(self) -> int:
+        return hba_launch_count(self.h)
 
     def export_state(self) -> np.ndarray:
         return hba_export_state(self.h, 0)

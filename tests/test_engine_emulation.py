@@ -37,15 +37,17 @@ def emu():
     lib.emu_export.argtypes = [vp, vp, ctypes.c_size_t]
     lib.emu_stats.argtypes = [vp, vp]
     lib.emu_set_dyn.argtypes = [vp, u32]
+    lib.emu_set_staged.argtypes = [vp, ctypes.c_int]
     return lib
 
 
 class Emu:
-    def __init__(self, lib, A, mb, nt, dyn_words=None):
+    def __init__(self, lib, A, mb, nt, dyn_words=None, staged=False):
         self.lib, self.h = lib, lib.emu_create(A, mb, nt)
         assert self.h
         if dyn_words is not None:
             lib.emu_set_dyn(self.h, dyn_words)
+        lib.emu_set_staged(self.h, int(staged))
 
     def batch(self, f, s):
         f = np.ascontiguousarray(f, np.uint64)
@@ -71,9 +73,9 @@ class Emu:
         self.lib.emu_destroy(self.h)
 
 
-def _check(emu, wl, nt, every=1, dyn_words=None):
+def _check(emu, wl, nt, every=1, dyn_words=None, staged=False):
     trace, o = oracle_trace(wl)
-    e = Emu(emu, wl.arena, wl.min_block, nt, dyn_words)
+    e = Emu(emu, wl.arena, wl.min_block, nt, dyn_words, staged)
     import oracle as _o
     ref = _o.Oracle(wl.arena, wl.min_block)
     try:
@@ -117,6 +119,17 @@ def test_lifetimes(emu, nt):
     from paper_2405_07079_gb300 import workloads as W
     wl = W.Workload("life", 1 << 30, 512, lambda: W.Lifetimes(n_ops=300_000, batch=8192, mean_life=100))
     _check(emu, wl, nt, every=4)
+
+
+@pytest.mark.parametrize("nt", [256, 1024])
+def test_staged_by_cluster(emu, nt):
+    """The gathered records written straight into the free phase's shared
+    memory (what the gathering CTAs of a cluster do), with the table and the
+    per-free arrays after them."""
+    from paper_2405_07079_gb300 import workloads as W
+    wl = W.Workload("life", 1 << 28, 512, lambda: W.Lifetimes(n_ops=200_000, batch=4096, mean_life=60))
+    _check(emu, wl, nt, every=3, dyn_words=1 << 20, staged=True)
+    _check(emu, W.tiny(n_ops=6000), nt, dyn_words=1 << 20, staged=True)
 
 
 @pytest.mark.parametrize("nt", [32, 1024])

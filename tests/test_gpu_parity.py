@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 KiB, MiB, GiB = 1 << 10, 1 << 20, 1 << 30
 
 
-def _run(wl, threads=None, max_batches=None, state_every=0, canary=False):
+def _run(wl, threads=None, max_batches=None, state_every=0, canary=False, ctas=0):
     import torch
 
     from paper_2405_07079_gb300 import Allocator
@@ -27,7 +27,7 @@ def _run(wl, threads=None, max_batches=None, state_every=0, canary=False):
         # a real arena of the managed size, filled with the canary byte; the
         # allocator never receives its address, so it must stay untouched
         guard = torch.full((wl.arena,), 0xA5, dtype=torch.uint8, device=dev)
-    with Allocator(wl.arena, wl.min_block, threads=threads) as a:
+    with Allocator(wl.arena, wl.min_block, threads=threads, ctas=ctas) as a:
         for b, (f, s, out, st) in enumerate(trace):
             dst = torch.empty(f.size, dtype=torch.uint8, device=dev)
             go = from_dev(a.step(to_dev(f, dev), to_dev(s, dev), status=dst)) if s.size else np.zeros(0, np.uint64)
@@ -76,20 +76,38 @@ def test_worked_examples(gpu_lib):
                 assert [int(x) for x in a.export_state()] == case["final"], case["name"]
 
 
-@pytest.mark.parametrize("threads", [32, 128, 256, 512, 1024])
-def test_tiny_full(gpu_lib, threads):
-    """1 MiB arena, 10,000 ops in batches of 64, canary arena untouched."""
+@pytest.mark.parametrize("threads,ctas", [(32, 0), (128, 0), (256, 0), (512, 0), (1024, 0), (256, 1), (1024, 1),
+                                          (1024, 2), (512, 8)])
+def test_tiny_full(gpu_lib, threads, ctas):
+    """1 MiB arena, 10,000 ops in batches of 64, canary arena untouched;
+    every CTA width, with and without the gathering cluster."""
     from paper_2405_07079_gb300 import workloads as W
 
-    _run(W.tiny(), threads=threads, state_every=16, canary=True)
+    _run(W.tiny(), threads=threads, state_every=16, canary=True, ctas=ctas)
 
 
-@pytest.mark.parametrize("threads", [128, 1024])
-def test_large_reduced(gpu_lib, threads):
+@pytest.mark.parametrize("threads,ctas", [(128, 0), (1024, 0), (1024, 1), (256, 3)])
+def test_large_reduced(gpu_lib, threads, ctas):
     from paper_2405_07079_gb300 import workloads as W
 
     wl = W.Workload("large-1GiB", 1 * GiB, 512, lambda: W.Lifetimes(n_ops=400_000, batch=8192, mean_life=300))
-    _run(wl, threads=threads, state_every=5)
+    _run(wl, threads=threads, state_every=5, ctas=ctas)
+
+
+@pytest.mark.parametrize("ctas,per_batch", [(0, 2), (4, 1)])
+def test_launches_per_batch(gpu_lib, ctas, per_batch):
+    """A batch with frees is the prep grid plus the engine, or one cluster
+    launch (counted by the handle)."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator
+
+    dev = torch.device("cuda")
+    with Allocator(1 << 24, 256, threads=1024, ctas=ctas) as a:
+        out = a.step(None, torch.full((8,), 4096, dtype=torch.int64, device=dev))
+        n0 = a.launches()
+        a.step(out[:4], torch.full((4,), 512, dtype=torch.int64, device=dev))
+        assert a.launches() - n0 == per_batch
 
 
 def test_large_full(gpu_lib):
