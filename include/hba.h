@@ -145,14 +145,14 @@ hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_
  * is a packaging choice of this library.
  *
  * Every handle normally carries its own device scratch for batch work,
- * allocated by hba_create* and proportional to max_batch (about 84 bytes per
+ * allocated by hba_create* and proportional to max_batch (about 92 bytes per
  * free).  Some callers cannot afford that allocation: a process that keeps
  * many small handles under a fixed device-memory budget, or one whose device
  * memory is reserved up front by another pool, so that cudaMalloc would fail
  * or would have to be avoided.  Such callers can create their handles with
  * max_batch = 1 and run their batches here.  This call makes no allocation
  * at all: its kernels use one static device array compiled into the library
- * (room for HBA_STATIC_MAX_FREES frees, 336 KiB, held by every device
+ * (room for HBA_STATIC_MAX_FREES frees, 368 KiB, held by every device
  * that loads the library until the process exits).
  *
  * Same arguments, results and stream semantics as hba_step.  nf above

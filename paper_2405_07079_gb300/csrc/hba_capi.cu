@@ -166,11 +166,11 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
 // barriers are __syncwarp), WPC arenas per CTA at a time.  For many small
 // arena batches, where a CTA per arena would spend its time in barriers.
 constexpr int WPC = 8;
-// at least this many CTAs per SM (a register budget for ptxas; 0 = its choice)
-#ifndef HBA_MULTI_WARP_MINB
-#define HBA_MULTI_WARP_MINB 2
-#endif
-__global__ void __launch_bounds__(WPC * 32, HBA_MULTI_WARP_MINB) k_multi_warp(Arena* ars, Rec* pool, const uint32_t* frow,
+// MINB: at least this many CTAs per SM, a register budget for ptxas.  Two
+// builds: 2 CTAs per SM (more registers, no spills) when the grid fits the
+// SMs at that occupancy, 4 when it does not (more CTAs resident at once).
+template <int MINB>
+__global__ void __launch_bounds__(WPC * 32, MINB) k_multi_warp(Arena* ars, Rec* pool, const uint32_t* frow,
                                                           const uint64_t* frees, uint8_t* st, const uint32_t* arow,
                                                           const uint64_t* sizes, uint64_t* out, uint32_t* scr,
                                                           const uint32_t* gi, uint32_t nf_total, uint32_t n_arenas,
@@ -207,6 +207,7 @@ struct SmemLimits {
     uint32_t single_dyn = 0, multi_dyn = 0;  // bytes
     uint32_t alloc_words = 0;                 // minimum dynamic words (alloc phase)
     uint32_t cluster_max = 0;                 // largest batch cluster that fits (0: none)
+    uint32_t sms = 0;                         // SMs of the device (warp mode)
 };
 
 template <int NT>
@@ -274,11 +275,16 @@ SmemLimits set_smem_limits_warp() {
         L.single_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
         cudaFuncSetAttribute(k_single<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn);
     }
-    if (cudaFuncGetAttributes(&fa, k_multi_warp) == cudaSuccess) {
+    if (cudaFuncGetAttributes(&fa, k_multi_warp<2>) == cudaSuccess) {
         const uint32_t total = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
-        cudaFuncSetAttribute(k_multi_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
+        cudaFuncSetAttribute(k_multi_warp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
+        cudaFuncSetAttribute(k_multi_warp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
         L.multi_dyn = (total / WPC) & ~15u;  // per warp
     }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    L.cluster_max = 0;
+    L.sms = (uint32_t)sms;
     return L;
 }
 
@@ -886,7 +892,8 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
         bool pdl = false;
         const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, h->d_gi, d_out, na_total, s, &pdl);
         if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
-        cudaError_t e = launch_pdl(k_multi_warp, grid, WPC * 32, per * WPC, s, pdl, h->d_arenas, h->d_rec, d_free_rowptr,
+        auto k = grid <= 2 * L.sms ? k_multi_warp<2> : k_multi_warp<4>;
+        cudaError_t e = launch_pdl(k, grid, WPC * 32, per * WPC, s, pdl, h->d_arenas, h->d_rec, d_free_rowptr,
                                    d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr,
                                    (const uint32_t*)h->d_gi, nf_total, n, per / 4, pre ? 1u : 0u);
         if (e != cudaSuccess) return HBA_ERR_CUDA;

@@ -103,9 +103,9 @@ constexpr uint32_t ST_NONE = 0, ST_USED = 1, ST_FREE = 2, ST_NEW = 3, ST_DEL = 4
 constexpr uint64_t FAIL64 = ~0ull;
 constexpr int NBINS = 32;  // granule classes 0..28 are reachable
 // global scratch per free: absorbed blocks (2 words) always; the free
-// phase's working arrays (table < 4, 7 per-free arrays, 2 absorbed) when
+// phase's working arrays (table < 8, 7 per-free arrays, 2 absorbed) when
 // they do not fit in shared memory
-constexpr uint32_t SCRATCH_WORDS_PER_FREE = 16;
+constexpr uint32_t SCRATCH_WORDS_PER_FREE = 18;
 constexpr uint32_t GATHER_WORDS = 5;
 // alloc phase: after a block-wide round that resolved fewer than
 // STRETCH_BELOW lanes before its event, one warp goes on through up to
@@ -136,6 +136,11 @@ constexpr uint32_t CARVE_RUN = HBA_CARVE_RUN;
 #define HBA_SERIAL_AFTER 2
 #endif
 constexpr uint32_t SERIAL_AFTER = HBA_SERIAL_AFTER;
+// record tables up to this size are prefetched into L2 whole at batch start
+#ifndef HBA_PREFETCH_TABLE_MAX
+#define HBA_PREFETCH_TABLE_MAX (2u << 20)
+#endif
+constexpr uint64_t PREFETCH_TABLE_MAX = HBA_PREFETCH_TABLE_MAX;
 // free phase: with at most LEAD_MAX runs, every free finds its run by a
 // search among the runs' leaders (in address order); otherwise by pointer
 // jumping, following JUMP_HOPS links per pass.  With at most SERIAL_PUSH_MAX
@@ -207,6 +212,8 @@ HBA_DEV uint32_t at_max_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; if (v > 
 HBA_DEV uint32_t at_add_u32(uint32_t* p, uint32_t v) { uint32_t o = *p; *p = o + v; return o; }
 HBA_DEV void at_add_i64(int64_t* p, int64_t v) { *p += v; }
 HBA_DEV uint32_t at_cas_u32(uint32_t* p, uint32_t cmp, uint32_t v) { uint32_t o = *p; if (o == cmp) *p = v; return o; }
+HBA_DEV uint64_t at_cas_u64(uint64_t* p, uint64_t cmp, uint64_t v) { uint64_t o = *p; if (o == cmp) *p = v; return o; }
+HBA_DEV uint64_t at_min_u64(uint64_t* p, uint64_t v) { uint64_t o = *p; if (v < o) *p = v; return o; }
 #else
 HBA_DEV Rec ldr(const Rec* r, uint32_t g) {
     uint4 v = *reinterpret_cast<const uint4*>(r + g);
@@ -217,6 +224,12 @@ HBA_DEV uint32_t at_min_u32(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
 HBA_DEV uint32_t at_max_u32(uint32_t* p, uint32_t v) { return atomicMax(p, v); }
 HBA_DEV uint32_t at_add_u32(uint32_t* p, uint32_t v) { return atomicAdd(p, v); }
 HBA_DEV uint32_t at_cas_u32(uint32_t* p, uint32_t cmp, uint32_t v) { return atomicCAS(p, cmp, v); }
+HBA_DEV uint64_t at_cas_u64(uint64_t* p, uint64_t cmp, uint64_t v) {
+    return atomicCAS(reinterpret_cast<unsigned long long*>(p), (unsigned long long)cmp, (unsigned long long)v);
+}
+HBA_DEV uint64_t at_min_u64(uint64_t* p, uint64_t v) {
+    return atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
 HBA_DEV void at_add_i64(int64_t* p, int64_t v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
@@ -570,21 +583,23 @@ HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec, XReg& X, bool cache = false) {
 // ---------------------------------------------------------------------------
 
 // Open-addressing table: granule -> lowest free index that names it.  A slot
-// holds a free index j; its key is the granule gG[j] of that free.  Only
-// valid frees (starts of in-use blocks) are inserted.
+// holds the key and the free index in one 64-bit word (granule << 32 | j),
+// so that a probe is one load and duplicates of a key keep the lowest index
+// with a 64-bit min.  Only valid frees (starts of in-use blocks) go in.
+constexpr uint64_t GT_EMPTY = ~0ull;
 struct GTable {
-    uint32_t* slot;
-    const uint32_t* gG;
+    uint64_t* slot;
     uint32_t mask;  // capacity - 1 (capacity: power of two >= 2 * keys)
 };
 HBA_DEV uint32_t gt_hash(uint32_t g, uint32_t mask) { return (g * 0x9E3779B1u >> 7) & mask; }
 HBA_DEV void gt_insert_min(const GTable& t, uint32_t g, uint32_t j) {
+    const uint64_t kv = (uint64_t)g << 32 | j;
     uint32_t s = gt_hash(g, t.mask);
     while (true) {
-        const uint32_t k = at_cas_u32(&t.slot[s], NIL, j);
-        if (k == NIL) return;
-        if (t.gG[k] == g) {
-            at_min_u32(&t.slot[s], j);
+        const uint64_t old = at_cas_u64(&t.slot[s], GT_EMPTY, kv);
+        if (old == GT_EMPTY) return;
+        if ((uint32_t)(old >> 32) == g) {
+            at_min_u64(&t.slot[s], kv);
             return;
         }
         s = (s + 1) & t.mask;
@@ -594,26 +609,28 @@ HBA_DEV void gt_insert_min(const GTable& t, uint32_t g, uint32_t j) {
 HBA_DEV uint32_t gt_find(const GTable& t, uint32_t g) {
     uint32_t s = gt_hash(g, t.mask);
     while (true) {
-        const uint32_t k = t.slot[s];
-        if (k == NIL) return NIL;
-        if (t.gG[k] == g) return k;
+        const uint64_t v = t.slot[s];
+        if (v == GT_EMPTY) return NIL;
+        if ((uint32_t)(v >> 32) == g) return (uint32_t)v;
         s = (s + 1) & t.mask;
     }
 }
-// Capacity of the granule table for nf frees, and the shared-memory words of
-// the free phase (gathered records 5 nf, table, roots, per-run maxima, run
-// slots, run heads and flags 6 nf).
+// Capacity of the granule table for nf frees (slots of two words), where it
+// starts (word offset, even: after the five staged words per free), and the
+// shared-memory words of the free phase (gathered records 5 nf, table,
+// roots, per-run maxima, run slots, run heads and flags 6 nf).
 HBA_HD uint32_t gt_capacity(uint32_t nf) {
     uint32_t c = 2;
     while (c < 2 * nf) c <<= 1;
     return c;
 }
-HBA_HD uint32_t free_smem_words(uint32_t nf) { return 11 * nf + gt_capacity(nf) + 4; }
+HBA_HD uint32_t gt_offset(uint32_t nf) { return (GATHER_WORDS * nf + 1u) & ~1u; }
+HBA_HD uint32_t free_smem_words(uint32_t nf) { return gt_offset(nf) + 2 * gt_capacity(nf) + 6 * nf + 4; }
 // Where the granule table of nf frees lives: in shared memory after the five
 // staged words per free when the free phase fits there, else at the start of
 // the global scratch.
-HBA_HD uint32_t* gt_slots(uint32_t nf, uint32_t* dyn, uint32_t dyn_words, uint32_t* scr) {
-    return free_smem_words(nf) <= dyn_words ? dyn + GATHER_WORDS * nf : scr;
+HBA_HD uint64_t* gt_slots(uint32_t nf, uint32_t* dyn, uint32_t dyn_words, uint32_t* scr) {
+    return reinterpret_cast<uint64_t*>(free_smem_words(nf) <= dyn_words ? dyn + gt_offset(nf) : scr);
 }
 
 constexpr uint32_t FL_WIN = 4;  // flag: this free is applied
@@ -635,13 +652,13 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const uint32_t* gRE;
     if (sm) {
         gG = w; gSZ = w + nf; gL = w + 2 * nf; gLL = w + 3 * nf; gRE = w + 4 * nf;
-        w += 5 * nf;
+        w += gt_offset(nf);
     } else {
         const uint32_t gs = a.gstride;
         gG = a.gi; gSZ = a.gi + gs; gL = a.gi + 2 * gs; gLL = a.gi + 3 * gs; gRE = a.gi + 4 * gs;
     }
-    GTable T{w, gG, hcap - 1};  // w == gt_slots(nf, ...): cleared by arena_step
-    uint32_t* root = w + hcap;          // pointer-jumping root (a free index)
+    GTable T{reinterpret_cast<uint64_t*>(w), hcap - 1};  // == gt_slots(nf, ...): cleared by arena_step
+    uint32_t* root = w + 2 * hcap;      // pointer-jumping root (a free index)
     uint32_t* rmaxj = root + nf;        // largest free index of the run (at the root)
     uint32_t* rend = rmaxj + nf;        // right end of the run (at the root)
     uint32_t* runAt = rend + nf;        // run leader whose last free is j, or NIL
@@ -652,9 +669,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
 
     // F1: stage the gathered records (shared-memory layout), and put the
     // valid frees into the granule table (lowest index wins).  The table was
-    // cleared before the prep grid finished; a free's granule is staged
-    // before the free is inserted, so that whoever finds it in the table
-    // reads its key.
+    // cleared before the prep grid finished.
     HBA_FOR_THREADS(tid) {
         if (sm && !a.staged) {
             const uint32_t gs = a.gstride;
@@ -676,7 +691,6 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                         for (uint32_t q = 0; q < GATHER_WORDS; ++q) d[q * nf + j] = v[e][q];
                     }
                 }
-                fence_block();
                 HBA_PROF(9);
                 HBA_UNROLL
                 for (int e = 0; e < 4; ++e) {
@@ -1678,17 +1692,23 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t 
         }
         if (a.nf) {
             // the free phase's granule table, cleared ahead
-            uint32_t* slot = gt_slots(a.nf, dyn, dyn_words, a.scr);
+            uint64_t* slot = gt_slots(a.nf, dyn, dyn_words, a.scr);
             const uint32_t cap = gt_capacity(a.nf);
-            for (uint32_t q = tid; q < cap; q += NT) slot[q] = NIL;
+            for (uint32_t q = tid; q < cap; q += NT) slot[q] = GT_EMPTY;
         }
     }
     HBA_SYNC();
     HBA_FOR_THREADS(tid) {
         // the first chunk's request sizes on their way to L2 (inputs: not
-        // written by the preceding grid)
+        // written by the preceding grid); a small arena's whole record table
+        // too, so that chains of list pops do not each wait for DRAM
         const uint32_t n0 = a.na < (uint32_t)NT ? a.na : (uint32_t)NT;
         for (uint32_t q = (uint32_t)tid * 16u; q < n0; q += 16u * NT) prefetch_l2(a.sizes + q);
+        if ((uint64_t)S.G * sizeof(Rec) <= PREFETCH_TABLE_MAX) {
+            const uint32_t lines = (uint32_t)(((uint64_t)S.G * sizeof(Rec) + 127u) / 128u);
+            for (uint32_t q = (uint32_t)tid; q < lines; q += NT)
+                prefetch_l2(reinterpret_cast<const char*>(a.rec) + (size_t)q * 128u);
+        }
         if (a.wait_prep == WAIT_GRID) grid_dep_wait();
         else if (a.wait_prep == WAIT_CLUSTER) cluster_wait();
     }
