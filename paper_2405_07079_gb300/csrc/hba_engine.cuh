@@ -126,10 +126,10 @@ constexpr uint32_t GATHER_WORDS = 5;
 constexpr uint32_t STRETCH_BELOW = HBA_STRETCH_BELOW;
 constexpr uint32_t STRETCH_LANES = HBA_STRETCH_LANES;
 constexpr uint32_t SERIAL_LANES = HBA_SERIAL_LANES;
-#ifndef HBA_CARVE_RUN
-#define HBA_CARVE_RUN 4
+#ifndef HBA_QUIET_RUN
+#define HBA_QUIET_RUN 4
 #endif
-constexpr uint32_t CARVE_RUN = HBA_CARVE_RUN;
+constexpr uint32_t QUIET_RUN = HBA_QUIET_RUN;
 // a block-wide round that resolved at most SERIAL_AFTER lanes before its
 // event counts as "events one after another"
 #ifndef HBA_SERIAL_AFTER
@@ -1178,25 +1178,26 @@ HBA_DEV void x_bcast(XReg& X) {
 }
 
 // Lane q (an event) alone, then up to `more` further lanes one by one (one
-// thread), stopping before the lane that would make more than CARVE_RUN
-// carves from X in a row (long stretches of carves go faster in parallel);
-// returns the first lane not applied.
+// thread), stopping before the lane that would make more than QUIET_RUN
+// lanes in a row that pop no list (carves from X and failures: the lanes
+// that block-wide or warp-wide rounds resolve in parallel); returns the
+// first lane not applied.
 template <int NT>
 HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
                          uint32_t more) {
     seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
     ++q;
     const uint32_t end = q + more < stop ? q + more : stop;
-    uint32_t carves = 0;
+    uint32_t quiet = 0;
     for (; q < end; ++q) {
         const uint32_t sg = S.sgr[q], c = S.ccl[q];
-        bool carve = false;
-        if (sg && X.xok) {
-            const uint64_t cand = ((X.mask | (1ull << X.xL)) >> c) << c;
-            carve = cand && ctz64(cand) == X.xL;
+        bool pop = false;
+        if (sg) {
+            const uint64_t cand = ((X.mask | (X.xok ? (1ull << X.xL) : 0ull)) >> c) << c;
+            pop = cand && !(X.xok && ctz64(cand) == X.xL);
         }
-        carves = carve ? carves + 1 : 0;
-        if (carves > CARVE_RUN) break;
+        quiet = pop ? 0 : quiet + 1;
+        if (quiet > QUIET_RUN) break;
         seq_request<NT>(S, a, X, p + q, S.s64[q], sg, c);
     }
     return q;
