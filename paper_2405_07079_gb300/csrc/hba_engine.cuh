@@ -130,6 +130,11 @@ constexpr uint32_t SERIAL_LANES = HBA_SERIAL_LANES;
 #define HBA_QUIET_RUN 4
 #endif
 constexpr uint32_t QUIET_RUN = HBA_QUIET_RUN;
+// ... and at most QUIET_FIRST such lanes before the run's first further pop
+#ifndef HBA_QUIET_FIRST
+#define HBA_QUIET_FIRST 0
+#endif
+constexpr uint32_t QUIET_FIRST = HBA_QUIET_FIRST;
 // a block-wide round that resolved at most SERIAL_AFTER lanes before its
 // event counts as "events one after another"
 #ifndef HBA_SERIAL_AFTER
@@ -1180,15 +1185,15 @@ HBA_DEV void x_bcast(XReg& X) {
 // Lane q (an event) alone, then up to `more` further lanes one by one (one
 // thread), stopping before the lane that would make more than QUIET_RUN
 // lanes in a row that pop no list (carves from X and failures: the lanes
-// that block-wide or warp-wide rounds resolve in parallel); returns the
-// first lane not applied.
+// that block-wide or warp-wide rounds resolve in parallel), or more than
+// QUIET_FIRST before any further pop; returns the first lane not applied.
 template <int NT>
 HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
                          uint32_t more) {
     seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
     ++q;
     const uint32_t end = q + more < stop ? q + more : stop;
-    uint32_t quiet = 0;
+    uint32_t quiet = 0, quiet_max = QUIET_FIRST;
     for (; q < end; ++q) {
         const uint32_t sg = S.sgr[q], c = S.ccl[q];
         bool pop = false;
@@ -1196,8 +1201,12 @@ HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, ui
             const uint64_t cand = ((X.mask | (X.xok ? (1ull << X.xL) : 0ull)) >> c) << c;
             pop = cand && !(X.xok && ctz64(cand) == X.xL);
         }
-        quiet = pop ? 0 : quiet + 1;
-        if (quiet > QUIET_RUN) break;
+        if (pop) {
+            quiet = 0;
+            quiet_max = QUIET_RUN;  // pops do come one after another here
+        } else if (++quiet > quiet_max) {
+            break;
+        }
         seq_request<NT>(S, a, X, p + q, S.s64[q], sg, c);
     }
     return q;
@@ -1484,33 +1493,6 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             HBA_PROF(17);
             break;
         }
-        // A0: load the chunk [p, p + NT) once (each thread its own lane,
-        // copied in ahead into S.stg[chunk parity]) and start copying the
-        // next chunk into the other half
-        HBA_FOR_THREADS(tid) {
-            const uint32_t i = p + tid;
-            const uint32_t par = (p / NT) & 1u;
-            uint32_t sg = 0, c = 0;
-            uint64_t s = 0;
-            rec_copy_wait();
-            if (i < na) {
-                s = S.stg[par * NT + tid];
-                if (i + NT < na) u64_copy_async(&S.stg[(par ^ 1u) * NT + tid], a.sizes + i + NT);
-                if (s != 0 && s <= S.A) {
-                    sg = (uint32_t)((s + mbm) >> lg);
-                    c = clog2(sg);
-                }
-            }
-            S.sgr[tid] = sg;
-            S.ccl[tid] = (uint8_t)c;
-            S.s64[tid] = s;
-            if (tid == 0) {
-                S.r = 0;
-                S.evb[0] = S.evb[1] = NT;
-            }
-        }
-        HBA_SYNC();
-        HBA_PROF(11);
         const uint32_t n_here = na - p < (uint32_t)NT ? na - p : (uint32_t)NT;
         // Rounds over the chunk.  Each round classifies the unresolved lanes
         // [r, n_here) against the current state, assuming that every lane
@@ -1520,12 +1502,34 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
         // parallel; the event lane is applied alone; the next round starts
         // after it.
         for (int round = 0;; ++round) {
-            const uint32_t r = S.r;
+            const uint32_t r = round == 0 ? 0u : S.r;
             uint32_t* evp = &S.evb[round & 1];
             // A: classify the lanes of the warps that hold unresolved lanes
             // (own lane only: no barrier before the scan); warps wholly
-            // outside [r, n_here) sit the round out
+            // outside [r, n_here) sit the round out.  The first round also
+            // loads the chunk (each thread its own lane, copied in ahead into
+            // S.stg[chunk parity]) and starts copying the next chunk into the
+            // other half.
             HBA_FOR_THREADS(tid) {
+                if (round == 0) {
+                    const uint32_t i = p + tid;
+                    const uint32_t par = (p / NT) & 1u;
+                    uint32_t sg = 0, c = 0;
+                    uint64_t s = 0;
+                    rec_copy_wait();
+                    if (i < na) {
+                        s = S.stg[par * NT + tid];
+                        if (i + NT < na) u64_copy_async(&S.stg[(par ^ 1u) * NT + tid], a.sizes + i + NT);
+                        if (s != 0 && s <= S.A) {
+                            sg = (uint32_t)((s + mbm) >> lg);
+                            c = clog2(sg);
+                        }
+                    }
+                    S.sgr[tid] = sg;
+                    S.ccl[tid] = (uint8_t)c;
+                    S.s64[tid] = s;
+                    if (tid == 0) S.evb[0] = NT;
+                }
                 if (warp_in_window<NT>(tid >> 5, r, n_here)) {
                     uint8_t cl = CL_NONE;
                     const uint32_t sg = S.sgr[tid];
