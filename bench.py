@@ -354,7 +354,12 @@ def run_multi(args, rank, world, local_rank):
         d["ref_out"] = o.copy()
         batches.append(d)
     t_rec = time.time() - t_rec
-    best, table = autotune_multi(ma, batches, n_probe=3)
+    if args.shape:
+        best = tuple(int(x) for x in args.shape.split(","))
+        ma.set_shape(*best)
+        table = {}
+    else:
+        best, table = autotune_multi(ma, batches, n_probe=3)
     nb = len(batches)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -461,7 +466,7 @@ def run_serve(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     arena, page = 80 << 30, 16 << 10
     sweep = []
-    plain = None
+    kept = [None, None]  # the first rate's run and the fastest later one, for the plain replay
     lams = [float(x) * 1e6 for x in args.lams.split(",")]
     for li, lam in enumerate(lams):
         arr = workloads.serving_arrivals(lam, args.serve_seconds)
@@ -477,26 +482,32 @@ def run_serve(args, rank, world, local_rank):
                       "elapsed_s": sec, "ops_per_s": ops / sec, "admitted_per_s": rep["admitted"] / sec,
                       "p50_us": float(np.percentile(lat, 50)) if lat.size else None,
                       "p99_us": float(np.percentile(lat, 99)) if lat.size else None, "status": rep["status"]})
-        if li == 0:
-            # the plain form on the same batches: one launch per logged tick
-            ticks = log_batches(log)
-            dt = []
-            for fid, aid in ticks:
-                f = torch.from_numpy(served[fid, 0].view(np.int64)).to(dev)
-                s_ = torch.from_numpy(arr[aid, 1].view(np.int64)).to(dev)
-                dt.append((f, s_, torch.empty(max(aid.size, 1), dtype=torch.int64, device=dev), aid))
-            stream = torch.cuda.current_stream()
-            with Allocator(arena, page, threads=256) as pa:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for f, s_, o, aid in dt:
-                    hba_step(pa.h, _ptr(f), f.numel(), 0, _ptr(s_), s_.numel(), _ptr(o), int(stream.cuda_stream))
-                e1.record(stream)
-                torch.cuda.synchronize()
-                pms = e0.elapsed_time(e1)
-                equal = all(np.array_equal(o[:aid.size].cpu().numpy().view(np.uint64), served[aid, 0]) for f, s_, o, aid in dt)
-            plain = {"lambda_req_s": lam, "ticks": len(dt), "ops_per_s": ops / (pms / 1e3), "elapsed_s": pms / 1e3,
-                     "results_equal": bool(equal)}
+        keep = li == 0 or sweep[-1]["ops_per_s"] >= max(r["ops_per_s"] for r in sweep)
+        if keep:
+            kept[0 if li == 0 else 1] = (lam, arr, served, log, ops)
+
+    def plain_replay(lam, arr, served, log, ops):
+        """The plain form on the same batches: one launch pair per logged tick,
+        back to back from the host; results must equal the serving loop's."""
+        dt = []
+        for fid, aid in log_batches(log):
+            f = torch.from_numpy(served[fid, 0].view(np.int64)).to(dev)
+            s_ = torch.from_numpy(arr[aid, 1].view(np.int64)).to(dev)
+            dt.append((f, s_, torch.empty(max(aid.size, 1), dtype=torch.int64, device=dev), aid))
+        stream = torch.cuda.current_stream()
+        with Allocator(arena, page, threads=256) as pa:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for f, s_, o, aid in dt:
+                hba_step(pa.h, _ptr(f), f.numel(), 0, _ptr(s_), s_.numel(), _ptr(o), int(stream.cuda_stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms = e0.elapsed_time(e1)
+            equal = all(np.array_equal(o[:aid.size].cpu().numpy().view(np.uint64), served[aid, 0]) for f, s_, o, aid in dt)
+        return {"lambda_req_s": lam, "ticks": len(dt), "ops_per_s": ops / (pms / 1e3), "elapsed_s": pms / 1e3,
+                "results_equal": bool(equal)}
+
+    plain = [plain_replay(*k) for k in kept if k is not None]
     best = max(sweep, key=lambda r: r["ops_per_s"])
     (sec_all,), (ops_all,) = reduce_over_ranks([best["elapsed_s"]], [best["ops_per_s"] * best["elapsed_s"]], world,
                                                torch.device("cuda", local_rank))
@@ -512,7 +523,10 @@ def run_serve(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "latency_us": {"p50": best["p50_us"], "p99": best["p99_us"], "unit": "arrival to result, admitted requests",
                        "at_lambda": best["lambda_req_s"]},
-        "sweep": sweep, "plain_form_same_batches": plain, "gpu_launches": len(sweep),
+        "sweep": sweep, "plain_form_same_batches": plain,
+        "serving_over_plain_at_best": (best["ops_per_s"] / plain[-1]["ops_per_s"]
+                                       if plain and plain[-1]["lambda_req_s"] == best["lambda_req_s"] else None),
+        "gpu_launches": len(sweep),
     }
 
 
@@ -589,6 +603,8 @@ def main():
     ap.add_argument("--arenas", type=int, default=4096)
     ap.add_argument("--batches", type=int, default=200)
     ap.add_argument("--plain-arenas", type=int, default=64)
+    ap.add_argument("--shape", default="",
+                    help="batched form: threads,ctas,smem_bytes instead of autotuning")
     ap.add_argument("--threads", type=int, default=None)
     ap.add_argument("--ctas", type=int, default=0,
                     help="single arena: batch cluster size (0 or 1 = prep grid + engine; 2..8 = engine CTA + gathering CTAs)")

@@ -545,7 +545,10 @@ bool check_geometry(uint64_t arena_bytes, uint64_t min_block, uint32_t* lg, uint
 }
 
 // ---- the serving loop ----------------------------------------------------
-constexpr int SERVE_NT = 256;
+#ifndef HBA_SERVE_NT
+#define HBA_SERVE_NT 256
+#endif
+constexpr int SERVE_NT = HBA_SERVE_NT;
 __global__ void __launch_bounds__(SERVE_NT, 1) k_serve(hba::ServeArgs g, uint32_t dyn_words) {
     __shared__ hba::Smem<SERVE_NT> S;
     __shared__ hba::ServeSmem<SERVE_NT> Q;

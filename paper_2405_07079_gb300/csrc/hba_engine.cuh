@@ -281,6 +281,60 @@ HBA_HD void gather_words(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, ui
     w[3] = LL;
     w[4] = Rend;
 }
+// The same for up to four frees at once, their record loads issued side by
+// side (first the named blocks, then all their neighbours): one thread keeps
+// several independent loads in flight.  valid[e] false: w[e] is not written.
+HBA_HD void gather_words4(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, const uint64_t off[4],
+                          const bool valid[4], uint32_t w[4][GATHER_WORDS]) {
+    uint32_t gg[4];
+    Rec r[4];
+    HBA_UNROLL
+    for (int e = 0; e < 4; ++e) {
+        gg[e] = NIL;
+        r[e] = Rec{0, NIL, 0, 0};
+        if (valid[e] && off[e] < A && (off[e] & ((1ull << lg) - 1ull)) == 0) {
+            gg[e] = (uint32_t)(off[e] >> lg);
+            r[e] = rec[gg[e]];
+        }
+    }
+    Rec rl[4];
+    uint32_t rx[4];
+    HBA_UNROLL
+    for (int e = 0; e < 4; ++e) {
+        rl[e] = Rec{0, NIL, 0, 0};
+        rx[e] = 0;
+        if (gg[e] != NIL && st_of(r[e].x) == ST_USED) {
+            const uint32_t L = r[e].y, Rend = gg[e] + sz_of(r[e].x);
+            if (L != NIL) rl[e] = rec[L];
+            if (Rend < G) rx[e] = rec[Rend].x;
+        }
+    }
+    HBA_UNROLL
+    for (int e = 0; e < 4; ++e) {
+        if (!valid[e]) continue;
+        uint32_t g = NIL, szf = 0, L = NIL, LL = NIL, Rend = 0;
+        if (gg[e] != NIL && st_of(r[e].x) == ST_USED) {
+            g = gg[e];
+            const uint32_t sz = sz_of(r[e].x);
+            szf = sz;
+            L = r[e].y;
+            Rend = g + sz;
+            if (st_of(rl[e].x) == ST_FREE) {
+                szf |= F_LFREE;
+                LL = rl[e].y;
+            }
+            if (st_of(rx[e]) == ST_FREE) {
+                szf |= F_RFREE;
+                Rend += sz_of(rx[e]);
+            }
+        }
+        w[e][0] = g;
+        w[e][1] = szf;
+        w[e][2] = L;
+        w[e][3] = LL;
+        w[e][4] = Rend;
+    }
+}
 HBA_HD void gather_free(const Rec* rec, uint64_t A, uint32_t G, uint32_t lg, uint64_t off, uint32_t* gi,
                         uint32_t n, uint32_t j) {
     uint32_t w[GATHER_WORDS];

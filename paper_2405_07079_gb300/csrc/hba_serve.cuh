@@ -249,11 +249,30 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
             if (Q.stop) break;
             continue;
         }
-        // 4: the batch -- gather the records the frees need, then the engine
-        for (uint32_t j = tid; j < nf; j += NT)
-            gather_free(g.rec, A, g.ar->G, lg, g.t_frees[j], g.gi, nf, j);
+        // 4: the batch -- gather the records the frees need (four frees a
+        // thread at a time, straight into the free phase's shared-memory
+        // layout when it fits there), then the engine
+        const bool staged = nf && free_smem_words(nf) <= dyn_words;
+        uint32_t* gdst = staged ? dyn : g.gi;
+        for (uint32_t j0 = tid; j0 < nf; j0 += 4 * NT) {
+            uint64_t off[4];
+            bool valid[4];
+            uint32_t w[4][GATHER_WORDS];
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t j = j0 + (uint32_t)e * NT;
+                valid[e] = j < nf;
+                off[e] = valid[e] ? g.t_frees[j] : 0;
+            }
+            gather_words4(g.rec, A, g.ar->G, lg, off, valid, w);
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t j = j0 + (uint32_t)e * NT;
+                if (valid[e])
+                    for (uint32_t q = 0; q < GATHER_WORDS; ++q) gdst[q * nf + j] = w[e][q];
+            }
+        }
         __syncthreads();
-        StepArgs a{g.ar, g.rec, g.t_frees, nf, nullptr, g.t_sizes, na, g.t_out, g.scr, g.gi, nf, 0, WAIT_NONE, 0};
+        StepArgs a{g.ar, g.rec, g.t_frees, nf, nullptr, g.t_sizes, na, g.t_out, g.scr, g.gi, nf, 0, WAIT_NONE,
+                   staged ? 1u : 0u};
         arena_step<NT>(S, a, dyn, dyn_words);
         if (tid == 0) Q.now = globaltimer_ns() - Q.t0;
         __syncthreads();
