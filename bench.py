@@ -165,6 +165,72 @@ def reduce_over_ranks(maxes, sums, world: int, device=None):
     return t.tolist(), c.tolist()
 
 
+def _oracle_arenas(work):
+    """Pool worker: the oracle over whole per-arena request sequences.
+    work = list of (arena_bytes, min_block, [(frees, sizes), ...]); returns
+    (ops, oracle seconds, results per arena)."""
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    ops, secs, res = 0, 0.0, []
+    for arena, mb, seq in work:
+        o = oracle.Oracle(arena, mb)
+        outs = []
+        for f, s in seq:
+            t0 = time.perf_counter()
+            out, st = o.batch(f, s)
+            secs += time.perf_counter() - t0
+            ops += f.size + s.size
+            outs.append((out, st))
+        res.append(outs)
+    return ops, secs, res
+
+
+def oracle_pool_baseline(arenas, mb, seqs, cores=None) -> tuple:
+    """The oracle on independent arenas, sharded over the host's cores
+    (spawned processes).  Returns (ops/s over the pool's wall time, cores,
+    per-arena results)."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    cores = cores or max(1, min(len(os.sched_getaffinity(0)), len(arenas)))
+    shards = [[] for _ in range(cores)]
+    for i, (a, seq) in enumerate(zip(arenas, seqs)):
+        shards[i % cores].append((int(a), mb, seq))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_arenas, [[] for _ in range(cores)])  # workers up before the clock starts
+        t0 = time.perf_counter()
+        parts = pool.map(_oracle_arenas, shards)
+        wall = time.perf_counter() - t0
+    ops = sum(p[0] for p in parts)
+    res = [None] * len(arenas)
+    for c, part in enumerate(parts):
+        for k, r in enumerate(part[2]):
+            res[c + k * cores] = r
+    return ops / wall, cores, res
+
+
+def cuda_replay_ops_multi(batches, arenas):
+    """Operation list for the CUDA allocators from a batched trace: per batch,
+    for each of the given arenas, its applied frees then its served
+    allocations (offsets are per arena)."""
+    live, ops, nslot = {}, [], 0
+    for b in batches:
+        fr, ar = b["hfrow"], b["harow"]
+        for i in arenas:
+            for j in range(int(fr[i]), int(fr[i + 1])):
+                if b["ref_st"][j] == 0:
+                    ops.append(-(live.pop((i, int(b["hf"][j]))) + 1))
+            for k in range(int(ar[i]), int(ar[i + 1])):
+                off = int(b["ref_out"][k])
+                if off != int(FAIL):
+                    live[(i, off)] = nslot
+                    nslot += 1
+                    ops.append(int(b["hs"][k]))
+    return np.asarray(ops, dtype=np.int64)
+
+
 def cuda_allocator_comparison(batches, alloc, flush, stream, max_ops: int = 60_000) -> dict:
     """The same operations through cudaMalloc/cudaFree and cudaMallocAsync/
     cudaFreeAsync (host-timed per call), beside this allocator on the same
@@ -341,7 +407,7 @@ def run_multi(args, rank, world, local_rank):
         frow, f, arow, s = b
         d = {"frow": torch.from_numpy(frow.view(np.int32)).to(dev), "f": torch.from_numpy(f.view(np.int64)).to(dev),
              "arow": torch.from_numpy(arow.view(np.int32)).to(dev), "s": torch.from_numpy(s.view(np.int64)).to(dev),
-             "nf": f.size, "na": s.size, "ops": f.size + s.size, "hfrow": frow, "harow": arow}
+             "nf": f.size, "na": s.size, "ops": f.size + s.size, "hfrow": frow, "harow": arow, "hf": f, "hs": s}
         d["out"] = torch.empty(s.size, dtype=torch.int64, device=dev)
         d["st"] = torch.empty(f.size, dtype=torch.uint8, device=dev)
         ma.step(d["frow"], d["f"], d["arow"], d["s"], d["out"], d["st"])
@@ -352,6 +418,7 @@ def run_multi(args, rank, world, local_rank):
         d["bytes"] = (BYTES_ALLOC_OK * n_ok + BYTES_ALLOC_FAIL * (s.size - n_ok)
                       + BYTES_FREE_OK * n_fok + BYTES_FREE_REJECTED * (f.size - n_fok))
         d["ref_out"] = o.copy()
+        d["ref_st"] = stat.copy()
         batches.append(d)
     t_rec = time.time() - t_rec
     if args.shape:
@@ -426,6 +493,31 @@ def run_multi(args, rank, world, local_rank):
     ma.close()
     if rank != 0:
         return None
+    extra = {}
+    if not args.no_cpu_baseline:
+        # the oracle on the first arenas, whole sequences, sharded over the host cores
+        K = min(args.oracle_arenas, args.arenas)
+        seqs = [[(b["hf"][int(b["hfrow"][i]):int(b["hfrow"][i + 1])], b["hs"][int(b["harow"][i]):int(b["harow"][i + 1])])
+                 for b in batches] for i in range(K)]
+        v, cores, res = oracle_pool_baseline(A[:K], 256, seqs)
+        for i in range(K):
+            for bi, b in enumerate(batches):
+                a0, a1 = int(b["harow"][i]), int(b["harow"][i + 1])
+                if not np.array_equal(res[i][bi][0], b["ref_out"][a0:a1]):
+                    raise AssertionError(f"oracle and batched form differ: arena {i}, batch {bi}")
+        extra["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"the first {K} arenas, all {nb} batches, sharded over {cores} "
+                                           "spawned processes; wall time of the pool (results equal the GPU's)"}
+    if not args.no_cuda_baseline:
+        from paper_2405_07079_gb300 import cuda_replay
+        ops_l = cuda_replay_ops_multi(batches[:nb_plain], range(P))
+        sptr = int(stream.cuda_stream)
+        extra["cuda_allocators"] = {"sample": f"the plain-form comparison's requests (first {P} arenas, "
+                                              f"{nb_plain} batches): applied frees and served allocations "
+                                              f"({ops_l.size} ops)", "unit": UNIT}
+        for mode in ("cudaMalloc", "cudaMallocAsync"):
+            torch.cuda.synchronize()
+            extra["cuda_allocators"][mode] = cuda_replay.replay(ops_l, mode, sptr)
     peak, peak_src = _peaks()
     achieved = nbytes / busy_s / 1e9
     lat = sorted(step_ms)
@@ -450,6 +542,7 @@ def run_multi(args, rank, world, local_rank):
         "gpu_launches": 2 * steps,
         "clocks": clocks.summary(),
     }
+    line.update(extra)
     return line
 
 
@@ -508,6 +601,44 @@ def run_serve(args, rank, world, local_rank):
                 "results_equal": bool(equal)}
 
     plain = [plain_replay(*k) for k in kept if k is not None]
+    extra = {}
+    lam0, arr0, served0, log0, ops0 = kept[0]
+    ticks0 = log_batches(log0)
+    if not args.no_cpu_baseline and rank == 0:
+        # the oracle on the first rate's ticks, one host core
+        import oracle
+        oracle.build()
+        o = oracle.Oracle(arena, page)
+        t_or, n_or = 0.0, 0
+        for fid, aid in ticks0:
+            f, s_ = served0[fid, 0].copy(), arr0[aid, 1].copy()
+            t0 = time.perf_counter()
+            out, _ = o.batch(f, s_)
+            t_or += time.perf_counter() - t0
+            n_or += f.size + s_.size
+            if not np.array_equal(out, served0[aid, 0]):
+                raise AssertionError("oracle and serving loop differ")
+        extra["cpu_baseline"] = {"value": n_or / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"the {len(ticks0)} ticks of the {lam0 / 1e6:g} M req/s run, replayed in "
+                                           "order (results equal the serving loop's); oracle calls timed"}
+    if not args.no_cuda_baseline and rank == 0:
+        from paper_2405_07079_gb300 import cuda_replay
+        live, ops_l, nslot = {}, [], 0
+        for fid, aid in ticks0:
+            for off in served0[fid, 0].tolist():
+                ops_l.append(-(live.pop(off) + 1))
+            for sz, off in zip(arr0[aid, 1].tolist(), served0[aid, 0].tolist()):
+                if off != int(FAIL):
+                    live[off] = nslot
+                    nslot += 1
+                    ops_l.append(int(sz))
+        ops_l = np.asarray(ops_l, dtype=np.int64)
+        sptr = int(torch.cuda.current_stream().cuda_stream)
+        extra["cuda_allocators"] = {"sample": f"the {lam0 / 1e6:g} M req/s run's served allocations and frees in "
+                                              f"tick order ({ops_l.size} ops)", "unit": UNIT}
+        for mode in ("cudaMalloc", "cudaMallocAsync"):
+            torch.cuda.synchronize()
+            extra["cuda_allocators"][mode] = cuda_replay.replay(ops_l, mode, sptr)
     best = max(sweep, key=lambda r: r["ops_per_s"])
     (sec_all,), (ops_all,) = reduce_over_ranks([best["elapsed_s"]], [best["ops_per_s"] * best["elapsed_s"]], world,
                                                torch.device("cuda", local_rank))
@@ -527,6 +658,7 @@ def run_serve(args, rank, world, local_rank):
         "serving_over_plain_at_best": (best["ops_per_s"] / plain[-1]["ops_per_s"]
                                        if plain and plain[-1]["lambda_req_s"] == best["lambda_req_s"] else None),
         "gpu_launches": len(sweep),
+        **extra,
     }
 
 
@@ -603,6 +735,8 @@ def main():
     ap.add_argument("--arenas", type=int, default=4096)
     ap.add_argument("--batches", type=int, default=200)
     ap.add_argument("--plain-arenas", type=int, default=64)
+    ap.add_argument("--oracle-arenas", type=int, default=256,
+                    help="batched form: arenas the oracle baseline runs (whole sequences)")
     ap.add_argument("--shape", default="",
                     help="batched form: threads,ctas,smem_bytes instead of autotuning")
     ap.add_argument("--threads", type=int, default=None)
