@@ -68,12 +68,14 @@ template <int NT>
 __global__ void __launch_bounds__(NT, 1) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
                                                uint8_t* st, const uint64_t* sizes, uint32_t na,
                                                uint64_t* out, uint32_t* scr, const uint32_t* gi,
-                                               uint32_t dyn_words, uint32_t prefilled) {
+                                               uint32_t dyn_words, uint32_t prefilled, uint32_t self_gather) {
     __shared__ hba::Smem<NT> S;
     extern __shared__ __align__(16) uint32_t dyn[];
     // waits for the preceding prep grid (gathered records, pre-filled
-    // failures) once it has read the arena header
-    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled, hba::WAIT_GRID, 0};
+    // failures) once it has read the arena header; or, with no prep grid,
+    // gathers itself
+    hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled,
+                    self_gather ? hba::WAIT_NONE : hba::WAIT_GRID, 0, self_gather};
     hba::arena_step<NT>(S, a, dyn, dyn_words);
 }
 
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(NT, 1) k_single_cl(Arena* ar, Rec* rec, const 
     asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(nrank));
     if (rank == 0) {
         hba::cluster_arrive_relaxed();
-        hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefill, hba::WAIT_CLUSTER, staged};
+        hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefill, hba::WAIT_CLUSTER, staged, 0};
         hba::arena_step<NT>(S, a, dyn, dyn_words);
         return;
     }
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            nf_total,
                            prefilled,
                            first ? hba::WAIT_GRID : hba::WAIT_NONE,
+                           0,
                            0};
         first = false;
         hba::arena_step<NT>(S, args, dyn, dyn_words);
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_multi_warp(Arena* ars, Rec* 
                            nf_total,
                            prefilled,
                            first ? hba::WAIT_GRID : hba::WAIT_NONE,
+                           0,
                            0};
         first = false;
         hba::arena_step<32>(S[w], args, mine, warp_dyn_words);
@@ -326,6 +330,12 @@ __global__ void k_prep(const Arena* ars, const Rec* pool, const uint32_t* frow, 
 
 // Allocation batches at least this large get their failures pre-filled.
 constexpr uint32_t PREFILL_MIN = 2048;
+// Batches with at most this many frees (and no pre-filling) are gathered by
+// the engine CTA itself: one launch instead of two.
+#ifndef HBA_SELF_GATHER_MAX
+#define HBA_SELF_GATHER_MAX 512
+#endif
+constexpr uint32_t SELF_GATHER_MAX = HBA_SELF_GATHER_MAX;
 
 // Launch the prep grid if the batch needs one; returns whether out[] is
 // pre-filled.  *pdl is set when the next launch may depend on it.
@@ -450,18 +460,21 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
         ++h->launches;
         return HBA_OK;
     }
+    // small batches without pre-filling: the engine gathers its frees itself
+    // (one launch); otherwise the prep grid gathers on many SMs
+    const uint32_t self = nf <= SELF_GATHER_MAX && !fill ? 1u : 0u;
     bool pdl = false;
-    const bool pre = launch_prep(h, nullptr, frees, nf, gi, out, na, s, &pdl);
+    const bool pre = self ? false : launch_prep(h, nullptr, frees, nf, gi, out, na, s, &pdl);
     if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     const uint32_t pf = pre ? 1u : 0u;
     const uint32_t* g = gi;
     switch (h->threads) {
-        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
-        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
-        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
-        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
-        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
-        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf); break;
+        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
+        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
+        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
+        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
+        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
+        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
     }
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     ++h->launches;

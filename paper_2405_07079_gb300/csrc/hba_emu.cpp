@@ -25,6 +25,7 @@ struct Emu {
     int nt;
     uint32_t dyn_words = 600;
     int staged = 0;  // write the gathered records straight into the shared-memory layout
+    int self = 0;    // the engine gathers its frees' records itself
 };
 
 template <int NT>
@@ -34,15 +35,17 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
     if (e->scr.size() < (size_t)SCRATCH_WORDS_PER_FREE * nf) e->scr.resize((size_t)SCRATCH_WORDS_PER_FREE * nf);
     // the gather that a separate grid does on the GPU
     std::vector<uint32_t> gi((size_t)GATHER_WORDS * nf + 1);
-    for (uint32_t j = 0; j < nf; ++j)
-        gather_free(e->rec.data(), e->ar.arena_bytes, e->ar.G, e->ar.lg, frees[j], gi.data(), nf, j);
-    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0, WAIT_NONE, 0};
+    if (!e->self)
+        for (uint32_t j = 0; j < nf; ++j)
+            gather_free(e->rec.data(), e->ar.arena_bytes, e->ar.G, e->ar.lg, frees[j], gi.data(), nf, j);
+    StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0, WAIT_NONE, 0,
+               e->self ? 1u : 0u};
     // "shared memory": at least what the alloc phase needs, plus a test knob so
     // that both placements of the free-phase arrays run
     const uint32_t words = std::max(alloc_dyn_words<NT>(), e->dyn_words);
     std::vector<uint64_t> dyn(words / 2 + 1);
     uint32_t* d = reinterpret_cast<uint32_t*>(dyn.data());
-    if (e->staged && nf && free_smem_words(nf) <= words) {
+    if (!e->self && e->staged && nf && free_smem_words(nf) <= words) {
         // what the gathering CTAs of a cluster do on the GPU
         memcpy(d, gi.data(), sizeof(uint32_t) * GATHER_WORDS * nf);
         a.staged = 1;
@@ -71,6 +74,7 @@ void emu_destroy(void* h) { delete (Emu*)h; }
 
 void emu_set_dyn(void* h, uint32_t words) { ((Emu*)h)->dyn_words = words; }
 void emu_set_staged(void* h, int staged) { ((Emu*)h)->staged = staged; }
+void emu_set_self(void* h, int self) { ((Emu*)h)->self = self; }
 
 int emu_step(void* h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
              uint32_t na, uint64_t* out) {

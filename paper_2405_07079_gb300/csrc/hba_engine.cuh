@@ -558,14 +558,13 @@ struct StepArgs {
                          // this cluster)
     uint32_t staged;     // the gathered records are already in the free phase's
                          // shared-memory layout (written there by the cluster)
+    uint32_t self_gather;  // no gathering grid ran: the CTA gathers its frees'
+                           // records itself (small batches), into the free
+                           // phase's shared-memory layout or, when that does
+                           // not fit, into gi
 };
 constexpr uint32_t WAIT_NONE = 0, WAIT_GRID = 1, WAIT_CLUSTER = 2;
 
-HBA_DEV void fence_block() {
-#ifndef HBA_EMULATE
-    __threadfence_block();
-#endif
-}
 HBA_DEV void grid_dep_wait() {
 #ifndef HBA_EMULATE
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -1771,9 +1770,36 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t 
         if (a.wait_prep == WAIT_GRID) grid_dep_wait();
         else if (a.wait_prep == WAIT_CLUSTER) cluster_wait();
     }
+    StepArgs b = a;
+    if (a.self_gather && a.nf) {
+        // four frees a thread at a time, their record loads side by side
+        const bool sm = free_smem_words(a.nf) <= dyn_words;
+        uint32_t* dst = sm ? dyn : const_cast<uint32_t*>(a.gi);
+        HBA_FOR_THREADS(tid) {
+            for (uint32_t j0 = tid; j0 < a.nf; j0 += 4 * NT) {
+                uint64_t off[4];
+                bool valid[4];
+                uint32_t w[4][GATHER_WORDS];
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t j = j0 + (uint32_t)e * NT;
+                    valid[e] = j < a.nf;
+                    off[e] = valid[e] ? a.frees[j] : 0;
+                }
+                gather_words4(a.rec, S.A, S.G, S.lg, off, valid, w);
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t j = j0 + (uint32_t)e * NT;
+                    if (valid[e])
+                        for (uint32_t q = 0; q < GATHER_WORDS; ++q) dst[q * a.nf + j] = w[e][q];
+                }
+            }
+        }
+        HBA_SYNC();
+        b.staged = sm ? 1u : 0u;
+        b.gstride = a.nf;
+    }
     HBA_PROF(0);
-    if (a.nf) free_phase<NT>(S, a);
-    if (a.na) alloc_phase<NT>(S, a);
+    if (b.nf) free_phase<NT>(S, b);
+    if (b.na) alloc_phase<NT>(S, b);
     HBA_FOR_THREADS(tid) {
         for (int b = tid; b < NBINS; b += NT) a.ar->heads[b] = S.heads[b];
         if (tid == 0) {

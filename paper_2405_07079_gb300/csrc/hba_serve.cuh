@@ -272,7 +272,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
         }
         __syncthreads();
         StepArgs a{g.ar, g.rec, g.t_frees, nf, nullptr, g.t_sizes, na, g.t_out, g.scr, g.gi, nf, 0, WAIT_NONE,
-                   staged ? 1u : 0u};
+                   staged ? 1u : 0u, 0};
         arena_step<NT>(S, a, dyn, dyn_words);
         if (tid == 0) Q.now = globaltimer_ns() - Q.t0;
         __syncthreads();

@@ -38,16 +38,18 @@ def emu():
     lib.emu_stats.argtypes = [vp, vp]
     lib.emu_set_dyn.argtypes = [vp, u32]
     lib.emu_set_staged.argtypes = [vp, ctypes.c_int]
+    lib.emu_set_self.argtypes = [vp, ctypes.c_int]
     return lib
 
 
 class Emu:
-    def __init__(self, lib, A, mb, nt, dyn_words=None, staged=False):
+    def __init__(self, lib, A, mb, nt, dyn_words=None, staged=False, self_gather=False):
         self.lib, self.h = lib, lib.emu_create(A, mb, nt)
         assert self.h
         if dyn_words is not None:
             lib.emu_set_dyn(self.h, dyn_words)
         lib.emu_set_staged(self.h, int(staged))
+        lib.emu_set_self(self.h, int(self_gather))
 
     def batch(self, f, s):
         f = np.ascontiguousarray(f, np.uint64)
@@ -73,9 +75,9 @@ class Emu:
         self.lib.emu_destroy(self.h)
 
 
-def _check(emu, wl, nt, every=1, dyn_words=None, staged=False):
+def _check(emu, wl, nt, every=1, dyn_words=None, staged=False, self_gather=False):
     trace, o = oracle_trace(wl)
-    e = Emu(emu, wl.arena, wl.min_block, nt, dyn_words, staged)
+    e = Emu(emu, wl.arena, wl.min_block, nt, dyn_words, staged, self_gather)
     import oracle as _o
     ref = _o.Oracle(wl.arena, wl.min_block)
     try:
@@ -130,6 +132,16 @@ def test_staged_by_cluster(emu, nt):
     wl = W.Workload("life", 1 << 28, 512, lambda: W.Lifetimes(n_ops=200_000, batch=4096, mean_life=60))
     _check(emu, wl, nt, every=3, dyn_words=1 << 20, staged=True)
     _check(emu, W.tiny(n_ops=6000), nt, dyn_words=1 << 20, staged=True)
+
+
+@pytest.mark.parametrize("nt,dyn_words", [(4, None), (256, 1 << 20), (256, 0), (1024, 1 << 20)])
+def test_self_gather(emu, nt, dyn_words):
+    """The engine gathers its frees' records itself (no gathering grid), into
+    the shared-memory layout when it fits, else into the global buffer."""
+    from paper_2405_07079_gb300 import workloads as W
+    _check(emu, W.tiny(n_ops=6000), nt, dyn_words=dyn_words, self_gather=True)
+    wl = W.Workload("life", 1 << 28, 512, lambda: W.Lifetimes(n_ops=100_000, batch=2048, mean_life=60))
+    _check(emu, wl, nt, every=5, dyn_words=dyn_words, self_gather=True)
 
 
 @pytest.mark.parametrize("nt", [32, 1024])

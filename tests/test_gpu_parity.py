@@ -94,20 +94,31 @@ def test_large_reduced(gpu_lib, threads, ctas):
     _run(wl, threads=threads, state_every=5, ctas=ctas)
 
 
-@pytest.mark.parametrize("ctas,per_batch", [(0, 2), (4, 1)])
-def test_launches_per_batch(gpu_lib, ctas, per_batch):
-    """A batch with frees is the prep grid plus the engine, or one cluster
-    launch (counted by the handle)."""
+@pytest.mark.parametrize("ctas,na,per_batch", [(0, 4, 1), (0, 4096, 2), (4, 4, 1), (4, 4096, 1)])
+def test_launches_per_batch(gpu_lib, ctas, na, per_batch):
+    """Launches per batch with frees (counted by the handle): a small batch is
+    gathered by the engine itself; a batch with many allocations gets the prep
+    grid (gather + pre-filled failures) before the engine; a cluster does
+    both in one launch.  Results equal the oracle's either way."""
+    import numpy as np
     import torch
 
+    import oracle
     from paper_2405_07079_gb300 import Allocator
 
     dev = torch.device("cuda")
+    ref = oracle.Oracle(1 << 24, 256)
     with Allocator(1 << 24, 256, threads=1024, ctas=ctas) as a:
-        out = a.step(None, torch.full((8,), 4096, dtype=torch.int64, device=dev))
+        s1 = np.full(8, 4096, np.uint64)
+        out = a.step(None, torch.from_numpy(s1.view(np.int64)).to(dev))
+        ro, _ = ref.batch(np.zeros(0, np.uint64), s1)
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), ro)
         n0 = a.launches()
-        a.step(out[:4], torch.full((4,), 512, dtype=torch.int64, device=dev))
+        s2 = np.full(na, 512, np.uint64)
+        o2 = a.step(out[:4], torch.from_numpy(s2.view(np.int64)).to(dev))
         assert a.launches() - n0 == per_batch
+        r2, _ = ref.batch(ro[:4], s2)
+        assert np.array_equal(o2.cpu().numpy().view(np.uint64), r2)
 
 
 def test_large_full(gpu_lib):
