@@ -663,7 +663,11 @@ def run_serve(args, rank, world, local_rank):
 
 
 def alloc_threads(args):
-    return args.threads or 1024
+    """CTA width of the plain form: --threads, else the library's choice by
+    batch size (1,024 for the large and frag batches, 128 for tiny ones)."""
+    if args.threads:
+        return args.threads
+    return 128 if args.workload == "tiny" else 1024
 
 
 def oracle_steps(wl, n_steps=None, warmup=0):

@@ -207,7 +207,9 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
 
 /* Launch shape of the handle's batch kernel: threads per CTA (one of 64,
  * 128, 256, 512, 1024: a CTA applies one arena's batch; or 32: warp mode,
- * every warp applies its own arena's batch, 8 arenas per CTA); number of
+ * every warp applies its own arena's batch, 8 arenas per CTA; a new
+ * single-arena handle picks per batch: 128 for batches of at most 256 frees
+ * and 256 allocations, else 1024); number of
  * CTAs: for a multi-arena handle, the grid (0 = enough for every arena;
  * fewer CTAs loop over the arenas); for a single-arena handle with 256 or
  * more threads, the size of the batch's thread-block cluster (0 or 1 = no

@@ -39,7 +39,7 @@ struct hba_s {
     uint64_t* d_stage_o = nullptr;
     uint8_t* d_stage_st = nullptr;
     // launch shapes
-    uint32_t threads = 1024;    // single-arena CTA width
+    uint32_t threads = 0;       // single-arena CTA width (0: by batch size)
     uint32_t m_threads = 256;   // multi-arena CTA width
     uint32_t m_ctas = 0;        // multi-arena grid (0 = one CTA per arena)
     uint32_t smem_bytes = 0;    // dynamic shared memory per CTA (0 = automatic)
@@ -330,6 +330,10 @@ __global__ void k_prep(const Arena* ars, const Rec* pool, const uint32_t* frow, 
 
 // Allocation batches at least this large get their failures pre-filled.
 constexpr uint32_t PREFILL_MIN = 2048;
+// Single-arena batches of at most this many frees and this many allocations
+// run on 128-thread CTAs when the handle leaves the width automatic; larger
+// ones on 1,024.
+constexpr uint32_t AUTO_SMALL_BATCH = 256;
 // Batches with at most this many frees (and no pre-filling) are gathered by
 // the engine CTA itself: one launch instead of two.
 #ifndef HBA_SELF_GATHER_MAX
@@ -430,7 +434,10 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
                            uint32_t na, uint64_t* out, cudaStream_t s, uint32_t* gi, uint32_t* scr) {
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
-    const int li = limit_index(h->threads);
+    // CTA width: the handle's, or by batch size (small batches pay less per
+    // barrier with fewer threads)
+    const uint32_t nt = h->threads ? h->threads : (std::max(nf, na) <= AUTO_SMALL_BATCH ? 128u : 1024u);
+    const int li = limit_index(nt);
     const SmemLimits& L = g_limits[li];
     const uint32_t maxdyn = L.single_dyn;
     const uint32_t base = 4 * L.alloc_words;
@@ -447,11 +454,11 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     const uint32_t dw = dyn / 4;
     const bool fill = na >= PREFILL_MIN;
     cudaError_t e;
-    if (h->threads >= 256 && h->single_ctas >= 2 && L.cluster_max >= 2 && (nf || fill)) {
+    if (nt >= 256 && h->single_ctas >= 2 && L.cluster_max >= 2 && (nf || fill)) {
         const uint32_t ncl = std::min(h->single_ctas, L.cluster_max);
         const uint32_t staged = nf && hba::free_smem_words(nf) <= dw ? 1u : 0u;
         const uint32_t pf = fill ? 1u : 0u;
-        switch (h->threads) {
+        switch (nt) {
             case 256: e = launch_cluster(k_single_cl<256>, ncl, 256, dyn, s, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf, staged); break;
             case 512: e = launch_cluster(k_single_cl<512>, ncl, 512, dyn, s, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf, staged); break;
             default: e = launch_cluster(k_single_cl<1024>, ncl, 1024, dyn, s, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf, staged); break;
@@ -468,7 +475,7 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     const uint32_t pf = pre ? 1u : 0u;
     const uint32_t* g = gi;
-    switch (h->threads) {
+    switch (nt) {
         case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
         case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
         case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
