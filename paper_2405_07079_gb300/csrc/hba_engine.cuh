@@ -158,6 +158,11 @@ constexpr uint64_t PREFETCH_TABLE_MAX = HBA_PREFETCH_TABLE_MAX;
 #define HBA_SERIAL_PUSH_MAX 8
 #endif
 constexpr uint32_t LEAD_MAX = HBA_LEAD_MAX;
+// free batches up to this size stage their gathered records in shared memory
+#ifndef HBA_STAGE_MAX_FREES
+#define HBA_STAGE_MAX_FREES 1024
+#endif
+constexpr uint32_t STAGE_MAX_FREES = HBA_STAGE_MAX_FREES;
 constexpr uint32_t SERIAL_PUSH_MAX = HBA_SERIAL_PUSH_MAX;
 static_assert(SERIAL_PUSH_MAX <= LEAD_MAX, "the serial push uses the leader search's order");
 constexpr int JUMP_HOPS = 2;
@@ -702,19 +707,23 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     // are staged there first); otherwise in global memory, reading the
     // gathered records where the prep grid left them.
     const bool sm = free_smem_words(nf) <= S.dyn_words;
+    // the gathered records are (or get staged) in shared memory: staging pays
+    // for small free batches, large ones read them where they were gathered
+    const bool copy = a.staged || (sm && nf <= STAGE_MAX_FREES);
     uint32_t* w = sm ? S.dyn : a.scr;
+    uint32_t* const base = w;
     const uint32_t* gG;
     const uint32_t* gSZ;
     const uint32_t* gL;
     const uint32_t* gLL;
     const uint32_t* gRE;
-    if (sm) {
+    if (sm && copy) {
         gG = w; gSZ = w + nf; gL = w + 2 * nf; gLL = w + 3 * nf; gRE = w + 4 * nf;
-        w += gt_offset(nf);
     } else {
         const uint32_t gs = a.gstride;
         gG = a.gi; gSZ = a.gi + gs; gL = a.gi + 2 * gs; gLL = a.gi + 3 * gs; gRE = a.gi + 4 * gs;
     }
+    if (sm) w += gt_offset(nf);
     GTable T{reinterpret_cast<uint64_t*>(w), hcap - 1};  // == gt_slots(nf, ...): cleared by arena_step
     uint32_t* root = w + 2 * hcap;      // pointer-jumping root (a free index)
     uint32_t* rmaxj = root + nf;        // largest free index of the run (at the root)
@@ -722,14 +731,14 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     uint32_t* runAt = rend + nf;        // run leader whose last free is j, or NIL
     uint32_t* lh = runAt + nf;          // leftmost block of the run's left part
     uint32_t* fl = lh + nf;             // bit0: erase L, bit1: erase R, FL_WIN
-    uint32_t* runs = sm ? const_cast<uint32_t*>(gLL) : fl + nf;  // run leaders in order
+    uint32_t* runs = sm ? base + 3 * nf : fl + nf;  // run leaders in order (over gLL: read by then)
     uint32_t* ul = sm ? a.scr : fl + 2 * nf;                     // [2 nf] absorbed old free blocks
 
     // F1: stage the gathered records (shared-memory layout), and put the
     // valid frees into the granule table (lowest index wins).  The table was
     // cleared before the prep grid finished.
     HBA_FOR_THREADS(tid) {
-        if (sm && !a.staged) {
+        if (sm && copy && !a.staged) {
             const uint32_t gs = a.gstride;
             uint32_t* d = S.dyn;
             // four frees of a thread at a time: their 20 loads in flight together
@@ -1247,6 +1256,7 @@ HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, ui
     ++q;
     const uint32_t end = q + more < stop ? q + more : stop;
     uint32_t quiet = 0, quiet_max = QUIET_FIRST;
+    HBA_PROF(26);
     for (; q < end; ++q) {
         const uint32_t sg = S.sgr[q], c = S.ccl[q];
         bool pop = false;
@@ -1261,6 +1271,7 @@ HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, ui
             break;
         }
         seq_request<NT>(S, a, X, p + q, S.s64[q], sg, c);
+        HBA_PROF(27);
     }
     return q;
 }
@@ -1345,6 +1356,7 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
             }
         }
         q += ev;
+        HBA_PROF(25);
         if (ev == nl) break;
         q = seq_run<NT>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
     }
@@ -1432,6 +1444,7 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
             }
         }
         q += ev;
+        if (lane == 0) HBA_PROF(25);
         if (ev == nl) break;
         uint32_t qn = 0;
         if (lane == 0) qn = seq_run<NT>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
