@@ -39,8 +39,10 @@
  * Streams and ownership.  Every device pointer argument is caller-owned
  * device memory that must stay valid until the work enqueued on `stream`
  * completes.  Calls are asynchronous with respect to the host unless stated
- * otherwise; a handle's calls must be ordered on one stream (or ordered by the
- * caller with events).  The library allocates its metadata and scratch in
+ * otherwise.  A handle's work is ordered: a call on another stream than the
+ * handle's previous call waits for that call's work (an event the handle
+ * records after every call; not while the stream is being captured, where
+ * the caller orders).  The library allocates its metadata and scratch in
  * hba_create* and never in the batch calls.  `stream` is a cudaStream_t (NULL
  * = the legacy default stream).
  *

@@ -45,6 +45,11 @@ struct hba_s {
     uint32_t smem_bytes = 0;    // dynamic shared memory per CTA (0 = automatic)
     uint32_t single_ctas = 0;   // single arena: CTAs of the batch cluster (0, 1 = prep grid + engine)
     uint64_t launches = 0;      // kernels this handle has launched
+    // the last stream the handle's work went to, and an event after that work
+    // (a call on another stream waits for it)
+    cudaEvent_t ev = nullptr;
+    cudaStream_t last = nullptr;
+    bool have_last = false;
     uint64_t* d_largest = nullptr;
 };
 
@@ -524,6 +529,7 @@ hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_fr
     if (cudaMalloc(&h->d_gi, 4ull * hba::GATHER_WORDS * std::max<uint64_t>(scr_frees, 1)) != cudaSuccess)
         return HBA_ERR_OUT_OF_MEMORY;
     if (cudaMalloc(&h->d_largest, sizeof(uint64_t) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    HBA_CUDA_TRY(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
     if (stage) {
         if (cudaMalloc(&h->d_stage_f, 8ull * stage) != cudaSuccess ||
             cudaMalloc(&h->d_stage_s, 8ull * stage) != cudaSuccess ||
@@ -533,6 +539,27 @@ hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_fr
     }
     return HBA_OK;
 }
+
+// Orders a call's work after the handle's previous work when the streams
+// differ (an event recorded after every call); does nothing while the stream
+// is being captured.
+struct StreamOrder {
+    hba_t h;
+    cudaStream_t s;
+    bool on = false;
+    StreamOrder(hba_t h_, cudaStream_t s_) : h(h_), s(s_) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (!h || !h->ev || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        on = true;
+        if (h->have_last && h->last != s) cudaStreamWaitEvent(s, h->ev, 0);
+    }
+    ~StreamOrder() {
+        if (!on) return;
+        cudaEventRecord(h->ev, s);
+        h->last = s;
+        h->have_last = true;
+    }
+};
 
 hba_status_t reset_impl(hba_t h, cudaStream_t s) {
     HBA_CUDA_TRY(cudaMemsetAsync(h->d_rec, 0, sizeof(Rec) * h->total_granules, s));
@@ -554,6 +581,7 @@ void free_all(hba_t h) {
     cudaFree(h->d_stage_s);
     cudaFree(h->d_stage_o);
     cudaFree(h->d_stage_st);
+    if (h->ev) cudaEventDestroy(h->ev);
 }
 
 bool check_geometry(uint64_t arena_bytes, uint64_t min_block, uint32_t* lg, uint64_t* a) {
@@ -717,11 +745,13 @@ extern "C" {
 hba_status_t hba_serve_run(hba_t h, const hba_arrival_t* d_arrivals, uint64_t n, hba_served_t* d_served,
                            uint32_t* d_log, uint64_t log_cap, const hba_serve_config_t* cfg,
                            hba_serve_report_t* report, hba_stream_t stream) {
+    StreamOrder order(h, (cudaStream_t)stream);
     return serve_impl(h, d_arrivals, n, d_served, d_log, log_cap, cfg, report, (cudaStream_t)stream);
 }
 
 hba_status_t hba_step_static(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status,
                              const uint64_t* d_sizes, uint32_t na, uint64_t* d_out_offsets, hba_stream_t stream) {
+    StreamOrder order(h, (cudaStream_t)stream);
     return step_static_impl(h, d_frees, nf, d_status, d_sizes, na, d_out_offsets, (cudaStream_t)stream);
 }
 
@@ -802,20 +832,24 @@ hba_status_t hba_destroy(hba_t h) {
 
 hba_status_t hba_alloc_batch(hba_t h, const uint64_t* d_sizes, uint32_t n, uint64_t* d_out_offsets,
                              hba_stream_t stream) {
+    StreamOrder order(h, (cudaStream_t)stream);
     return step_impl(h, nullptr, 0, nullptr, d_sizes, n, d_out_offsets, (cudaStream_t)stream);
 }
 
 hba_status_t hba_free_batch(hba_t h, const uint64_t* d_offsets, uint32_t n, hba_stream_t stream) {
+    StreamOrder order(h, (cudaStream_t)stream);
     return step_impl(h, d_offsets, n, nullptr, nullptr, 0, nullptr, (cudaStream_t)stream);
 }
 
 hba_status_t hba_free_batch_ex(hba_t h, const uint64_t* d_offsets, uint32_t n, uint8_t* d_status,
                                hba_stream_t stream) {
+    StreamOrder order(h, (cudaStream_t)stream);
     return step_impl(h, d_offsets, n, d_status, nullptr, 0, nullptr, (cudaStream_t)stream);
 }
 
 hba_status_t hba_step(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status, const uint64_t* d_sizes,
                       uint32_t na, uint64_t* d_out_offsets, hba_stream_t stream) {
+    StreamOrder order(h, (cudaStream_t)stream);
     return step_impl(h, d_frees, nf, d_status, d_sizes, na, d_out_offsets, (cudaStream_t)stream);
 }
 
@@ -825,6 +859,7 @@ hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_
     if (nf > h->max_batch || na > h->max_batch) return HBA_ERR_INVALID_ARGUMENT;
     if ((nf && !h_frees) || (na && (!h_sizes || !h_out_offsets))) return HBA_ERR_INVALID_ARGUMENT;
     cudaStream_t s = (cudaStream_t)stream;
+    StreamOrder order(h, s);
     if (nf) HBA_CUDA_TRY(cudaMemcpyAsync(h->d_stage_f, h_frees, 8ull * nf, cudaMemcpyHostToDevice, s));
     if (na) HBA_CUDA_TRY(cudaMemcpyAsync(h->d_stage_s, h_sizes, 8ull * na, cudaMemcpyHostToDevice, s));
     hba_status_t r = step_impl(h, h->d_stage_f, nf, h_status ? h->d_stage_st : nullptr, h->d_stage_s, na,
@@ -838,6 +873,7 @@ hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_
 
 hba_status_t hba_reset(hba_t h, hba_stream_t stream) {
     if (!h) return HBA_ERR_INVALID_ARGUMENT;
+    StreamOrder order(h, (cudaStream_t)stream);
     return reset_impl(h, (cudaStream_t)stream);
 }
 
@@ -904,6 +940,7 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     if (nf_total > h->scr_frees) return HBA_ERR_INVALID_ARGUMENT;
     if ((nf_total && !d_frees) || (na_total && (!d_sizes || !d_out))) return HBA_ERR_INVALID_ARGUMENT;
     cudaStream_t s = (cudaStream_t)stream;
+    StreamOrder order(h, s);
     const uint32_t n = h->n_arenas;
     if (h->m_threads == 32) {
         // warp mode: WPC arenas per CTA, per-warp dynamic shared memory

@@ -316,3 +316,36 @@ def test_batched_generator_matches_per_arena_oracles(gpu_lib, threads):
             assert np.array_equal(ma.export_state(i), orcs[i].export_state()), i
     finally:
         ma.close()
+
+
+def test_calls_on_two_streams_are_ordered(gpu_lib):
+    """Batches issued back to back on two different streams, with no host
+    synchronisation between them: the handle orders the second after the
+    first (its internal event), so results equal the oracle's."""
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import Allocator, workloads as W
+
+    dev = torch.device("cuda")
+    wl = W.Workload("life", 1 << 28, 512, lambda: W.Lifetimes(n_ops=60_000, batch=2048, mean_life=40))
+    trace, _ = oracle_trace(wl)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    with Allocator(wl.arena, wl.min_block) as a:
+        for b, (f, s, out, st) in enumerate(trace):
+            stream = streams[b % 2]
+            with torch.cuda.stream(stream):
+                df, ds = to_dev(f, dev), to_dev(s, dev)
+                dst = torch.empty(f.size, dtype=torch.uint8, device=dev)
+                o = torch.empty(max(s.size, 1), dtype=torch.int64, device=dev)
+                a.step(df if f.size else None, ds if s.size else None, out=o, status=dst, stream=stream)
+                outs.append((o, dst, df, ds))
+        torch.cuda.synchronize()
+        for b, ((o, dst, _, _), (f, s, out, st)) in enumerate(zip(outs, trace)):
+            assert np.array_equal(from_dev(o)[:s.size], out), f"batch {b}"
+            assert np.array_equal(from_dev(dst), st), f"batch {b} frees"
+        ref = oracle.Oracle(wl.arena, wl.min_block)
+        for f, s, _, _ in trace:
+            ref.batch(f, s)
+        assert np.array_equal(a.export_state(), ref.export_state())
