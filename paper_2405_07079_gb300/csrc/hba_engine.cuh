@@ -11,8 +11,7 @@
 //     (a direct-indexed version of the address-keyed table of §3.3):
 //        x = size in granules (bits 0..28) | state (bits 29..31)
 //        y = granule of the previous adjacent block ("prev_adj", §3.3)
-//        z = next block in its free list (free blocks), or the free claim
-//            (in-use blocks), or the compact free index (during a free phase)
+//        z = next block in its free list (free blocks; NIL for in-use ones)
 //        w = previous block in its free list (free blocks)
 //     Only records at block starts are meaningful; every other granule has
 //     x == 0 (state NONE), which is what validates a free in O(1).
@@ -27,31 +26,38 @@
 //   of address-adjacent free blocks together with the free blocks they touch.
 //   Applying the frees one by one leaves each run merged into one block whose
 //   list push happened at the time of the LAST free inside the run (the last
-//   free joins everything).  So: find runs by pointer jumping over
-//   "predecessor freed block" links, take per run the leftmost start, the
-//   right end and the largest free index, unlink the absorbed free blocks,
-//   and push the merged blocks in increasing order of that index.
+//   free joins everything).  So: find each free's run (runs are disjoint
+//   address ranges: with few runs, a search among the runs' leftmost frees;
+//   otherwise pointer jumping over "predecessor freed block" links), take
+//   per run the leftmost start, the right end and the largest free index,
+//   unlink the absorbed free blocks, and push the merged blocks in
+//   increasing order of that index.
 //   Alloc phase.  Allocations only ever pop list heads and push remainders,
 //   so the most recent remainder X is always the head of its list.  While
 //   X's class L and the rest of the bitmap stay fixed, each request is
 //   either a carve from X (lowest eligible list is L), a failure (no
 //   eligible list), or an "other" pop from another list.  A block-wide scan
-//   of carve sizes resolves a whole chunk of requests at once; the chunk
-//   ends at the first "other" (applied by one thread) or at the carve that
-//   drops X below 2^L granules.  X's record is written ("materialised") only
+//   of carve sizes resolves a stretch of requests at once, up to the first
+//   lane whose outcome differs from that speculation (an "other", or a carve
+//   that X, shrunk by the carves before it, no longer serves); that event is
+//   applied by one thread.  Where events are dense, one warp goes on with
+//   warp-wide rounds (shuffles, no block barrier), or one thread applies the
+//   next lanes one by one.  X's record is written ("materialised") only
 //   when another remainder replaces it or the phase ends -- the
 //   intermediate push/pop pairs of the sequential algorithm cancel out.
 //
 // Record reads for the frees are gathered before the engine runs, on many
 // SMs (gather_free, one thread per free): one SM alone can keep only so many
-// random loads in flight.
+// random loads in flight.  Small batches are gathered by the engine's own
+// threads, four frees a thread at a time (gather_words4).
 //
 // The same source compiles for the GPU and, with HBA_EMULATE, for a
 // host-only emulation used by the test suite: each HBA_FOR_THREADS body is a
 // phase run by every thread, HBA_SYNC is the barrier between phases.  Inside
 // a phase threads never read what another thread writes in that phase, except
 // through atomics whose result is read after the barrier (and the pointer
-// jumping, where any value read is a valid ancestor).
+// jumping, where any value read is a valid ancestor); warp-level exchanges
+// (ballots, shuffles) have host versions written over the 32 lanes.
 #pragma once
 #include <stddef.h>
 #include <stdint.h>
