@@ -292,7 +292,6 @@ SmemLimits set_smem_limits_warp() {
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    L.cluster_max = 0;
     L.sms = (uint32_t)sms;
     return L;
 }
