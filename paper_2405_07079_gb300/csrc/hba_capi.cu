@@ -460,7 +460,7 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     cudaError_t e;
     if (nt >= 256 && h->single_ctas >= 2 && L.cluster_max >= 2 && (nf || fill)) {
         const uint32_t ncl = std::min(h->single_ctas, L.cluster_max);
-        const uint32_t staged = nf && hba::free_smem_words(nf) <= dw ? 1u : 0u;
+        const uint32_t staged = nf && hba::stage_fits(nf, dw) ? 1u : 0u;
         const uint32_t pf = fill ? 1u : 0u;
         switch (nt) {
             case 256: e = launch_cluster(k_single_cl<256>, ncl, 256, dyn, s, ar, rec, frees, nf, st, sizes, na, out, scr, gi, dw, pf, staged); break;
@@ -497,7 +497,10 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
     if (!h || h->n_arenas != 1) return HBA_ERR_INVALID_ARGUMENT;
     if ((nf && !frees) || (na && (!sizes || !out))) return HBA_ERR_INVALID_ARGUMENT;
     // frees beyond the scratch capacity go in consecutive slices (exact:
-    // frees apply one by one in index order)
+    // frees apply one by one in index order).  Slicing at what one free
+    // phase keeps in shared memory was measured slower on the fragmentation
+    // workload (16,384 frees: four sliced launch pairs against one free
+    // phase on global scratch), so it is not done.
     while (nf > h->max_batch) {
         hba_status_t r = launch_single(h, frees, h->max_batch, st, nullptr, 0, nullptr, s, h->d_gi, h->d_scr);
         if (r != HBA_OK) return r;

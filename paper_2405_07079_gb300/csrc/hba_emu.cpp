@@ -45,7 +45,7 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
     const uint32_t words = std::max(alloc_dyn_words<NT>(), e->dyn_words);
     std::vector<uint64_t> dyn(words / 2 + 1);
     uint32_t* d = reinterpret_cast<uint32_t*>(dyn.data());
-    if (!e->self && e->staged && nf && free_smem_words(nf) <= words) {
+    if (!e->self && e->staged && nf && stage_fits(nf, words)) {
         // what the gathering CTAs of a cluster do on the GPU
         memcpy(d, gi.data(), sizeof(uint32_t) * GATHER_WORDS * nf);
         a.staged = 1;

@@ -693,8 +693,17 @@ HBA_HD uint32_t gt_capacity(uint32_t nf) {
     while (c < 2 * nf) c <<= 1;
     return c;
 }
-HBA_HD uint32_t gt_offset(uint32_t nf) { return (GATHER_WORDS * nf + 1u) & ~1u; }
-HBA_HD uint32_t free_smem_words(uint32_t nf) { return gt_offset(nf) + 2 * gt_capacity(nf) + 6 * nf + 4; }
+// Free batches up to STAGE_MAX_FREES keep a region for the staged gathered
+// records (five words per free, at the start); larger ones read the gathered
+// records where they were gathered, and their run list takes its own array.
+HBA_HD bool stage_layout(uint32_t nf) { return nf <= STAGE_MAX_FREES; }
+HBA_HD uint32_t gt_offset(uint32_t nf) { return stage_layout(nf) ? (GATHER_WORDS * nf + 1u) & ~1u : 0u; }
+HBA_HD uint32_t free_smem_words(uint32_t nf) {
+    return gt_offset(nf) + 2 * gt_capacity(nf) + 6 * nf + (stage_layout(nf) ? 0u : nf) + 4;
+}
+// whether the gathered records of nf frees can be written straight into the
+// free phase's shared-memory layout
+HBA_HD bool stage_fits(uint32_t nf, uint32_t dyn_words) { return stage_layout(nf) && free_smem_words(nf) <= dyn_words; }
 // Where the granule table of nf frees lives: in shared memory after the five
 // staged words per free when the free phase fits there, else at the start of
 // the global scratch.
@@ -715,7 +724,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     const bool sm = free_smem_words(nf) <= S.dyn_words;
     // the gathered records are (or get staged) in shared memory: staging pays
     // for small free batches, large ones read them where they were gathered
-    const bool copy = a.staged || (sm && nf <= STAGE_MAX_FREES);
+    const bool copy = sm && stage_layout(nf);
     uint32_t* w = sm ? S.dyn : a.scr;
     uint32_t* const base = w;
     const uint32_t* gG;
@@ -737,7 +746,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
     uint32_t* runAt = rend + nf;        // run leader whose last free is j, or NIL
     uint32_t* lh = runAt + nf;          // leftmost block of the run's left part
     uint32_t* fl = lh + nf;             // bit0: erase L, bit1: erase R, FL_WIN
-    uint32_t* runs = sm ? base + 3 * nf : fl + nf;  // run leaders in order (over gLL: read by then)
+    uint32_t* runs = copy ? base + 3 * nf : fl + nf;  // run leaders in order (over gLL: read by then)
     uint32_t* ul = sm ? a.scr : fl + 2 * nf;                     // [2 nf] absorbed old free blocks
 
     // F1: stage the gathered records (shared-memory layout), and put the
@@ -1792,7 +1801,7 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t 
     StepArgs b = a;
     if (a.self_gather && a.nf) {
         // four frees a thread at a time, their record loads side by side
-        const bool sm = free_smem_words(a.nf) <= dyn_words;
+        const bool sm = stage_fits(a.nf, dyn_words);
         uint32_t* dst = sm ? dyn : const_cast<uint32_t*>(a.gi);
         HBA_FOR_THREADS(tid) {
             for (uint32_t j0 = tid; j0 < a.nf; j0 += 4 * NT) {

@@ -252,7 +252,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
         // 4: the batch -- gather the records the frees need (four frees a
         // thread at a time, straight into the free phase's shared-memory
         // layout when it fits there), then the engine
-        const bool staged = nf && free_smem_words(nf) <= dyn_words;
+        const bool staged = nf && stage_fits(nf, dyn_words);
         uint32_t* gdst = staged ? dyn : g.gi;
         for (uint32_t j0 = tid; j0 < nf; j0 += 4 * NT) {
             uint64_t off[4];
