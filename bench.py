@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per engine launch on the large workload, from an
 # ncu capture of that kernel (profiles/); None until the current kernel has
 # been captured.
-K_SINGLE_LARGE_DRAM_BYTES = None
+K_SINGLE_LARGE_DRAM_BYTES = 159_744
 
 
 def _peaks():
