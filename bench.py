@@ -12,8 +12,11 @@ is one batch: its frees, then its allocations, in one kernel launch.
    steps, then K timed steps, each bracketed by CUDA events on the launching
    stream; between steps a 256 MiB buffer is written to flush L2 (untimed);
    when the trace wraps the allocator is reset (untimed).
-3. e2e: the same replay through ``hba_step_host`` (pinned host buffers, the
-   copies and the result read-back inside the timed region).
+3. e2e: the same replay through the host-buffer entry points (pinned host
+   buffers; the copies and the result read-back inside the timed region):
+   ``hba_step_host_async`` with three steps in flight, the host reading each
+   step's result two steps later (the reported ``e2e``), and the synchronous
+   ``hba_step_host`` beside it.
 
 ``--impl reference`` times the CPU oracle (the sequential statement of
 Algorithms 4/5) on the same workload, one batch per step.
@@ -275,11 +278,59 @@ def cuda_allocator_comparison(batches, alloc, flush, stream, max_ops: int = 60_0
     return res
 
 
+E2E_DEPTH = 3  # host-buffer steps in flight in the pipelined end-to-end run
+
+
+def e2e_host_calls(alloc, batches, steps, sptr, pipelined):
+    """Replay ``steps`` batches of the trace through the host-buffer entry
+    points (pinned inputs; copies, batch and result copy inside the call),
+    from a fresh state, timed on the host.  Pipelined: hba_step_host_async
+    with E2E_DEPTH output buffers in turn, the host waiting for and reading
+    step k's first offset before issuing step k + E2E_DEPTH - 1.  Otherwise
+    hba_step_host, which waits every step.  Returns (seconds, ops, H2D bytes,
+    D2H bytes)."""
+    import torch
+
+    from paper_2405_07079_gb300 import hba_step_host, hba_step_host_async
+    from paper_2405_07079_gb300.hba import _ptr
+
+    nb = len(batches)
+    stream = torch.cuda.current_stream()
+    depth = E2E_DEPTH if pipelined else 1
+    houts = [torch.empty(max(1, max(b["na"] for b in batches)), dtype=torch.int64).pin_memory()
+             for _ in range(depth)]
+    done = [torch.cuda.Event() for _ in range(depth)]
+    alloc.reset()
+    torch.cuda.synchronize()
+    n_ops = h2d = d2h = 0
+    seen = 0
+    pos = 0
+    t0 = time.perf_counter()
+    for k in range(steps):
+        if pos == nb:
+            alloc.reset(); pos = 0
+        b = batches[pos]; pos += 1
+        j = k % depth
+        if pipelined:
+            if k >= depth - 1:
+                i = (k - depth + 1) % depth
+                done[i].synchronize()
+                seen ^= int(houts[i][0])
+            hba_step_host_async(alloc.h, _ptr(b["hf"]), b["nf"], 0, _ptr(b["hs"]), b["na"], _ptr(houts[j]), sptr)
+            done[j].record(stream)
+        else:
+            hba_step_host(alloc.h, _ptr(b["hf"]), b["nf"], 0, _ptr(b["hs"]), b["na"], _ptr(houts[j]), sptr)
+            seen ^= int(houts[j][0])
+        n_ops += b["ops"]; h2d += 8 * (b["nf"] + b["na"]); d2h += 8 * b["na"]
+    stream.synchronize()
+    elapsed = time.perf_counter() - t0
+    return elapsed, n_ops, h2d, d2h
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
-    from paper_2405_07079_gb300 import Allocator, hba_step_host, workloads
-    from paper_2405_07079_gb300.hba import _ptr
+    from paper_2405_07079_gb300 import Allocator, workloads
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -327,22 +378,12 @@ def run_gpu(args, rank, world, local_rank):
     ops = sum(batches[i]["ops"] for i in idx)
     nbytes = sum(batches[i]["bytes"] for i in idx)
 
-    # e2e through the public host-buffer entry point, from a fresh state
-    alloc.reset()
-    torch.cuda.synchronize()
-    hout = torch.empty(65536, dtype=torch.int64).pin_memory()
-    e2e_ops, e2e_h2d, e2e_d2h = 0, 0, 0
-    pos = 0
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        if pos == nb:
-            alloc.reset(); pos = 0
-        b = batches[pos]; pos += 1
-        hba_step_host(alloc.h, _ptr(b["hf"]), b["nf"], 0, _ptr(b["hs"]), b["na"], _ptr(hout), sptr)
-        e2e_ops += b["ops"]; e2e_h2d += 8 * (b["nf"] + b["na"]); e2e_d2h += 8 * b["na"]
-    e2e_s = time.perf_counter() - t0
+    # e2e through the public host-buffer entry points, from a fresh state
+    e2e_s, e2e_ops, e2e_h2d, e2e_d2h = e2e_host_calls(alloc, batches, args.steps, sptr, pipelined=True)
+    sync_s, sync_ops, _, _ = e2e_host_calls(alloc, batches, args.steps, sptr, pipelined=False)
 
-    (busy_s, e2e_s), (ops_all, e2e_all) = reduce_over_ranks([busy_s, e2e_s], [ops, e2e_ops], world, dev)
+    (busy_s, e2e_s, sync_s), (ops_all, e2e_all, sync_all) = reduce_over_ranks(
+        [busy_s, e2e_s, sync_s], [ops, e2e_ops, sync_ops], world, dev)
     stats = alloc.stats()
     cuda_cmp = None
     if rank == 0 and not args.no_cuda_baseline:
@@ -375,7 +416,11 @@ def run_gpu(args, rank, world, local_rank):
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "unit": "per batch of one step"},
         "e2e": {"value": e2e_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d // max(1, args.steps),
-                "d2h_bytes_per_step": e2e_d2h // max(1, args.steps), "api": "hba_step_host"},
+                "d2h_bytes_per_step": e2e_d2h // max(1, args.steps), "api": "hba_step_host_async",
+                "form": (f"{E2E_DEPTH} steps in flight; each step's offsets are read on the host "
+                         f"{E2E_DEPTH - 1} steps later; no L2 flush between steps"),
+                "synchronous": {"value": sync_all / sync_s, "unit": UNIT, "api": "hba_step_host",
+                                "form": "one host wait per step"}},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "final_stats": {k: stats[k] for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail")},

@@ -95,8 +95,9 @@ typedef struct {
 
 /* Create a single-arena handle on the current CUDA device (§3.3 out-of-band
  * table, §5.1 initial state: one free block [0, arena)).  Allocates the
- * offset-to-block table (16 bytes per min_block granule) and scratch for
- * batches of up to 65,536 frees.  Synchronous.  *out is set only on HBA_OK. */
+ * offset-to-block table (16 bytes per min_block granule), scratch for
+ * batches of up to 65,536 frees, and the staging and streams of the
+ * host-buffer calls.  Synchronous.  *out is set only on HBA_OK. */
 hba_status_t hba_create(uint64_t arena_bytes, uint64_t min_block, int policy, hba_t* out);
 
 /* As hba_create, with scratch sized for batches of up to max_batch frees
@@ -137,6 +138,35 @@ hba_status_t hba_step(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_
 hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_t* h_status,
                            const uint64_t* h_sizes, uint32_t na, uint64_t* h_out_offsets,
                            hba_stream_t stream);
+
+/* hba_step_host without the host wait, for callers that keep several batches
+ * in flight.  Same arguments, checks and results; returns once the work is
+ * enqueued.
+ *
+ * Ordering.  The batch applies after every earlier call on this handle,
+ * whatever its stream.  The results are in h_status / h_out_offsets once
+ * `stream` reaches the point of this call: synchronise the stream, or record
+ * an event on it after the call and wait for that.  The input copies do NOT
+ * wait for work enqueued on `stream` before the call: h_frees and h_sizes
+ * must already hold the batch when the call is made, and all four host
+ * buffers must stay allocated and untouched until the results are in.  Page-
+ * locked host memory is required for the copies to overlap anything.
+ *
+ * Pipeline.  A single-arena handle keeps two device staging slots, used in
+ * turn, and three streams of its own (input copies, the engine, result
+ * copies), made by hba_create with the hba_step_host staging: 50 bytes per
+ * max_batch request.  Call k's input
+ * copies run while call k-1's batch is on the GPU; before a slot is reused,
+ * its previous results must have reached the host -- the device waits for
+ * that, the host never does.
+ *
+ * While `stream` is being captured into a CUDA graph, the call enqueues the
+ * copies and the batch on `stream` itself, in order, on the handle's
+ * hba_step_host staging; the graph must then not be replayed concurrently
+ * with that function. */
+hba_status_t hba_step_host_async(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_t* h_status,
+                                 const uint64_t* h_sizes, uint32_t na, uint64_t* h_out_offsets,
+                                 hba_stream_t stream);
 
 /* ---- batches that allocate nothing ------------------------------------- */
 

@@ -27,6 +27,7 @@ SIGNATURES = {
     "hba_free_batch_ex": (i32, [vp, vp, u32, vp, vp]),
     "hba_step": (i32, [vp, vp, u32, vp, vp, u32, vp, vp]),
     "hba_step_host": (i32, [vp, vp, u32, vp, vp, u32, vp, vp]),
+    "hba_step_host_async": (i32, [vp, vp, u32, vp, vp, u32, vp, vp]),
     "hba_step_static": (i32, [vp, vp, u32, vp, vp, u32, vp, vp]),
     "hba_reset": (i32, [vp, vp]),
     "hba_stats": (i32, [vp, vp]),

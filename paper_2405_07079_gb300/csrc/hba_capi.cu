@@ -38,6 +38,23 @@ struct hba_s {
     uint64_t* d_stage_s = nullptr;
     uint64_t* d_stage_o = nullptr;
     uint8_t* d_stage_st = nullptr;
+    // pipelined host-buffer calls (hba_step_host_async): two staging slots,
+    // used in turn, and three internal streams -- input copies, the engine,
+    // result copies -- so that one call's copies overlap its neighbours'
+    // kernels.  Made at create, with the hba_step_host staging.
+    struct Slot {
+        uint64_t* f = nullptr;
+        uint64_t* s = nullptr;
+        uint64_t* o = nullptr;
+        uint8_t* st = nullptr;
+        cudaEvent_t in = nullptr;    // inputs copied
+        cudaEvent_t done = nullptr;  // batch applied
+        cudaEvent_t out = nullptr;   // results copied back
+        bool used = false;
+    };
+    Slot slot[2];
+    cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+    uint32_t next_slot = 0;
     // launch shapes
     uint32_t threads = 0;       // single-arena CTA width (0: by batch size)
     uint32_t m_threads = 256;   // multi-arena CTA width
@@ -512,6 +529,22 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
     return launch_single(h, frees, nf, st, sizes, na, out, s, h->d_gi, h->d_scr);
 }
 
+// The staging slots and streams of hba_step_host_async, for n requests a side.
+hba_status_t make_pipeline(hba_t h, uint64_t n) {
+    for (hba_s::Slot& q : h->slot) {
+        if (cudaMalloc(&q.f, 8 * n) != cudaSuccess || cudaMalloc(&q.s, 8 * n) != cudaSuccess ||
+            cudaMalloc(&q.o, 8 * n) != cudaSuccess || cudaMalloc(&q.st, n) != cudaSuccess)
+            return HBA_ERR_OUT_OF_MEMORY;
+        HBA_CUDA_TRY(cudaEventCreateWithFlags(&q.in, cudaEventDisableTiming));
+        HBA_CUDA_TRY(cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming));
+        HBA_CUDA_TRY(cudaEventCreateWithFlags(&q.out, cudaEventDisableTiming));
+    }
+    HBA_CUDA_TRY(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
+    HBA_CUDA_TRY(cudaStreamCreateWithFlags(&h->s_run, cudaStreamNonBlocking));
+    HBA_CUDA_TRY(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
+    return HBA_OK;
+}
+
 hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_frees, uint32_t stage) {
     g_limits[0] = set_smem_limits<64>();
     g_limits[1] = set_smem_limits<128>();
@@ -538,6 +571,7 @@ hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_fr
             cudaMalloc(&h->d_stage_o, 8ull * stage) != cudaSuccess ||
             cudaMalloc(&h->d_stage_st, stage) != cudaSuccess)
             return HBA_ERR_OUT_OF_MEMORY;
+        return make_pipeline(h, stage);
     }
     return HBA_OK;
 }
@@ -583,6 +617,18 @@ void free_all(hba_t h) {
     cudaFree(h->d_stage_s);
     cudaFree(h->d_stage_o);
     cudaFree(h->d_stage_st);
+    for (hba_s::Slot& q : h->slot) {
+        cudaFree(q.f);
+        cudaFree(q.s);
+        cudaFree(q.o);
+        cudaFree(q.st);
+        if (q.in) cudaEventDestroy(q.in);
+        if (q.done) cudaEventDestroy(q.done);
+        if (q.out) cudaEventDestroy(q.out);
+    }
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_run) cudaStreamDestroy(h->s_run);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
     if (h->ev) cudaEventDestroy(h->ev);
 }
 
@@ -870,6 +916,50 @@ hba_status_t hba_step_host(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_
     if (na) HBA_CUDA_TRY(cudaMemcpyAsync(h_out_offsets, h->d_stage_o, 8ull * na, cudaMemcpyDeviceToHost, s));
     if (nf && h_status) HBA_CUDA_TRY(cudaMemcpyAsync(h_status, h->d_stage_st, nf, cudaMemcpyDeviceToHost, s));
     HBA_CUDA_TRY(cudaStreamSynchronize(s));
+    return HBA_OK;
+}
+
+hba_status_t hba_step_host_async(hba_t h, const uint64_t* h_frees, uint32_t nf, uint8_t* h_status,
+                                 const uint64_t* h_sizes, uint32_t na, uint64_t* h_out_offsets,
+                                 hba_stream_t stream) {
+    if (!h || h->n_arenas != 1 || !h->d_stage_f) return HBA_ERR_INVALID_ARGUMENT;
+    if (nf > h->max_batch || na > h->max_batch) return HBA_ERR_INVALID_ARGUMENT;
+    if ((nf && !h_frees) || (na && (!h_sizes || !h_out_offsets))) return HBA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HBA_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        // inside a capture every step stays on the captured stream, in order
+        if (nf) HBA_CUDA_TRY(cudaMemcpyAsync(h->d_stage_f, h_frees, 8ull * nf, cudaMemcpyHostToDevice, s));
+        if (na) HBA_CUDA_TRY(cudaMemcpyAsync(h->d_stage_s, h_sizes, 8ull * na, cudaMemcpyHostToDevice, s));
+        hba_status_t r = step_impl(h, h->d_stage_f, nf, h_status ? h->d_stage_st : nullptr, h->d_stage_s, na,
+                                   h->d_stage_o, s);
+        if (r != HBA_OK) return r;
+        if (na) HBA_CUDA_TRY(cudaMemcpyAsync(h_out_offsets, h->d_stage_o, 8ull * na, cudaMemcpyDeviceToHost, s));
+        if (nf && h_status) HBA_CUDA_TRY(cudaMemcpyAsync(h_status, h->d_stage_st, nf, cudaMemcpyDeviceToHost, s));
+        return HBA_OK;
+    }
+    hba_status_t r = HBA_OK;
+    hba_s::Slot& q = h->slot[h->next_slot];
+    h->next_slot ^= 1;
+    // the slot's previous results must be out before its inputs are replaced
+    if (q.used) HBA_CUDA_TRY(cudaStreamWaitEvent(h->s_in, q.out, 0));
+    if (nf) HBA_CUDA_TRY(cudaMemcpyAsync(q.f, h_frees, 8ull * nf, cudaMemcpyHostToDevice, h->s_in));
+    if (na) HBA_CUDA_TRY(cudaMemcpyAsync(q.s, h_sizes, 8ull * na, cudaMemcpyHostToDevice, h->s_in));
+    HBA_CUDA_TRY(cudaEventRecord(q.in, h->s_in));
+    HBA_CUDA_TRY(cudaStreamWaitEvent(h->s_run, q.in, 0));
+    {
+        StreamOrder order(h, h->s_run);
+        r = step_impl(h, q.f, nf, h_status ? q.st : nullptr, q.s, na, q.o, h->s_run);
+    }
+    if (r != HBA_OK) return r;
+    HBA_CUDA_TRY(cudaEventRecord(q.done, h->s_run));
+    HBA_CUDA_TRY(cudaStreamWaitEvent(h->s_out, q.done, 0));
+    if (na) HBA_CUDA_TRY(cudaMemcpyAsync(h_out_offsets, q.o, 8ull * na, cudaMemcpyDeviceToHost, h->s_out));
+    if (nf && h_status) HBA_CUDA_TRY(cudaMemcpyAsync(h_status, q.st, nf, cudaMemcpyDeviceToHost, h->s_out));
+    HBA_CUDA_TRY(cudaEventRecord(q.out, h->s_out));
+    q.used = true;
+    HBA_CUDA_TRY(cudaStreamWaitEvent(s, q.out, 0));
     return HBA_OK;
 }
 

@@ -57,6 +57,12 @@ def hba_step_host(h: int, h_frees: int, nf: int, h_status: int, h_sizes: int, na
     check("hba_step_host", _lib().hba_step_host(h, h_frees, nf, h_status, h_sizes, na, h_out, stream))
 
 
+def hba_step_host_async(h: int, h_frees: int, nf: int, h_status: int, h_sizes: int, na: int, h_out: int,
+                        stream: int = 0) -> None:
+    check("hba_step_host_async",
+          _lib().hba_step_host_async(h, h_frees, nf, h_status, h_sizes, na, h_out, stream))
+
+
 HBA_STATIC_MAX_FREES = 4096
 
 

@@ -18,7 +18,8 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for must in ("hba_create", "hba_alloc_batch", "hba_free_batch", "hba_stats", "hba_destroy",
-                 "hba_export_state", "hba_multi_create", "hba_multi_step", "hba_step_host"):
+                 "hba_export_state", "hba_multi_create", "hba_multi_step", "hba_step_host",
+                 "hba_step_host_async"):
         assert must in names
 
 
@@ -47,6 +48,8 @@ def test_invalid_arguments_rejected_without_device_work():
     assert lib.hba_create(1 << 40, 8, 0, ctypes.byref(h)) == 1        # more than 2^29 - 1 granules
     assert lib.hba_destroy(None) == 1
     assert lib.hba_step(None, None, 0, None, None, 0, None, None) == 1
+    assert lib.hba_step_host(None, None, 0, None, None, 0, None, None) == 1
+    assert lib.hba_step_host_async(None, None, 0, None, None, 0, None, None) == 1
 
 
 def test_product_path_has_no_cpu_fallback():

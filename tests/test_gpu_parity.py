@@ -232,6 +232,99 @@ def test_host_entry_point(gpu_lib):
             assert np.array_equal(go, out) and np.array_equal(gst, st)
 
 
+def _pinned(a: np.ndarray):
+    """A page-locked copy of a uint64 or uint8 array (a CPU torch tensor, kept
+    alive by the caller) and its numpy view."""
+    import torch
+
+    t = torch.from_numpy(np.ascontiguousarray(a).view(np.int64 if a.dtype == np.uint64 else np.uint8)).pin_memory()
+    v = t.numpy()
+    return t, (v.view(np.uint64) if a.dtype == np.uint64 else v)
+
+
+@pytest.mark.parametrize("wl_name,max_batches", [("tiny", None), ("large", 8)])
+def test_host_async_pipeline(gpu_lib, wl_name, max_batches):
+    """hba_step_host_async with every batch of the trace in flight at once and
+    one wait on the caller's stream at the end: every offset and status
+    equals the oracle's.  A device-buffer hba_step on the caller's stream in
+    the middle of the pipeline is ordered with the calls around it."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator, hba_step_host_async
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = {"tiny": lambda: W.tiny(n_ops=3000), "large": W.large}[wl_name]()
+    trace, o = oracle_trace(wl, max_batches)
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    mid = len(trace) // 2
+    keep, results = [], []
+    with Allocator(wl.arena, wl.min_block) as a:
+        for b, (f, s, out, st) in enumerate(trace):
+            if b == mid:
+                dst = torch.empty(f.size, dtype=torch.uint8, device=dev)
+                go = a.step(to_dev(f, dev), to_dev(s, dev), status=dst) if s.size else None
+                if not s.size:
+                    a.step(to_dev(f, dev), None, status=dst)
+                results.append(("dev", go, dst))
+                continue
+            tf, hf = _pinned(f)
+            ts, hs = _pinned(s)
+            to, ho = _pinned(np.zeros(s.size, np.uint64))
+            tst, hst = _pinned(np.zeros(f.size, np.uint8))
+            keep += [tf, ts, to, tst]
+            hba_step_host_async(a.h, hf.ctypes.data if f.size else 0, f.size, hst.ctypes.data if f.size else 0,
+                                hs.ctypes.data if s.size else 0, s.size, ho.ctypes.data if s.size else 0,
+                                int(stream.cuda_stream))
+            results.append(("host", ho, hst))
+        stream.synchronize()
+        for b, ((f, s, out, st), (kind, go, gst)) in enumerate(zip(trace, results)):
+            if kind == "dev":
+                go = from_dev(go) if go is not None else np.zeros(0, np.uint64)
+                gst = from_dev(gst)
+            i = first_diff(go, out)
+            assert i is None, f"batch {b} ({kind}): alloc {i}: gpu {go[i]:#x} oracle {out[i]:#x}"
+            assert first_diff(gst, st) is None, f"batch {b} ({kind}): free status differs"
+        assert np.array_equal(a.export_state(), o.export_state())
+
+
+def test_host_async_in_a_cuda_graph(gpu_lib):
+    """While the stream is captured, hba_step_host_async records its copies
+    and the batch on it; replaying the graph applies the batch like a direct
+    call, and the pipelined form carries on from that state."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator, hba_step_host_async
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.tiny(n_ops=400)
+    trace, _ = oracle_trace(wl, 3)
+    (f0, s0, out0, _), (f1, s1, out1, st1) = trace[0], trace[1]
+    assert f0.size == 0 and s0.size and s1.size
+    with Allocator(wl.arena, wl.min_block) as a:
+        ts, hs = _pinned(s0)
+        to, ho = _pinned(np.zeros(s0.size, np.uint64))
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+            hba_step_host_async(a.h, 0, 0, 0, hs.ctypes.data, s0.size, ho.ctypes.data, int(cap.cuda_stream))
+        torch.cuda.synchronize()
+        assert a.stats()["alloc_ok"] + a.stats()["alloc_fail"] == 0  # capturing ran nothing
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(ho, out0)
+        tf1, hf1 = _pinned(f1)
+        ts1, hs1 = _pinned(s1)
+        to1, ho1 = _pinned(np.zeros(s1.size, np.uint64))
+        tst1, hst1 = _pinned(np.zeros(f1.size, np.uint8))
+        stream = torch.cuda.current_stream()
+        hba_step_host_async(a.h, hf1.ctypes.data if f1.size else 0, f1.size, hst1.ctypes.data if f1.size else 0,
+                            hs1.ctypes.data, s1.size, ho1.ctypes.data, int(stream.cuda_stream))
+        stream.synchronize()
+        assert np.array_equal(ho1, out1) and np.array_equal(hst1, st1)
+
+
 def test_multi_arena_matches_per_arena_oracle(gpu_lib):
     """Independent arenas in one launch: arena i's results equal a single-arena
     oracle run of arena i's sub-trace."""
