@@ -86,6 +86,21 @@ def test_tiny_full(gpu_lib, threads, ctas):
     _run(W.tiny(), threads=threads, state_every=16, canary=True, ctas=ctas)
 
 
+@pytest.mark.parametrize("threads", [128, 1024])
+@pytest.mark.parametrize("granules,batch,p_free", [(4096, 3000, 0.2), (8192, 64, 0.4), (8193, 64, 0.4)])
+def test_small_record_tables(gpu_lib, threads, granules, batch, p_free):
+    """Small arenas (1-2 MiB, record tables of 64-128 KiB, which the engine
+    prefetches into L2 whole) with small batches (one launch, the engine
+    gathering its frees) and batches large enough for the prep grid (at
+    least 2,048 allocations, most of them failing in a full arena)."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.Workload("small-table", granules * 256, 256,
+                    lambda: W.TinyRandom(n_ops=40 * batch if batch > 64 else 6000, batch=batch, p_free=p_free,
+                                         hi=16 * KiB if batch > 64 else 64 * KiB))
+    _run(wl, threads=threads, state_every=4, canary=True)
+
+
 @pytest.mark.parametrize("threads,ctas", [(128, 0), (1024, 0), (1024, 1), (256, 3)])
 def test_large_reduced(gpu_lib, threads, ctas):
     from paper_2405_07079_gb300 import workloads as W
