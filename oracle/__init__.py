@@ -69,6 +69,7 @@ def _load():
             lib.orc_export.restype = ctypes.c_size_t
             lib.orc_export.argtypes = [vp, vp, ctypes.c_size_t]
             lib.orc_stats.argtypes = [vp, vp]
+            lib.orc_space.argtypes = [vp, vp]
             _lib = lib
     return _lib
 
@@ -129,6 +130,13 @@ class Oracle:
         buf = np.zeros(9, dtype=np.uint64)
         self._lib.orc_stats(self._h, buf.ctypes.data)
         return {k: int(v) for k, v in zip(self.STAT_KEYS, buf)}
+
+    def space(self) -> dict:
+        """Largest free block and extent (end of the highest in-use block,
+        0 when none): the memory-usage view of §6, Fig. 4."""
+        buf = np.zeros(2, dtype=np.uint64)
+        self._lib.orc_space(self._h, buf.ctypes.data)
+        return {"largest_free": int(buf[0]), "extent": int(buf[1])}
 
 
 def decode_state(words) -> dict:

@@ -317,6 +317,30 @@ size_t orc_export(const orc* o, uint64_t* buf, size_t cap) {
     return n;
 }
 
+/* The arena's space, as §6 (Fig. 4) looks at it: out[0] = the largest free
+ * block, out[1] = the extent -- the end of the highest in-use block (0 when
+ * none is in use), the prefix of the arena that has to be backed by device
+ * memory.  The largest free block is in the highest non-empty list, since
+ * list k holds exactly the free blocks whose floor(log2 size) is k. */
+void orc_space(const orc* o, uint64_t out[2]) {
+    uint64_t largest = 0, extent = 0;
+    if (o->bitmask) {
+        const unsigned k = floor_log2(o->bitmask);
+        uint64_t cnt = 0;
+        for (uint64_t p = o->free_lists[k]; p != ORC_NIL && cnt <= o->count; cnt++) {
+            const orc_entry* e = ht_find(o, p);
+            if (!e) break;
+            if (e->size > largest) largest = e->size;
+            p = e->next_free;
+        }
+    }
+    for (uint64_t b = 0; b < o->nbuckets; b++)
+        for (const orc_entry* e = o->buckets[b]; e; e = e->chain)
+            if (!e->free && e->addr + e->size > extent) extent = e->addr + e->size;
+    out[0] = largest;
+    out[1] = extent;
+}
+
 /* Counters: alloc_ok, alloc_fail, free_ok, free_fail, used_bytes,
  * used_blocks, blocks, requested_bytes, bitmask. */
 void orc_stats(const orc* o, uint64_t out[9]) {

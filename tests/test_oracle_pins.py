@@ -187,6 +187,8 @@ def test_carving_prefix_sums():
             assert o.malloc(int(s)) == expect
             if expect != FAIL:
                 used += sp
+            # the carved prefix is the extent; the rest is one free block
+            assert o.space() == {"extent": used, "largest_free": A - used}
 
 
 def test_frag_fill_and_full_arena_closed_forms():
@@ -197,12 +199,29 @@ def test_frag_fill_and_full_arena_closed_forms():
     o = oracle.Oracle(n * 4096, 256)
     out, _ = o.batch(np.zeros(0, np.uint64), np.full(n, 4096, np.uint64))
     assert np.array_equal(out, np.arange(n, dtype=np.uint64) * 4096)
+    assert o.space() == {"extent": n * 4096, "largest_free": 0}
     _, st = o.batch(out[0::2], np.zeros(0, np.uint64))
     assert not st.any()
+    # the last block (odd index) stays in use: the extent does not shrink
+    assert o.space() == {"extent": n * 4096, "largest_free": 4096}
     out2, _ = o.batch(np.zeros(0, np.uint64), np.array([4097, 8192, 1 << 20], np.uint64))
     assert (out2 == FAIL).all()
     s = oracle.decode_state(o.export_state())
     assert s["bitmask"] == 1 << 12 and len(s["bins"][12]) == n // 2
+
+
+def test_space_of_the_first_worked_example():
+    """W1 (A = 4096, min block 256) batch by batch: extent = end of the
+    highest in-use block, largest free block from the free blocks left."""
+    u = lambda *v: np.array(v, dtype=np.uint64)
+    o = oracle.Oracle(4096, 256)
+    assert o.space() == {"extent": 0, "largest_free": 4096}
+    o.batch(u(), u(1000, 256, 3000))                  # [0,1024) [1024,1280) used
+    assert o.space() == {"extent": 1280, "largest_free": 4096 - 1280}
+    o.batch(u(0), u(2048))                            # [1280,3328) used, [0,1024) free
+    assert o.space() == {"extent": 3328, "largest_free": 1024}
+    o.batch(u(1024, 1280), u(512))                    # everything merged, then [0,512)
+    assert o.space() == {"extent": 512, "largest_free": 3584}
 
 
 def test_release_all_returns_one_block():
@@ -221,6 +240,7 @@ def test_release_all_returns_one_block():
         assert not st.any()
         s = oracle.decode_state(o.export_state())
         assert s["blocks"] == [(0, 1 << 22, True)] and s["bins"][22] == [0]
+        assert o.space() == {"extent": 0, "largest_free": 1 << 22}
 
 
 def test_exact_powers_of_two_fit_from_own_class():
@@ -304,6 +324,10 @@ def test_invariants_on_workload_traces():
             s = oracle.decode_state(o.export_state())
             assert stt["used_bytes"] == sum(sz for _, sz, fr in s["blocks"] if not fr)
             assert stt["blocks"] == len(s["blocks"])
+            # the space report against a walk of the blocks in address order
+            sp = o.space()
+            assert sp["largest_free"] == max([sz for _, sz, fr in s["blocks"] if fr], default=0)
+            assert sp["extent"] == max([off + sz for off, sz, fr in s["blocks"] if not fr], default=0)
 
 
 def test_property_hypothesis():
