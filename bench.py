@@ -122,14 +122,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def record_trace(wl, alloc, dev):
-    """Drive the client closed loop against the GPU allocator (untimed)."""
+def record_trace(wl, alloc, dev, space=None):
+    """Drive the client closed loop against the GPU allocator (untimed).
+    ``space``: a list that receives, after every batch, the memory-usage
+    sample of §6 (Fig. 4): the bytes the client has live (sum of its live
+    requests), the allocator's used bytes (rounded blocks), its extent (end
+    of the highest in-use block: what has to be backed), and its largest
+    free block and free bytes."""
     import torch
-
-    from paper_2405_07079_gb300.hba import _ptr
 
     client = wl.make()
     batches = []
+    live = {}
+    live_bytes = 0
     while (b := client.next_batch()) is not None:
         f, s = b
         df = torch.from_numpy(f.view(np.int64)).to(dev)
@@ -144,12 +149,45 @@ def record_trace(wl, alloc, dev):
         n_fok = int((stat == 0).sum())
         nbytes = (BYTES_ALLOC_OK * n_ok + BYTES_ALLOC_FAIL * (s.size - n_ok)
                   + BYTES_FREE_OK * n_fok + BYTES_FREE_REJECTED * (f.size - n_fok))
+        if space is not None:
+            for off, fs in zip(f.tolist(), stat.tolist()):
+                if fs == 0:
+                    live_bytes -= live.pop(off)
+            for sz, off in zip(s.tolist(), o.tolist()):
+                if off != int(FAIL):
+                    live[off] = sz
+                    live_bytes += sz
+            st_ = alloc.stats()
+            space.append((live_bytes, st_["used_bytes"], st_["extent_bytes"], st_["largest_free"],
+                          st_["free_bytes"]))
         batches.append({"f": df, "s": ds, "out": out, "st": st, "nf": f.size, "na": s.size,
                         "host": (f, stat, s, o),
                         "ops": f.size + s.size, "bytes": nbytes,
                         "hf": torch.from_numpy(f.view(np.int64).copy()).pin_memory(),
                         "hs": torch.from_numpy(s.view(np.int64).copy()).pin_memory()})
     return batches
+
+
+def space_report(samples, arena: int) -> dict:
+    """Summary of the per-batch memory-usage samples of ``record_trace``:
+    fragmentation = 1 - live / extent (the ratio §6 reads off Fig. 4: memory
+    the client uses against memory that must be provisioned), the rounding
+    share 1 - live / used, and largest free block / free bytes."""
+    frag = [1 - lv / ex for lv, _, ex, _, _ in samples if ex]
+    rnd = [1 - lv / us for lv, us, _, _, _ in samples if us]
+    lff = [lf / fb for _, _, _, lf, fb in samples if fb]
+    q = lambda v, p: sorted(v)[min(len(v) - 1, int(p * len(v)))] if v else None
+    mean = lambda v: sum(v) / len(v) if v else None
+    step = max(1, len(samples) // 16)
+    return {"source": "hba_stats after every batch of the recorded trace (untimed)",
+            "fragmentation": {"definition": "1 - live client bytes / extent (end of the highest in-use block)",
+                              "mean": mean(frag), "p50": q(frag, 0.5), "max": max(frag) if frag else None,
+                              "final": frag[-1] if frag else None},
+            "rounding": {"definition": "1 - live client bytes / bytes in in-use blocks", "mean": mean(rnd)},
+            "largest_free_over_free": {"mean": mean(lff), "min": min(lff) if lff else None},
+            "peak_extent_bytes": max((ex for _, _, ex, _, _ in samples), default=0), "arena_bytes": arena,
+            "series": {"every_batches": step, "columns": ["live_bytes", "used_bytes", "extent_bytes"],
+                       "rows": [list(x[:3]) for x in samples[::step]]}}
 
 
 def reduce_over_ranks(maxes, sums, world: int, device=None):
@@ -334,9 +372,11 @@ def run_gpu(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag}[args.workload]()
+    wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag,
+          "usage": workloads.usage}[args.workload]()
     alloc = Allocator(wl.arena, wl.min_block, threads=args.threads, ctas=args.ctas)
-    batches = record_trace(wl, alloc, dev)
+    space = []
+    batches = record_trace(wl, alloc, dev, space)
     nb = len(batches)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -424,6 +464,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "final_stats": {k: stats[k] for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail")},
+        "memory_usage": space_report(space, alloc.arena_bytes),
     }
     if cuda_cmp is not None:
         line["cuda_allocators"] = cuda_cmp
@@ -709,10 +750,11 @@ def run_serve(args, rank, world, local_rank):
 
 def alloc_threads(args):
     """CTA width of the plain form: --threads, else the library's choice by
-    batch size (1,024 for the large and frag batches, 128 for tiny ones)."""
+    batch size (1,024 for the large and frag batches, 128 for the tiny ones
+    and the one-op batches of the memory-usage workload)."""
     if args.threads:
         return args.threads
-    return 128 if args.workload == "tiny" else 1024
+    return 128 if args.workload in ("tiny", "usage") else 1024
 
 
 def oracle_steps(wl, n_steps=None, warmup=0):
@@ -757,7 +799,8 @@ def run_reference(args, rank, world):
         return None
     from paper_2405_07079_gb300 import workloads
 
-    wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag}[args.workload]()
+    wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag,
+          "usage": workloads.usage}[args.workload]()
     t, ops, k = oracle_steps(wl, n_steps=args.steps, warmup=args.warmup)
     v = ops / t
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
@@ -778,7 +821,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1530)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["large", "tiny", "frag", "multi", "serve"], default="large")
+    ap.add_argument("--workload", choices=["large", "tiny", "frag", "usage", "multi", "serve"], default="large")
     ap.add_argument("--lams", default="1,2,5,10,20,50")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--arenas", type=int, default=4096)

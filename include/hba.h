@@ -89,6 +89,10 @@ typedef struct {
     uint64_t largest_free;           /* size of the largest free block */
     uint64_t bitmask;                /* availability bitmap (bit k: list k non-empty); arena 0 */
     uint64_t arena_bytes;            /* managed bytes (sum over arenas) */
+    uint64_t extent_bytes;           /* end of the highest in-use block, 0 when none (sum
+                                        over arenas): the part of the arena that has to be
+                                        backed by device memory, the "provisioned" memory
+                                        of §6 (Fig. 4) */
     uint32_t n_arenas;
     uint32_t device_error;           /* 0, or a code the device recorded */
 } hba_stats_t;
@@ -204,8 +208,10 @@ hba_status_t hba_step_static(hba_t h, const uint64_t* d_frees, uint32_t nf, uint
  * counters.  Asynchronous on stream. */
 hba_status_t hba_reset(hba_t h, hba_stream_t stream);
 
-/* Read the counters.  Waits for all work on the device to finish.  Also
- * reports HBA_ERR_STATE if the device recorded a metadata error. */
+/* Read the counters and the space report (largest free block; extent, from
+ * a scan of the whole record table: 16 bytes read per granule).  Waits for
+ * all work on the device to finish.  Also reports HBA_ERR_STATE if the
+ * device recorded a metadata error. */
 hba_status_t hba_stats(hba_t h, hba_stats_t* out);
 
 /* Canonical state of arena `arena` (0 for a single-arena handle), as 64-bit

@@ -50,7 +50,7 @@ class HbaError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes", "used_blocks", "blocks",
-        "requested_bytes", "free_bytes", "largest_free", "bitmask", "arena_bytes")] + [
+        "requested_bytes", "free_bytes", "largest_free", "bitmask", "arena_bytes", "extent_bytes")] + [
         ("n_arenas", ctypes.c_uint32), ("device_error", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:

@@ -68,6 +68,7 @@ struct hba_s {
     cudaStream_t last = nullptr;
     bool have_last = false;
     uint64_t* d_largest = nullptr;
+    uint32_t* d_extent = nullptr;  // per arena: end granule of the highest in-use block
 };
 
 namespace {
@@ -364,6 +365,46 @@ constexpr uint32_t SELF_GATHER_MAX = HBA_SELF_GATHER_MAX;
 
 // Launch the prep grid if the batch needs one; returns whether out[] is
 // pre-filled.  *pdl is set when the next launch may depend on it.
+// Extent of every arena: the end (in granules) of its highest in-use block,
+// 0 when none is in use.  The start granule of every in-use block holds an
+// ST_USED record and no other granule does, so this is a max-reduction over
+// the record table.  A CTA takes a tile of 64 x blockDim granules, a thread
+// every blockDim-th granule of it (coalesced); a thread finds the arena of
+// its first granule by binary search over the record bases (contiguous,
+// ascending) and steps to the next arena at a boundary.  ext[] must be zero.
+__global__ void k_extent(const Arena* ars, const Rec* pool, uint32_t n_arenas, uint64_t total, uint32_t* ext) {
+    const uint64_t T = 64ull * blockDim.x;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * T; t0 < total; t0 += (uint64_t)gridDim.x * T) {
+        uint64_t q = t0 + threadIdx.x;
+        if (q >= total) continue;
+        uint32_t lo = 0, hi = n_arenas - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) / 2;
+            if (ars[mid].rec_base <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        uint32_t a = lo;
+        uint64_t base = ars[a].rec_base, end = base + ars[a].G;
+        uint32_t best = 0;
+        const uint64_t stop = t0 + T < total ? t0 + T : total;
+        for (; q < stop; q += blockDim.x) {
+            while (q >= end && a + 1 < n_arenas) {
+                if (best) atomicMax(&ext[a], best);
+                best = 0;
+                ++a;
+                base = ars[a].rec_base;
+                end = base + ars[a].G;
+            }
+            const uint32_t x = pool[q].x;
+            if (hba::st_of(x) == hba::ST_USED) {
+                const uint32_t e = (uint32_t)(q - base) + hba::sz_of(x);
+                if (e > best) best = e;
+            }
+        }
+        if (best) atomicMax(&ext[a], best);
+    }
+}
+
 bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint32_t* gi, uint64_t* out,
                  uint32_t na, cudaStream_t s, bool* pdl);
 
@@ -564,6 +605,7 @@ hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_fr
     if (cudaMalloc(&h->d_gi, 4ull * hba::GATHER_WORDS * std::max<uint64_t>(scr_frees, 1)) != cudaSuccess)
         return HBA_ERR_OUT_OF_MEMORY;
     if (cudaMalloc(&h->d_largest, sizeof(uint64_t) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc(&h->d_extent, sizeof(uint32_t) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
     HBA_CUDA_TRY(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
     if (stage) {
         if (cudaMalloc(&h->d_stage_f, 8ull * stage) != cudaSuccess ||
@@ -613,6 +655,7 @@ void free_all(hba_t h) {
     cudaFree(h->d_scr);
     cudaFree(h->d_gi);
     cudaFree(h->d_largest);
+    cudaFree(h->d_extent);
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_s);
     cudaFree(h->d_stage_o);
@@ -975,10 +1018,20 @@ hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
     k_largest<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->d_largest);
     ++h->launches;
     HBA_CUDA_TRY(cudaGetLastError());
+    HBA_CUDA_TRY(cudaMemset(h->d_extent, 0, sizeof(uint32_t) * h->n_arenas));
+    {
+        const uint64_t tiles = (h->total_granules + 64ull * 256 - 1) / (64ull * 256);
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, 1), 8192);
+        k_extent<<<grid, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->total_granules, h->d_extent);
+        ++h->launches;
+        HBA_CUDA_TRY(cudaGetLastError());
+    }
     std::vector<Arena> ar(h->n_arenas);
     std::vector<uint64_t> largest(h->n_arenas);
+    std::vector<uint32_t> extent(h->n_arenas);
     HBA_CUDA_TRY(cudaMemcpy(ar.data(), h->d_arenas, sizeof(Arena) * h->n_arenas, cudaMemcpyDeviceToHost));
     HBA_CUDA_TRY(cudaMemcpy(largest.data(), h->d_largest, 8ull * h->n_arenas, cudaMemcpyDeviceToHost));
+    HBA_CUDA_TRY(cudaMemcpy(extent.data(), h->d_extent, 4ull * h->n_arenas, cudaMemcpyDeviceToHost));
     memset(out, 0, sizeof(*out));
     out->n_arenas = h->n_arenas;
     for (uint32_t i = 0; i < h->n_arenas; ++i) {
@@ -993,6 +1046,7 @@ hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
         out->requested_bytes += a.requested;
         out->arena_bytes += a.arena_bytes;
         out->largest_free = std::max(out->largest_free, largest[i]);
+        out->extent_bytes += (uint64_t)extent[i] << a.lg;
         if (a.err && !out->device_error) out->device_error = a.err;
     }
     out->free_bytes = out->arena_bytes - out->used_bytes;

@@ -333,6 +333,48 @@ class MultiLifetimes:
         self.offs = np.insert(self.offs, pos, no)
 
 
+class RandomSlots:
+    """The malloc-large pattern as §6 describes it, as a client: ``slots``
+    slots, and per op a slot drawn uniformly; a slot that holds a block has
+    it freed, an empty one gets a malloc of a log-uniform size in
+    ``[lo, hi]`` (1 kB to 16 MB by default; a failed malloc leaves the slot
+    empty).  Ops are cut into batches of at most ``batch`` ops in which every
+    free comes before every malloc and no slot appears twice, so that the
+    batched trace applies the ops in their sequential order."""
+
+    def __init__(self, n_ops=5000, slots=64, lo=1 * KiB, hi=16 * MiB, batch=1, seed=BASE_SEED + 6):
+        self.n_ops, self.slots, self.lo, self.hi, self.bs = n_ops, slots, lo, hi, batch
+        self.s_pick, self.s_size = Stream(seed, "slot"), Stream(seed, "size")
+        self.held: list[int | None] = [None] * slots
+        self.t = 0
+        self._filling: list[int] = []
+
+    def next_batch(self):
+        if self.t >= self.n_ops:
+            return None
+        frees, sizes, touched = [], [], set()
+        self._filling = []
+        while self.t < self.n_ops and len(frees) + len(sizes) < self.bs:
+            j = min(int(self.s_pick.unif([self.t])[0] * self.slots), self.slots - 1)
+            held = self.held[j]
+            if j in touched or (held is not None and sizes):
+                break  # the op would break sequential order: it starts the next batch
+            touched.add(j)
+            if held is not None:
+                frees.append(held)
+                self.held[j] = None
+            else:
+                sizes.append(int(log_uniform(self.s_size.unif([self.t]), self.lo, self.hi)[0]))
+                self._filling.append(j)
+            self.t += 1
+        return np.array(frees, dtype=np.uint64), np.array(sizes, dtype=np.uint64)
+
+    def feed(self, out):
+        for j, off in zip(self._filling, np.asarray(out).tolist()):
+            if off != FAIL:
+                self.held[j] = int(off)
+
+
 def serving_arrivals(lam: float, seconds: float, page=16 * KiB, max_pages=512, hold_mean_ns=20e6,
                      seed=BASE_SEED + 5):
     """Open-loop requests: Poisson arrivals at ``lam`` per second for
@@ -386,6 +428,12 @@ def frag(n_fill=1_000_000, n_big=50_000, batch=16_384, arena=4 * GiB):
     return Workload("frag-4GiB", arena, 256,
                     lambda: FragStress(n_fill=n_fill, n_big=n_big, batch=batch),
                     "4 GiB arena, min block 256 B, fill 1M x 4 KiB, free evens, 50k big, free all")
+
+
+def usage(n_ops=5000, slots=64, batch=1, arena=4 * GiB):
+    return Workload("usage-4GiB", arena, 4 * KiB, lambda: RandomSlots(n_ops=n_ops, slots=slots, batch=batch),
+                    "4 GiB arena, min block 4 KiB, 5,000 ops on 64 slots (free if held, else malloc "
+                    "log-uniform 1 kB-16 MB), one op per batch")
 
 
 def drain(client, alloc_batch):

@@ -73,11 +73,13 @@ int main(void) {
     memset(&sx, 0, sizeof sx);
     if (hba_stats(h, &sx) != HBA_OK) ++fails;
     if (sx.used_bytes != 512 || sx.blocks != 2 || sx.bitmask != (1ull << 11) || sx.alloc_ok != 4 ||
-        sx.alloc_fail != 1 || sx.free_ok != 3) {
-        printf("stats: used %llu blocks %llu bitmask %llx alloc_ok %llu alloc_fail %llu free_ok %llu\n",
+        sx.alloc_fail != 1 || sx.free_ok != 3 || sx.extent_bytes != 512 || sx.largest_free != 3584) {
+        printf("stats: used %llu blocks %llu bitmask %llx alloc_ok %llu alloc_fail %llu free_ok %llu "
+               "extent %llu largest free %llu\n",
                (unsigned long long)sx.used_bytes, (unsigned long long)sx.blocks,
                (unsigned long long)sx.bitmask, (unsigned long long)sx.alloc_ok,
-               (unsigned long long)sx.alloc_fail, (unsigned long long)sx.free_ok);
+               (unsigned long long)sx.alloc_fail, (unsigned long long)sx.free_ok,
+               (unsigned long long)sx.extent_bytes, (unsigned long long)sx.largest_free);
         ++fails;
     }
     hba_destroy(h);

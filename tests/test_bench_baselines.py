@@ -63,3 +63,22 @@ def test_cuda_replay_ops_multi_is_well_formed():
             assert -op - 1 in live
             live.remove(-op - 1)
     assert n == sum(int((b["ref_out"] != FAIL).sum()) for b in batches)
+
+
+def test_space_report_definitions():
+    """The memory-usage summary: fragmentation 1 - live / extent, rounding
+    1 - live / used, largest free / free bytes; batches with nothing in use
+    or nothing free are left out of the ratios they would divide by zero."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    samples = [(0, 0, 0, 4096, 4096),        # nothing live yet
+               (50, 64, 100, 30, 40),
+               (300, 400, 1000, 0, 0)]       # arena full
+    r = bench.space_report(samples, 4096)
+    assert r["fragmentation"]["mean"] == (0.5 + 0.7) / 2
+    assert r["fragmentation"]["final"] == 0.7 and r["fragmentation"]["max"] == 0.7
+    assert r["rounding"]["mean"] == ((1 - 50 / 64) + (1 - 300 / 400)) / 2
+    assert r["largest_free_over_free"]["mean"] == (1.0 + 0.75) / 2
+    assert r["peak_extent_bytes"] == 1000 and r["arena_bytes"] == 4096
+    assert r["series"]["rows"][1] == [50, 64, 100]

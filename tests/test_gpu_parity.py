@@ -41,6 +41,8 @@ def _run(wl, threads=None, max_batches=None, state_every=0, canary=False, ctas=0
                 lock.batch(f, s)
                 if b % state_every == 0:
                     assert np.array_equal(a.export_state(), lock.export_state()), f"batch {b}: state differs"
+                    got, ref = a.stats(), lock.space()
+                    assert (got["extent_bytes"], got["largest_free"]) == (ref["extent"], ref["largest_free"]), b
         gs = a.export_state()
         assert np.array_equal(gs, o.export_state()), "final state differs"
         check_invariants(gs)
@@ -49,6 +51,8 @@ def _run(wl, threads=None, max_batches=None, state_every=0, canary=False, ctas=0
         for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes", "used_blocks",
                   "blocks", "requested_bytes", "bitmask"):
             assert got[k] == ref[k], (k, got[k], ref[k])
+        sp = o.space()
+        assert got["extent_bytes"] == sp["extent"] and got["largest_free"] == sp["largest_free"]
     if canary:
         torch.cuda.synchronize()
         assert bool((guard == 0xA5).all()), "the managed arena was written"

@@ -313,7 +313,8 @@ def test_invariants_on_workload_traces():
 
     for wl in (W.tiny(n_ops=3000),
                W.Workload("l", 1 << 28, 512, lambda: W.Lifetimes(n_ops=60_000, batch=2048, mean_life=200)),
-               W.frag(n_fill=8000, n_big=800, batch=1024, arena=64 << 20)):
+               W.frag(n_fill=8000, n_big=800, batch=1024, arena=64 << 20),
+               W.Workload("u", 1 << 28, 4096, lambda: W.RandomSlots(n_ops=3000, slots=48, hi=4 << 20, batch=8))):
         o = oracle.Oracle(wl.arena, wl.min_block)
         cl = wl.make()
         while (b := cl.next_batch()) is not None:
@@ -328,6 +329,26 @@ def test_invariants_on_workload_traces():
             sp = o.space()
             assert sp["largest_free"] == max([sz for _, sz, fr in s["blocks"] if fr], default=0)
             assert sp["extent"] == max([off + sz for off, sz, fr in s["blocks"] if not fr], default=0)
+
+
+def test_random_slots_batches_keep_sequential_order():
+    """The malloc-large stand-in cut into batches of up to 16 ops gives the
+    same results, op for op, and the same final state as one op per batch:
+    its batches never put a malloc before a free or touch a slot twice."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    runs = []
+    for bs in (1, 16):
+        o = oracle.Oracle(1 << 30, 4096)
+        cl = W.RandomSlots(n_ops=1500, slots=24, batch=bs)
+        ops = []
+        while (b := cl.next_batch()) is not None:
+            out, st = o.batch(*b)
+            cl.feed(out)
+            ops += [("f", int(x), int(t)) for x, t in zip(b[0], st)] + [("a", int(x), int(y)) for x, y in zip(b[1], out)]
+        runs.append((ops, o.export_state().tolist(), o.space()))
+    assert runs[0] == runs[1]
+    assert len(runs[0][0]) == 1500
 
 
 def test_property_hypothesis():
