@@ -58,6 +58,8 @@ def _load():
             u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
             lib.orc_create.restype = vp
             lib.orc_create.argtypes = [u64, u64]
+            lib.orc_create_policy.restype = vp
+            lib.orc_create_policy.argtypes = [u64, u64, ctypes.c_int]
             lib.orc_destroy.argtypes = [vp]
             lib.orc_arena.restype = u64
             lib.orc_arena.argtypes = [vp]
@@ -78,15 +80,20 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data if a.size else None
 
 
+POLICIES = {"segfit": 0, "tlsf": 1}
+
+
 class Oracle:
-    """One arena managed by the sequential oracle."""
+    """One arena managed by the sequential oracle: segregated fit (§5.1),
+    or with ``policy="tlsf"`` two-level segregated fit (§5.2)."""
 
     STAT_KEYS = ("alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes",
                  "used_blocks", "blocks", "requested_bytes", "bitmask")
 
-    def __init__(self, arena_bytes: int, min_block: int):
+    def __init__(self, arena_bytes: int, min_block: int, policy: str = "segfit"):
         self._lib = _load()
-        self._h = self._lib.orc_create(int(arena_bytes), int(min_block))
+        self.policy = policy
+        self._h = self._lib.orc_create_policy(int(arena_bytes), int(min_block), POLICIES[policy])
         if not self._h:
             raise ValueError("invalid arena_bytes/min_block")
         self.arena = int(self._lib.orc_arena(self._h))
@@ -139,8 +146,9 @@ class Oracle:
         return {"largest_free": int(buf[0]), "extent": int(buf[1])}
 
 
-def decode_state(words) -> dict:
-    """Split a canonical state (R11) into its parts for readable assertions."""
+def decode_state(words, policy: str = "segfit") -> dict:
+    """Split a canonical state (R11; T4 for TLSF) into its parts for
+    readable assertions."""
     w = [int(x) for x in words]
     arena, min_block, nblocks = w[0], w[1], w[2]
     blocks = []
@@ -155,11 +163,16 @@ def decode_state(words) -> dict:
         a = off + sz
         i += 2
     bins = []
-    for _ in range(64):
+    for _ in range(64 if policy == "segfit" else 64 * 16):
         cnt = w[i]
         bins.append(w[i + 1:i + 1 + cnt])
         i += 1 + cnt
     bitmask = w[i]
-    assert i + 1 == len(w), "trailing words in canonical state"
+    i += 1
+    slmask = []
+    if policy == "tlsf":
+        slmask = w[i:i + 64]
+        i += 64
+    assert i == len(w), "trailing words in canonical state"
     return {"arena": arena, "min_block": min_block, "nblocks": nblocks,
-            "blocks": blocks, "bins": bins, "bitmask": bitmask}
+            "blocks": blocks, "bins": bins, "bitmask": bitmask, "slmask": slmask}

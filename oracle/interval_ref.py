@@ -19,6 +19,15 @@ two pin each other:
   becomes free, merges with free neighbours on both sides (found by scanning
   the ordered list), and the merged interval gets a fresh stamp.
 
+Two-level segregated fit (§5.2, ``policy="tlsf"``) in the same terms: the
+list of a free interval of size z is (f, k) with f = floor(log2 z) and
+k = floor(16 (z - 2^f) / 2^f), i.e. the sixteenth of [2^f, 2^(f+1)) that z
+falls in; the list's lower bound is (16 + k) 2^f / 16.  An allocation of s'
+may take a list whose lower bound is >= s' (then all of its members fit);
+the lowest such list wins, and inside it the largest stamp.  The oracle finds
+that list with bit masks and a rounding trick instead; this statement uses
+the bounds themselves.
+
 Pure-Python loops: for arenas of a few dozen granules and short traces only.
 """
 from __future__ import annotations
@@ -34,9 +43,21 @@ def _ceil_log2(x: int) -> int:
     return (x - 1).bit_length() if x > 1 else 0
 
 
+def _tlsf_list(z: int):
+    f = _floor_log2(z)
+    return f, (16 * (z - (1 << f))) >> f
+
+
+def _tlsf_fits(lst, s: int) -> bool:
+    f, k = lst
+    return (16 + k) << f >= 16 * s
+
+
 class IntervalAllocator:
-    def __init__(self, arena_bytes: int, min_block: int):
+    def __init__(self, arena_bytes: int, min_block: int, policy: str = "segfit"):
         assert min_block >= 8 and min_block & (min_block - 1) == 0
+        assert policy in ("segfit", "tlsf")
+        self.policy = policy
         self.arena = arena_bytes - arena_bytes % min_block
         assert self.arena > 0
         self.min_block = min_block
@@ -56,9 +77,17 @@ class IntervalAllocator:
         c = _ceil_log2(s)
         best = None
         for k, (st, sz, fr, stamp) in enumerate(self.iv):
-            if not fr or _floor_log2(sz) < c:
+            if not fr:
                 continue
-            key = (_floor_log2(sz), -stamp)
+            if self.policy == "tlsf":
+                lst = _tlsf_list(sz)
+                if not _tlsf_fits(lst, s):
+                    continue
+                key = (lst, -stamp)
+            else:
+                if _floor_log2(sz) < c:
+                    continue
+                key = (_floor_log2(sz), -stamp)
             if best is None or key < best[0]:
                 best = (key, k)
         if best is None:
@@ -90,10 +119,23 @@ class IntervalAllocator:
         return out, st
 
     def export_state(self) -> list:
-        """Same canonical words as the C oracle (blocks, bins by stamp, bitmap)."""
+        """Same canonical words as the C oracle (blocks, bins by stamp, bitmap;
+        TLSF: the 64 x 16 lists, the first-level and second-level masks)."""
         w = [self.arena, self.min_block, len(self.iv)]
         for st, sz, fr, _ in self.iv:
             w += [st, sz | (int(fr) << 63)]
+        if self.policy == "tlsf":
+            fl, sl = 0, [0] * 64
+            for f in range(64):
+                for k in range(16):
+                    members = sorted((v for v in self.iv if v[2] and _tlsf_list(v[1]) == (f, k)),
+                                     key=lambda v: -v[3])
+                    w.append(len(members))
+                    w += [v[0] for v in members]
+                    if members:
+                        fl |= 1 << f
+                        sl[f] |= 1 << k
+            return w + [fl] + sl
         bitmask = 0
         for b in range(64):
             members = sorted((v for v in self.iv if v[2] and _floor_log2(v[1]) == b),

@@ -15,7 +15,8 @@
  *     the next/previous block of its free list, the previous adjacent block
  *     and a collision link (the six-word entry of §3.3), plus the free flag
  *     that the pseudocode of Algorithms 4/5 reads;
- *   - free_lists[64], the head address of each power-of-two size class;
+ *   - free_lists[64], the head address of each power-of-two size class
+ *     (TLSF: 64 x 16 lists, see T1 below);
  *   - a 64-bit availability bitmap, bit k set iff list k is non-empty (§5.1).
  *
  * Readings of the pseudocode (each one is exercised by a named test):
@@ -46,6 +47,24 @@
  *       index order.
  *   R11 the canonical state exported for comparison lists the blocks in
  *       address order, then each bin's list head to tail, then the bitmap.
+ *
+ * Two-level segregated fit (§5.2) is the same two algorithms with the
+ * two-tier lookup the section describes: a first-level bitmap over the
+ * power-of-two classes, each of whose bits summarises a second-level bitmap
+ * that splits the class linearly into ORC_SL lists.  Readings:
+ *   T1  ORC_SL = 16 lists per power of two (the paper gives no count).  The
+ *       list of a block of `size` bytes is (fl, sl) with fl = floor(log2
+ *       size) and sl the next four bits below the leading one: it holds the
+ *       sizes [2^fl + sl 2^(fl-4), 2^fl + (sl+1) 2^(fl-4)).
+ *   T2  the strict rule of R2 carries over: an allocation of s' bytes takes
+ *       the lowest non-empty list whose lower bound is >= s', so that any of
+ *       its blocks fits (found by rounding s' up to the next list bound, as
+ *       TLSF's mapping search does, then looking at the second-level bitmap
+ *       of that class and, failing that, at the first-level bitmap above it).
+ *   T3  everything else (LIFO lists, splitting at s', coalescing, R3-R10) is
+ *       unchanged; pushes go to the list that holds the block's size.
+ *   T4  the canonical state lists the 64 x 16 lists in (fl, sl) order, then
+ *       the first-level bitmap, then the 64 second-level bitmaps.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -53,6 +72,10 @@
 
 #define ORC_NIL UINT64_MAX   /* the "null block" that ends a list (§5.1) */
 #define ORC_FAIL UINT64_MAX  /* returned by a failed allocation (R9) */
+#define ORC_SEGFIT 0
+#define ORC_TLSF 1
+#define ORC_SL 16            /* second-level lists per power of two (T1) */
+#define ORC_NLISTS (64 * ORC_SL)
 
 typedef struct orc_entry {
     uint64_t addr;            /* key: block address (offset in the arena) */
@@ -70,8 +93,11 @@ typedef struct orc {
     orc_entry** buckets;
     uint64_t nbuckets;        /* power of two */
     uint64_t count;           /* entries in the table = blocks */
-    uint64_t free_lists[64];
-    uint64_t bitmask;
+    int policy;               /* ORC_SEGFIT or ORC_TLSF */
+    uint64_t free_lists[ORC_NLISTS];  /* segregated fit uses the first 64 */
+    uint64_t bitmask;         /* segregated fit: bit k <=> list k non-empty;
+                                 TLSF: first level, bit fl <=> slmask[fl] != 0 */
+    uint16_t slmask[64];      /* TLSF second level: bit sl <=> list (fl, sl) non-empty */
     /* counters reported by orc_stats */
     uint64_t alloc_ok, alloc_fail, free_ok, free_fail;
     uint64_t used_bytes, used_blocks, requested_bytes;
@@ -136,42 +162,90 @@ static void ht_erase(orc* o, uint64_t addr) {
 }
 
 /* ---- free lists (LIFO, R8) --------------------------------------------- */
-/* Push at the head of bin floor(log2 size) and set the bin's bit
- * (Algorithm 4 split branch; Algorithm 5 final push). */
+/* The list that holds a free block of `size` bytes: bin floor(log2 size)
+ * (Algorithm 4 split, Algorithm 5 push); TLSF: fl * ORC_SL + sl (T1). */
+static unsigned list_of(const orc* o, uint64_t size) {
+    const unsigned fl = floor_log2(size);
+    if (o->policy == ORC_SEGFIT) return fl;
+    const uint64_t top = fl >= 4 ? size >> (fl - 4) : size << (4 - fl);  /* 16 + sl */
+    return fl * ORC_SL + (unsigned)(top - ORC_SL);
+}
+
+static void mark(orc* o, unsigned list, int nonempty) {
+    if (o->policy == ORC_SEGFIT) {
+        if (nonempty) o->bitmask |= 1ull << list;
+        else o->bitmask &= ~(1ull << list);
+        return;
+    }
+    const unsigned fl = list / ORC_SL, sl = list % ORC_SL;
+    if (nonempty) o->slmask[fl] |= (uint16_t)(1u << sl);
+    else o->slmask[fl] &= (uint16_t)~(1u << sl);
+    if (o->slmask[fl]) o->bitmask |= 1ull << fl;
+    else o->bitmask &= ~(1ull << fl);
+}
+
+/* Push at the head of the block's list and set its bit (Algorithm 4 split
+ * branch; Algorithm 5 final push). */
 static void list_push(orc* o, orc_entry* e) {
-    unsigned bin = floor_log2(e->size);
+    unsigned bin = list_of(o, e->size);
     e->next_free = o->free_lists[bin];
     e->prev_free = ORC_NIL;
     orc_entry* nx = ht_find(o, e->next_free);        /* R5: skip if empty */
     if (nx) nx->prev_free = e->addr;
     o->free_lists[bin] = e->addr;
-    o->bitmask |= 1ull << bin;
+    mark(o, bin, 1);
 }
 
-/* Remove e from the list of its size class; clear the bit if the list
- * empties (Algorithm 5 remove(right) with the emptiness test of R7). */
+/* Remove e from the list of its size; clear the bit if the list empties
+ * (Algorithm 5 remove(right) with the emptiness test of R7). */
 static void list_unlink(orc* o, orc_entry* e) {
-    unsigned bin = floor_log2(e->size);
+    unsigned bin = list_of(o, e->size);
     orc_entry* pv = ht_find(o, e->prev_free);
     orc_entry* nx = ht_find(o, e->next_free);
     if (pv) pv->next_free = e->next_free;
     else o->free_lists[bin] = e->next_free;
     if (nx) nx->prev_free = e->prev_free;
-    if (o->free_lists[bin] == ORC_NIL) o->bitmask &= ~(1ull << bin);
+    if (o->free_lists[bin] == ORC_NIL) mark(o, bin, 0);
     e->next_free = e->prev_free = ORC_NIL;
 }
 
+/* The list an allocation of s bytes (rounded, R3) takes, or -1 when none
+ * qualifies.  Segregated fit: the lowest set bit of the bitmap at a position
+ * >= c = ceil(log2 s) (R1, R2).  TLSF (T2): round s up to the lower bound of
+ * the next list (unless it is one already), take that list's (fl, sl), then
+ * the lowest non-empty list at or above it: in the second-level bitmap of fl,
+ * else in the first-level bitmap above fl. */
+static int take_list(const orc* o, uint64_t s) {
+    if (o->policy == ORC_SEGFIT) {
+        unsigned c = ceil_log2(s);
+        uint64_t eligible = c >= 64 ? 0 : (o->bitmask >> c) << c;
+        return eligible ? __builtin_ctzll(eligible) : -1;
+    }
+    const unsigned f0 = floor_log2(s);
+    const uint64_t r = f0 >= 4 ? s + (1ull << (f0 - 4)) - 1 : s;
+    const unsigned t = list_of(o, r);
+    const unsigned fl = t / ORC_SL, sl = t % ORC_SL;
+    const unsigned above = o->slmask[fl] & (0xFFFFu << sl) & 0xFFFFu;
+    if (above) return (int)(fl * ORC_SL + __builtin_ctz(above));
+    const uint64_t fbits = fl + 1 >= 64 ? 0 : (o->bitmask >> (fl + 1)) << (fl + 1);
+    if (!fbits) return -1;
+    const unsigned f = (unsigned)__builtin_ctzll(fbits);
+    return (int)(f * ORC_SL + __builtin_ctz(o->slmask[f]));
+}
+
 /* ---- public API -------------------------------------------------------- */
-orc* orc_create(uint64_t arena_bytes, uint64_t min_block) {
+orc* orc_create_policy(uint64_t arena_bytes, uint64_t min_block, int policy) {
     if (min_block < 8 || (min_block & (min_block - 1))) return NULL;
+    if (policy != ORC_SEGFIT && policy != ORC_TLSF) return NULL;
     uint64_t a = arena_bytes - arena_bytes % min_block;
     if (a == 0) return NULL;
     orc* o = (orc*)calloc(1, sizeof(orc));
     o->arena = a;
     o->min_block = min_block;
+    o->policy = policy;
     o->nbuckets = 1024;
     o->buckets = (orc_entry**)calloc(o->nbuckets, sizeof(orc_entry*));
-    for (int k = 0; k < 64; k++) o->free_lists[k] = ORC_NIL;
+    for (int k = 0; k < ORC_NLISTS; k++) o->free_lists[k] = ORC_NIL;
     /* initial state: the whole heap is one free block (cf. §3.1, "the free
      * list always has at least one entry: the heap itself") */
     orc_entry* e = ht_insert(o, 0);
@@ -179,6 +253,10 @@ orc* orc_create(uint64_t arena_bytes, uint64_t min_block) {
     e->free = 1;
     list_push(o, e);
     return o;
+}
+
+orc* orc_create(uint64_t arena_bytes, uint64_t min_block) {
+    return orc_create_policy(arena_bytes, min_block, ORC_SEGFIT);
 }
 
 void orc_destroy(orc* o) {
@@ -198,10 +276,8 @@ uint64_t orc_malloc(orc* o, uint64_t size) {
     if (size == 0 || size > o->arena) { o->alloc_fail++; return ORC_FAIL; }
     uint64_t s = (size + o->min_block - 1) / o->min_block * o->min_block;   /* R3 */
     if (s > o->arena) { o->alloc_fail++; return ORC_FAIL; }
-    unsigned c = ceil_log2(s);                                              /* R1 */
-    uint64_t eligible = c >= 64 ? 0 : (o->bitmask >> c) << c;                /* R1, R2 */
-    if (!eligible) { o->alloc_fail++; return ORC_FAIL; }
-    unsigned order = (unsigned)__builtin_ctzll(eligible);
+    const int order = take_list(o, s);                                      /* R1, R2; T2 */
+    if (order < 0) { o->alloc_fail++; return ORC_FAIL; }
 
     /* take the head of the chosen list */
     orc_entry* it = ht_find(o, o->free_lists[order]);
@@ -280,11 +356,12 @@ void orc_batch(orc* o, const uint64_t* frees, uint32_t nf, uint8_t* free_status,
     for (uint32_t i = 0; i < na; i++) out[i] = orc_malloc(o, sizes[i]);
 }
 
-/* Canonical state (R11), as 64-bit words:
+/* Canonical state (R11, T4), as 64-bit words:
  *   arena, min_block, nblocks,
  *   nblocks pairs (offset, size | free << 63) in address order,
- *   for each bin k = 0..63: count_k, then the offsets head -> tail,
- *   bitmask.
+ *   for each list k = 0..63 (TLSF: 0..1023, k = fl * 16 + sl): count_k,
+ *   then the offsets head -> tail,
+ *   bitmask (TLSF: the first level), and for TLSF the 64 second-level masks.
  * Returns the number of words; writes at most cap of them. */
 size_t orc_export(const orc* o, uint64_t* buf, size_t cap) {
     size_t n = 0;
@@ -300,7 +377,8 @@ size_t orc_export(const orc* o, uint64_t* buf, size_t cap) {
         PUT(e->size | ((uint64_t)(e->free != 0) << 63));
         a += e->size;
     }
-    for (int k = 0; k < 64; k++) {
+    const int nlists = o->policy == ORC_SEGFIT ? 64 : ORC_NLISTS;
+    for (int k = 0; k < nlists; k++) {
         size_t at = n;
         PUT(0);
         uint64_t cnt = 0;
@@ -313,6 +391,8 @@ size_t orc_export(const orc* o, uint64_t* buf, size_t cap) {
         if (at < cap) buf[at] = cnt;
     }
     PUT(o->bitmask);
+    if (o->policy == ORC_TLSF)
+        for (int f = 0; f < 64; f++) PUT(o->slmask[f]);
 #undef PUT
     return n;
 }
@@ -321,11 +401,14 @@ size_t orc_export(const orc* o, uint64_t* buf, size_t cap) {
  * block, out[1] = the extent -- the end of the highest in-use block (0 when
  * none is in use), the prefix of the arena that has to be backed by device
  * memory.  The largest free block is in the highest non-empty list, since
- * list k holds exactly the free blocks whose floor(log2 size) is k. */
+ * lists hold disjoint size ranges in increasing order (list k of segregated
+ * fit: the sizes with floor(log2 size) = k; TLSF: T1). */
 void orc_space(const orc* o, uint64_t out[2]) {
     uint64_t largest = 0, extent = 0;
     if (o->bitmask) {
-        const unsigned k = floor_log2(o->bitmask);
+        /* TLSF: the highest second-level list of the highest class */
+        const unsigned f = floor_log2(o->bitmask);
+        const unsigned k = o->policy == ORC_SEGFIT ? f : f * ORC_SL + floor_log2(o->slmask[f]);
         uint64_t cnt = 0;
         for (uint64_t p = o->free_lists[k]; p != ORC_NIL && cnt <= o->count; cnt++) {
             const orc_entry* e = ht_find(o, p);

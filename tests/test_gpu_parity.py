@@ -105,6 +105,16 @@ def test_small_record_tables(gpu_lib, threads, granules, batch, p_free):
     _run(wl, threads=threads, state_every=4, canary=True)
 
 
+@pytest.mark.parametrize("batch", [1, 16])
+def test_usage_workload(gpu_lib, batch):
+    """The malloc-large stand-in (one op per batch, and batches of up to 16
+    ops in sequential order): every result, the state, and the space report
+    (extent, largest free block) against the oracle."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    _run(W.usage(n_ops=2000, batch=batch), state_every=50 if batch == 1 else 10, canary=False)
+
+
 @pytest.mark.parametrize("threads,ctas", [(128, 0), (1024, 0), (1024, 1), (256, 3)])
 def test_large_reduced(gpu_lib, threads, ctas):
     from paper_2405_07079_gb300 import workloads as W

@@ -351,6 +351,148 @@ def test_random_slots_batches_keep_sequential_order():
     assert len(runs[0][0]) == 1500
 
 
+# ---- two-level segregated fit (§5.2) ----------------------------------------
+TLSF_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "tlsf_worked_examples.json")
+
+
+def load_tlsf_golden():
+    with open(TLSF_GOLDEN) as f:
+        doc = json.load(f)
+    cases = []
+    for c in doc["cases"]:
+        fin = c["final"]
+        w = [c["arena"], c["min_block"], len(fin["blocks"])]
+        for off, size, free in fin["blocks"]:
+            w += [off, size | (int(free) << 63)]
+        for k in range(64 * 16):
+            lst = fin["lists"].get(str(k), [])
+            w += [len(lst)] + list(lst)
+        w.append(fin["flmask"])
+        w += [fin["slmask"].get(str(f), 0) for f in range(64)]
+        cases.append({"name": c["name"], "arena": c["arena"], "min_block": c["min_block"],
+                      "batches": c["batches"], "final": w})
+    return cases
+
+
+def _tlsf_oracle(A, mb):
+    return oracle.Oracle(A, mb, "tlsf")
+
+
+def _tlsf_interval(A, mb):
+    return IntervalAllocator(A, mb, "tlsf")
+
+
+@pytest.mark.parametrize("make", [_tlsf_oracle, _tlsf_interval])
+@pytest.mark.parametrize("case", load_tlsf_golden(), ids=lambda c: c["name"].split()[0])
+def test_tlsf_worked_example(make, case):
+    a = make(case["arena"], case["min_block"])
+    for frees, sizes, expect in case["batches"]:
+        out, st = a.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        assert [int(x) for x in out] == expect, case["name"]
+        assert not any(int(x) for x in st)
+    assert [int(x) for x in a.export_state()] == case["final"], case["name"]
+
+
+@pytest.mark.parametrize("mutant", ["no_rounding", "eight_lists", "power_of_two_search"])
+def test_tlsf_worked_examples_catch_mutants(monkeypatch, mutant):
+    """Plausible TLSF mistakes planted in the brute-force statement: taking
+    the list that holds s' itself (no rounding up to a list bound), eight
+    second-level lists instead of sixteen, and the first level alone (the
+    segregated-fit class rule).  Each one fails a worked example."""
+    from oracle import interval_ref as ir
+
+    if mutant == "no_rounding":
+        monkeypatch.setattr(ir, "_tlsf_fits", lambda lst, s: lst >= ir._tlsf_list(s))
+    elif mutant == "eight_lists":
+        monkeypatch.setattr(ir, "_tlsf_list",
+                            lambda z: (ir._floor_log2(z), 2 * ((8 * (z - (1 << ir._floor_log2(z)))) >> ir._floor_log2(z))))
+    else:
+        monkeypatch.setattr(ir, "_tlsf_fits", lambda lst, s: 1 << lst[0] >= s)
+    caught = False
+    for case in load_tlsf_golden():
+        a = ir.IntervalAllocator(case["arena"], case["min_block"], "tlsf")
+        ok = True
+        for frees, sizes, expect in case["batches"]:
+            out, _ = a.batch(frees, sizes)
+            ok &= [int(x) for x in out] == expect
+        ok &= a.export_state() == case["final"]
+        caught |= not ok
+    assert caught, mutant
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_tlsf_oracle_equals_interval_allocator_random(seed):
+    rng = np.random.default_rng(1000 + seed)
+    mb = int(rng.choice([8, 16, 256]))
+    A = mb * int(rng.integers(1, 400))
+    o, r = oracle.Oracle(A, mb, "tlsf"), IntervalAllocator(A, mb, "tlsf")
+    held = []
+    for _ in range(80):
+        nf = int(rng.integers(0, 4)) if held else 0
+        frees = [held.pop(int(rng.integers(0, len(held)))) for _ in range(min(nf, len(held)))]
+        if rng.random() < 0.3:
+            frees.append(int(rng.integers(0, A // mb + 2)) * mb)  # often invalid
+        sizes = [int(rng.integers(0, A // 2 + mb)) for _ in range(int(rng.integers(0, 5)))]
+        oo, os_ = o.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        ro, rs = r.batch(frees, sizes)
+        assert [int(x) for x in oo] == ro and [int(x) for x in os_] == rs
+        held += [x for x in ro if x != FAIL and x not in held]
+        held = [h for h in held if h not in frees or h in ro]
+    assert [int(x) for x in o.export_state()] == r.export_state()
+
+
+def test_tlsf_oracle_equals_interval_allocator_exhaustive():
+    """Every sequence of up to four ops from a small alphabet on arenas of
+    5, 12 and 31 granules: TLSF in both statements agrees op for op."""
+    n = 0
+    for G in (5, 12, 31):
+        mb = 16
+        alphabet = [("a", 16), ("a", 40), ("a", 100), ("a", 200), ("f", 0), ("f", 16), ("f", 48)]
+        for seq in itertools.product(alphabet, repeat=4):
+            o, r = oracle.Oracle(G * mb, mb, "tlsf"), IntervalAllocator(G * mb, mb, "tlsf")
+            for kind, v in seq:
+                if kind == "a":
+                    assert o.malloc(v) == r.malloc(v)
+                else:
+                    assert o.free(v) == r.free(v)
+            assert [int(x) for x in o.export_state()] == r.export_state()
+            n += 1
+    assert n == 3 * len(alphabet) ** 4
+
+
+def test_tlsf_invariants_and_space_on_workload_traces():
+    """Every intermediate TLSF state tiles the arena, never leaves two free
+    blocks adjacent, keeps every free block in the list its size maps to,
+    and its space report matches a walk of the blocks."""
+    from paper_2405_07079_gb300 import workloads as W
+    from oracle.interval_ref import _tlsf_list
+
+    for wl in (W.tiny(n_ops=2000),
+               W.Workload("l", 1 << 28, 512, lambda: W.Lifetimes(n_ops=30_000, batch=2048, mean_life=200)),
+               W.usage(n_ops=1500, batch=8)):
+        o = oracle.Oracle(wl.arena, wl.min_block, "tlsf")
+        cl = wl.make()
+        while (b := cl.next_batch()) is not None:
+            out, st = o.batch(*b)
+            cl.feed(out)
+            s = oracle.decode_state(o.export_state(), "tlsf")
+            blocks = s["blocks"]
+            assert sum(sz for _, sz, _ in blocks) == s["arena"]
+            assert all(not (a[2] and b2[2]) for a, b2 in zip(blocks, blocks[1:]))
+            listed = {off: k for k, lst in enumerate(s["bins"]) for off in lst}
+            free = {off: sz for off, sz, fr in blocks if fr}
+            assert set(listed) == set(free)
+            for off, k in listed.items():
+                f, sl = _tlsf_list(free[off])
+                assert k == 16 * f + sl
+            for f in range(64):
+                m = sum(1 << k for k in range(16) if s["bins"][16 * f + k])
+                assert s["slmask"][f] == m and bool(s["bitmask"] >> f & 1) == bool(m)
+            sp = o.space()
+            assert sp["largest_free"] == max(free.values(), default=0)
+            assert sp["extent"] == max([off + sz for off, sz, fr in blocks if not fr], default=0)
+
+
 def test_property_hypothesis():
     hyp = pytest.importorskip("hypothesis")
     st = pytest.importorskip("hypothesis.strategies")
