@@ -208,14 +208,14 @@ def reduce_over_ranks(maxes, sums, world: int, device=None):
 
 def _oracle_arenas(work):
     """Pool worker: the oracle over whole per-arena request sequences.
-    work = list of (arena_bytes, min_block, [(frees, sizes), ...]); returns
+    work = list of (arena_bytes, min_block, policy, [(frees, sizes), ...]); returns
     (ops, oracle seconds, results per arena)."""
     sys.path.insert(0, ROOT)
     import oracle
 
     ops, secs, res = 0, 0.0, []
-    for arena, mb, seq in work:
-        o = oracle.Oracle(arena, mb)
+    for arena, mb, policy, seq in work:
+        o = oracle.Oracle(arena, mb, policy)
         outs = []
         for f, s in seq:
             t0 = time.perf_counter()
@@ -227,7 +227,7 @@ def _oracle_arenas(work):
     return ops, secs, res
 
 
-def oracle_pool_baseline(arenas, mb, seqs, cores=None) -> tuple:
+def oracle_pool_baseline(arenas, mb, seqs, cores=None, policy="segfit") -> tuple:
     """The oracle on independent arenas, sharded over the host's cores
     (spawned processes).  Returns (ops/s over the pool's wall time, cores,
     per-arena results)."""
@@ -238,7 +238,7 @@ def oracle_pool_baseline(arenas, mb, seqs, cores=None) -> tuple:
     cores = cores or max(1, min(len(os.sched_getaffinity(0)), len(arenas)))
     shards = [[] for _ in range(cores)]
     for i, (a, seq) in enumerate(zip(arenas, seqs)):
-        shards[i % cores].append((int(a), mb, seq))
+        shards[i % cores].append((int(a), mb, policy, seq))
     with mp.get_context("spawn").Pool(cores) as pool:
         pool.map(_oracle_arenas, [[] for _ in range(cores)])  # workers up before the clock starts
         t0 = time.perf_counter()
@@ -374,7 +374,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag,
           "usage": workloads.usage}[args.workload]()
-    alloc = Allocator(wl.arena, wl.min_block, threads=args.threads, ctas=args.ctas)
+    alloc = Allocator(wl.arena, wl.min_block, threads=args.threads, ctas=args.ctas, policy=args.policy)
     space = []
     batches = record_trace(wl, alloc, dev, space)
     nb = len(batches)
@@ -438,19 +438,23 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": ops_all / busy_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * busy_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl.name + ": " + wl.note, "parallelism": f"replicas x{world}",
-                   "form": ("plain single arena: one thread-block cluster per batch (engine CTA + CTAs that "
+        "config": {"workload": wl.name + ": " + wl.note, "policy": args.policy, "parallelism": f"replicas x{world}",
+                   "form": ("two-level segregated fit: one warp applies the batch (k_tlsf<1>)"
+                            if args.policy == "tlsf" else
+                            "plain single arena: one thread-block cluster per batch (engine CTA + CTAs that "
                             "gather the frees' records into its shared memory and pre-fill failures)"
                             if args.ctas >= 2 else "plain single arena: prep grid + engine kernel per batch"),
-                   "threads_per_cta": alloc_threads(args),
+                   "threads_per_cta": 32 if args.policy == "tlsf" else alloc_threads(args),
                    "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
                    "ops_per_step_mean": ops / max(1, args.steps)},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak,
                      "traffic": (K_SINGLE_LARGE_DRAM_BYTES
-                                 if args.workload == "large" and alloc_threads(args) == 1024 and args.ctas < 2 else None),
+                                 if args.workload == "large" and alloc_threads(args) == 1024 and args.ctas < 2
+                                 and args.policy == "segfit" else None),
                      "peak_source": f"{peak_src} hbm_gbs",
-                     "kernel": (f"k_single_cl<{alloc_threads(args)}>" if args.ctas >= 2
+                     "kernel": ("k_tlsf<1>" if args.policy == "tlsf" else
+                                f"k_single_cl<{alloc_threads(args)}>" if args.ctas >= 2
                                 else f"k_prep + k_single<{alloc_threads(args)}>"),
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
@@ -469,7 +473,7 @@ def run_gpu(args, rank, world, local_rank):
     if cuda_cmp is not None:
         line["cuda_allocators"] = cuda_cmp
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
+        line["cpu_baseline"] = cpu_baseline(wl, args.policy)
     return line
 
 
@@ -486,7 +490,7 @@ def run_multi(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     A = workloads.multi_arena_sizes(args.arenas)
     gen = workloads.MultiLifetimes(A, n_batches=args.batches)
-    ma = MultiAllocator(A, 256, max_total_frees=args.arenas * 2048 + 1)
+    ma = MultiAllocator(A, 256, max_total_frees=args.arenas * 2048 + 1, policy=args.policy)
     t_rec = time.time()
     batches = []
     while (b := gen.next_batch()) is not None:
@@ -507,7 +511,9 @@ def run_multi(args, rank, world, local_rank):
         d["ref_st"] = stat.copy()
         batches.append(d)
     t_rec = time.time() - t_rec
-    if args.shape:
+    if args.policy == "tlsf":
+        best, table = "one warp per arena (two-level segregated fit)", {}
+    elif args.shape:
         best = tuple(int(x) for x in args.shape.split(","))
         ma.set_shape(*best)
         table = {}
@@ -534,6 +540,8 @@ def run_multi(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    from paper_2405_07079_gb300 import hba_launch_count
+    launches0 = hba_launch_count(ma.h)
     with ClockSampler(local_rank) as clocks:
         for k in range(steps):
             if pos == nb:
@@ -544,6 +552,7 @@ def run_multi(args, rank, world, local_rank):
             ev[k][1].record(stream)
             idx.append(pos); pos += 1
         torch.cuda.synchronize()
+    launches = hba_launch_count(ma.h) - launches0
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -555,7 +564,7 @@ def run_multi(args, rank, world, local_rank):
     # the plain form on the same requests: the first P arenas, one handle and
     # one launch per arena per batch; results must equal the batched form's
     P = min(args.plain_arenas, args.arenas)
-    plain = [Allocator(int(A[i]), 256, max_batch=2048) for i in range(P)]
+    plain = [Allocator(int(A[i]), 256, max_batch=2048, policy=args.policy) for i in range(P)]
     plain_ops, plain_ms, nb_plain = 0, 0.0, min(nb, 20)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for bi in range(nb_plain):
@@ -585,7 +594,7 @@ def run_multi(args, rank, world, local_rank):
         K = min(args.oracle_arenas, args.arenas)
         seqs = [[(b["hf"][int(b["hfrow"][i]):int(b["hfrow"][i + 1])], b["hs"][int(b["harow"][i]):int(b["harow"][i + 1])])
                  for b in batches] for i in range(K)]
-        v, cores, res = oracle_pool_baseline(A[:K], 256, seqs)
+        v, cores, res = oracle_pool_baseline(A[:K], 256, seqs, policy=args.policy)
         for i in range(K):
             for bi, b in enumerate(batches):
                 a0, a1 = int(b["harow"][i]), int(b["harow"][i + 1])
@@ -611,21 +620,26 @@ def run_multi(args, rank, world, local_rank):
         "metric": METRIC, "value": ops_all / busy_all, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * busy_all / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
+        "config": {"policy": args.policy,
+                   "workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
                                f"min block 256 B, U{{0..2048}} requests per arena per batch, {nb} batches",
-                   "form": "batched: prep grid + one multi-arena launch per batch", "parallelism": f"replicas x{world}",
-                   "shape": {"threads": best[0], "ctas": best[1], "smem_bytes": best[2]},
+                   "form": ("batched: one launch per batch, one warp per arena (k_tlsf<4>)" if args.policy == "tlsf"
+                            else "batched: prep grid + one multi-arena launch per batch"),
+                   "parallelism": f"replicas x{world}",
+                   "shape": (best if isinstance(best, str) else
+                             {"threads": best[0], "ctas": best[1], "smem_bytes": best[2]}),
                    "l2": "flushed between steps (256 MiB write, untimed)", "ops_per_step_mean": ops / steps,
                    "record_s": round(t_rec, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_multi",
+                     "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                     "kernel": "k_tlsf<4>" if args.policy == "tlsf" else "k_multi",
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "unit": "per batch of all arenas"},
         "plain_form_same_requests": {"arenas": P, "batches": nb_plain, "value": plain_ops / (plain_ms / 1e3),
                                      "unit": UNIT, "results_equal": True},
         "autotune_ms": {f"t{t}_c{c}_s{m}": round(v, 3) for (t, c, m), v in sorted(table.items())},
-        "gpu_launches": 2 * steps,
+        "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
     line.update(extra)
@@ -757,14 +771,14 @@ def alloc_threads(args):
     return 128 if args.workload in ("tiny", "usage") else 1024
 
 
-def oracle_steps(wl, n_steps=None, warmup=0):
+def oracle_steps(wl, n_steps=None, warmup=0, policy="segfit"):
     """Closed-loop client + oracle.  The first ``warmup`` batches run untimed;
     returns (oracle seconds, ops, timed steps) over the next ``n_steps``
     batches (None: to the end of the trace).  The trace restarts from a fresh
     oracle when it ends."""
     import oracle
 
-    o = oracle.Oracle(wl.arena, wl.min_block)
+    o = oracle.Oracle(wl.arena, wl.min_block, policy)
     client = wl.make()
     t_or, ops, k, seen = 0.0, 0, 0, 0
     while n_steps is None or k < n_steps:
@@ -772,7 +786,7 @@ def oracle_steps(wl, n_steps=None, warmup=0):
         if b is None:
             if n_steps is None:
                 break
-            o = oracle.Oracle(wl.arena, wl.min_block)
+            o = oracle.Oracle(wl.arena, wl.min_block, policy)
             client = wl.make()
             continue
         t0 = time.perf_counter()
@@ -787,8 +801,8 @@ def oracle_steps(wl, n_steps=None, warmup=0):
     return t_or, ops, k
 
 
-def cpu_baseline(wl) -> dict:
-    t, ops, k = oracle_steps(wl)
+def cpu_baseline(wl, policy="segfit") -> dict:
+    t, ops, k = oracle_steps(wl, policy=policy)
     return {"value": ops / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"the whole trace ({k} batches, {ops} ops), closed loop, single thread; "
                       f"oracle calls timed ({t:.3f} s)"}
@@ -801,13 +815,14 @@ def run_reference(args, rank, world):
 
     wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag,
           "usage": workloads.usage}[args.workload]()
-    t, ops, k = oracle_steps(wl, n_steps=args.steps, warmup=args.warmup)
+    t, ops, k = oracle_steps(wl, n_steps=args.steps, warmup=args.warmup, policy=args.policy)
     v = ops / t
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": wl.name + ": " + wl.note, "parallelism": "single host thread",
+            "config": {"workload": wl.name + ": " + wl.note, "policy": args.policy,
+                       "parallelism": "single host thread",
                        "form": "sequential CPU oracle, one batch per step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"batches {args.warmup}..{args.warmup + args.steps - 1} of the trace "
@@ -822,6 +837,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=["large", "tiny", "frag", "usage", "multi", "serve"], default="large")
+    ap.add_argument("--policy", choices=["segfit", "tlsf"], default="segfit",
+                    help="segregated fit (§5.1) or two-level segregated fit (§5.2); the serving loop is segfit only")
     ap.add_argument("--lams", default="1,2,5,10,20,50")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--arenas", type=int, default=4096)
@@ -848,6 +865,8 @@ def main():
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
         if args.workload == "serve":
+            if args.policy != "segfit":
+                ap.error("the serving loop runs segregated fit only")
             line = run_serve(args, rank, world, local_rank)
         elif args.workload == "multi":
             if args.steps == 1530:

@@ -24,6 +24,17 @@
  *   - deallocation coalesces the block with a free left and/or right address
  *     neighbour and pushes the result at the head of its list.
  *
+ * HBA_POLICY_TLSF is two-level segregated fit (§5.2): the same two
+ * algorithms, with each power-of-two class split linearly into 16 lists (the
+ * paper does not fix the count) and a second-level bitmap per class under
+ * the first-level one.  A free block of z bytes is in list (floor(log2 z),
+ * the four bits below the leading one); an allocation takes the head of the
+ * lowest non-empty list whose lower bound is >= s' (every block there
+ * fits).  TLSF handles run one warp per arena, applying the requests one by
+ * one; hba_serve_run rejects them, hba_set_shape has no effect on them.  The
+ * canonical state lists the 64 x 16 byte lists, then the first-level bitmap,
+ * then the 64 second-level bitmaps.
+ *
  * Batch semantics.  One batch = a free call followed by an alloc call on the
  * same stream (or one hba_step call): all frees in index order, then all
  * allocations in index order, exactly as if applied one by one.  Results are
@@ -72,7 +83,8 @@ typedef enum {
 } hba_status_t;
 
 typedef enum {
-    HBA_POLICY_SEGFIT = 0 /* §5.1 segregated fit; other values are rejected */
+    HBA_POLICY_SEGFIT = 0, /* §5.1 segregated fit */
+    HBA_POLICY_TLSF = 1    /* §5.2 two-level segregated fit; other values are rejected */
 } hba_policy_t;
 
 #define HBA_FAIL ((uint64_t)~0ull)

@@ -16,6 +16,7 @@
 #include "hba.h"
 #include "hba_engine.cuh"
 #include "hba_serve.cuh"
+#include "hba_tlsf.cuh"
 
 using hba::Arena;
 using hba::Rec;
@@ -69,6 +70,11 @@ struct hba_s {
     bool have_last = false;
     uint64_t* d_largest = nullptr;
     uint32_t* d_extent = nullptr;  // per arena: end granule of the highest in-use block
+    // two-level segregated fit (§5.2): per-arena lists and bitmaps, and their
+    // initial state (for reset)
+    int policy = HBA_POLICY_SEGFIT;
+    hba::TlsfLists* d_tlsf = nullptr;
+    std::vector<hba::TlsfLists> h_tlsf;
 };
 
 namespace {
@@ -405,6 +411,49 @@ __global__ void k_extent(const Arena* ars, const Rec* pool, uint32_t n_arenas, u
     }
 }
 
+// Two-level segregated fit: one warp per arena, WPC arenas per CTA, the
+// grid striding over the arenas.  frow / arow: each arena's row offsets into
+// frees / sizes (n_arenas + 1 entries), or null for a single arena, whose
+// requests are frees[0, nf) and sizes[0, na).
+template <int WPC>
+__global__ void __launch_bounds__(WPC * 32) k_tlsf(Arena* ars, hba::TlsfLists* lists, Rec* pool, uint32_t n_arenas,
+                                                  const uint32_t* frow, const uint64_t* frees, uint8_t* fstat,
+                                                  uint32_t nf, const uint32_t* arow, const uint64_t* sizes,
+                                                  uint64_t* out, uint32_t na) {
+    __shared__ hba::TlsfLists Lw[WPC];
+    const uint32_t w = threadIdx.x >> 5;
+    for (uint32_t a = blockIdx.x * WPC + w; a < n_arenas; a += gridDim.x * WPC) {
+        const uint32_t f0 = frow ? frow[a] : 0u, f1 = frow ? frow[a + 1] : nf;
+        const uint32_t a0 = arow ? arow[a] : 0u, a1 = arow ? arow[a + 1] : na;
+        Arena& ar = ars[a];
+        hba::tl_arena_warp(ar, lists[a], pool + ar.rec_base, Lw[w], frees, fstat, f0, f1, sizes, out, a0, a1);
+        __syncwarp();
+    }
+}
+
+// Largest free block of every TLSF arena: the highest non-empty list is
+// walked (bounded by the arena's block count).
+__global__ void k_largest_tlsf(const Arena* ars, const hba::TlsfLists* lists, const Rec* pool, uint32_t n_arenas,
+                               uint64_t* out) {
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_arenas) return;
+    const Arena& ar = ars[a];
+    const hba::TlsfLists& L = lists[a];
+    uint64_t best = 0;
+    if (L.flmask) {
+        const uint32_t f = hba::flog2(L.flmask);
+        const uint32_t k = f * hba::TL_SL + hba::flog2(L.slmask[f]);
+        const Rec* rec = pool + ar.rec_base;
+        uint64_t guard = 0;
+        for (uint32_t h = L.heads[k]; h != hba::NIL && guard <= (uint64_t)ar.blocks; ++guard) {
+            const uint32_t sz = hba::sz_of(rec[h].x);
+            if (sz > best) best = sz;
+            h = rec[h].z;
+        }
+    }
+    out[a] = best << ar.lg;
+}
+
 bool launch_prep(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint32_t* gi, uint64_t* out,
                  uint32_t na, cudaStream_t s, bool* pdl);
 
@@ -550,10 +599,30 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     return HBA_OK;
 }
 
+// A TLSF batch: one warp for a single arena, else four arenas per CTA.
+hba_status_t launch_tlsf(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint8_t* st,
+                         const uint32_t* arow, const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
+    const uint32_t n = h->n_arenas;
+    if (n == 1) {
+        k_tlsf<1><<<1, 32, 0, s>>>(h->d_arenas, h->d_tlsf, h->d_rec, 1u, frow, frees, st, nf, arow, sizes, out, na);
+    } else {
+        const uint32_t sms = g_limits[5].sms ? g_limits[5].sms : 152u;
+        const uint32_t grid = std::min((n + 3u) / 4u, 16u * sms);
+        k_tlsf<4><<<grid, 128, 0, s>>>(h->d_arenas, h->d_tlsf, h->d_rec, n, frow, frees, st, nf, arow, sizes, out,
+                                        na);
+    }
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+}
+
 hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
                        uint32_t na, uint64_t* out, cudaStream_t s) {
     if (!h || h->n_arenas != 1) return HBA_ERR_INVALID_ARGUMENT;
     if ((nf && !frees) || (na && (!sizes || !out))) return HBA_ERR_INVALID_ARGUMENT;
+    if (h->policy == HBA_POLICY_TLSF) {
+        if (nf == 0 && na == 0) return HBA_OK;
+        return launch_tlsf(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
+    }
     // frees beyond the scratch capacity go in consecutive slices (exact:
     // frees apply one by one in index order).  Slicing at what one free
     // phase keeps in shared memory was measured slower on the fragmentation
@@ -641,6 +710,9 @@ struct StreamOrder {
 
 hba_status_t reset_impl(hba_t h, cudaStream_t s) {
     HBA_CUDA_TRY(cudaMemsetAsync(h->d_rec, 0, sizeof(Rec) * h->total_granules, s));
+    if (h->d_tlsf)
+        HBA_CUDA_TRY(cudaMemcpyAsync(h->d_tlsf, h->h_tlsf.data(), sizeof(hba::TlsfLists) * h->n_arenas,
+                                     cudaMemcpyHostToDevice, s));
     HBA_CUDA_TRY(cudaMemcpyAsync(h->d_arenas, h->h_init.data(), sizeof(Arena) * h->n_arenas,
                                  cudaMemcpyHostToDevice, s));
     k_init_records<<<(h->n_arenas + 255) / 256, 256, 0, s>>>(h->d_arenas, h->d_rec, h->n_arenas);
@@ -656,6 +728,7 @@ void free_all(hba_t h) {
     cudaFree(h->d_gi);
     cudaFree(h->d_largest);
     cudaFree(h->d_extent);
+    cudaFree(h->d_tlsf);
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_s);
     cudaFree(h->d_stage_o);
@@ -711,6 +784,7 @@ hba_status_t serve_impl(hba_t h, const hba_arrival_t* arr, uint64_t n, hba_serve
                         uint64_t log_cap, const hba_serve_config_t* cfg, hba_serve_report_t* rep, cudaStream_t s) {
     if (!h || h->n_arenas != 1 || !rep || (n && (!arr || !served)) || n >= 0xFFFFFFFFull || (log_cap && !log))
         return HBA_ERR_INVALID_ARGUMENT;
+    if (h->policy != HBA_POLICY_SEGFIT) return HBA_ERR_INVALID_ARGUMENT;  // the loop runs segregated fit
     hba_serve_config_t c = cfg ? *cfg : hba_serve_config_t{};
     if (!c.queue_depth) c.queue_depth = 1u << 20;
     if (!c.max_batch) c.max_batch = 4096;
@@ -822,6 +896,8 @@ hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8
     if ((nf && !frees) || (na && (!sizes || !out))) return HBA_ERR_INVALID_ARGUMENT;
     if (nf > HBA_STATIC_MAX_FREES) return HBA_ERR_INVALID_ARGUMENT;
     if (nf == 0 && na == 0) return HBA_OK;
+    if (h->policy == HBA_POLICY_TLSF)  // needs no scratch
+        return launch_tlsf(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     uint32_t* base = static_scratch_address();
     if (!base) return HBA_ERR_CUDA;
     uint32_t* gi = base;
@@ -855,9 +931,23 @@ hba_status_t hba_launch_count(hba_t h, uint64_t* count) {
     return HBA_OK;
 }
 
+namespace {
+// The per-arena lists of a TLSF handle and their initial state (one free
+// block per arena).
+hba_status_t alloc_tlsf(hba_t h, int policy, const std::vector<Arena>& init) {
+    h->policy = policy;
+    if (policy != HBA_POLICY_TLSF) return HBA_OK;
+    h->h_tlsf.resize(init.size());
+    for (size_t i = 0; i < init.size(); ++i) hba::tl_init_host(&h->h_tlsf[i], init[i].G);
+    if (cudaMalloc(&h->d_tlsf, sizeof(hba::TlsfLists) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    return HBA_OK;
+}
+bool known_policy(int policy) { return policy == HBA_POLICY_SEGFIT || policy == HBA_POLICY_TLSF; }
+}  // namespace
+
 hba_status_t hba_create_ex(uint64_t arena_bytes, uint64_t min_block, int policy, uint32_t max_batch,
                            hba_t* out) {
-    if (!out || policy != HBA_POLICY_SEGFIT || max_batch == 0) return HBA_ERR_INVALID_ARGUMENT;
+    if (!out || !known_policy(policy) || max_batch == 0) return HBA_ERR_INVALID_ARGUMENT;
     uint32_t lg;
     uint64_t a;
     if (!check_geometry(arena_bytes, min_block, &lg, &a)) return HBA_ERR_INVALID_ARGUMENT;
@@ -869,6 +959,7 @@ hba_status_t hba_create_ex(uint64_t arena_bytes, uint64_t min_block, int policy,
     std::vector<Arena> init(1);
     hba::arena_init_host(&init[0], a, lg, 0);
     hba_status_t r = alloc_meta(h, init, max_batch, max_batch);
+    if (r == HBA_OK) r = alloc_tlsf(h, policy, init);
     if (r == HBA_OK) r = reset_impl(h, 0);
     if (r == HBA_OK && cudaDeviceSynchronize() != cudaSuccess) r = HBA_ERR_CUDA;
     if (r != HBA_OK) {
@@ -886,7 +977,7 @@ hba_status_t hba_create(uint64_t arena_bytes, uint64_t min_block, int policy, hb
 
 hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, uint64_t min_block, int policy,
                               uint32_t max_total_frees, hba_t* out) {
-    if (!out || !arena_bytes || n_arenas == 0 || policy != HBA_POLICY_SEGFIT) return HBA_ERR_INVALID_ARGUMENT;
+    if (!out || !arena_bytes || n_arenas == 0 || !known_policy(policy)) return HBA_ERR_INVALID_ARGUMENT;
     std::vector<Arena> init(n_arenas);
     uint64_t base = 0;
     uint32_t lg = 0;
@@ -902,6 +993,7 @@ hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, ui
     h->total_granules = base;
     h->max_batch = max_total_frees;
     hba_status_t r = alloc_meta(h, init, max_total_frees, 0);
+    if (r == HBA_OK) r = alloc_tlsf(h, policy, init);
     if (r == HBA_OK) r = reset_impl(h, 0);
     if (r == HBA_OK && cudaDeviceSynchronize() != cudaSuccess) r = HBA_ERR_CUDA;
     if (r != HBA_OK) {
@@ -1015,7 +1107,11 @@ hba_status_t hba_reset(hba_t h, hba_stream_t stream) {
 hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
     if (!h || !out) return HBA_ERR_INVALID_ARGUMENT;
     HBA_CUDA_TRY(cudaDeviceSynchronize());
-    k_largest<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->d_largest);
+    if (h->d_tlsf)
+        k_largest_tlsf<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_tlsf, h->d_rec, h->n_arenas,
+                                                           h->d_largest);
+    else
+        k_largest<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->d_largest);
     ++h->launches;
     HBA_CUDA_TRY(cudaGetLastError());
     HBA_CUDA_TRY(cudaMemset(h->d_extent, 0, sizeof(uint32_t) * h->n_arenas));
@@ -1061,6 +1157,12 @@ hba_status_t hba_export_state(hba_t h, uint32_t arena, uint64_t* host_buf, size_
     HBA_CUDA_TRY(cudaMemcpy(&ar, h->d_arenas + arena, sizeof(Arena), cudaMemcpyDeviceToHost));
     std::vector<Rec> rec(ar.G);
     HBA_CUDA_TRY(cudaMemcpy(rec.data(), h->d_rec + ar.rec_base, sizeof(Rec) * ar.G, cudaMemcpyDeviceToHost));
+    if (h->d_tlsf) {
+        hba::TlsfLists L;
+        HBA_CUDA_TRY(cudaMemcpy(&L, h->d_tlsf + arena, sizeof(L), cudaMemcpyDeviceToHost));
+        *len = hba::tl_export(ar, L, rec.data(), host_buf, cap);
+        return HBA_OK;
+    }
     *len = hba::export_canonical(ar, rec.data(), host_buf, cap);
     return HBA_OK;
 }
@@ -1088,6 +1190,9 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     cudaStream_t s = (cudaStream_t)stream;
     StreamOrder order(h, s);
     const uint32_t n = h->n_arenas;
+    if (h->policy == HBA_POLICY_TLSF)
+        return launch_tlsf(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes, na_total,
+                           d_out, s);
     if (h->m_threads == 32) {
         // warp mode: WPC arenas per CTA, per-warp dynamic shared memory
         const SmemLimits& L = g_limits[5];

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "hba_engine.cuh"
+#include "hba_tlsf.cuh"
 
 using namespace hba;
 
@@ -87,6 +88,56 @@ int emu_step(void* h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uin
         default: return 1;
     }
     return 0;
+}
+
+// Two-level segregated fit: the per-op functions the GPU warp applies, run
+// one request at a time.
+struct TlEmu {
+    Arena ar;
+    TlsfLists L;
+    std::vector<Rec> rec;
+};
+
+void* emu_tlsf_create(uint64_t arena_bytes, uint64_t min_block) {
+    if (min_block < 8 || (min_block & (min_block - 1))) return nullptr;
+    const uint32_t lg = (uint32_t)__builtin_ctzll(min_block);
+    const uint64_t a = arena_bytes - arena_bytes % min_block;
+    if (a == 0 || (a >> lg) > MAX_GRANULES) return nullptr;
+    TlEmu* e = new TlEmu();
+    arena_init_host(&e->ar, a, lg, 0);
+    tl_init_host(&e->L, e->ar.G);
+    e->ar.mask = e->L.flmask;
+    e->rec.assign(e->ar.G, Rec{0, 0, 0, 0});
+    e->rec[0] = initial_record(e->ar);
+    return e;
+}
+
+void emu_tlsf_destroy(void* h) { delete (TlEmu*)h; }
+
+void emu_tlsf_step(void* h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes, uint32_t na,
+                   uint64_t* out) {
+    TlEmu* e = (TlEmu*)h;
+    TlCount c;
+    tl_batch_serial(e->L, e->rec.data(), e->ar.arena_bytes, e->ar.G, e->ar.lg, frees, nf, st, sizes, na, out, c);
+    tl_apply_counts(e->ar, e->L, c);
+}
+
+size_t emu_tlsf_export(void* h, uint64_t* buf, size_t cap) {
+    TlEmu* e = (TlEmu*)h;
+    return tl_export(e->ar, e->L, e->rec.data(), buf, cap);
+}
+
+void emu_tlsf_stats(void* h, uint64_t* out) {
+    const Arena& a = ((TlEmu*)h)->ar;
+    out[0] = a.alloc_ok;
+    out[1] = a.alloc_fail;
+    out[2] = a.free_ok;
+    out[3] = a.free_fail;
+    out[4] = (uint64_t)a.used_g << a.lg;
+    out[5] = a.used_blocks;
+    out[6] = a.blocks;
+    out[7] = a.requested;
+    out[8] = a.mask << a.lg;
 }
 
 size_t emu_export(void* h, uint64_t* buf, size_t cap) {

@@ -16,6 +16,8 @@ from ._lib import HbaError, ServeConfig, ServeReport, Stats, check, load
 
 HBA_FAIL = 0xFFFFFFFFFFFFFFFF
 HBA_POLICY_SEGFIT = 0
+HBA_POLICY_TLSF = 1
+POLICIES = {"segfit": HBA_POLICY_SEGFIT, "tlsf": HBA_POLICY_TLSF}
 
 
 def _lib():
@@ -181,11 +183,13 @@ class Allocator:
     """One arena.  Inputs/outputs are uint64 (int64-typed) CUDA tensors."""
 
     def __init__(self, arena_bytes: int, min_block: int, max_batch: int = 65536, threads: int | None = None,
-                 smem_bytes: int = 0, ctas: int = 0):
+                 smem_bytes: int = 0, ctas: int = 0, policy: str = "segfit"):
         """``ctas``: size of the batch's thread-block cluster (0 or 1: a
         separate gathering grid, then the engine; 2..8: the engine CTA plus
-        gathering CTAs; see hba_set_shape)."""
-        self.h = hba_create(arena_bytes, min_block, HBA_POLICY_SEGFIT, max_batch)
+        gathering CTAs; see hba_set_shape).  ``policy``: "segfit" (§5.1) or
+        "tlsf" (§5.2)."""
+        self.policy = policy
+        self.h = hba_create(arena_bytes, min_block, POLICIES[policy], max_batch)
         self.arena_bytes = arena_bytes - arena_bytes % min_block
         self.min_block = min_block
         self.max_batch = max_batch
@@ -239,8 +243,9 @@ class Allocator:
 class MultiAllocator:
     """Many independent arenas; one launch applies one batch to all of them."""
 
-    def __init__(self, arena_bytes, min_block: int, max_total_frees: int = 1 << 22):
-        self.h = hba_multi_create(arena_bytes, min_block, HBA_POLICY_SEGFIT, max_total_frees)
+    def __init__(self, arena_bytes, min_block: int, max_total_frees: int = 1 << 22, policy: str = "segfit"):
+        self.policy = policy
+        self.h = hba_multi_create(arena_bytes, min_block, POLICIES[policy], max_total_frees)
         self.n = len(arena_bytes)
 
     def close(self):

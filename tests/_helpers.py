@@ -6,14 +6,14 @@ import numpy as np
 FAIL = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
-def oracle_trace(wl, max_batches=None):
+def oracle_trace(wl, max_batches=None, policy="segfit"):
     """Run the workload's client closed-loop against the oracle.
 
     Returns (trace, oracle) where trace is a list of
     (frees, sizes, out, status) with the oracle's results."""
     import oracle
 
-    o = oracle.Oracle(wl.arena, wl.min_block)
+    o = oracle.Oracle(wl.arena, wl.min_block, policy)
     cl = wl.make()
     trace = []
     while max_batches is None or len(trace) < max_batches:

@@ -39,6 +39,13 @@ def emu():
     lib.emu_set_dyn.argtypes = [vp, u32]
     lib.emu_set_staged.argtypes = [vp, ctypes.c_int]
     lib.emu_set_self.argtypes = [vp, ctypes.c_int]
+    lib.emu_tlsf_create.restype = vp
+    lib.emu_tlsf_create.argtypes = [u64, u64]
+    lib.emu_tlsf_destroy.argtypes = [vp]
+    lib.emu_tlsf_step.argtypes = [vp, vp, u32, vp, vp, u32, vp]
+    lib.emu_tlsf_export.restype = ctypes.c_size_t
+    lib.emu_tlsf_export.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.emu_tlsf_stats.argtypes = [vp, vp]
     return lib
 
 
@@ -171,3 +178,65 @@ def test_many_small_arenas_random(emu):
             assert np.array_equal(o.export_state(), e.export_state()), trial
             held = [a for a in held if a not in set(fr)] + [int(x) for x in oo if x != 0xFFFFFFFFFFFFFFFF]
         e.close()
+
+
+def _check_tlsf(emu, wl, every=1):
+    """The TLSF per-op functions of the GPU kernel, applied one request at a
+    time on the host, against the TLSF oracle: every result, every status,
+    the canonical state (lists and both bitmap levels) and the counters."""
+    import oracle as _o
+
+    ref = _o.Oracle(wl.arena, wl.min_block, "tlsf")
+    h = emu.emu_tlsf_create(wl.arena, wl.min_block)
+    assert h
+    p = lambda a: a.ctypes.data if a.size else None
+
+    def export():
+        n = emu.emu_tlsf_export(h, None, 0)
+        b = np.empty(n, np.uint64)
+        emu.emu_tlsf_export(h, b.ctypes.data, n)
+        return b
+
+    try:
+        cl = wl.make()
+        b = 0
+        while (req := cl.next_batch()) is not None:
+            f = np.ascontiguousarray(req[0], np.uint64)
+            s = np.ascontiguousarray(req[1], np.uint64)
+            out = np.empty(s.size, np.uint64)
+            st = np.empty(f.size, np.uint8)
+            emu.emu_tlsf_step(h, p(f), f.size, p(st), p(s), s.size, p(out))
+            ro, rs = ref.batch(f, s)
+            cl.feed(ro)
+            assert np.array_equal(out, ro), f"batch {b} allocs"
+            assert np.array_equal(st, rs), f"batch {b} frees"
+            if b % every == 0:
+                assert np.array_equal(export(), ref.export_state()), f"batch {b} state"
+            b += 1
+        assert np.array_equal(export(), ref.export_state())
+        got = np.zeros(9, np.uint64)
+        emu.emu_tlsf_stats(h, got.ctypes.data)
+        assert [int(x) for x in got] == list(ref.stats().values())
+    finally:
+        emu.emu_tlsf_destroy(h)
+
+
+def test_tlsf_ops_on_workloads(emu):
+    from paper_2405_07079_gb300 import workloads as W
+
+    _check_tlsf(emu, W.tiny(n_ops=6000))
+    _check_tlsf(emu, W.usage(n_ops=3000, batch=8), every=10)
+    _check_tlsf(emu, W.Workload("life", 1 << 28, 512, lambda: W.Lifetimes(n_ops=60_000, batch=2048, mean_life=100)),
+                every=4)
+    _check_tlsf(emu, W.frag(n_fill=20_000, n_big=2000, batch=2048, arena=1 << 27), every=5)
+
+
+def test_tlsf_ops_on_small_random_arenas(emu):
+    """Tiny arenas of 8-byte to 256-byte granules (list classes below the
+    second-level split, exact lists), every op kind including invalid and
+    duplicate frees."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    for mb, G in ((8, 37), (16, 200), (256, 1000), (8, 3)):
+        _check_tlsf(emu, W.Workload("t", mb * G, mb, lambda: W.TinyRandom(n_ops=3000, batch=7, p_free=0.45,
+                                                                        lo=1, hi=mb * G // 3 + 1)))
