@@ -167,8 +167,14 @@ HBA_HD uint32_t tl_take(TlsfLists& L, Rec* rec, uint32_t G, uint32_t k, uint32_t
     const uint32_t Y = L.heads[k];
     const Rec ry = rec[Y];
     L.heads[k] = ry.z;
-    if (ry.z != NIL) rec[ry.z].w = NIL;
-    else tl_mark(L, k, false);
+    if (ry.z != NIL) {
+#ifdef __CUDA_ARCH__
+        prefetch_l2(rec + ry.z);  // the new head: the next pop of this list reads it
+#endif
+        rec[ry.z].w = NIL;
+    } else {
+        tl_mark(L, k, false);
+    }
     const uint32_t ysz = sz_of(ry.x);
     rec[Y] = Rec{mkx(r, ST_USED), ry.y, NIL, NIL};
     if (ysz > r) {  // split: the remainder goes to the head of its list
@@ -276,7 +282,11 @@ __device__ inline void tl_arena_warp(Arena& ar, TlsfLists& Lg, Rec* rec, TlsfLis
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t A = ar.arena_bytes;
     const uint32_t G = ar.G, lg = ar.lg;
-    for (uint32_t k = lane; k < TL_NL; k += 32) Lw.heads[k] = Lg.heads[k];
+    for (uint32_t k = lane; k < TL_NL; k += 32) {
+        const uint32_t h = Lg.heads[k];
+        Lw.heads[k] = h;
+        if (h != NIL && a1 > a0) prefetch_l2(rec + h);  // the heads the allocations may pop
+    }
     Lw.slmask[lane] = Lg.slmask[lane];  // TL_FL == 32
     if (lane == 0) Lw.flmask = Lg.flmask;
     __syncwarp();
