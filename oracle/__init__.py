@@ -30,6 +30,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "segfit_oracle.c")
+_HAL_SRC = os.path.join(_HERE, "hal_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libsegfit_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -41,11 +42,11 @@ def build(force: bool = False) -> str:
     """Compile ``segfit_oracle.c`` into ``_build/libsegfit_oracle.so`` (gcc)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     stale = (not os.path.exists(_LIB)
-             or os.path.getmtime(_LIB) < os.path.getmtime(_SRC))
+             or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HAL_SRC)))
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, _SRC, _HAL_SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -72,6 +73,17 @@ def _load():
             lib.orc_export.argtypes = [vp, vp, ctypes.c_size_t]
             lib.orc_stats.argtypes = [vp, vp]
             lib.orc_space.argtypes = [vp, vp]
+            lib.hal_create.restype = vp
+            lib.hal_create.argtypes = [u64, u64, ctypes.c_int]
+            lib.hal_destroy.argtypes = [vp]
+            lib.hal_malloc.restype = u64
+            lib.hal_malloc.argtypes = [vp, u64]
+            lib.hal_free.restype = ctypes.c_int
+            lib.hal_free.argtypes = [vp, u64]
+            lib.hal_batch.argtypes = [vp, vp, u32, vp, vp, u32, vp]
+            lib.hal_export.restype = ctypes.c_size_t
+            lib.hal_export.argtypes = [vp, vp, ctypes.c_size_t]
+            lib.hal_stats.argtypes = [vp, vp]
             _lib = lib
     return _lib
 
@@ -144,6 +156,75 @@ class Oracle:
         buf = np.zeros(2, dtype=np.uint64)
         self._lib.orc_space(self._h, buf.ctypes.data)
         return {"largest_free": int(buf[0]), "extent": int(buf[1])}
+
+
+FITS = {"first": 0, "next": 1, "best": 2}
+
+
+class HalOracle:
+    """One arena managed by a sequential fit on address-sorted free and used
+    lists (§3.1 Algorithms 1 and 2, §4 Algorithm 3 and its first-fit and
+    next-fit variants), with partial deallocation."""
+
+    STAT_KEYS = ("alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes", "used_blocks", "blocks",
+                 "requested_bytes", "largest_free", "extent")
+
+    def __init__(self, arena_bytes: int, min_block: int, fit: str = "first"):
+        self._lib = _load()
+        self.fit = fit
+        self._h = self._lib.hal_create(int(arena_bytes), int(min_block), FITS[fit])
+        if not self._h:
+            raise ValueError("invalid arena_bytes/min_block/fit")
+        self.min_block = int(min_block)
+
+    def close(self):
+        if self._h:
+            self._lib.hal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def malloc(self, size: int) -> int:
+        return int(self._lib.hal_malloc(self._h, int(size)))
+
+    def free(self, addr: int) -> int:
+        return int(self._lib.hal_free(self._h, int(addr)))
+
+    def batch(self, frees, sizes):
+        f = np.ascontiguousarray(frees, dtype=np.uint64)
+        s = np.ascontiguousarray(sizes, dtype=np.uint64)
+        out = np.empty(s.size, dtype=np.uint64)
+        st = np.empty(f.size, dtype=np.uint8)
+        self._lib.hal_batch(self._h, _ptr(f), f.size, _ptr(st), _ptr(s), s.size, _ptr(out))
+        return out, st
+
+    def export_state(self) -> np.ndarray:
+        n = self._lib.hal_export(self._h, None, 0)
+        buf = np.empty(n, dtype=np.uint64)
+        self._lib.hal_export(self._h, buf.ctypes.data, n)
+        return buf
+
+    def stats(self) -> dict:
+        buf = np.zeros(10, dtype=np.uint64)
+        self._lib.hal_stats(self._h, buf.ctypes.data)
+        return {k: int(v) for k, v in zip(self.STAT_KEYS, buf)}
+
+
+def decode_hal_state(words) -> dict:
+    """Split a sequential-fit canonical state (H10) into its parts."""
+    w = [int(x) for x in words]
+    arena, mb, nf = w[0], w[1], w[2]
+    free = [(w[3 + 2 * i], w[4 + 2 * i]) for i in range(nf)]
+    i = 3 + 2 * nf
+    nu = w[i]
+    used = [(w[i + 1 + 2 * k], w[i + 2 + 2 * k]) for k in range(nu)]
+    i += 1 + 2 * nu
+    assert i + 1 == len(w), "trailing words in canonical state"
+    return {"arena": arena, "min_block": mb, "free": free, "used": used, "rover": w[i]}
 
 
 def decode_state(words, policy: str = "segfit") -> dict:

@@ -493,6 +493,211 @@ def test_tlsf_invariants_and_space_on_workload_traces():
             assert sp["extent"] == max([off + sz for off, sz, fr in blocks if not fr], default=0)
 
 
+# ---- sequential fits on address-sorted lists (§3.1, §4) ---------------------
+HAL_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hal_worked_examples.json")
+
+
+def load_hal_golden():
+    with open(HAL_GOLDEN) as f:
+        doc = json.load(f)
+    cases = []
+    for c in doc["cases"]:
+        fin = c["final"]
+        w = [c["arena"], c["min_block"], len(fin["free"])]
+        for a, z in fin["free"]:
+            w += [a, z]
+        w.append(len(fin["used"]))
+        for a, z in fin["used"]:
+            w += [a, z]
+        w.append(fin["rover"])
+        cases.append({"name": c["name"], "fit": c["fit"], "arena": c["arena"], "min_block": c["min_block"],
+                      "batches": c["batches"], "final": w})
+    return cases
+
+
+def _hal_oracle(A, mb, fit):
+    return oracle.HalOracle(A, mb, fit)
+
+
+def _granule_fits(A, mb, fit):
+    from oracle.fits_ref import GranuleFits
+
+    return GranuleFits(A, mb, fit)
+
+
+def _run_hal_case(a, case):
+    ok = True
+    for frees, sizes, expect, expect_st in case["batches"]:
+        out, st = a.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        ok &= [int(x) for x in out] == expect and [int(x) for x in st] == expect_st
+    return ok and [int(x) for x in a.export_state()] == case["final"]
+
+
+@pytest.mark.parametrize("make", [_hal_oracle, _granule_fits])
+@pytest.mark.parametrize("case", load_hal_golden(), ids=lambda c: c["name"].split()[0])
+def test_hal_worked_example(make, case):
+    a = make(case["arena"], case["min_block"], case["fit"])
+    for frees, sizes, expect, expect_st in case["batches"]:
+        out, st = a.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        assert [int(x) for x in out] == expect, case["name"]
+        assert [int(x) for x in st] == expect_st, case["name"]
+    assert [int(x) for x in a.export_state()] == case["final"], case["name"]
+
+
+@pytest.mark.parametrize("mutant", ["best_ties_high", "next_no_wrap", "free_head", "next_from_start", "no_partial"])
+def test_hal_worked_examples_catch_mutants(monkeypatch, mutant):
+    """Plausible mistakes planted in the brute-force statement, each caught
+    by a worked example: best fit preferring the higher address on a tie,
+    next fit that does not wrap around, partial deallocation that frees the
+    head of the block instead of its tail, next fit that ignores the rover,
+    and a partial free that is rejected."""
+    from oracle import fits_ref as fr
+
+    cls = fr.GranuleFits
+    if mutant == "best_ties_high":
+        orig = cls.malloc
+
+        def malloc(self, size):
+            if self.fit != "best":
+                return orig(self, size)
+            s = -(-size // self.mb)
+            fits = [r for r in self._runs() if r[1] >= s]
+            if not size or not fits:
+                return fr.FAIL
+            start = min(fits, key=lambda r: (r[1], -r[0]))[0]
+            for g in range(start, start + s):
+                self.owner[g] = start
+            self.size[start] = s
+            self.rover = start + s
+            return start * self.mb
+        monkeypatch.setattr(cls, "malloc", malloc)
+    elif mutant in ("next_no_wrap", "next_from_start"):
+        orig_runs = cls._runs
+
+        def runs(self):
+            r = orig_runs(self)
+            if self.fit == "next" and mutant == "next_no_wrap":
+                return [x for x in r if x[0] + x[1] > self.rover] or r[:0]
+            return r
+        monkeypatch.setattr(cls, "_runs", runs)
+        if mutant == "next_from_start":
+            orig = cls.malloc
+
+            def malloc(self, size):
+                self.rover = 0
+                return orig(self, size)
+            monkeypatch.setattr(cls, "malloc", malloc)
+    elif mutant == "free_head":
+        def free(self, addr):
+            if addr % self.mb or addr >= self.G * self.mb:
+                return 1
+            g = addr // self.mb
+            b = self.owner[g]
+            if b is None:
+                return 1
+            end = b + self.size[b]
+            lo, hi = (b, g) if g != b else (b, end)
+            for q in range(lo, hi):
+                self.owner[q] = None
+            if g == b:
+                del self.size[b]
+            else:
+                for q in range(g, end):
+                    self.owner[q] = g
+                self.size[g] = end - g
+                del self.size[b]
+            return 0
+        monkeypatch.setattr(cls, "free", free)
+    else:
+        orig = cls.free
+
+        def free(self, addr):
+            g = addr // self.mb if addr < self.G * self.mb else None
+            if g is not None and self.owner[g] is not None and self.owner[g] != g:
+                return 1
+            return orig(self, addr)
+        monkeypatch.setattr(cls, "free", free)
+    caught = [not _run_hal_case(fr.GranuleFits(c["arena"], c["min_block"], c["fit"]), c) for c in load_hal_golden()]
+    assert any(caught), mutant
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+@pytest.mark.parametrize("seed", range(12))
+def test_hal_oracle_equals_granule_fits_random(fit, seed):
+    from oracle.fits_ref import GranuleFits
+
+    rng = np.random.default_rng(2000 + seed)
+    mb = int(rng.choice([8, 16, 256]))
+    A = mb * int(rng.integers(1, 120))
+    o, r = oracle.HalOracle(A, mb, fit), GranuleFits(A, mb, fit)
+    held = []
+    for _ in range(60):
+        frees = []
+        for _ in range(int(rng.integers(0, 4))):
+            if held and rng.random() < 0.7:
+                a = held[int(rng.integers(0, len(held)))]
+                # the start, or an interior granule (partial deallocation)
+                frees.append(a + mb * int(rng.integers(0, 3)) if rng.random() < 0.4 else a)
+            else:
+                frees.append(int(rng.integers(0, A // mb + 2)) * mb + int(rng.choice([0, 0, 0, 3])))
+        sizes = [int(rng.integers(0, A // 2 + mb)) for _ in range(int(rng.integers(0, 5)))]
+        oo, os_ = o.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        ro, rs = r.batch(frees, sizes)
+        assert [int(x) for x in oo] == ro and [int(x) for x in os_] == rs
+        held = [a for a in held if a not in frees] + [x for x in ro if x != FAIL]
+    assert [int(x) for x in o.export_state()] == r.export_state()
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+def test_hal_oracle_equals_granule_fits_exhaustive(fit):
+    """Every sequence of four ops from a small alphabet (allocations of 1-3
+    granules, frees of starts and interiors) on arenas of 4 and 9 granules."""
+    from oracle.fits_ref import GranuleFits
+
+    mb = 16
+    alphabet = [("a", 16), ("a", 20), ("a", 48), ("f", 0), ("f", 16), ("f", 32), ("f", 40)]
+    n = 0
+    for G in (4, 9):
+        for seq in itertools.product(alphabet, repeat=4):
+            o, r = oracle.HalOracle(G * mb, mb, fit), GranuleFits(G * mb, mb, fit)
+            for kind, v in seq:
+                if kind == "a":
+                    assert o.malloc(v) == r.malloc(v)
+                else:
+                    assert o.free(v) == r.free(v)
+            assert [int(x) for x in o.export_state()] == r.export_state()
+            n += 1
+    assert n == 2 * len(alphabet) ** 4
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+def test_hal_invariants_on_workload_traces(fit):
+    """After every batch: free and used blocks tile the arena without
+    overlap, no two free blocks touch, sizes are multiples of min_block, and
+    the counters match the lists."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    for wl in (W.tiny(n_ops=2000), W.usage(n_ops=1500, batch=8),
+               W.frag(n_fill=4000, n_big=400, batch=512, arena=32 << 20)):
+        o = oracle.HalOracle(wl.arena, wl.min_block, fit)
+        cl = wl.make()
+        while (b := cl.next_batch()) is not None:
+            out, st = o.batch(*b)
+            cl.feed(out)
+            s = oracle.decode_hal_state(o.export_state())
+            blocks = sorted([(a, z, True) for a, z in s["free"]] + [(a, z, False) for a, z in s["used"]])
+            pos = 0
+            for a, z, fr in blocks:
+                assert a == pos and z > 0 and a % wl.min_block == 0 and z % wl.min_block == 0
+                pos = a + z
+            assert pos == s["arena"]
+            assert all(f1[0] + f1[1] < f2[0] for f1, f2 in zip(s["free"], s["free"][1:]))
+            stt = o.stats()
+            assert stt["used_bytes"] == sum(z for _, z in s["used"])
+            assert stt["largest_free"] == max([z for _, z in s["free"]], default=0)
+            assert stt["extent"] == max([a + z for a, z in s["used"]], default=0)
+
+
 def test_property_hypothesis():
     hyp = pytest.importorskip("hypothesis")
     st = pytest.importorskip("hypothesis.strategies")
