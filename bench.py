@@ -206,6 +206,16 @@ def reduce_over_ranks(maxes, sums, world: int, device=None):
     return t.tolist(), c.tolist()
 
 
+FIT_POLICIES = ("first", "next", "best")
+
+
+def _make_oracle(oracle, arena, mb, policy):
+    """The oracle of a policy: segregated fit / TLSF, or a sequential fit."""
+    if policy in FIT_POLICIES:
+        return oracle.HalOracle(arena, mb, policy)
+    return oracle.Oracle(arena, mb, policy)
+
+
 def _oracle_arenas(work):
     """Pool worker: the oracle over whole per-arena request sequences.
     work = list of (arena_bytes, min_block, policy, [(frees, sizes), ...]); returns
@@ -215,7 +225,7 @@ def _oracle_arenas(work):
 
     ops, secs, res = 0, 0.0, []
     for arena, mb, policy, seq in work:
-        o = oracle.Oracle(arena, mb, policy)
+        o = _make_oracle(oracle, arena, mb, policy)
         outs = []
         for f, s in seq:
             t0 = time.perf_counter()
@@ -441,10 +451,13 @@ def run_gpu(args, rank, world, local_rank):
         "config": {"workload": wl.name + ": " + wl.note, "policy": args.policy, "parallelism": f"replicas x{world}",
                    "form": ("two-level segregated fit: one warp applies the batch (k_tlsf<1>)"
                             if args.policy == "tlsf" else
+                            f"{args.policy} fit on address-sorted lists: one CTA applies the batch (k_fits<256>)"
+                            if args.policy in FIT_POLICIES else
                             "plain single arena: one thread-block cluster per batch (engine CTA + CTAs that "
                             "gather the frees' records into its shared memory and pre-fill failures)"
                             if args.ctas >= 2 else "plain single arena: prep grid + engine kernel per batch"),
-                   "threads_per_cta": 32 if args.policy == "tlsf" else alloc_threads(args),
+                   "threads_per_cta": (32 if args.policy == "tlsf" else 256 if args.policy in FIT_POLICIES
+                                       else alloc_threads(args)),
                    "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
                    "ops_per_step_mean": ops / max(1, args.steps)},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
@@ -454,6 +467,7 @@ def run_gpu(args, rank, world, local_rank):
                                  and args.policy == "segfit" else None),
                      "peak_source": f"{peak_src} hbm_gbs",
                      "kernel": ("k_tlsf<1>" if args.policy == "tlsf" else
+                                "k_fits<256>" if args.policy in FIT_POLICIES else
                                 f"k_single_cl<{alloc_threads(args)}>" if args.ctas >= 2
                                 else f"k_prep + k_single<{alloc_threads(args)}>"),
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
@@ -513,6 +527,8 @@ def run_multi(args, rank, world, local_rank):
     t_rec = time.time() - t_rec
     if args.policy == "tlsf":
         best, table = "one warp per arena (two-level segregated fit)", {}
+    elif args.policy in FIT_POLICIES:
+        best, table = f"one CTA per arena ({args.policy} fit)", {}
     elif args.shape:
         best = tuple(int(x) for x in args.shape.split(","))
         ma.set_shape(*best)
@@ -624,6 +640,8 @@ def run_multi(args, rank, world, local_rank):
                    "workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
                                f"min block 256 B, U{{0..2048}} requests per arena per batch, {nb} batches",
                    "form": ("batched: one launch per batch, one warp per arena (k_tlsf<4>)" if args.policy == "tlsf"
+                            else "batched: one launch per batch, one CTA per arena (k_fits<256>)"
+                            if args.policy in FIT_POLICIES
                             else "batched: prep grid + one multi-arena launch per batch"),
                    "parallelism": f"replicas x{world}",
                    "shape": (best if isinstance(best, str) else
@@ -632,7 +650,8 @@ def run_multi(args, rank, world, local_rank):
                    "record_s": round(t_rec, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
-                     "kernel": "k_tlsf<4>" if args.policy == "tlsf" else "k_multi",
+                     "kernel": ("k_tlsf<4>" if args.policy == "tlsf" else "k_fits<256>"
+                                if args.policy in FIT_POLICIES else "k_multi"),
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "unit": "per batch of all arenas"},
@@ -778,7 +797,7 @@ def oracle_steps(wl, n_steps=None, warmup=0, policy="segfit"):
     oracle when it ends."""
     import oracle
 
-    o = oracle.Oracle(wl.arena, wl.min_block, policy)
+    o = _make_oracle(oracle, wl.arena, wl.min_block, policy)
     client = wl.make()
     t_or, ops, k, seen = 0.0, 0, 0, 0
     while n_steps is None or k < n_steps:
@@ -786,7 +805,7 @@ def oracle_steps(wl, n_steps=None, warmup=0, policy="segfit"):
         if b is None:
             if n_steps is None:
                 break
-            o = oracle.Oracle(wl.arena, wl.min_block, policy)
+            o = _make_oracle(oracle, wl.arena, wl.min_block, policy)
             client = wl.make()
             continue
         t0 = time.perf_counter()
@@ -837,8 +856,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=["large", "tiny", "frag", "usage", "multi", "serve"], default="large")
-    ap.add_argument("--policy", choices=["segfit", "tlsf"], default="segfit",
-                    help="segregated fit (§5.1) or two-level segregated fit (§5.2); the serving loop is segfit only")
+    ap.add_argument("--policy", choices=["segfit", "tlsf", "first", "next", "best"], default="segfit",
+                    help="segregated fit (§5.1), two-level segregated fit (§5.2), or a sequential fit on "
+                         "address-sorted lists (§4); the serving loop is segfit only")
     ap.add_argument("--lams", default="1,2,5,10,20,50")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--arenas", type=int, default=4096)

@@ -35,6 +35,21 @@
  * canonical state lists the 64 x 16 byte lists, then the first-level bitmap,
  * then the 64 second-level bitmaps.
  *
+ * HBA_POLICY_FIRST_FIT, _NEXT_FIT and _BEST_FIT are the sequential fits of
+ * §4 on the address-sorted free and in-use lists of §3.1 (Algorithm 1
+ * allocates from the front of the chosen free block, Algorithm 2 frees and
+ * coalesces).  First fit takes the lowest-address free block that fits; next
+ * fit starts from the free block holding or following the end of the last
+ * allocation and wraps around; best fit takes the smallest block that fits,
+ * the lowest address among equal sizes.  A free at an address inside an
+ * in-use block (a multiple of min_block) is a partial deallocation: the
+ * block keeps its head, the tail from that address is freed.  These handles
+ * run one CTA per arena, one request at a time; hba_serve_run rejects them,
+ * hba_set_shape has no effect on them.  Their canonical state is the free
+ * list and the in-use list as (offset, size) pairs in address order, each
+ * preceded by its length, then the next-fit position, after arena and
+ * min_block.
+ *
  * Batch semantics.  One batch = a free call followed by an alloc call on the
  * same stream (or one hba_step call): all frees in index order, then all
  * allocations in index order, exactly as if applied one by one.  Results are
@@ -83,8 +98,11 @@ typedef enum {
 } hba_status_t;
 
 typedef enum {
-    HBA_POLICY_SEGFIT = 0, /* §5.1 segregated fit */
-    HBA_POLICY_TLSF = 1    /* §5.2 two-level segregated fit; other values are rejected */
+    HBA_POLICY_SEGFIT = 0,    /* §5.1 segregated fit */
+    HBA_POLICY_TLSF = 1,      /* §5.2 two-level segregated fit */
+    HBA_POLICY_FIRST_FIT = 2, /* §4 first fit on address-sorted lists (§3.1) */
+    HBA_POLICY_NEXT_FIT = 3,  /* §4 next fit */
+    HBA_POLICY_BEST_FIT = 4   /* §4 best fit (Algorithm 3); other values are rejected */
 } hba_policy_t;
 
 #define HBA_FAIL ((uint64_t)~0ull)

@@ -17,6 +17,7 @@
 #include "hba_engine.cuh"
 #include "hba_serve.cuh"
 #include "hba_tlsf.cuh"
+#include "hba_fits.cuh"
 
 using hba::Arena;
 using hba::Rec;
@@ -75,6 +76,12 @@ struct hba_s {
     int policy = HBA_POLICY_SEGFIT;
     hba::TlsfLists* d_tlsf = nullptr;
     std::vector<hba::TlsfLists> h_tlsf;
+    // sequential fits (§3.1, §4): per-arena header, free and used arrays
+    // (granules + 1 entries per arena each, at record base + arena index)
+    hba::FitHdr* d_fhdr = nullptr;
+    hba::FitBlk* d_fpool = nullptr;
+    hba::FitBlk* d_upool = nullptr;
+    std::vector<hba::FitHdr> h_fhdr;
 };
 
 namespace {
@@ -431,6 +438,46 @@ __global__ void __launch_bounds__(WPC * 32) k_tlsf(Arena* ars, hba::TlsfLists* l
     }
 }
 
+// Sequential fits: one CTA per arena, the grid striding over the arenas.
+// frow / arow as for k_tlsf.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_fits(Arena* ars, hba::FitHdr* hdr, hba::FitBlk* fpool, hba::FitBlk* upool,
+                                            uint32_t n_arenas, const uint32_t* frow, const uint64_t* frees,
+                                            uint8_t* fstat, uint32_t nf, const uint32_t* arow, const uint64_t* sizes,
+                                            uint64_t* out, uint32_t na) {
+    __shared__ hba::FitSmem<NT> S;
+    for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
+        Arena& ar = ars[a];
+        const uint64_t base = ar.rec_base + a;
+        const uint32_t f0 = frow ? frow[a] : 0u, f1 = frow ? frow[a + 1] : nf;
+        const uint32_t a0 = arow ? arow[a] : 0u, a1 = arow ? arow[a + 1] : na;
+        hba::fit_arena<NT>(S, ar, hdr[a], fpool + base, upool + base, ar.G + 1, frees, fstat, f0, f1, sizes, out,
+                           a0, a1);
+    }
+}
+
+// Initial free arrays of the sequential fits: one block [0, G) per arena.
+__global__ void k_fits_init(const Arena* ars, hba::FitBlk* fpool, uint32_t n_arenas) {
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_arenas) return;
+    fpool[ars[a].rec_base + a] = hba::FitBlk{0u, ars[a].G};
+}
+
+// Space report of the sequential fits: largest free block (bytes) and
+// extent (granules: the end of the last used block, the used array being
+// sorted by address).
+__global__ void k_fits_space(const Arena* ars, const hba::FitHdr* hdr, const hba::FitBlk* fpool,
+                             const hba::FitBlk* upool, uint32_t n_arenas, uint64_t* largest, uint32_t* extent) {
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_arenas) return;
+    const uint64_t base = ars[a].rec_base + a;
+    uint32_t m = 0;
+    for (uint32_t i = 0; i < hdr[a].nfree; ++i) m = max(m, fpool[base + i].z);
+    largest[a] = (uint64_t)m << ars[a].lg;
+    const uint32_t nu = hdr[a].nused;
+    extent[a] = nu ? upool[base + nu - 1].a + upool[base + nu - 1].z : 0u;
+}
+
 // Largest free block of every TLSF arena: the highest non-empty list is
 // walked (bounded by the arena's block count).
 __global__ void k_largest_tlsf(const Arena* ars, const hba::TlsfLists* lists, const Rec* pool, uint32_t n_arenas,
@@ -615,6 +662,23 @@ hba_status_t launch_tlsf(hba_t h, const uint32_t* frow, const uint64_t* frees, u
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
 
+bool is_fit(int policy) {
+    return policy == HBA_POLICY_FIRST_FIT || policy == HBA_POLICY_NEXT_FIT || policy == HBA_POLICY_BEST_FIT;
+}
+
+// A sequential-fit batch: one CTA of FIT_NT threads per arena.
+constexpr int FIT_NT = 256;
+hba_status_t launch_fits(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint8_t* st,
+                         const uint32_t* arow, const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
+    const uint32_t n = h->n_arenas;
+    const uint32_t sms = g_limits[5].sms ? g_limits[5].sms : 152u;
+    const uint32_t grid = std::min(n, 8u * sms);
+    k_fits<FIT_NT><<<grid, FIT_NT, 0, s>>>(h->d_arenas, h->d_fhdr, h->d_fpool, h->d_upool, n, frow, frees, st, nf,
+                                           arow, sizes, out, na);
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+}
+
 hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
                        uint32_t na, uint64_t* out, cudaStream_t s) {
     if (!h || h->n_arenas != 1) return HBA_ERR_INVALID_ARGUMENT;
@@ -622,6 +686,10 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
     if (h->policy == HBA_POLICY_TLSF) {
         if (nf == 0 && na == 0) return HBA_OK;
         return launch_tlsf(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
+    }
+    if (is_fit(h->policy)) {
+        if (nf == 0 && na == 0) return HBA_OK;
+        return launch_fits(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     }
     // frees beyond the scratch capacity go in consecutive slices (exact:
     // frees apply one by one in index order).  Slicing at what one free
@@ -717,6 +785,12 @@ hba_status_t reset_impl(hba_t h, cudaStream_t s) {
                                  cudaMemcpyHostToDevice, s));
     k_init_records<<<(h->n_arenas + 255) / 256, 256, 0, s>>>(h->d_arenas, h->d_rec, h->n_arenas);
     ++h->launches;
+    if (h->d_fhdr) {  // after the arena headers, whose record bases it reads
+        HBA_CUDA_TRY(cudaMemcpyAsync(h->d_fhdr, h->h_fhdr.data(), sizeof(hba::FitHdr) * h->n_arenas,
+                                     cudaMemcpyHostToDevice, s));
+        k_fits_init<<<(h->n_arenas + 255) / 256, 256, 0, s>>>(h->d_arenas, h->d_fpool, h->n_arenas);
+        ++h->launches;
+    }
     HBA_CUDA_TRY(cudaGetLastError());
     return HBA_OK;
 }
@@ -729,6 +803,9 @@ void free_all(hba_t h) {
     cudaFree(h->d_largest);
     cudaFree(h->d_extent);
     cudaFree(h->d_tlsf);
+    cudaFree(h->d_fhdr);
+    cudaFree(h->d_fpool);
+    cudaFree(h->d_upool);
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_s);
     cudaFree(h->d_stage_o);
@@ -898,6 +975,7 @@ hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8
     if (nf == 0 && na == 0) return HBA_OK;
     if (h->policy == HBA_POLICY_TLSF)  // needs no scratch
         return launch_tlsf(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
+    if (is_fit(h->policy)) return launch_fits(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     uint32_t* base = static_scratch_address();
     if (!base) return HBA_ERR_CUDA;
     uint32_t* gi = base;
@@ -934,15 +1012,38 @@ hba_status_t hba_launch_count(hba_t h, uint64_t* count) {
 namespace {
 // The per-arena lists of a TLSF handle and their initial state (one free
 // block per arena).
-hba_status_t alloc_tlsf(hba_t h, int policy, const std::vector<Arena>& init) {
+// The per-arena structures of the policies other than segregated fit, and
+// their initial state (one free block per arena).  The arena headers' bitmap
+// field reports the first-level bitmap for TLSF, nothing for the fits.
+hba_status_t alloc_policy(hba_t h, int policy) {
     h->policy = policy;
-    if (policy != HBA_POLICY_TLSF) return HBA_OK;
-    h->h_tlsf.resize(init.size());
-    for (size_t i = 0; i < init.size(); ++i) hba::tl_init_host(&h->h_tlsf[i], init[i].G);
-    if (cudaMalloc(&h->d_tlsf, sizeof(hba::TlsfLists) * init.size()) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    const size_t n = h->h_init.size();
+    if (policy == HBA_POLICY_TLSF) {
+        h->h_tlsf.resize(n);
+        for (size_t i = 0; i < n; ++i) {
+            hba::tl_init_host(&h->h_tlsf[i], h->h_init[i].G);
+            h->h_init[i].mask = h->h_tlsf[i].flmask;
+        }
+        if (cudaMalloc(&h->d_tlsf, sizeof(hba::TlsfLists) * n) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    } else if (is_fit(policy)) {
+        h->h_fhdr.assign(n, hba::FitHdr{1u, 0u, 0u, 0u});
+        const uint32_t fit = policy == HBA_POLICY_FIRST_FIT ? hba::FIT_FIRST
+                             : policy == HBA_POLICY_NEXT_FIT ? hba::FIT_NEXT : hba::FIT_BEST;
+        for (size_t i = 0; i < n; ++i) {
+            h->h_fhdr[i].fit = fit;
+            h->h_init[i].mask = 0;
+        }
+        const size_t entries = h->total_granules + n;
+        if (cudaMalloc(&h->d_fhdr, sizeof(hba::FitHdr) * n) != cudaSuccess ||
+            cudaMalloc(&h->d_fpool, sizeof(hba::FitBlk) * entries) != cudaSuccess ||
+            cudaMalloc(&h->d_upool, sizeof(hba::FitBlk) * entries) != cudaSuccess)
+            return HBA_ERR_OUT_OF_MEMORY;
+    }
     return HBA_OK;
 }
-bool known_policy(int policy) { return policy == HBA_POLICY_SEGFIT || policy == HBA_POLICY_TLSF; }
+bool known_policy(int policy) {
+    return policy == HBA_POLICY_SEGFIT || policy == HBA_POLICY_TLSF || is_fit(policy);
+}
 }  // namespace
 
 hba_status_t hba_create_ex(uint64_t arena_bytes, uint64_t min_block, int policy, uint32_t max_batch,
@@ -959,7 +1060,7 @@ hba_status_t hba_create_ex(uint64_t arena_bytes, uint64_t min_block, int policy,
     std::vector<Arena> init(1);
     hba::arena_init_host(&init[0], a, lg, 0);
     hba_status_t r = alloc_meta(h, init, max_batch, max_batch);
-    if (r == HBA_OK) r = alloc_tlsf(h, policy, init);
+    if (r == HBA_OK) r = alloc_policy(h, policy);
     if (r == HBA_OK) r = reset_impl(h, 0);
     if (r == HBA_OK && cudaDeviceSynchronize() != cudaSuccess) r = HBA_ERR_CUDA;
     if (r != HBA_OK) {
@@ -993,7 +1094,7 @@ hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, ui
     h->total_granules = base;
     h->max_batch = max_total_frees;
     hba_status_t r = alloc_meta(h, init, max_total_frees, 0);
-    if (r == HBA_OK) r = alloc_tlsf(h, policy, init);
+    if (r == HBA_OK) r = alloc_policy(h, policy);
     if (r == HBA_OK) r = reset_impl(h, 0);
     if (r == HBA_OK && cudaDeviceSynchronize() != cudaSuccess) r = HBA_ERR_CUDA;
     if (r != HBA_OK) {
@@ -1107,15 +1208,19 @@ hba_status_t hba_reset(hba_t h, hba_stream_t stream) {
 hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
     if (!h || !out) return HBA_ERR_INVALID_ARGUMENT;
     HBA_CUDA_TRY(cudaDeviceSynchronize());
-    if (h->d_tlsf)
+    if (h->d_fhdr) {  // the fits keep no record table: their lists give both figures
+        k_fits_space<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_fhdr, h->d_fpool, h->d_upool,
+                                                         h->n_arenas, h->d_largest, h->d_extent);
+    } else if (h->d_tlsf) {
         k_largest_tlsf<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_tlsf, h->d_rec, h->n_arenas,
                                                            h->d_largest);
-    else
+    } else {
         k_largest<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->d_largest);
+    }
     ++h->launches;
     HBA_CUDA_TRY(cudaGetLastError());
-    HBA_CUDA_TRY(cudaMemset(h->d_extent, 0, sizeof(uint32_t) * h->n_arenas));
-    {
+    if (!h->d_fhdr) {
+        HBA_CUDA_TRY(cudaMemset(h->d_extent, 0, sizeof(uint32_t) * h->n_arenas));
         const uint64_t tiles = (h->total_granules + 64ull * 256 - 1) / (64ull * 256);
         const uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, 1), 8192);
         k_extent<<<grid, 256>>>(h->d_arenas, h->d_rec, h->n_arenas, h->total_granules, h->d_extent);
@@ -1155,6 +1260,20 @@ hba_status_t hba_export_state(hba_t h, uint32_t arena, uint64_t* host_buf, size_
     HBA_CUDA_TRY(cudaDeviceSynchronize());
     Arena ar;
     HBA_CUDA_TRY(cudaMemcpy(&ar, h->d_arenas + arena, sizeof(Arena), cudaMemcpyDeviceToHost));
+    if (h->d_fhdr) {
+        hba::FitHdr H;
+        HBA_CUDA_TRY(cudaMemcpy(&H, h->d_fhdr + arena, sizeof(H), cudaMemcpyDeviceToHost));
+        const uint64_t base = ar.rec_base + arena;
+        std::vector<hba::FitBlk> fa(H.nfree), ua(H.nused);
+        if (H.nfree)
+            HBA_CUDA_TRY(cudaMemcpy(fa.data(), h->d_fpool + base, sizeof(hba::FitBlk) * H.nfree,
+                                    cudaMemcpyDeviceToHost));
+        if (H.nused)
+            HBA_CUDA_TRY(cudaMemcpy(ua.data(), h->d_upool + base, sizeof(hba::FitBlk) * H.nused,
+                                    cudaMemcpyDeviceToHost));
+        *len = hba::fit_export(ar, H, fa.data(), ua.data(), host_buf, cap);
+        return HBA_OK;
+    }
     std::vector<Rec> rec(ar.G);
     HBA_CUDA_TRY(cudaMemcpy(rec.data(), h->d_rec + ar.rec_base, sizeof(Rec) * ar.G, cudaMemcpyDeviceToHost));
     if (h->d_tlsf) {
@@ -1192,6 +1311,9 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     const uint32_t n = h->n_arenas;
     if (h->policy == HBA_POLICY_TLSF)
         return launch_tlsf(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes, na_total,
+                           d_out, s);
+    if (is_fit(h->policy))
+        return launch_fits(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes, na_total,
                            d_out, s);
     if (h->m_threads == 32) {
         // warp mode: WPC arenas per CTA, per-warp dynamic shared memory

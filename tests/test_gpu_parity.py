@@ -643,3 +643,165 @@ def test_tlsf_multi_arena_matches_per_arena_oracles(gpu_lib):
     assert st_["alloc_ok"] == sum(o.stats()["alloc_ok"] for o in orcs)
     assert st_["extent_bytes"] == sum(o.space()["extent"] for o in orcs)
     m.close()
+
+
+# ---- sequential fits on address-sorted lists (§3.1, §4) ------------------------
+
+
+def _hal_trace(wl, fit, max_batches=None):
+    import oracle
+
+    o = oracle.HalOracle(wl.arena, wl.min_block, fit)
+    cl = wl.make()
+    trace = []
+    while max_batches is None or len(trace) < max_batches:
+        b = cl.next_batch()
+        if b is None:
+            break
+        out, st = o.batch(*b)
+        cl.feed(out)
+        trace.append((b[0], b[1], out, st))
+    return trace, o
+
+
+def _run_fit(trace, o, arena, min_block, fit, state_every=0):
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import Allocator
+
+    dev = torch.device("cuda")
+    lock = oracle.HalOracle(arena, min_block, fit) if state_every else None
+    with Allocator(arena, min_block, policy=fit) as a:
+        for b, (f, s, out, st) in enumerate(trace):
+            dst = torch.empty(f.size, dtype=torch.uint8, device=dev)
+            go = a.step(to_dev(f, dev) if f.size else None, to_dev(s, dev) if s.size else None, status=dst)
+            if s.size:
+                i = first_diff(from_dev(go), out)
+                assert i is None, f"{fit} batch {b}: alloc {i}"
+            assert first_diff(from_dev(dst), st) is None, f"{fit} batch {b}: free status"
+            if lock is not None:
+                lock.batch(f, s)
+                if b % state_every == 0:
+                    assert np.array_equal(a.export_state(), lock.export_state()), f"{fit} batch {b}: state"
+        assert np.array_equal(a.export_state(), o.export_state()), f"{fit}: final state"
+        got, ref = a.stats(), o.stats()
+        for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes", "used_blocks", "blocks",
+                  "requested_bytes", "largest_free"):
+            assert got[k] == ref[k], (fit, k, got[k], ref[k])
+        assert got["extent_bytes"] == ref["extent"]
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+def test_fits_worked_examples(gpu_lib, fit):
+    import sys
+
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator
+
+    sys.path.insert(0, __import__("os").path.dirname(__file__))
+    from test_oracle_pins import load_hal_golden
+
+    dev = torch.device("cuda")
+    for case in [c for c in load_hal_golden() if c["fit"] == fit]:
+        with Allocator(case["arena"], case["min_block"], policy=fit) as a:
+            for frees, sizes, expect, expect_st in case["batches"]:
+                f = np.array(frees, np.uint64)
+                s_ = np.array(sizes, np.uint64)
+                st = torch.empty(f.size, dtype=torch.uint8, device=dev)
+                out = a.step(to_dev(f, dev) if f.size else None, to_dev(s_, dev) if s_.size else None, status=st)
+                if s_.size:
+                    assert [int(x) for x in from_dev(out)] == expect, case["name"]
+                assert [int(x) for x in from_dev(st)] == expect_st, case["name"]
+            assert [int(x) for x in a.export_state()] == case["final"], case["name"]
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+def test_fits_tiny_and_usage(gpu_lib, fit):
+    from paper_2405_07079_gb300 import workloads as W
+
+    for wl, every in ((W.tiny(n_ops=4000), 8), (W.usage(n_ops=1500, batch=16), 10)):
+        trace, o = _hal_trace(wl, fit)
+        _run_fit(trace, o, wl.arena, wl.min_block, fit, state_every=every)
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+def test_fits_lifetimes_large_lists(gpu_lib, fit):
+    """Batches of 4,096 requests on a 256 MiB arena: free lists of hundreds
+    to thousands of entries (multi-step scans and shifts), long failure runs."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.Workload("life", 256 * MiB, 512, lambda: W.Lifetimes(n_ops=60_000, batch=4096, mean_life=400))
+    trace, o = _hal_trace(wl, fit)
+    _run_fit(trace, o, wl.arena, wl.min_block, fit, state_every=3)
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+def test_fits_partial_and_invalid_frees(gpu_lib, fit):
+    """Random batches whose frees name block starts, interior granules
+    (partial deallocation), misaligned and unknown offsets."""
+    rng = np.random.default_rng({"first": 5, "next": 6, "best": 7}[fit])
+    import oracle
+
+    A, mb = 8 * MiB, 4096
+    o = oracle.HalOracle(A, mb, fit)
+    held, trace = [], []
+    for _ in range(300):
+        frees = []
+        for _ in range(int(rng.integers(0, 24))):
+            if held and rng.random() < 0.8:
+                h = held[int(rng.integers(0, len(held)))]
+                frees.append(h + mb * int(rng.integers(0, 4)) if rng.random() < 0.35 else h)
+            else:
+                frees.append(int(rng.integers(0, A // mb + 4)) * mb + int(rng.choice([0, 0, 8])))
+        sizes = (rng.integers(1, 64, int(rng.integers(0, 40))) * 4096 - rng.integers(0, 4096, 1)).astype(np.uint64)
+        f = np.array(frees, np.uint64)
+        out, st = o.batch(f, sizes)
+        trace.append((f, sizes, out, st))
+        held = [h for h in held if h not in frees] + [int(x) for x in out if x != FAIL]
+    o2 = oracle.HalOracle(A, mb, fit)
+    for f, s, _, _ in trace:
+        o2.batch(f, s)
+    _run_fit(trace, o2, A, mb, fit, state_every=25)
+
+
+def test_fits_multi_arena(gpu_lib):
+    """Independent first/next/best-fit arenas, one CTA each, in one launch."""
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import MultiAllocator
+    from paper_2405_07079_gb300 import workloads as W
+
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(33)
+    n = 41
+    sizes_a = (rng.integers(1, 32, n) * 256 * 1024 + rng.integers(0, 4, n) * 256).astype(np.uint64)
+    mb = 256
+    for fit in ("first", "next", "best"):
+        m = MultiAllocator(sizes_a, mb, max_total_frees=1 << 16, policy=fit)
+        orcs = [oracle.HalOracle(int(x), mb, fit) for x in sizes_a]
+        clients = [W.Lifetimes(n_ops=10**9, batch=int(rng.integers(0, 300)), mean_life=100,
+                               seed=W.BASE_SEED + 500 + i, scale=float(x) / (16 * GiB), min_size=256)
+                   for i, x in enumerate(sizes_a)]
+        for b in range(8):
+            fr, sz, exp_o, exp_s = [], [], [], []
+            for i in range(n):
+                f, s_ = clients[i].next_batch()
+                ro, rs = orcs[i].batch(f, s_)
+                clients[i].feed(ro)
+                fr.append(f); sz.append(s_); exp_o.append(ro); exp_s.append(rs)
+            frow = np.concatenate([[0], np.cumsum([x.size for x in fr])]).astype(np.uint32)
+            arow = np.concatenate([[0], np.cumsum([x.size for x in sz])]).astype(np.uint32)
+            F = np.concatenate(fr).astype(np.uint64)
+            S = np.concatenate(sz).astype(np.uint64)
+            out = torch.empty(S.size, dtype=torch.int64, device=dev)
+            st = torch.empty(F.size, dtype=torch.uint8, device=dev)
+            m.step(to_dev(frow.view(np.int32), dev), to_dev(F, dev), to_dev(arow.view(np.int32), dev),
+                   to_dev(S, dev), out, st)
+            assert np.array_equal(from_dev(out), np.concatenate(exp_o)), f"{fit} batch {b}"
+            assert np.array_equal(from_dev(st), np.concatenate(exp_s))
+        for i in range(n):
+            assert np.array_equal(m.export_state(i), orcs[i].export_state()), (fit, i)
+        m.close()
