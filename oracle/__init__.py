@@ -31,6 +31,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "segfit_oracle.c")
 _HAL_SRC = os.path.join(_HERE, "hal_oracle.c")
+_BM_SRC = os.path.join(_HERE, "bitmask_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libsegfit_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -42,11 +43,11 @@ def build(force: bool = False) -> str:
     """Compile ``segfit_oracle.c`` into ``_build/libsegfit_oracle.so`` (gcc)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     stale = (not os.path.exists(_LIB)
-             or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HAL_SRC)))
+             or os.path.getmtime(_LIB) < max(map(os.path.getmtime, (_SRC, _HAL_SRC, _BM_SRC))))
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, _HAL_SRC])
+                               "-o", tmp, _SRC, _HAL_SRC, _BM_SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -84,6 +85,17 @@ def _load():
             lib.hal_export.restype = ctypes.c_size_t
             lib.hal_export.argtypes = [vp, vp, ctypes.c_size_t]
             lib.hal_stats.argtypes = [vp, vp]
+            lib.bm_create.restype = vp
+            lib.bm_create.argtypes = [u64, u64]
+            lib.bm_destroy.argtypes = [vp]
+            lib.bm_malloc.restype = u64
+            lib.bm_malloc.argtypes = [vp, u64]
+            lib.bm_free.restype = ctypes.c_int
+            lib.bm_free.argtypes = [vp, u64]
+            lib.bm_batch.argtypes = [vp, vp, u32, vp, vp, u32, vp]
+            lib.bm_export.restype = ctypes.c_size_t
+            lib.bm_export.argtypes = [vp, vp, ctypes.c_size_t]
+            lib.bm_stats.argtypes = [vp, vp]
             _lib = lib
     return _lib
 
@@ -211,6 +223,56 @@ class HalOracle:
     def stats(self) -> dict:
         buf = np.zeros(10, dtype=np.uint64)
         self._lib.hal_stats(self._h, buf.ctypes.data)
+        return {k: int(v) for k, v in zip(self.STAT_KEYS, buf)}
+
+
+class BitmaskOracle:
+    """A bitmask pool (§3.2): one free bit per unit of ``unit`` bytes, runs
+    found by next fit, a second out-of-band bitmap marking block starts."""
+
+    STAT_KEYS = HalOracle.STAT_KEYS
+
+    def __init__(self, pool_bytes: int, unit: int):
+        self._lib = _load()
+        self._h = self._lib.bm_create(int(pool_bytes), int(unit))
+        if not self._h:
+            raise ValueError("invalid pool_bytes/unit")
+        self.unit = int(unit)
+
+    def close(self):
+        if self._h:
+            self._lib.bm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def malloc(self, size: int) -> int:
+        return int(self._lib.bm_malloc(self._h, int(size)))
+
+    def free(self, addr: int) -> int:
+        return int(self._lib.bm_free(self._h, int(addr)))
+
+    def batch(self, frees, sizes):
+        f = np.ascontiguousarray(frees, dtype=np.uint64)
+        s = np.ascontiguousarray(sizes, dtype=np.uint64)
+        out = np.empty(s.size, dtype=np.uint64)
+        st = np.empty(f.size, dtype=np.uint8)
+        self._lib.bm_batch(self._h, _ptr(f), f.size, _ptr(st), _ptr(s), s.size, _ptr(out))
+        return out, st
+
+    def export_state(self) -> np.ndarray:
+        n = self._lib.bm_export(self._h, None, 0)
+        buf = np.empty(n, dtype=np.uint64)
+        self._lib.bm_export(self._h, buf.ctypes.data, n)
+        return buf
+
+    def stats(self) -> dict:
+        buf = np.zeros(10, dtype=np.uint64)
+        self._lib.bm_stats(self._h, buf.ctypes.data)
         return {k: int(v) for k, v in zip(self.STAT_KEYS, buf)}
 
 

@@ -102,3 +102,54 @@ class GranuleFits:
         for b, n in used:
             w += [b * mb, n * mb]
         return w + [self.rover * mb]
+
+
+class BlockListPool:
+    """The bitmask pool (§3.2) restated without bits: the in-use blocks are
+    a list of (first unit, units) intervals; a unit is free iff no interval
+    covers it.  Next fit over candidate starts: the lowest start at or after
+    the rover whose k units are all free, else the lowest start of all.  A
+    free must name the first unit of a listed block and removes it.  The
+    second bitmap of the C oracle is the list's set of starts."""
+
+    def __init__(self, pool_bytes: int, unit: int):
+        self.unit = unit
+        self.N = pool_bytes // unit
+        self.blocks = []  # (first unit, units), in allocation order
+        self.rover = 0
+
+    def _free_at(self, p, k):
+        return p + k <= self.N and all(not (a < p + k and p < a + n) for a, n in self.blocks)
+
+    def malloc(self, size: int) -> int:
+        k = -(-size // self.unit) if size else 0
+        if size == 0 or size > self.N * self.unit or k > 64 or k > self.N:
+            return FAIL
+        order = list(range(self.rover, self.N)) + list(range(0, self.rover))
+        p = next((q for q in order if self._free_at(q, k)), None)
+        if p is None:
+            return FAIL
+        self.blocks.append((p, k))
+        self.rover = p + k
+        return p * self.unit
+
+    def free(self, addr: int) -> int:
+        if addr % self.unit:
+            return 1
+        p = addr // self.unit
+        for i, (a, n) in enumerate(self.blocks):
+            if a == p:
+                del self.blocks[i]
+                return 0
+        return 1
+
+    def batch(self, frees, sizes):
+        st = [self.free(int(a)) for a in frees]
+        out = [self.malloc(int(s)) for s in sizes]
+        return out, st
+
+    def export_state(self) -> list:
+        w = [self.N * self.unit, self.unit, len(self.blocks)]
+        for a, n in sorted(self.blocks):
+            w += [a * self.unit, n * self.unit]
+        return w + [self.rover * self.unit]

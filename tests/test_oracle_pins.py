@@ -698,6 +698,150 @@ def test_hal_invariants_on_workload_traces(fit):
             assert stt["extent"] == max([a + z for a, z in s["used"]], default=0)
 
 
+# ---- bitmask pool (§3.2) ----------------------------------------------------
+BM_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "bitmask_worked_examples.json")
+
+
+def load_bitmask_golden():
+    with open(BM_GOLDEN) as f:
+        doc = json.load(f)
+    cases = []
+    for c in doc["cases"]:
+        fin = c["final"]
+        w = [c["pool"], c["unit"], len(fin["blocks"])]
+        for a, z in fin["blocks"]:
+            w += [a, z]
+        w.append(fin["rover"])
+        cases.append({"name": c["name"], "pool": c["pool"], "unit": c["unit"], "batches": c["batches"], "final": w})
+    return cases
+
+
+def _bm_oracle(P, u):
+    return oracle.BitmaskOracle(P, u)
+
+
+def _bm_ref(P, u):
+    from oracle.fits_ref import BlockListPool
+
+    return BlockListPool(P, u)
+
+
+@pytest.mark.parametrize("make", [_bm_oracle, _bm_ref])
+@pytest.mark.parametrize("case", load_bitmask_golden(), ids=lambda c: c["name"].split()[0])
+def test_bitmask_worked_example(make, case):
+    a = make(case["pool"], case["unit"])
+    for frees, sizes, expect, expect_st in case["batches"]:
+        out, st = a.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        assert [int(x) for x in out] == expect, case["name"]
+        assert [int(x) for x in st] == expect_st, case["name"]
+    assert [int(x) for x in a.export_state()] == case["final"], case["name"]
+
+
+@pytest.mark.parametrize("mutant", ["first_fit", "runs_wrap", "free_to_next_free", "k_limit"])
+def test_bitmask_worked_examples_catch_mutants(monkeypatch, mutant):
+    """Plausible mistakes planted in the block-list statement, each caught
+    by a worked example: first fit instead of next fit, runs that wrap past
+    the pool's end, a free that releases units up to the next free unit
+    (ignoring block starts), and a size limit one unit off."""
+    from oracle import fits_ref as fr
+
+    cls = fr.BlockListPool
+    if mutant == "first_fit":
+        orig = cls.malloc
+
+        def malloc(self, size):
+            self.rover = 0
+            return orig(self, size)
+        monkeypatch.setattr(cls, "malloc", malloc)
+    elif mutant == "runs_wrap":
+        def free_at(self, p, k):
+            units = [(p + j) % self.N for j in range(k)]
+            return k <= self.N and all(not any(a <= q < a + n for a, n in self.blocks) for q in units)
+        monkeypatch.setattr(cls, "_free_at", free_at)
+    elif mutant == "free_to_next_free":
+        orig = cls.free
+
+        def free(self, addr):
+            p = addr // self.unit
+            blk = next((b for b in self.blocks if b[0] == p), None)
+            r = orig(self, addr)
+            if r == 0:  # also release the in-use blocks that follow, up to the next free unit
+                q = p + blk[1]
+                while (nxt := next((b for b in self.blocks if b[0] == q), None)) is not None:
+                    self.blocks.remove(nxt)
+                    q += nxt[1]
+            return r
+        monkeypatch.setattr(cls, "free", free)
+    else:
+        def malloc(self, size):  # the 64-unit limit off by one
+            k = -(-size // self.unit) if size else 0
+            if size == 0 or size > self.N * self.unit or k > 65 or k > self.N:
+                return fr.FAIL
+            order = list(range(self.rover, self.N)) + list(range(0, self.rover))
+            p = next((q for q in order if self._free_at(q, k)), None)
+            if p is None:
+                return fr.FAIL
+            self.blocks.append((p, k))
+            self.rover = p + k
+            return p * self.unit
+        monkeypatch.setattr(cls, "malloc", malloc)
+    caught = False
+    for c in load_bitmask_golden():
+        a = cls(c["pool"], c["unit"])
+        ok = True
+        for frees, sizes, expect, expect_st in c["batches"]:
+            out, st = a.batch(frees, sizes)
+            ok &= [int(x) for x in out] == expect and [int(x) for x in st] == expect_st
+        ok &= a.export_state() == c["final"]
+        caught |= not ok
+    assert caught, mutant
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_bitmask_oracle_equals_block_list_random(seed):
+    from oracle.fits_ref import BlockListPool
+
+    rng = np.random.default_rng(3000 + seed)
+    u = int(rng.choice([8, 16, 64]))
+    N = int(rng.integers(1, 400))
+    o, r = oracle.BitmaskOracle(N * u, u), BlockListPool(N * u, u)
+    held = []
+    for _ in range(60):
+        frees = []
+        for _ in range(int(rng.integers(0, 5))):
+            if held and rng.random() < 0.75:
+                h = held[int(rng.integers(0, len(held)))]
+                frees.append(h + (u if rng.random() < 0.15 else 0))
+            else:
+                frees.append(int(rng.integers(0, N + 3)) * u + int(rng.choice([0, 0, 4])))
+        sizes = [int(rng.integers(0, min(N, 70) * u + 2)) for _ in range(int(rng.integers(0, 6)))]
+        oo, os_ = o.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+        ro, rs = r.batch(frees, sizes)
+        assert [int(x) for x in oo] == ro and [int(x) for x in os_] == rs
+        held = [h for h in held if h not in frees] + [x for x in ro if x != FAIL]
+    assert [int(x) for x in o.export_state()] == r.export_state()
+
+
+def test_bitmask_oracle_equals_block_list_exhaustive():
+    """Every sequence of four ops from a small alphabet on pools of 3 and 7
+    units."""
+    from oracle.fits_ref import BlockListPool
+
+    alphabet = [("a", 8), ("a", 16), ("a", 20), ("f", 0), ("f", 8), ("f", 16), ("f", 4)]
+    n = 0
+    for N in (3, 7):
+        for seq in itertools.product(alphabet, repeat=4):
+            o, r = oracle.BitmaskOracle(N * 8, 8), BlockListPool(N * 8, 8)
+            for kind, v in seq:
+                if kind == "a":
+                    assert o.malloc(v) == r.malloc(v)
+                else:
+                    assert o.free(v) == r.free(v)
+            assert [int(x) for x in o.export_state()] == r.export_state()
+            n += 1
+    assert n == 2 * len(alphabet) ** 4
+
+
 def test_property_hypothesis():
     hyp = pytest.importorskip("hypothesis")
     st = pytest.importorskip("hypothesis.strategies")
