@@ -210,9 +210,12 @@ FIT_POLICIES = ("first", "next", "best")
 
 
 def _make_oracle(oracle, arena, mb, policy):
-    """The oracle of a policy: segregated fit / TLSF, or a sequential fit."""
+    """The oracle of a policy: segregated fit / TLSF, a sequential fit, or
+    the bitmask pool."""
     if policy in FIT_POLICIES:
         return oracle.HalOracle(arena, mb, policy)
+    if policy == "bitmask":
+        return oracle.BitmaskOracle(arena, mb)
     return oracle.Oracle(arena, mb, policy)
 
 
@@ -383,7 +386,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag,
-          "usage": workloads.usage}[args.workload]()
+          "usage": workloads.usage, "objects": workloads.objects}[args.workload]()
     alloc = Allocator(wl.arena, wl.min_block, threads=args.threads, ctas=args.ctas, policy=args.policy)
     space = []
     batches = record_trace(wl, alloc, dev, space)
@@ -453,10 +456,13 @@ def run_gpu(args, rank, world, local_rank):
                             if args.policy == "tlsf" else
                             f"{args.policy} fit on address-sorted lists: one CTA applies the batch (k_fits<256>)"
                             if args.policy in FIT_POLICIES else
+                            "bitmask pool: one CTA applies the batch, bitmaps in shared memory (k_bitmask<256>)"
+                            if args.policy == "bitmask" else
                             "plain single arena: one thread-block cluster per batch (engine CTA + CTAs that "
                             "gather the frees' records into its shared memory and pre-fill failures)"
                             if args.ctas >= 2 else "plain single arena: prep grid + engine kernel per batch"),
-                   "threads_per_cta": (32 if args.policy == "tlsf" else 256 if args.policy in FIT_POLICIES
+                   "threads_per_cta": (32 if args.policy == "tlsf"
+                                       else 256 if args.policy in FIT_POLICIES + ("bitmask",)
                                        else alloc_threads(args)),
                    "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
                    "ops_per_step_mean": ops / max(1, args.steps)},
@@ -468,6 +474,7 @@ def run_gpu(args, rank, world, local_rank):
                      "peak_source": f"{peak_src} hbm_gbs",
                      "kernel": ("k_tlsf<1>" if args.policy == "tlsf" else
                                 "k_fits<256>" if args.policy in FIT_POLICIES else
+                                "k_bitmask<256>" if args.policy == "bitmask" else
                                 f"k_single_cl<{alloc_threads(args)}>" if args.ctas >= 2
                                 else f"k_prep + k_single<{alloc_threads(args)}>"),
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
@@ -787,7 +794,7 @@ def alloc_threads(args):
     and the one-op batches of the memory-usage workload)."""
     if args.threads:
         return args.threads
-    return 128 if args.workload in ("tiny", "usage") else 1024
+    return 128 if args.workload in ("tiny", "usage", "objects") else 1024
 
 
 def oracle_steps(wl, n_steps=None, warmup=0, policy="segfit"):
@@ -833,7 +840,7 @@ def run_reference(args, rank, world):
     from paper_2405_07079_gb300 import workloads
 
     wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag,
-          "usage": workloads.usage}[args.workload]()
+          "usage": workloads.usage, "objects": workloads.objects}[args.workload]()
     t, ops, k = oracle_steps(wl, n_steps=args.steps, warmup=args.warmup, policy=args.policy)
     v = ops / t
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
@@ -855,10 +862,11 @@ def main():
     ap.add_argument("--steps", type=int, default=1530)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["large", "tiny", "frag", "usage", "multi", "serve"], default="large")
-    ap.add_argument("--policy", choices=["segfit", "tlsf", "first", "next", "best"], default="segfit",
-                    help="segregated fit (§5.1), two-level segregated fit (§5.2), or a sequential fit on "
-                         "address-sorted lists (§4); the serving loop is segfit only")
+    ap.add_argument("--workload", choices=["large", "tiny", "frag", "usage", "objects", "multi", "serve"],
+                    default="large")
+    ap.add_argument("--policy", choices=["segfit", "tlsf", "first", "next", "best", "bitmask"], default="segfit",
+                    help="segregated fit (§5.1), two-level segregated fit (§5.2), a sequential fit on "
+                         "address-sorted lists (§4), or the bitmask pool (§3.2); the serving loop is segfit only")
     ap.add_argument("--lams", default="1,2,5,10,20,50")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--arenas", type=int, default=4096)

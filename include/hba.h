@@ -50,6 +50,18 @@
  * preceded by its length, then the next-fit position, after arena and
  * min_block.
  *
+ * HBA_POLICY_BITMASK is the bitmask pool of §3.2: one bit per min_block unit
+ * says whether the unit is free.  An allocation of up to 64 units takes k
+ * consecutive free units by next fit (the lowest start at or after the end
+ * of the last allocation, else the lowest start of all; runs do not wrap);
+ * larger requests fail.  A second out-of-band bitmap marks the first unit of
+ * each in-use block; a free must name such a unit and releases the units up
+ * to the next marked or free unit.  A pool holds at most 786,432 units
+ * (HBA_ERR_INVALID_ARGUMENT at create); each runs on one CTA with both
+ * bitmaps in shared memory.  The canonical state is the in-use blocks
+ * (offset, size) in address order, preceded by their count, then the
+ * next-fit position, after the pool size and the unit.
+ *
  * Batch semantics.  One batch = a free call followed by an alloc call on the
  * same stream (or one hba_step call): all frees in index order, then all
  * allocations in index order, exactly as if applied one by one.  Results are
@@ -102,7 +114,8 @@ typedef enum {
     HBA_POLICY_TLSF = 1,      /* §5.2 two-level segregated fit */
     HBA_POLICY_FIRST_FIT = 2, /* §4 first fit on address-sorted lists (§3.1) */
     HBA_POLICY_NEXT_FIT = 3,  /* §4 next fit */
-    HBA_POLICY_BEST_FIT = 4   /* §4 best fit (Algorithm 3); other values are rejected */
+    HBA_POLICY_BEST_FIT = 4,  /* §4 best fit (Algorithm 3) */
+    HBA_POLICY_BITMASK = 5    /* §3.2 bitmask pool of small objects; other values are rejected */
 } hba_policy_t;
 
 #define HBA_FAIL ((uint64_t)~0ull)

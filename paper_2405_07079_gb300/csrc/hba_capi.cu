@@ -18,6 +18,7 @@
 #include "hba_serve.cuh"
 #include "hba_tlsf.cuh"
 #include "hba_fits.cuh"
+#include "hba_bitmask.cuh"
 
 using hba::Arena;
 using hba::Rec;
@@ -82,6 +83,12 @@ struct hba_s {
     hba::FitBlk* d_fpool = nullptr;
     hba::FitBlk* d_upool = nullptr;
     std::vector<hba::FitHdr> h_fhdr;
+    // bitmask pools (§3.2): per-pool header, free and start bitmaps
+    hba::BmHdr* d_bmh = nullptr;
+    uint64_t* d_bmF = nullptr;
+    uint64_t* d_bmS = nullptr;
+    std::vector<hba::BmHdr> h_bmh;
+    uint32_t bm_wmax = 0;  // largest pool, in words
 };
 
 namespace {
@@ -456,6 +463,67 @@ __global__ void __launch_bounds__(NT) k_fits(Arena* ars, hba::FitHdr* hdr, hba::
     }
 }
 
+// Bitmask pools: one CTA per pool, both bitmaps in dynamic shared memory
+// (2 x bm_wmax words).  frow / arow as for k_tlsf.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_bitmask(Arena* ars, hba::BmHdr* hdr, uint64_t* gF, uint64_t* gS,
+                                               uint32_t n_arenas, uint32_t wmax, const uint32_t* frow,
+                                               const uint64_t* frees, uint8_t* fstat, uint32_t nf,
+                                               const uint32_t* arow, const uint64_t* sizes, uint64_t* out,
+                                               uint32_t na) {
+    __shared__ hba::BmSmem<NT> S_;
+    extern __shared__ __align__(16) uint64_t bm_dyn[];
+    for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
+        const uint32_t f0 = frow ? frow[a] : 0u, f1 = frow ? frow[a + 1] : nf;
+        const uint32_t a0 = arow ? arow[a] : 0u, a1 = arow ? arow[a + 1] : na;
+        hba::BmHdr& H = hdr[a];
+        hba::bm_pool<NT>(S_, ars[a], H, gF + H.wbase, gS + H.wbase, bm_dyn, bm_dyn + wmax, frees, fstat, f0, f1,
+                         sizes, out, a0, a1);
+    }
+}
+
+// Initial bitmaps: every unit free (bits past the pool's end clear), no starts.
+__global__ void k_bm_init(const Arena* ars, const hba::BmHdr* hdr, uint64_t* gF, uint64_t* gS, uint32_t n_arenas) {
+    for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
+        const uint32_t N = ars[a].G, W = hdr[a].words;
+        uint64_t* F = gF + hdr[a].wbase;
+        uint64_t* S = gS + hdr[a].wbase;
+        for (uint32_t w = threadIdx.x; w < W; w += blockDim.x) {
+            const uint32_t lo = w << 6;
+            F[w] = N - lo >= 64 ? ~0ull : (1ull << (N - lo)) - 1ull;
+            S[w] = 0;
+        }
+    }
+}
+
+// Space report of the bitmask pools: longest free run (bytes), extent (units:
+// one past the highest in-use unit), and the block count (in-use blocks +
+// free runs) into the arena header.
+__global__ void k_bm_space(Arena* ars, const hba::BmHdr* hdr, const uint64_t* gF, const uint64_t* gS,
+                           uint32_t n_arenas, uint64_t* largest, uint32_t* extent) {
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_arenas) return;
+    const uint32_t N = ars[a].G;
+    const uint64_t* F = gF + hdr[a].wbase;
+    const uint64_t* S = gS + hdr[a].wbase;
+    uint32_t run = 0, longest = 0, runs = 0, used = 0, top = 0;
+    for (uint32_t u = 0; u < N; ++u) {
+        const uint64_t fw = F[u >> 6];
+        used += (uint32_t)((S[u >> 6] >> (u & 63)) & 1ull);
+        if ((fw >> (u & 63)) & 1ull) {
+            if (run == 0) ++runs;
+            ++run;
+            if (run > longest) longest = run;
+        } else {
+            run = 0;
+            top = u + 1;
+        }
+    }
+    largest[a] = (uint64_t)longest << ars[a].lg;
+    extent[a] = top;
+    ars[a].blocks = (int64_t)used + runs;
+}
+
 // Initial free arrays of the sequential fits: one block [0, G) per arena.
 __global__ void k_fits_init(const Arena* ars, hba::FitBlk* fpool, uint32_t n_arenas) {
     const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -679,6 +747,21 @@ hba_status_t launch_fits(hba_t h, const uint32_t* frow, const uint64_t* frees, u
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
 
+// A bitmask batch: one CTA of BM_NT threads per pool.
+constexpr int BM_NT = 256;
+hba_status_t launch_bitmask(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint8_t* st,
+                            const uint32_t* arow, const uint64_t* sizes, uint32_t na, uint64_t* out,
+                            cudaStream_t s) {
+    const uint32_t n = h->n_arenas;
+    const uint32_t sms = g_limits[5].sms ? g_limits[5].sms : 152u;
+    const uint32_t grid = std::min(n, 4u * sms);
+    const uint32_t dyn = 16u * h->bm_wmax;
+    k_bitmask<BM_NT><<<grid, BM_NT, dyn, s>>>(h->d_arenas, h->d_bmh, h->d_bmF, h->d_bmS, n, h->bm_wmax, frow, frees,
+                                              st, nf, arow, sizes, out, na);
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+}
+
 hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
                        uint32_t na, uint64_t* out, cudaStream_t s) {
     if (!h || h->n_arenas != 1) return HBA_ERR_INVALID_ARGUMENT;
@@ -690,6 +773,10 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
     if (is_fit(h->policy)) {
         if (nf == 0 && na == 0) return HBA_OK;
         return launch_fits(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
+    }
+    if (h->policy == HBA_POLICY_BITMASK) {
+        if (nf == 0 && na == 0) return HBA_OK;
+        return launch_bitmask(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     }
     // frees beyond the scratch capacity go in consecutive slices (exact:
     // frees apply one by one in index order).  Slicing at what one free
@@ -785,6 +872,13 @@ hba_status_t reset_impl(hba_t h, cudaStream_t s) {
                                  cudaMemcpyHostToDevice, s));
     k_init_records<<<(h->n_arenas + 255) / 256, 256, 0, s>>>(h->d_arenas, h->d_rec, h->n_arenas);
     ++h->launches;
+    if (h->d_bmh) {  // after the arena headers, whose sizes it reads
+        HBA_CUDA_TRY(cudaMemcpyAsync(h->d_bmh, h->h_bmh.data(), sizeof(hba::BmHdr) * h->n_arenas,
+                                     cudaMemcpyHostToDevice, s));
+        k_bm_init<<<std::min<uint32_t>(h->n_arenas, 1024u), 256, 0, s>>>(h->d_arenas, h->d_bmh, h->d_bmF, h->d_bmS,
+                                                                        h->n_arenas);
+        ++h->launches;
+    }
     if (h->d_fhdr) {  // after the arena headers, whose record bases it reads
         HBA_CUDA_TRY(cudaMemcpyAsync(h->d_fhdr, h->h_fhdr.data(), sizeof(hba::FitHdr) * h->n_arenas,
                                      cudaMemcpyHostToDevice, s));
@@ -806,6 +900,9 @@ void free_all(hba_t h) {
     cudaFree(h->d_fhdr);
     cudaFree(h->d_fpool);
     cudaFree(h->d_upool);
+    cudaFree(h->d_bmh);
+    cudaFree(h->d_bmF);
+    cudaFree(h->d_bmS);
     cudaFree(h->d_stage_f);
     cudaFree(h->d_stage_s);
     cudaFree(h->d_stage_o);
@@ -976,6 +1073,7 @@ hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8
     if (h->policy == HBA_POLICY_TLSF)  // needs no scratch
         return launch_tlsf(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     if (is_fit(h->policy)) return launch_fits(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
+    if (h->policy == HBA_POLICY_BITMASK) return launch_bitmask(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     uint32_t* base = static_scratch_address();
     if (!base) return HBA_ERR_CUDA;
     uint32_t* gi = base;
@@ -1025,6 +1123,23 @@ hba_status_t alloc_policy(hba_t h, int policy) {
             h->h_init[i].mask = h->h_tlsf[i].flmask;
         }
         if (cudaMalloc(&h->d_tlsf, sizeof(hba::TlsfLists) * n) != cudaSuccess) return HBA_ERR_OUT_OF_MEMORY;
+    } else if (policy == HBA_POLICY_BITMASK) {
+        h->h_bmh.resize(n);
+        uint64_t words = 0;
+        for (size_t i = 0; i < n; ++i) {
+            const uint32_t W = (h->h_init[i].G + 63u) / 64u;
+            if (W > hba::BM_MAX_WORDS) return HBA_ERR_INVALID_ARGUMENT;
+            h->h_bmh[i] = hba::BmHdr{words, W, 0u};
+            h->bm_wmax = std::max(h->bm_wmax, W);
+            h->h_init[i].mask = 0;
+            words += W;
+        }
+        if (cudaFuncSetAttribute(k_bitmask<BM_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(16u * hba::BM_MAX_WORDS)) != cudaSuccess)
+            return HBA_ERR_CUDA;
+        if (cudaMalloc(&h->d_bmh, sizeof(hba::BmHdr) * n) != cudaSuccess ||
+            cudaMalloc(&h->d_bmF, 8 * words) != cudaSuccess || cudaMalloc(&h->d_bmS, 8 * words) != cudaSuccess)
+            return HBA_ERR_OUT_OF_MEMORY;
     } else if (is_fit(policy)) {
         h->h_fhdr.assign(n, hba::FitHdr{1u, 0u, 0u, 0u});
         const uint32_t fit = policy == HBA_POLICY_FIRST_FIT ? hba::FIT_FIRST
@@ -1042,7 +1157,8 @@ hba_status_t alloc_policy(hba_t h, int policy) {
     return HBA_OK;
 }
 bool known_policy(int policy) {
-    return policy == HBA_POLICY_SEGFIT || policy == HBA_POLICY_TLSF || is_fit(policy);
+    return policy == HBA_POLICY_SEGFIT || policy == HBA_POLICY_TLSF || is_fit(policy) ||
+           policy == HBA_POLICY_BITMASK;
 }
 }  // namespace
 
@@ -1211,6 +1327,9 @@ hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
     if (h->d_fhdr) {  // the fits keep no record table: their lists give both figures
         k_fits_space<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_fhdr, h->d_fpool, h->d_upool,
                                                          h->n_arenas, h->d_largest, h->d_extent);
+    } else if (h->d_bmh) {  // nor do the bitmask pools: their bitmaps do
+        k_bm_space<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_bmh, h->d_bmF, h->d_bmS, h->n_arenas,
+                                                       h->d_largest, h->d_extent);
     } else if (h->d_tlsf) {
         k_largest_tlsf<<<(h->n_arenas + 255) / 256, 256>>>(h->d_arenas, h->d_tlsf, h->d_rec, h->n_arenas,
                                                            h->d_largest);
@@ -1219,7 +1338,7 @@ hba_status_t hba_stats(hba_t h, hba_stats_t* out) {
     }
     ++h->launches;
     HBA_CUDA_TRY(cudaGetLastError());
-    if (!h->d_fhdr) {
+    if (!h->d_fhdr && !h->d_bmh) {
         HBA_CUDA_TRY(cudaMemset(h->d_extent, 0, sizeof(uint32_t) * h->n_arenas));
         const uint64_t tiles = (h->total_granules + 64ull * 256 - 1) / (64ull * 256);
         const uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, 1), 8192);
@@ -1260,6 +1379,15 @@ hba_status_t hba_export_state(hba_t h, uint32_t arena, uint64_t* host_buf, size_
     HBA_CUDA_TRY(cudaDeviceSynchronize());
     Arena ar;
     HBA_CUDA_TRY(cudaMemcpy(&ar, h->d_arenas + arena, sizeof(Arena), cudaMemcpyDeviceToHost));
+    if (h->d_bmh) {
+        hba::BmHdr H;
+        HBA_CUDA_TRY(cudaMemcpy(&H, h->d_bmh + arena, sizeof(H), cudaMemcpyDeviceToHost));
+        std::vector<uint64_t> F(H.words), S(H.words);
+        HBA_CUDA_TRY(cudaMemcpy(F.data(), h->d_bmF + H.wbase, 8ull * H.words, cudaMemcpyDeviceToHost));
+        HBA_CUDA_TRY(cudaMemcpy(S.data(), h->d_bmS + H.wbase, 8ull * H.words, cudaMemcpyDeviceToHost));
+        *len = hba::bm_export(ar, H, F.data(), S.data(), host_buf, cap);
+        return HBA_OK;
+    }
     if (h->d_fhdr) {
         hba::FitHdr H;
         HBA_CUDA_TRY(cudaMemcpy(&H, h->d_fhdr + arena, sizeof(H), cudaMemcpyDeviceToHost));
@@ -1315,6 +1443,9 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     if (is_fit(h->policy))
         return launch_fits(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes, na_total,
                            d_out, s);
+    if (h->policy == HBA_POLICY_BITMASK)
+        return launch_bitmask(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes,
+                              na_total, d_out, s);
     if (h->m_threads == 32) {
         // warp mode: WPC arenas per CTA, per-warp dynamic shared memory
         const SmemLimits& L = g_limits[5];

@@ -18,8 +18,9 @@ HBA_FAIL = 0xFFFFFFFFFFFFFFFF
 HBA_POLICY_SEGFIT = 0
 HBA_POLICY_TLSF = 1
 HBA_POLICY_FIRST_FIT, HBA_POLICY_NEXT_FIT, HBA_POLICY_BEST_FIT = 2, 3, 4
+HBA_POLICY_BITMASK = 5
 POLICIES = {"segfit": HBA_POLICY_SEGFIT, "tlsf": HBA_POLICY_TLSF, "first": HBA_POLICY_FIRST_FIT,
-            "next": HBA_POLICY_NEXT_FIT, "best": HBA_POLICY_BEST_FIT}
+            "next": HBA_POLICY_NEXT_FIT, "best": HBA_POLICY_BEST_FIT, "bitmask": HBA_POLICY_BITMASK}
 
 
 def _lib():
@@ -189,7 +190,8 @@ class Allocator:
         """``ctas``: size of the batch's thread-block cluster (0 or 1: a
         separate gathering grid, then the engine; 2..8: the engine CTA plus
         gathering CTAs; see hba_set_shape).  ``policy``: "segfit" (§5.1),
-        "tlsf" (§5.2), or the sequential fits "first", "next", "best" (§4)."""
+        "tlsf" (§5.2), the sequential fits "first", "next", "best" (§4),
+        or the bitmask pool "bitmask" (§3.2)."""
         self.policy = policy
         self.h = hba_create(arena_bytes, min_block, POLICIES[policy], max_batch)
         self.arena_bytes = arena_bytes - arena_bytes % min_block

@@ -436,6 +436,12 @@ def usage(n_ops=5000, slots=64, batch=1, arena=4 * GiB):
                     "log-uniform 1 kB-16 MB), one op per batch")
 
 
+def objects(n_ops=200_000, batch=256, pool=1 * MiB):
+    return Workload("objects-1MiB", pool, 8, lambda: TinyRandom(n_ops=n_ops, batch=batch, p_free=0.45, lo=8, hi=512),
+                    "1 MiB pool of 8-byte units, 200,000 ops in batches of 256, 45% free, objects log-uniform "
+                    "8-512 B")
+
+
 def drain(client, alloc_batch):
     """Run a client to completion against ``alloc_batch(frees, sizes) -> out``.
 

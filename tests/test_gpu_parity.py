@@ -805,3 +805,150 @@ def test_fits_multi_arena(gpu_lib):
         for i in range(n):
             assert np.array_equal(m.export_state(i), orcs[i].export_state()), (fit, i)
         m.close()
+
+
+# ---- bitmask pool (§3.2) -------------------------------------------------------
+
+
+def _run_bitmask(trace, o, pool, unit, state_every=0):
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import Allocator
+
+    dev = torch.device("cuda")
+    lock = oracle.BitmaskOracle(pool, unit) if state_every else None
+    with Allocator(pool, unit, policy="bitmask") as a:
+        for b, (f, s, out, st) in enumerate(trace):
+            dst = torch.empty(f.size, dtype=torch.uint8, device=dev)
+            go = a.step(to_dev(f, dev) if f.size else None, to_dev(s, dev) if s.size else None, status=dst)
+            if s.size:
+                i = first_diff(from_dev(go), out)
+                assert i is None, f"batch {b}: alloc {i}"
+            assert first_diff(from_dev(dst), st) is None, f"batch {b}: free status"
+            if lock is not None:
+                lock.batch(f, s)
+                if b % state_every == 0:
+                    assert np.array_equal(a.export_state(), lock.export_state()), f"batch {b}: state"
+        assert np.array_equal(a.export_state(), o.export_state()), "final state"
+        got, ref = a.stats(), o.stats()
+        for k in ("alloc_ok", "alloc_fail", "free_ok", "free_fail", "used_bytes", "used_blocks", "blocks",
+                  "requested_bytes", "largest_free"):
+            assert got[k] == ref[k], (k, got[k], ref[k])
+        assert got["extent_bytes"] == ref["extent"]
+
+
+def test_bitmask_worked_examples(gpu_lib):
+    import sys
+
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator
+
+    sys.path.insert(0, __import__("os").path.dirname(__file__))
+    from test_oracle_pins import load_bitmask_golden
+
+    dev = torch.device("cuda")
+    for case in load_bitmask_golden():
+        with Allocator(case["pool"], case["unit"], policy="bitmask") as a:
+            for frees, sizes, expect, expect_st in case["batches"]:
+                f = np.array(frees, np.uint64)
+                s_ = np.array(sizes, np.uint64)
+                st = torch.empty(f.size, dtype=torch.uint8, device=dev)
+                out = a.step(to_dev(f, dev) if f.size else None, to_dev(s_, dev) if s_.size else None, status=st)
+                if s_.size:
+                    assert [int(x) for x in from_dev(out)] == expect, case["name"]
+                assert [int(x) for x in from_dev(st)] == expect_st, case["name"]
+            assert [int(x) for x in a.export_state()] == case["final"], case["name"]
+
+
+@pytest.mark.parametrize("pool,unit,batch", [(1 << 20, 8, 256), (1000 * 8, 8, 16), (786_432 * 16, 16, 2048)])
+def test_bitmask_objects(gpu_lib, pool, unit, batch):
+    """Pools of 131,072 units, of 1,000 units (a partial last word), and of
+    the largest size a pool may have (786,432 units): every result, the state
+    and the counters against the oracle."""
+    import oracle
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.Workload("objects", pool, unit, lambda: W.TinyRandom(n_ops=30 * batch if batch > 16 else 3000, batch=batch,
+                                                                p_free=0.45, lo=1, hi=64 * unit + 8))
+    o = oracle.BitmaskOracle(pool, unit)
+    cl = wl.make()
+    trace = []
+    while (b := cl.next_batch()) is not None:
+        out, st = o.batch(*b)
+        cl.feed(out)
+        trace.append((b[0], b[1], out, st))
+    o2 = oracle.BitmaskOracle(pool, unit)
+    for f, s, _, _ in trace:
+        o2.batch(f, s)
+    _run_bitmask(trace, o2, pool, unit, state_every=max(1, len(trace) // 8))
+
+
+def test_bitmask_invalid_frees_and_pool_limit(gpu_lib):
+    """Misaligned, interior, repeated and out-of-pool frees; a pool one unit
+    above the limit is refused at create."""
+    import oracle
+    from paper_2405_07079_gb300 import Allocator, HbaError
+
+    rng = np.random.default_rng(8)
+    pool, unit = 4096 * 8, 8
+    o = oracle.BitmaskOracle(pool, unit)
+    held, trace = [], []
+    for _ in range(120):
+        frees = []
+        for _ in range(int(rng.integers(0, 20))):
+            if held and rng.random() < 0.7:
+                h = held[int(rng.integers(0, len(held)))]
+                frees.append(h + int(rng.choice([0, 0, 0, unit, 3])))
+            else:
+                frees.append(int(rng.integers(0, pool // unit + 8)) * unit)
+        sizes = rng.integers(0, 70 * unit, int(rng.integers(0, 30))).astype(np.uint64)
+        f = np.array(frees, np.uint64)
+        out, st = o.batch(f, sizes)
+        trace.append((f, sizes, out, st))
+        held = [h for h in held if h not in frees] + [int(x) for x in out if x != FAIL]
+    o2 = oracle.BitmaskOracle(pool, unit)
+    for f, s, _, _ in trace:
+        o2.batch(f, s)
+    _run_bitmask(trace, o2, pool, unit, state_every=10)
+    with pytest.raises(HbaError):
+        Allocator((786_432 + 1) * 8, 8, policy="bitmask")
+
+
+def test_bitmask_multi_pool(gpu_lib):
+    """Independent pools of different sizes, one CTA each, in one launch."""
+    import torch
+
+    import oracle
+    from paper_2405_07079_gb300 import MultiAllocator
+    from paper_2405_07079_gb300 import workloads as W
+
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(44)
+    n = 29
+    sizes_a = (rng.integers(64, 20_000, n) * 8).astype(np.uint64)
+    m = MultiAllocator(sizes_a, 8, max_total_frees=1 << 16, policy="bitmask")
+    orcs = [oracle.BitmaskOracle(int(x), 8) for x in sizes_a]
+    clients = [W.TinyRandom(n_ops=10**9, batch=int(rng.integers(1, 200)), p_free=0.45, lo=1, hi=520,
+                            seed=W.BASE_SEED + 700 + i) for i in range(n)]
+    for b in range(10):
+        fr, sz, exp_o, exp_s = [], [], [], []
+        for i in range(n):
+            f, s_ = clients[i].next_batch()
+            ro, rs = orcs[i].batch(f, s_)
+            clients[i].feed(ro)
+            fr.append(f); sz.append(s_); exp_o.append(ro); exp_s.append(rs)
+        frow = np.concatenate([[0], np.cumsum([x.size for x in fr])]).astype(np.uint32)
+        arow = np.concatenate([[0], np.cumsum([x.size for x in sz])]).astype(np.uint32)
+        F = np.concatenate(fr).astype(np.uint64)
+        S = np.concatenate(sz).astype(np.uint64)
+        out = torch.empty(max(1, S.size), dtype=torch.int64, device=dev)
+        st = torch.empty(max(1, F.size), dtype=torch.uint8, device=dev)
+        m.step(to_dev(frow.view(np.int32), dev), to_dev(F, dev), to_dev(arow.view(np.int32), dev),
+               to_dev(S, dev), out, st)
+        assert np.array_equal(from_dev(out)[:S.size], np.concatenate(exp_o)), f"batch {b}"
+        assert np.array_equal(from_dev(st)[:F.size], np.concatenate(exp_s))
+    for i in range(n):
+        assert np.array_equal(m.export_state(i), orcs[i].export_state()), i
+    m.close()
