@@ -93,6 +93,7 @@ __device__ __forceinline__ uint64_t bm_run_starts(uint64_t lo, uint64_t hi, uint
 
 template <int NT>
 struct BmSmem {
+    uint64_t sz[NT];  // the current group of request sizes
     uint32_t rover, kfail, found, pad;
     int64_t cnt[6];  // alloc_ok, alloc_fail, free_ok, free_fail, used units, requested bytes
     uint32_t err;
@@ -169,7 +170,12 @@ __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint6
     // ---- allocations, one by one, each a CTA-wide run search
     const uint64_t P = (uint64_t)N << lg;
     for (uint32_t i = a0; i < a1; ++i) {
-        const uint64_t sz = sizes[i];
+        if ((i - a0) % NT == 0) {  // the next NT sizes, loaded together
+            __syncthreads();
+            if (i + t < a1) S_.sz[t] = sizes[i + t];
+            __syncthreads();
+        }
+        const uint64_t sz = S_.sz[(i - a0) % NT];
         const uint32_t k = (sz == 0 || sz > P) ? 0u : (uint32_t)((sz + (1ull << lg) - 1) >> lg);
         if (k == 0 || k > BM_MAX_RUN || k > N || k >= S_.kfail) {  // uniform: S_.kfail changes behind barriers
             if (t == 0) {

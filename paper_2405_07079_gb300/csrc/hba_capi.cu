@@ -451,15 +451,16 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_fits(Arena* ars, hba::FitHdr* hdr, hba::FitBlk* fpool, hba::FitBlk* upool,
                                             uint32_t n_arenas, const uint32_t* frow, const uint64_t* frees,
                                             uint8_t* fstat, uint32_t nf, const uint32_t* arow, const uint64_t* sizes,
-                                            uint64_t* out, uint32_t na) {
+                                            uint64_t* out, uint32_t na, uint32_t res_words) {
     __shared__ hba::FitSmem<NT> S;
+    extern __shared__ __align__(16) hba::FitBlk fit_res[];  // 2 x FIT_RES entries, or none
     for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
         Arena& ar = ars[a];
         const uint64_t base = ar.rec_base + a;
         const uint32_t f0 = frow ? frow[a] : 0u, f1 = frow ? frow[a + 1] : nf;
         const uint32_t a0 = arow ? arow[a] : 0u, a1 = arow ? arow[a + 1] : na;
-        hba::fit_arena<NT>(S, ar, hdr[a], fpool + base, upool + base, ar.G + 1, frees, fstat, f0, f1, sizes, out,
-                           a0, a1);
+        hba::fit_arena<NT>(S, ar, hdr[a], fpool + base, upool + base, ar.G + 1, res_words ? fit_res : nullptr, frees,
+                           fstat, f0, f1, sizes, out, a0, a1);
     }
 }
 
@@ -735,20 +736,27 @@ bool is_fit(int policy) {
 }
 
 // A sequential-fit batch: one CTA of FIT_NT threads per arena.
-constexpr int FIT_NT = 256;
+#ifndef HBA_FIT_NT
+#define HBA_FIT_NT 256
+#endif
+constexpr int FIT_NT = HBA_FIT_NT;
 hba_status_t launch_fits(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint8_t* st,
                          const uint32_t* arow, const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
     const uint32_t n = h->n_arenas;
     const uint32_t sms = g_limits[5].sms ? g_limits[5].sms : 152u;
     const uint32_t grid = std::min(n, 8u * sms);
-    k_fits<FIT_NT><<<grid, FIT_NT, 0, s>>>(h->d_arenas, h->d_fhdr, h->d_fpool, h->d_upool, n, frow, frees, st, nf,
-                                           arow, sizes, out, na);
+    const uint32_t res = (uint32_t)(2 * sizeof(hba::FitBlk) * hba::FIT_RES);  // shared-memory arrays
+    k_fits<FIT_NT><<<grid, FIT_NT, res, s>>>(h->d_arenas, h->d_fhdr, h->d_fpool, h->d_upool, n, frow, frees, st, nf,
+                                             arow, sizes, out, na, res / 4);
     ++h->launches;
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
 
 // A bitmask batch: one CTA of BM_NT threads per pool.
-constexpr int BM_NT = 256;
+#ifndef HBA_BM_NT
+#define HBA_BM_NT 256
+#endif
+constexpr int BM_NT = HBA_BM_NT;
 hba_status_t launch_bitmask(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint8_t* st,
                             const uint32_t* arow, const uint64_t* sizes, uint32_t na, uint64_t* out,
                             cudaStream_t s) {
@@ -1148,6 +1156,9 @@ hba_status_t alloc_policy(hba_t h, int policy) {
             h->h_fhdr[i].fit = fit;
             h->h_init[i].mask = 0;
         }
+        if (cudaFuncSetAttribute(k_fits<FIT_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * sizeof(hba::FitBlk) * hba::FIT_RES)) != cudaSuccess)
+            return HBA_ERR_CUDA;
         const size_t entries = h->total_granules + n;
         if (cudaMalloc(&h->d_fhdr, sizeof(hba::FitHdr) * n) != cudaSuccess ||
             cudaMalloc(&h->d_fpool, sizeof(hba::FitBlk) * entries) != cudaSuccess ||

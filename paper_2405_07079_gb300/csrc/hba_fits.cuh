@@ -60,8 +60,17 @@ inline size_t fit_export(const Arena& ar, const FitHdr& H, const FitBlk* fa, con
 }
 
 #ifndef HBA_EMULATE
+// Free and used arrays are worked on in shared memory when the batch cannot
+// grow either past FIT_RES entries (frees add at most one free entry each,
+// allocations at most one used entry each).
+#ifndef HBA_FIT_RES
+#define HBA_FIT_RES 4096u
+#endif
+constexpr uint32_t FIT_RES = HBA_FIT_RES;
+
 template <int NT>
 struct FitSmem {
+    uint64_t wz[NT];        // the current group of request sizes
     uint32_t nf, nu, rover, cap;
     uint32_t maxz;          // largest free block (valid when !dirty)
     uint32_t dirty;
@@ -182,12 +191,23 @@ __device__ uint32_t fit_pick(FitSmem<NT>& S, const FitBlk* fa, uint32_t s, uint3
 // One arena's batch.  fa / ua: the arena's free and used arrays (capacity
 // cap each); H: its header.
 template <int NT>
-__device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* fa, FitBlk* ua, uint32_t cap,
-                          const uint64_t* frees, uint8_t* fstat, uint32_t f0, uint32_t f1, const uint64_t* sizes,
-                          uint64_t* out, uint32_t a0, uint32_t a1) {
+__device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, FitBlk* gua, uint32_t gcap,
+                          FitBlk* res, const uint64_t* frees, uint8_t* fstat, uint32_t f0, uint32_t f1,
+                          const uint64_t* sizes, uint64_t* out, uint32_t a0, uint32_t a1) {
     const uint32_t t = threadIdx.x;
     const uint64_t A = ar.arena_bytes;
     const uint32_t lg = ar.lg, fit = H.fit;
+    // the arrays in shared memory (res: 2 x FIT_RES entries) when they stay small enough
+    const uint32_t nf0 = H.nfree, nu0 = H.nused;
+    const bool resident = res != nullptr && (uint64_t)nf0 + (f1 - f0) + 1 <= FIT_RES &&
+                          (uint64_t)nu0 + (a1 - a0) <= FIT_RES;
+    FitBlk* fa = resident ? res : gfa;
+    FitBlk* ua = resident ? res + FIT_RES : gua;
+    const uint32_t cap = resident ? FIT_RES : gcap;
+    if (resident) {
+        for (uint32_t q = t; q < nf0; q += NT) fa[q] = gfa[q];
+        for (uint32_t q = t; q < nu0; q += NT) ua[q] = gua[q];
+    }
     if (t == 0) {
         S.nf = H.nfree;
         S.nu = H.nused;
@@ -267,14 +287,21 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* fa, FitB
         __syncthreads();
     }
     // ---- allocations (Algorithm 1 on the fit's candidate), one by one; the
-    // requests that the largest free block cannot serve fail together
-    for (uint32_t i = a0; i < a1;) {
+    // requests that the largest free block cannot serve fail together.
+    // Sizes come NT at a time into shared memory; a window never crosses
+    // such a group.
+    for (uint32_t c0 = a0; c0 < a1; c0 += NT) {
+    const uint32_t cend = a1 - c0 < (uint32_t)NT ? a1 : c0 + NT;
+    __syncthreads();
+    if (c0 + t < cend) S.wz[t] = sizes[c0 + t];
+    __syncthreads();
+    for (uint32_t i = c0; i < cend;) {
         if (S.dirty) fit_refresh_max<NT>(S, fa);
-        const uint32_t n = a1 - i < (uint32_t)NT ? a1 - i : (uint32_t)NT;
+        const uint32_t n = cend - i;
         uint32_t sgr = 0;
         bool can = false;
         if (t < n) {
-            const uint64_t sz = sizes[i + t];
+            const uint64_t sz = S.wz[i - c0 + t];
             if (sz != 0 && sz <= A) {
                 sgr = (uint32_t)((sz + (1ull << lg) - 1) >> lg);
                 can = sgr <= S.maxz;
@@ -317,7 +344,7 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* fa, FitB
                 S.rover = b.a + s;
                 ++S.cnt[0];
                 S.cnt[4] += s;
-                S.cnt[6] += (int64_t)sizes[i + e];
+                S.cnt[6] += (int64_t)S.wz[i - c0 + e];
                 S.dirty = 1;
             }
             __syncthreads();
@@ -336,6 +363,12 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* fa, FitB
             __syncthreads();
         }
         i += e < n ? e + 1 : n;
+    }
+    }
+    if (resident) {
+        __syncthreads();
+        for (uint32_t q = t; q < S.nf; q += NT) gfa[q] = fa[q];
+        for (uint32_t q = t; q < S.nu; q += NT) gua[q] = ua[q];
     }
     if (t == 0) {
         H.nfree = S.nf;
