@@ -76,7 +76,7 @@ struct FitSmem {
     uint32_t dirty;
     uint32_t v[8];          // broadcast slots
     unsigned long long best;
-    int64_t cnt[7];         // alloc_ok, alloc_fail, free_ok, free_fail, usedg, (unused), requested
+    int64_t cnt[6];         // alloc_ok, alloc_fail, free_ok, free_fail, used granules, requested bytes
     uint32_t err;
 };
 
@@ -215,7 +215,7 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, Fit
         S.cap = cap;
         S.dirty = 1;
         S.err = 0;
-        for (int q = 0; q < 7; ++q) S.cnt[q] = 0;
+        for (int q = 0; q < 6; ++q) S.cnt[q] = 0;
     }
     __syncthreads();
     // ---- frees (Algorithm 2), one by one
@@ -344,7 +344,7 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, Fit
                 S.rover = b.a + s;
                 ++S.cnt[0];
                 S.cnt[4] += s;
-                S.cnt[6] += (int64_t)S.wz[i - c0 + e];
+                S.cnt[5] += (int64_t)S.wz[i - c0 + e];
                 S.dirty = 1;
             }
             __syncthreads();
@@ -381,7 +381,7 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, Fit
         ar.used_g += S.cnt[4];
         ar.used_blocks = S.nu;
         ar.blocks = (int64_t)S.nu + S.nf;
-        ar.requested += S.cnt[6];
+        ar.requested += S.cnt[5];
         if (S.err && !ar.err) ar.err = S.err;
     }
     __syncthreads();

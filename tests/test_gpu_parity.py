@@ -952,3 +952,46 @@ def test_bitmask_multi_pool(gpu_lib):
     for i in range(n):
         assert np.array_equal(m.export_state(i), orcs[i].export_state()), i
     m.close()
+
+
+@pytest.mark.parametrize("policy", ["segfit", "tlsf", "first", "next", "best", "bitmask"])
+def test_reset_and_host_pipeline_for_every_policy(gpu_lib, policy):
+    """hba_reset returns every policy to its initial state: a trace replayed
+    after a reset, through the pipelined host-buffer call, gives the same
+    results and state as the first pass through device buffers."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator, hba_step_host_async
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.objects(n_ops=3000, batch=64) if policy == "bitmask" else W.tiny(n_ops=3000)
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    with Allocator(wl.arena, wl.min_block, policy=policy) as a:
+        cl = wl.make()
+        first = []
+        while (b := cl.next_batch()) is not None:
+            f, s_ = b
+            st = torch.empty(f.size, dtype=torch.uint8, device=dev)
+            out = a.step(to_dev(f, dev) if f.size else None, to_dev(s_, dev) if s_.size else None, status=st)
+            o = from_dev(out) if s_.size else np.zeros(0, np.uint64)
+            cl.feed(o)
+            first.append((f, s_, o, from_dev(st)))
+        state = a.export_state()
+        a.reset()
+        keep, outs = [], []
+        for f, s_, _, _ in first:
+            hf = torch.from_numpy(np.ascontiguousarray(f).view(np.int64)).pin_memory()
+            hs = torch.from_numpy(np.ascontiguousarray(s_).view(np.int64)).pin_memory()
+            ho = torch.empty(max(1, s_.size), dtype=torch.int64).pin_memory()
+            hst = torch.empty(max(1, f.size), dtype=torch.uint8).pin_memory()
+            keep += [hf, hs, ho, hst]
+            hba_step_host_async(a.h, hf.data_ptr() if f.size else 0, f.size, hst.data_ptr() if f.size else 0,
+                                hs.data_ptr() if s_.size else 0, s_.size, ho.data_ptr() if s_.size else 0,
+                                int(stream.cuda_stream))
+            outs.append((ho, hst))
+        stream.synchronize()
+        for (f, s_, o, st), (ho, hst) in zip(first, outs):
+            assert np.array_equal(ho.numpy().view(np.uint64)[:s_.size], o)
+            assert np.array_equal(hst.numpy()[:f.size], st)
+        assert np.array_equal(a.export_state(), state)
