@@ -1,4 +1,7 @@
-"""CPU oracle of the segregated-fit allocator (§5.1, Algorithms 4 and 5).
+"""CPU oracles of the allocators of the paper: segregated fit (§5.1,
+Algorithms 4 and 5, the evaluated one), two-level segregated fit (§5.2), the
+sequential fits on address-sorted lists (§3.1, §4) and the bitmask pool
+(§3.2).
 
 TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py`` may import this package.  The
@@ -7,17 +10,24 @@ code: the only module both sides use is the seeded request generator
 (``paper_2405_07079_gb300.workloads``), which holds none of the allocator's
 arithmetic.
 
-Two independent statements of the same policy live here:
+Each policy has two independent statements that pin each other:
 
 * ``Oracle`` -- ``segfit_oracle.c``: the paper's own structures (hash table
   keyed by address, doubly linked LIFO free lists per power-of-two class, a
-  64-bit availability bitmap), Algorithms 4 and 5 step by step.
+  64-bit availability bitmap), Algorithms 4 and 5 step by step; with
+  ``policy="tlsf"`` the same algorithms with the two-tier lookup of §5.2.
+  ``space()`` reports the largest free block and the extent (Fig. 4).
 * ``interval_ref.IntervalAllocator`` -- a brute-force restatement over a
-  sorted list of intervals with push stamps, used on tiny arenas to pin the
-  first one (see that module's header).
+  sorted list of intervals with push stamps (both policies), used on tiny
+  arenas to pin the first one (see that module's header).
+* ``HalOracle`` -- ``hal_oracle.c``: first, next and best fit on sorted free
+  and used lists with partial deallocation; pinned by
+  ``fits_ref.GranuleFits``, a granule -> owner map.
+* ``BitmaskOracle`` -- ``bitmask_oracle.c``: the bitmask pool; pinned by
+  ``fits_ref.BlockListPool``, a list of in-use intervals.
 
-Parity of both against the paper's experiment (Fig. 3 / Fig. 4 of §6) is
-unpinned: the paper prints no data for those figures.
+Parity against the paper's experiment (Fig. 3 / Fig. 4 of §6) is unpinned:
+the paper prints no data for those figures.
 """
 from __future__ import annotations
 
