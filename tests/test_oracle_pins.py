@@ -864,3 +864,36 @@ def test_property_hypothesis():
         assert [int(x) for x in o.export_state()] == r.export_state()
 
     prop()
+
+
+def test_property_hypothesis_other_policies():
+    """Random op sequences (hypothesis) for TLSF, the three sequential fits
+    (frees of starts and interior granules) and the bitmask pool: each oracle
+    equals its independent restatement op for op and in its final state."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    from oracle.fits_ref import BlockListPool, GranuleFits
+
+    op = st.one_of(st.tuples(st.just("a"), st.integers(0, 600)),
+                   st.tuples(st.just("f"), st.integers(0, 40).map(lambda g: g * 16)),
+                   st.tuples(st.just("f"), st.integers(0, 700)))
+
+    def pair_run(o, r, batches):
+        for b in batches:
+            frees = [v for k, v in b if k == "f"]
+            sizes = [v for k, v in b if k == "a"]
+            oo, os_ = o.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
+            ro, rs = r.batch(frees, sizes)
+            assert [int(x) for x in oo] == list(ro) and [int(x) for x in os_] == list(rs)
+        assert [int(x) for x in o.export_state()] == r.export_state()
+
+    @hyp.settings(max_examples=150, deadline=None)
+    @hyp.given(st.lists(st.lists(op, max_size=6), max_size=10))
+    def prop(batches):
+        A, mb = 512, 16
+        pair_run(oracle.Oracle(A, mb, "tlsf"), IntervalAllocator(A, mb, "tlsf"), batches)
+        for fit in ("first", "next", "best"):
+            pair_run(oracle.HalOracle(A, mb, fit), GranuleFits(A, mb, fit), batches)
+        pair_run(oracle.BitmaskOracle(A, 8), BlockListPool(A, 8), batches)
+
+    prop()
