@@ -126,11 +126,15 @@ typedef struct {
     uint64_t free_ok, free_fail;     /* frees applied / rejected */
     uint64_t used_bytes;             /* bytes in in-use blocks (rounded sizes) */
     uint64_t used_blocks;            /* in-use blocks */
-    uint64_t blocks;                 /* all blocks, in use or free */
+    uint64_t blocks;                 /* all blocks, in use or free (bitmask pool: in-use
+                                        blocks and maximal free runs) */
     uint64_t requested_bytes;        /* sum of the sizes of served requests */
     uint64_t free_bytes;             /* arena bytes not in use */
-    uint64_t largest_free;           /* size of the largest free block */
-    uint64_t bitmask;                /* availability bitmap (bit k: list k non-empty); arena 0 */
+    uint64_t largest_free;           /* size of the largest free block (bitmask pool: the
+                                        longest free run) */
+    uint64_t bitmask;                /* availability bitmap (bit k: list k non-empty), arena 0;
+                                        TLSF: the first level; 0 for the sequential fits and
+                                        the bitmask pool */
     uint64_t arena_bytes;            /* managed bytes (sum over arenas) */
     uint64_t extent_bytes;           /* end of the highest in-use block, 0 when none (sum
                                         over arenas): the part of the arena that has to be
