@@ -9,8 +9,9 @@
 // of all; a run never wraps past the end of the pool.
 //
 // One CTA per pool.  Both bitmaps are copied into shared memory for the
-// batch and written back at the end.  Frees (one at a time, by thread 0) are
-// a few word operations each.  An allocation is a CTA-wide scan: thread t
+// batch and written back at the end.  Frees are applied one at a time by
+// lane 0 of warp 0 (the warp loads 32 offsets at a time), a few word
+// operations each.  An allocation is a CTA-wide scan: thread t
 // takes word w and computes the mask of starts in w that have k free units,
 // across w and w + 1 (128-bit AND of the shifted words, built by doubling);
 // the lowest start is an atomicMin, and the scan stops after the first group
