@@ -13,9 +13,9 @@
  *
  * Readings (each one is exercised by a named test):
  *   K1  allocation of `size` bytes needs k = ceil(size / unit) consecutive
- *       free units; size 0, or k above 64 units (the pool serves small
- *       objects, §3.2 "a pool of small memory chunks") or above the pool,
- *       fails.
+ *       free units, for any k up to the whole pool (§3.2's own example: 1 kB
+ *       at 8-byte units is a string of 128 free bits); size 0, or more units
+ *       than the pool holds, fails.
  *   K2  the run is found by next fit, as §3.2 proposes: of the positions p
  *       where units [p, p + k) are all free, the lowest p at or after the
  *       rover, else (wrapping) the lowest p of all; the rover, 0 at start,
@@ -36,7 +36,6 @@
 #include <string.h>
 
 #define BM_FAIL UINT64_MAX
-#define BM_MAX_UNITS 64
 
 typedef struct bm {
     uint64_t units, unit;     /* pool = units * unit bytes */
@@ -66,24 +65,27 @@ void bm_destroy(bm* b) {
     free(b);
 }
 
-static int run_free(const bm* b, uint64_t p, uint64_t k) {
-    for (uint64_t q = p; q < p + k; q++)
-        if (!b->free_bit[q]) return 0;
-    return 1;
+/* The lowest p in [lo, hi) such that units [p, p + k) are all free and
+ * p + k <= units, or UINT64_MAX: walk the units from lo, counting the free
+ * units in a row; the first time the count reaches k, the string of k set
+ * bits starts k - 1 units back. */
+static uint64_t first_run(const bm* b, uint64_t lo, uint64_t hi, uint64_t k) {
+    uint64_t run = 0;
+    for (uint64_t q = lo; q < b->units; q++) {
+        run = b->free_bit[q] ? run + 1 : 0;
+        if (run == k) return q + 1 - k < hi ? q + 1 - k : UINT64_MAX;
+    }
+    return UINT64_MAX;
 }
 
 uint64_t bm_malloc(bm* b, uint64_t size) {
     const uint64_t k = size ? (size + b->unit - 1) / b->unit : 0;      /* K1 */
-    if (size == 0 || size > b->units * b->unit || k > BM_MAX_UNITS || k > b->units) {
+    if (size == 0 || size > b->units * b->unit || k > b->units) {
         b->alloc_fail++;
         return BM_FAIL;
     }
-    uint64_t p = UINT64_MAX;                                           /* K2 */
-    for (uint64_t q = b->rover; q + k <= b->units; q++)
-        if (run_free(b, q, k)) { p = q; break; }
-    if (p == UINT64_MAX)
-        for (uint64_t q = 0; q + k <= b->units && q < b->rover; q++)
-            if (run_free(b, q, k)) { p = q; break; }
+    uint64_t p = first_run(b, b->rover, b->units, k);                  /* K2 */
+    if (p == UINT64_MAX) p = first_run(b, 0, b->rover, k);
     if (p == UINT64_MAX) { b->alloc_fail++; return BM_FAIL; }
     for (uint64_t q = p; q < p + k; q++) b->free_bit[q] = 0;
     b->start_bit[p] = 1;

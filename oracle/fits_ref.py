@@ -123,7 +123,7 @@ class BlockListPool:
 
     def malloc(self, size: int) -> int:
         k = -(-size // self.unit) if size else 0
-        if size == 0 or size > self.N * self.unit or k > 64 or k > self.N:
+        if size == 0 or size > self.N * self.unit or k > self.N:
             return FAIL
         order = list(range(self.rover, self.N)) + list(range(0, self.rover))
         p = next((q for q in order if self._free_at(q, k)), None)

@@ -737,12 +737,13 @@ def test_bitmask_worked_example(make, case):
     assert [int(x) for x in a.export_state()] == case["final"], case["name"]
 
 
-@pytest.mark.parametrize("mutant", ["first_fit", "runs_wrap", "free_to_next_free", "k_limit"])
+@pytest.mark.parametrize("mutant", ["first_fit", "runs_wrap", "free_to_next_free", "capped_at_64"])
 def test_bitmask_worked_examples_catch_mutants(monkeypatch, mutant):
     """Plausible mistakes planted in the block-list statement, each caught
     by a worked example: first fit instead of next fit, runs that wrap past
     the pool's end, a free that releases units up to the next free unit
-    (ignoring block starts), and a size limit one unit off."""
+    (ignoring block starts), and objects capped at 64 units (one 128-bit
+    window), which §3.2's 1 kB = 128-unit example rules out."""
     from oracle import fits_ref as fr
 
     cls = fr.BlockListPool
@@ -773,9 +774,9 @@ def test_bitmask_worked_examples_catch_mutants(monkeypatch, mutant):
             return r
         monkeypatch.setattr(cls, "free", free)
     else:
-        def malloc(self, size):  # the 64-unit limit off by one
+        def malloc(self, size):  # runs capped at 64 units
             k = -(-size // self.unit) if size else 0
-            if size == 0 or size > self.N * self.unit or k > 65 or k > self.N:
+            if size == 0 or size > self.N * self.unit or k > 64 or k > self.N:
                 return fr.FAIL
             order = list(range(self.rover, self.N)) + list(range(0, self.rover))
             p = next((q for q in order if self._free_at(q, k)), None)
@@ -814,7 +815,8 @@ def test_bitmask_oracle_equals_block_list_random(seed):
                 frees.append(h + (u if rng.random() < 0.15 else 0))
             else:
                 frees.append(int(rng.integers(0, N + 3)) * u + int(rng.choice([0, 0, 4])))
-        sizes = [int(rng.integers(0, min(N, 70) * u + 2)) for _ in range(int(rng.integers(0, 6)))]
+        sizes = [int(rng.integers(0, (min(N, 70) if rng.random() < 0.7 else N) * u + 2))
+                 for _ in range(int(rng.integers(0, 6)))]
         oo, os_ = o.batch(np.array(frees, np.uint64), np.array(sizes, np.uint64))
         ro, rs = r.batch(frees, sizes)
         assert [int(x) for x in oo] == ro and [int(x) for x in os_] == rs
