@@ -51,10 +51,11 @@
  * min_block.
  *
  * HBA_POLICY_BITMASK is the bitmask pool of §3.2: one bit per min_block unit
- * says whether the unit is free.  An allocation of up to 64 units takes k
- * consecutive free units by next fit (the lowest start at or after the end
- * of the last allocation, else the lowest start of all; runs do not wrap);
- * larger requests fail.  A second out-of-band bitmap marks the first unit of
+ * says whether the unit is free.  An allocation of k = ceil(size / unit)
+ * units (any k up to the pool; §3.2 finds 128 free bits for 1 kB at 8-byte
+ * units) takes k consecutive free units by next fit (the lowest start at or
+ * after the end of the last allocation, else the lowest start of all; runs
+ * do not wrap).  A second out-of-band bitmap marks the first unit of
  * each in-use block; a free must name such a unit and releases the units up
  * to the next marked or free unit.  A pool holds at most 786,432 units
  * (HBA_ERR_INVALID_ARGUMENT at create); each runs on one CTA with both
@@ -244,8 +245,10 @@ hba_status_t hba_step_host_async(hba_t h, const uint64_t* h_frees, uint32_t nf, 
  * calls whose work overlaps on the GPU (different streams without ordering
  * between them) race on it and corrupt each other's results, so order them.
  * Nothing in the array needs clearing between calls: each call writes every
- * word it reads.  The first call on a device looks up the array's device
- * address with that device current (HBA_ERR_CUDA if that fails); make that
+ * word it reads.  The first call in each CUDA context (the device's
+ * primary context, and again after cudaDeviceReset or under another
+ * context) looks up the array's device address in that context and keeps it
+ * for the context's later calls (HBA_ERR_CUDA if the lookup fails); make that
  * first call before any stream capture. */
 hba_status_t hba_step_static(hba_t h, const uint64_t* d_frees, uint32_t nf, uint8_t* d_status,
                              const uint64_t* d_sizes, uint32_t na, uint64_t* d_out_offsets,
@@ -289,6 +292,31 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
                             uint32_t nf_total, const uint32_t* d_alloc_rowptr,
                             const uint64_t* d_sizes, uint32_t na_total, uint64_t* d_out,
                             uint8_t* d_free_status, hba_stream_t stream);
+
+/* hba_multi_create with staging for hba_multi_step_host_async: two slots,
+ * each for max_total_frees frees, max_total_allocs allocations and both
+ * row-pointer arrays, allocated here (never by the calls).  max_total_allocs
+ * 0 = no staging (then it is hba_multi_create). */
+hba_status_t hba_multi_create_ex(uint32_t n_arenas, const uint64_t* arena_bytes, uint64_t min_block,
+                                 int policy, uint32_t max_total_frees, uint32_t max_total_allocs,
+                                 hba_t* out);
+
+/* hba_multi_step from HOST buffers: the batch of every arena (same CSR
+ * layout, §5.1 Algorithms 5 then 4 per arena), with the row pointers,
+ * frees and sizes in host memory and the offsets (and free statuses, if
+ * h_free_status is not NULL) written back to host memory.  Pipelined like
+ * hba_step_host_async: the copies go through the handle's two staging slots
+ * on internal streams, so call k's input copies overlap call k-1's kernels
+ * and its result copies overlap call k+1's; `stream` waits for the results,
+ * so synchronising it completes the call.  Returns at once; the host
+ * buffers must stay untouched (inputs) and unread (outputs) until then, and
+ * should be pinned for the copies to be asynchronous.  HBA_ERR_INVALID_
+ * ARGUMENT if the handle has no staging (hba_multi_create) or nf_total /
+ * na_total exceed max_total_frees / max_total_allocs. */
+hba_status_t hba_multi_step_host_async(hba_t h, const uint32_t* h_free_rowptr, const uint64_t* h_frees,
+                                       uint32_t nf_total, const uint32_t* h_alloc_rowptr,
+                                       const uint64_t* h_sizes, uint32_t na_total, uint64_t* h_out,
+                                       uint8_t* h_free_status, hba_stream_t stream);
 
 /* Launch shape of the handle's batch kernel: threads per CTA (one of 64,
  * 128, 256, 512, 1024: a CTA applies one arena's batch; or 32: warp mode,
@@ -360,10 +388,15 @@ typedef struct {
  * d_arrivals: device hba_arrival_t[n].  d_served: device hba_served_t[n],
  * written by the call.  d_log (device uint32, log_cap words, may be NULL
  * with log_cap 0): per tick [nf, na, nf request ids freed, na ids admitted],
- * so that the run can be replayed exactly.  Allocates its working buffers
- * (queue, timing wheel, tick buffers: about 90 MB at the defaults) at the
- * start and frees them at the end; synchronous.  Returns HBA_ERR_STATE if
- * the timing wheel overflowed (report.status 2). */
+ * so that the run can be replayed exactly.  The working buffers (queue,
+ * timing wheel, tick buffers: about 90 MB at the defaults) belong to the
+ * handle: the first run allocates them, later runs reuse them, and a run
+ * with a deeper queue or larger ticks than any before replaces them (freed
+ * by hba_destroy).  Synchronous.  A run that stops at time_limit_ns
+ * (report.status 1) or max_ticks (status 3) returns HBA_OK; one whose
+ * timing wheel overflowed (status 2: a hold beyond 4,096 buckets, or more
+ * than max_batch frees in one bucket) returns HBA_ERR_STATE, with the report
+ * filled in.  The handle stays usable after any of them. */
 hba_status_t hba_serve_run(hba_t h, const hba_arrival_t* d_arrivals, uint64_t n, hba_served_t* d_served,
                            uint32_t* d_log, uint64_t log_cap, const hba_serve_config_t* cfg,
                            hba_serve_report_t* report, hba_stream_t stream);

@@ -1,13 +1,14 @@
 """Build the CUDA library ``_build/libhba.so`` for sm_103a with nvcc.
 
 The library is compiled in-tree (never installed) from ``csrc/hba_capi.cu``
-and ``csrc/hba_engine.cuh``; the public header is ``include/hba.h`` at the
-repository root.  ``_build/libcuda_replay.so`` (host code only, from
+and the kernel headers it includes (``csrc/*.cuh``); the public header is
+``include/hba.h`` at the repository root.  ``_build/libcuda_replay.so`` (host code only, from
 ``csrc/cuda_replay.cu``) replays traces through the CUDA runtime's own
 allocators for the benchmark's comparison; it is compiled alongside.
 """
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -18,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhba.so")
 SOURCES = [os.path.join(CSRC, "hba_capi.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "hba_engine.cuh"), os.path.join(ROOT, "include", "hba.h")]
+DEPS = SOURCES + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "hba.h")]
 REPLAY_LIB = os.path.join(BUILD, "libcuda_replay.so")
 REPLAY_SOURCES = [os.path.join(CSRC, "cuda_replay.cu")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -4,27 +4,33 @@
 // whether the unit is free (a set bit is free); a second bitmap marks the
 // first unit of every in-use block, so that a free, which names only an
 // address, knows where its block ends (the next marked or free unit).
-// Allocation of k <= 64 units takes, by next fit, the lowest start at or
-// after the rover where k consecutive units are free, else the lowest start
-// of all; a run never wraps past the end of the pool.
+// Allocation of k units (any k up to the pool) takes, by next fit, the
+// lowest start at or after the rover where k consecutive units are free,
+// else the lowest start of all; a run never wraps past the end of the pool.
 //
 // One CTA per pool.  Both bitmaps are copied into shared memory for the
 // batch and written back at the end.  Frees are applied one at a time by
 // lane 0 of warp 0 (the warp loads 32 offsets at a time), a few word
-// operations each.  An allocation is a CTA-wide scan: thread t
-// takes word w and computes the mask of starts in w that have k free units,
-// across w and w + 1 (128-bit AND of the shifted words, built by doubling);
-// the lowest start is an atomicMin, and the scan stops after the first group
-// of words holding one.  Within a batch's allocations free space only
-// shrinks, so once k units cannot be found, every later request of k or more
-// fails at once.
+// operations each.  An allocation is a CTA-wide scan:
+//   k <= 64: thread t takes word w and computes the mask of starts in w that
+//     have k free units, across w and w + 1 (128-bit AND of the shifted
+//     words, built by doubling); the lowest start is an atomicMin, and the
+//     scan stops after the first group of words holding one.
+//   k > 64: a run this long leaves the word it starts in through its top
+//     bit, so the lowest start in word w is where w's leading free bits begin
+//     (or the rover, in the rover's word), and its length is those bits plus
+//     the free units from word w + 1 on: 64 per full word up to the next
+//     word that is not full, plus that word's trailing free bits.  Each
+//     thread owns a contiguous segment of words; a block-wide suffix minimum
+//     gives every segment the next non-full word after it.
+// Within a batch's allocations free space only shrinks, so once k units
+// cannot be found, every later request of k or more fails at once.
 #pragma once
 
 #include "hba_engine.cuh"
 
 namespace hba {
 
-constexpr uint32_t BM_MAX_RUN = 64;            // units per object at most
 constexpr uint32_t BM_MAX_WORDS = 12288;       // 786,432 units: both bitmaps in 192 KiB of shared memory
 
 struct BmHdr {
@@ -95,7 +101,8 @@ __device__ __forceinline__ uint64_t bm_run_starts(uint64_t lo, uint64_t hi, uint
 template <int NT>
 struct BmSmem {
     uint64_t sz[NT];  // the current group of request sizes
-    uint32_t rover, kfail, found, pad;
+    uint32_t rover, kfail, found, found_any;
+    uint32_t wmin[NT / 32];  // per-warp minima of the long-run search
     int64_t cnt[6];  // alloc_ok, alloc_fail, free_ok, free_fail, used units, requested bytes
     uint32_t err;
 };
@@ -109,16 +116,16 @@ __device__ void bm_free_one(BmSmem<NT>& S_, uint64_t* F, uint64_t* S, uint32_t W
         const uint32_t p = (uint32_t)(off >> lg);
         const uint32_t pw = p >> 6, pb = p & 63;
         if ((S[pw] >> pb) & 1ull) {
-            // the block ends at the next free or marked unit, at most 64 units on
+            // the block ends at the next free or marked unit, or the pool's end
             const uint64_t above = pb == 63 ? 0ull : ~0ull << (pb + 1);
             const uint64_t stop = (F[pw] | S[pw]) & above;
             uint32_t e;
             if (stop) {
                 e = (pw << 6) + ctz64(stop);
-            } else if (pw + 1 < W && (F[pw + 1] | S[pw + 1])) {
-                e = ((pw + 1) << 6) + ctz64(F[pw + 1] | S[pw + 1]);
             } else {
-                e = (pw + 2) << 6;  // past the next word: only where the block ends the pool
+                uint32_t x = pw + 1;
+                while (x < W && (F[x] | S[x]) == 0ull) ++x;
+                e = x < W ? (x << 6) + ctz64(F[x] | S[x]) : N;
             }
             if (e > N) e = N;
             for (uint32_t q = p; q < e;) {  // set F over [p, e), a word piece at a time
@@ -137,6 +144,62 @@ __device__ void bm_free_one(BmSmem<NT>& S_, uint64_t* F, uint64_t* S, uint32_t W
     ++S_.cnt[st ? 3 : 2];
 }
 
+// Lowest start of k > 64 free units (whole CTA; F in shared memory, W
+// words): at or after the rover if there is one, else the lowest of all;
+// 0xFFFFFFFF if none.  Every thread returns the same value.
+template <int NT>
+__device__ uint32_t bm_long_search(BmSmem<NT>& S_, const uint64_t* F, uint32_t W, uint32_t rover, uint32_t k) {
+    constexpr uint32_t NONE = 0xFFFFFFFFu;
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // segment of words [lo, hi) per thread; an odd length keeps the 16
+    // threads of a half-warp on distinct 8-byte bank pairs
+    const uint32_t c = ((W + NT - 1) / NT) | 1u;
+    const uint32_t lo = min(t * c, W), hi = min(lo + c, W);
+    uint32_t nf = W;  // first non-full word of the segment
+    for (uint32_t x = lo; x < hi; ++x)
+        if (F[x] != ~0ull) { nf = x; break; }
+    // exclusive suffix minimum over threads: the first non-full word after the segment
+    uint32_t v = nf;
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + o < 32) v = min(v, u);
+    }
+    uint32_t after = __shfl_down_sync(0xffffffffu, v, 1);
+    if (lane == 31) after = W;
+    if (lane == 0) S_.wmin[warp] = v;
+    if (t == 0) {
+        S_.found = NONE;
+        S_.found_any = NONE;
+    }
+    __syncthreads();
+    for (uint32_t q = warp + 1; q < NT / 32; ++q) after = min(after, S_.wmin[q]);
+    const uint32_t w0 = rover >> 6, rb = rover & 63;
+    uint32_t best0 = NONE, best1 = NONE;  // at or after the rover; anywhere
+    uint32_t nz = after;                  // next non-full word after x
+    for (uint32_t x = hi; x-- > lo;) {
+        const uint64_t f = F[x];
+        const uint32_t lead = (uint32_t)__clzll((long long)~f);  // free bits at the top of the word
+        if (lead) {
+            const uint32_t tail = 64u * (nz - x - 1) + (nz < W ? ctz64(~F[nz]) : 0u);  // free units from word x + 1
+            const uint32_t b = 64u - lead;
+            if (lead + tail >= k) best1 = (x << 6) + b;
+            if (x > w0) {
+                if (lead + tail >= k) best0 = (x << 6) + b;
+            } else if (x == w0) {  // the rover's word: starts at or after the rover only
+                const uint32_t bb = max(b, rb);
+                if (64u - bb + tail >= k) best0 = (x << 6) + bb;
+            }
+        }
+        if (f != ~0ull) nz = x;
+    }
+    if (best0 != NONE) atomicMin(&S_.found, best0);
+    if (best1 != NONE) atomicMin(&S_.found_any, best1);
+    __syncthreads();
+    const uint32_t r = S_.found != NONE ? S_.found : S_.found_any;
+    __syncthreads();
+    return r;
+}
+
 // The bitmaps of one pool in shared memory: F (free) and S (starts), W words each.
 template <int NT>
 __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint64_t* gS, uint64_t* F, uint64_t* S,
@@ -150,7 +213,7 @@ __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint6
     }
     if (t == 0) {
         S_.rover = H.rover;
-        S_.kfail = BM_MAX_RUN + 1;
+        S_.kfail = 0xFFFFFFFFu;
         for (int q = 0; q < 6; ++q) S_.cnt[q] = 0;
         S_.err = 0;
     }
@@ -178,7 +241,7 @@ __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint6
         }
         const uint64_t sz = S_.sz[(i - a0) % NT];
         const uint32_t k = (sz == 0 || sz > P) ? 0u : (uint32_t)((sz + (1ull << lg) - 1) >> lg);
-        if (k == 0 || k > BM_MAX_RUN || k > N || k >= S_.kfail) {  // uniform: S_.kfail changes behind barriers
+        if (k == 0 || k > N || k >= S_.kfail) {  // uniform: S_.kfail changes behind barriers
             if (t == 0) {
                 out[i] = FAIL64;
                 ++S_.cnt[1];
@@ -186,6 +249,11 @@ __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint6
             continue;
         }
         const uint32_t rover = S_.rover;
+        if (k > 64) {
+            const uint32_t p = bm_long_search<NT>(S_, F, W, rover, k);
+            if (t == 0) S_.found = p;
+            __syncthreads();
+        } else {
         const uint32_t w0 = rover >> 6 < W ? rover >> 6 : W;
         if (t == 0) S_.found = 0xFFFFFFFFu;
         __syncthreads();
@@ -206,6 +274,7 @@ __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint6
                 if (got) break;
             }
             if (S_.found != 0xFFFFFFFFu) break;
+        }
         }
         if (t == 0) {
             const uint32_t p = S_.found;
