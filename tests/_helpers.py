@@ -80,3 +80,19 @@ def check_invariants(words):
     assert sorted(listed) == sorted(size_of), "free blocks and list members differ"
     assert mask == s["bitmask"]
     return s
+
+
+def canary_intact(guard, byte=0xA5, chunk=1 << 30) -> bool:
+    """True iff every byte of the device tensor ``guard`` (uint8) still holds
+    ``byte``: compared as 64-bit words, a chunk at a time, so that a guard of
+    tens of GiB needs no guard-sized temporary."""
+    import torch
+
+    word = int.from_bytes(bytes([byte]) * 8, "little", signed=True)
+    n = guard.numel()
+    head = n - n % 8
+    w = guard[:head].view(torch.int64)
+    for i in range(0, w.numel(), chunk // 8):
+        if not bool((w[i:i + chunk // 8] == word).all()):
+            return False
+    return bool((guard[head:] == byte).all()) if head < n else True

@@ -71,3 +71,31 @@ def test_product_path_has_no_cpu_fallback():
             _lib.load(os.path.join(ROOT, "no_such_dir", "libhba.so"))
     finally:
         _lib._lib = _lib._lib_saved
+
+
+def test_every_imported_name_resolves():
+    """Every name the tests, the bench and the entry module import from the
+    package exists (checked without a GPU)."""
+    import ast
+    import glob
+    import importlib
+    import os
+
+    import paper_2405_07079_gb300 as P
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = (glob.glob(os.path.join(root, "tests", "*.py")) + glob.glob(os.path.join(root, "paper_2405_07079_gb300", "*.py"))
+             + [os.path.join(root, "bench.py"), os.path.join(root, "__graft_entry__.py")])
+    missing = []
+    for f in files:
+        with open(f) as fh:
+            tree = ast.parse(fh.read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.ImportFrom) and node.module in ("paper_2405_07079_gb300",
+                                                                    "paper_2405_07079_gb300.hba"):
+                mod = P if node.module == "paper_2405_07079_gb300" else importlib.import_module(node.module)
+                for a in node.names:
+                    sub = importlib.util.find_spec(f"paper_2405_07079_gb300.{a.name}")
+                    if not hasattr(mod, a.name) and sub is None:
+                        missing.append((os.path.basename(f), a.name))
+    assert not missing, missing

@@ -5,7 +5,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
-from _helpers import FAIL, check_invariants, first_diff, from_dev, oracle_trace, to_dev
+from _helpers import FAIL, canary_intact, check_invariants, first_diff, from_dev, oracle_trace, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,7 @@ def _run(wl, threads=None, max_batches=None, state_every=0, canary=False, ctas=0
         assert got["extent_bytes"] == sp["extent"] and got["largest_free"] == sp["largest_free"]
     if canary:
         torch.cuda.synchronize()
-        assert bool((guard == 0xA5).all()), "the managed arena was written"
+        assert canary_intact(guard), "the managed arena was written"
     return trace
 
 
@@ -153,10 +153,11 @@ def test_launches_per_batch(gpu_lib, ctas, na, per_batch):
 
 def test_large_full(gpu_lib):
     """16 GiB arena, 10M ops in batches of 65,536: every result of every batch
-    (the launch configuration the benchmark times)."""
+    (the launch configuration the benchmark times); a real 16 GiB arena
+    filled with the canary byte stays untouched."""
     from paper_2405_07079_gb300 import workloads as W
 
-    _run(W.large(), threads=1024, state_every=50)
+    _run(W.large(), threads=1024, state_every=50, canary=True)
 
 
 def test_frag_reduced(gpu_lib):
@@ -167,10 +168,11 @@ def test_frag_reduced(gpu_lib):
 
 
 def test_frag_full_returns_to_one_block(gpu_lib):
-    """4 GiB, 1M x 4 KiB fill, free evens, 50k big, free all -> one block."""
+    """4 GiB, 1M x 4 KiB fill, free evens, 50k big, free all -> one block;
+    a real 4 GiB arena filled with the canary byte stays untouched."""
     from paper_2405_07079_gb300 import workloads as W
 
-    trace = _run(W.frag(), threads=1024)
+    trace = _run(W.frag(), threads=1024, canary=True)
     fill = np.concatenate([t[2] for t in trace[:62]])
     assert np.array_equal(fill, np.arange(1_000_000, dtype=np.uint64) * 4096)
 
@@ -441,6 +443,131 @@ def test_batched_generator_matches_per_arena_oracles(gpu_lib, threads):
         ma.close()
 
 
+def _multi_oracle_trace(A, n_batches, max_ops, mean_life, mb=256):
+    """The batched workload over arenas A, closed loop against one oracle
+    per arena: [(frow, frees, arow, sizes, out, status)], and the oracles."""
+    import oracle
+    from paper_2405_07079_gb300 import workloads as W
+
+    gen = W.MultiLifetimes(A, n_batches=n_batches, max_ops=max_ops, mean_life=mean_life)
+    orcs = [oracle.Oracle(int(a), mb) for a in A]
+    trace = []
+    while (b := gen.next_batch()) is not None:
+        frow, f, arow, s = b
+        outs, sts = [], []
+        for i in range(A.size):
+            o, st = orcs[i].batch(f[frow[i]:frow[i + 1]], s[arow[i]:arow[i + 1]])
+            outs.append(o)
+            sts.append(st)
+        out, st = np.concatenate(outs), np.concatenate(sts)
+        gen.feed(out)
+        trace.append((frow, f, arow, s, out, st))
+    return trace, orcs
+
+
+def _multi_replay(A, trace, orcs, threads, ctas, mb=256, canaries=0):
+    """Replay a batched trace through one multi-arena handle of the given
+    launch shape: every offset and free status of every batch, and every
+    arena's final state, equal the per-arena oracles'.  The first
+    ``canaries`` arenas get a real buffer of their size filled with the
+    canary byte, which must stay untouched."""
+    import torch
+
+    from _helpers import canary_intact
+    from paper_2405_07079_gb300 import MultiAllocator
+
+    dev = torch.device("cuda")
+    guards = [torch.full((int(A[i]),), 0xA5, dtype=torch.uint8, device=dev) for i in range(canaries)]
+    m = MultiAllocator(A, mb, max_total_frees=max(1, max(t[1].size for t in trace)))
+    m.set_shape(threads, ctas, 0)
+    try:
+        for b, (frow, f, arow, s, out, st) in enumerate(trace):
+            dout = torch.empty(max(1, s.size), dtype=torch.int64, device=dev)
+            dst = torch.empty(max(1, f.size), dtype=torch.uint8, device=dev)
+            m.step(to_dev(frow.view(np.int32), dev), to_dev(f, dev), to_dev(arow.view(np.int32), dev),
+                   to_dev(s, dev), dout, dst)
+            i = first_diff(from_dev(dout)[:s.size], out)
+            assert i is None, f"shape {threads},{ctas} batch {b}: alloc {i}"
+            assert first_diff(from_dev(dst)[:f.size], st) is None, f"shape {threads},{ctas} batch {b}: frees"
+        for i in range(A.size):
+            assert np.array_equal(m.export_state(i), orcs[i].export_state()), (threads, ctas, i)
+        torch.cuda.synchronize()
+        assert all(canary_intact(g) for g in guards), "a managed arena was written"
+    finally:
+        m.close()
+
+
+@pytest.mark.parametrize("threads,ctas", [(32, 0), (32, 200), (128, 608), (256, 0)])
+def test_multi_arena_large_grids(gpu_lib, threads, ctas):
+    """2,700 arenas of 1-4 MiB, so that the launch shapes the full batched
+    configuration uses all run: warp mode with more CTAs than two per SM
+    (k_multi_warp built for four CTAs per SM), warp mode with 200 CTAs
+    looping over the arenas, 608 CTAs of 128 threads looping over the
+    arenas, and one CTA of 256 threads per arena."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    A = W.multi_arena_sizes(2700, lo=1 << 20, hi=4 << 20)
+    trace, orcs = _multi_oracle_trace(A, n_batches=8, max_ops=512, mean_life=300)
+    _multi_replay(A, trace, orcs, threads, ctas, canaries=4)
+
+
+def test_multi_arena_full_config_autotuned_shape(gpu_lib):
+    """The full batched configuration's arenas (4,096, log-uniform 64 MiB -
+    1 GiB) and request counts (U{0..2048} per arena per batch), three batches,
+    at the shape the autotuner picks on GB300 (warp mode, 608 CTAs): every
+    arena against its own oracle; two arenas get canary buffers."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    A = W.multi_arena_sizes()
+    trace, orcs = _multi_oracle_trace(A, n_batches=3, max_ops=2048, mean_life=1000)
+    assert sum(t[3].size for t in trace) > 7_000_000
+    _multi_replay(A, trace, orcs, 32, 608, canaries=2)
+
+
+def test_multi_step_host_async_matches_oracles(gpu_lib):
+    """hba_multi_step_host_async: the batched form from pinned host buffers,
+    three calls in flight before the host reads the first results (the two
+    staging slots are reused while earlier calls' copies are still queued):
+    every offset and free status equals the per-arena oracles', and a handle
+    made without staging refuses the call."""
+    import torch
+
+    from paper_2405_07079_gb300 import HbaError, MultiAllocator, hba_multi_step_host_async
+    from paper_2405_07079_gb300 import workloads as W
+
+    A = W.multi_arena_sizes(300, lo=1 << 20, hi=8 << 20)
+    trace, orcs = _multi_oracle_trace(A, n_batches=9, max_ops=1024, mean_life=200)
+    nf_max = max(t[1].size for t in trace)
+    na_max = max(t[3].size for t in trace)
+    m = MultiAllocator(A, 256, max_total_frees=nf_max, max_total_allocs=na_max)
+    stream = torch.cuda.current_stream()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    try:
+        keep = []
+        for frow, f, arow, s, out, st in trace:
+            hfr, har = pin(frow.view(np.int32)), pin(arow.view(np.int32))
+            hf, hs = pin(f.view(np.int64)), pin(s.view(np.int64))
+            ho = torch.empty(max(1, s.size), dtype=torch.int64).pin_memory()
+            hst = torch.empty(max(1, f.size), dtype=torch.uint8).pin_memory()
+            hba_multi_step_host_async(m.h, hfr.data_ptr(), hf.data_ptr() if f.size else 0, f.size, har.data_ptr(),
+                                      hs.data_ptr() if s.size else 0, s.size, ho.data_ptr() if s.size else 0,
+                                      hst.data_ptr() if f.size else 0, int(stream.cuda_stream))
+            keep.append((hfr, har, hf, hs, ho, hst, out, st))
+        stream.synchronize()
+        for b, (_, _, _, _, ho, hst, out, st) in enumerate(keep):
+            assert np.array_equal(ho.numpy().view(np.uint64)[:out.size], out), f"batch {b}"
+            assert np.array_equal(hst.numpy()[:st.size], st), f"batch {b} frees"
+        for i in range(A.size):
+            assert np.array_equal(m.export_state(i), orcs[i].export_state()), i
+    finally:
+        m.close()
+    plain = MultiAllocator(A[:4], 256, max_total_frees=16)
+    z = torch.zeros(8, dtype=torch.int32).pin_memory()
+    with pytest.raises(HbaError):
+        hba_multi_step_host_async(plain.h, z.data_ptr(), 0, 0, z.data_ptr(), 0, 0, 0, 0, 0)
+    plain.close()
+
+
 def test_calls_on_two_streams_are_ordered(gpu_lib):
     """Batches issued back to back on two different streams, with no host
     synchronisation between them: the handle orders the second after the
@@ -574,7 +701,7 @@ def test_tlsf_host_entry_points_and_serving_refusal(gpu_lib):
     from paper_2405_07079_gb300 import workloads as W
 
     wl = W.tiny(n_ops=1500)
-    trace, _ = oracle_trace(wl, policy="tlsf")
+    trace, orc = oracle_trace(wl, policy="tlsf")
     dev = torch.device("cuda")
     with Allocator(wl.arena, wl.min_block, policy="tlsf") as a, \
             Allocator(wl.arena, wl.min_block, policy="tlsf", max_batch=1) as b:
@@ -595,6 +722,10 @@ def test_tlsf_host_entry_points_and_serving_refusal(gpu_lib):
             torch.cuda.synchronize()
             if s.size:
                 assert np.array_equal(from_dev(dout), out)
+            if f.size:
+                assert np.array_equal(from_dev(dst), st)
+        assert np.array_equal(b.export_state(), orc.export_state())
+        assert np.array_equal(a.export_state(), orc.export_state())
         from paper_2405_07079_gb300 import serve, workloads
         arr = workloads.serving_arrivals(1e5, 0.001)
         with pytest.raises(HbaError):
@@ -862,16 +993,20 @@ def test_bitmask_worked_examples(gpu_lib):
             assert [int(x) for x in a.export_state()] == case["final"], case["name"]
 
 
-@pytest.mark.parametrize("pool,unit,batch", [(1 << 20, 8, 256), (1000 * 8, 8, 16), (786_432 * 16, 16, 2048)])
-def test_bitmask_objects(gpu_lib, pool, unit, batch):
+@pytest.mark.parametrize("pool,unit,batch,hi", [(1 << 20, 8, 256, 520), (1000 * 8, 8, 16, 520),
+                                                (786_432 * 16, 16, 2048, 1040), (1 << 20, 8, 256, 4096),
+                                                (786_432 * 8, 8, 512, 32768)])
+def test_bitmask_objects(gpu_lib, pool, unit, batch, hi):
     """Pools of 131,072 units, of 1,000 units (a partial last word), and of
     the largest size a pool may have (786,432 units): every result, the state
-    and the counters against the oracle."""
+    and the counters against the oracle.  Objects reach 65 units, and in the
+    last two cases 512 and 4,096 units (runs longer than one 128-bit window,
+    §3.2's 1 kB = 128-bit example and beyond)."""
     import oracle
     from paper_2405_07079_gb300 import workloads as W
 
     wl = W.Workload("objects", pool, unit, lambda: W.TinyRandom(n_ops=30 * batch if batch > 16 else 3000, batch=batch,
-                                                                p_free=0.45, lo=1, hi=64 * unit + 8))
+                                                                p_free=0.45, lo=1, hi=hi))
     o = oracle.BitmaskOracle(pool, unit)
     cl = wl.make()
     trace = []
@@ -883,6 +1018,51 @@ def test_bitmask_objects(gpu_lib, pool, unit, batch):
     for f, s, _, _ in trace:
         o2.batch(f, s)
     _run_bitmask(trace, o2, pool, unit, state_every=max(1, len(trace) // 8))
+
+
+@pytest.mark.parametrize("units,seed", [(4096, 0), (1000, 1), (8192, 2), (64 * 3, 3), (12288 * 64, 4)])
+def test_bitmask_long_runs_fragmented(gpu_lib, units, seed):
+    """Runs longer than 64 units in a pool fragmented around word
+    boundaries: fill with small objects, free a random half (holes of every
+    length, starting and ending anywhere in a word), then ask for runs of
+    65 units up to the whole pool, interleaved with small objects and frees;
+    finally free everything and take the whole pool in one request."""
+    import oracle
+
+    rng = np.random.default_rng(500 + seed)
+    unit = 8
+    pool = units * unit
+    o = oracle.BitmaskOracle(pool, unit)
+    held, trace = [], []
+
+    def batch(frees, sizes):
+        f = np.array(frees, np.uint64)
+        s = np.array(sizes, np.uint64)
+        out, st = o.batch(f, s)
+        trace.append((f, s, out, st))
+        return [int(x) for x in out if x != FAIL]
+
+    for _ in range(6):  # fill with objects of 1-40 units
+        held += batch([], rng.integers(1, 40 * unit, int(rng.integers(100, 400))).tolist())
+    rng.shuffle(held)
+    half = len(held) // 2
+    batch(held[:half], [])
+    held = held[half:]
+    for _ in range(25):
+        nf = int(rng.integers(0, min(len(held), 12) + 1))
+        idx = rng.choice(len(held), nf, replace=False) if nf else []
+        frees = [held[i] for i in idx]
+        held = [h for i, h in enumerate(held) if i not in set(idx)]
+        kinds = rng.random(int(rng.integers(1, 40)))
+        sizes = [int(rng.integers(1, 65 * unit)) if r < 0.3 else
+                 int(rng.integers(65 * unit, 700 * unit)) if r < 0.9 else
+                 int(rng.integers(1, pool + unit)) for r in kinds]
+        held += batch(frees, sizes)
+    batch(held, [pool, unit, pool // 2])
+    o2 = oracle.BitmaskOracle(pool, unit)
+    for f, s, _, _ in trace:
+        o2.batch(f, s)
+    _run_bitmask(trace, o2, pool, unit, state_every=3)
 
 
 def test_bitmask_invalid_frees_and_pool_limit(gpu_lib):
