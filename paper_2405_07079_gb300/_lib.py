@@ -34,6 +34,8 @@ SIGNATURES = {
     "hba_export_state": (i32, [vp, u32, vp, sz, vp]),
     "hba_multi_create": (i32, [u32, vp, u64, i32, u32, vp]),
     "hba_multi_step": (i32, [vp, vp, vp, u32, vp, vp, u32, vp, vp, vp]),
+    "hba_multi_create_ex": (i32, [u32, vp, u64, i32, u32, u32, vp]),
+    "hba_multi_step_host_async": (i32, [vp, vp, vp, u32, vp, vp, u32, vp, vp, vp]),
     "hba_set_shape": (i32, [vp, u32, u32, u32]),
     "hba_serve_run": (i32, [vp, vp, u64, vp, vp, u64, vp, vp, vp]),
     "hba_version": (ctypes.c_char_p, []),

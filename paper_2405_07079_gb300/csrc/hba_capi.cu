@@ -41,15 +41,17 @@ struct hba_s {
     uint64_t* d_stage_s = nullptr;
     uint64_t* d_stage_o = nullptr;
     uint8_t* d_stage_st = nullptr;
-    // pipelined host-buffer calls (hba_step_host_async): two staging slots,
-    // used in turn, and three internal streams -- input copies, the engine,
-    // result copies -- so that one call's copies overlap its neighbours'
-    // kernels.  Made at create, with the hba_step_host staging.
+    // pipelined host-buffer calls (hba_step_host_async,
+    // hba_multi_step_host_async): two staging slots, used in turn, and three
+    // internal streams -- input copies, the engine, result copies -- so that
+    // one call's copies overlap its neighbours' kernels.  Made at create.
     struct Slot {
         uint64_t* f = nullptr;
         uint64_t* s = nullptr;
         uint64_t* o = nullptr;
         uint8_t* st = nullptr;
+        uint32_t* fr = nullptr;  // many arenas: the two row-pointer arrays
+        uint32_t* ar = nullptr;
         cudaEvent_t in = nullptr;    // inputs copied
         cudaEvent_t done = nullptr;  // batch applied
         cudaEvent_t out = nullptr;   // results copied back
@@ -58,6 +60,7 @@ struct hba_s {
     Slot slot[2];
     cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
     uint32_t next_slot = 0;
+    uint64_t stage_allocs = 0;  // many arenas: allocations per host-buffer call (0: no staging)
     // launch shapes
     uint32_t threads = 0;       // single-arena CTA width (0: by batch size)
     uint32_t m_threads = 256;   // multi-arena CTA width
@@ -89,6 +92,12 @@ struct hba_s {
     uint64_t* d_bmS = nullptr;
     std::vector<hba::BmHdr> h_bmh;
     uint32_t bm_wmax = 0;  // largest pool, in words
+    // working buffers of hba_serve_run (queue, timing wheel, tick buffers),
+    // kept between runs; a run that asks for a deeper queue or larger ticks
+    // than any before replaces them
+    static constexpr int SERVE_BUFS = 11;
+    void* serve_buf[SERVE_BUFS] = {};
+    uint32_t serve_qcap = 0, serve_batch = 0;
 };
 
 namespace {
@@ -802,11 +811,17 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
     return launch_single(h, frees, nf, st, sizes, na, out, s, h->d_gi, h->d_scr);
 }
 
-// The staging slots and streams of hba_step_host_async, for n requests a side.
-hba_status_t make_pipeline(hba_t h, uint64_t n) {
+// The staging slots and streams of the pipelined host-buffer calls: nf_cap
+// frees and na_cap allocations a slot, and (many arenas) rows row pointers
+// of each kind.
+hba_status_t make_pipeline(hba_t h, uint64_t nf_cap, uint64_t na_cap, uint64_t rows) {
+    nf_cap = std::max<uint64_t>(nf_cap, 1);
+    na_cap = std::max<uint64_t>(na_cap, 1);
     for (hba_s::Slot& q : h->slot) {
-        if (cudaMalloc(&q.f, 8 * n) != cudaSuccess || cudaMalloc(&q.s, 8 * n) != cudaSuccess ||
-            cudaMalloc(&q.o, 8 * n) != cudaSuccess || cudaMalloc(&q.st, n) != cudaSuccess)
+        if (cudaMalloc(&q.f, 8 * nf_cap) != cudaSuccess || cudaMalloc(&q.s, 8 * na_cap) != cudaSuccess ||
+            cudaMalloc(&q.o, 8 * na_cap) != cudaSuccess || cudaMalloc(&q.st, nf_cap) != cudaSuccess)
+            return HBA_ERR_OUT_OF_MEMORY;
+        if (rows && (cudaMalloc(&q.fr, 4 * rows) != cudaSuccess || cudaMalloc(&q.ar, 4 * rows) != cudaSuccess))
             return HBA_ERR_OUT_OF_MEMORY;
         HBA_CUDA_TRY(cudaEventCreateWithFlags(&q.in, cudaEventDisableTiming));
         HBA_CUDA_TRY(cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming));
@@ -845,7 +860,7 @@ hba_status_t alloc_meta(hba_t h, const std::vector<Arena>& init, uint64_t scr_fr
             cudaMalloc(&h->d_stage_o, 8ull * stage) != cudaSuccess ||
             cudaMalloc(&h->d_stage_st, stage) != cudaSuccess)
             return HBA_ERR_OUT_OF_MEMORY;
-        return make_pipeline(h, stage);
+        return make_pipeline(h, stage, stage, 0);
     }
     return HBA_OK;
 }
@@ -920,6 +935,8 @@ void free_all(hba_t h) {
         cudaFree(q.s);
         cudaFree(q.o);
         cudaFree(q.st);
+        cudaFree(q.fr);
+        cudaFree(q.ar);
         if (q.in) cudaEventDestroy(q.in);
         if (q.done) cudaEventDestroy(q.done);
         if (q.out) cudaEventDestroy(q.out);
@@ -928,6 +945,10 @@ void free_all(hba_t h) {
     if (h->s_run) cudaStreamDestroy(h->s_run);
     if (h->s_out) cudaStreamDestroy(h->s_out);
     if (h->ev) cudaEventDestroy(h->ev);
+    for (void*& p : h->serve_buf) {
+        cudaFree(p);
+        p = nullptr;
+    }
 }
 
 bool check_geometry(uint64_t arena_bytes, uint64_t min_block, uint32_t* lg, uint64_t* a) {
@@ -988,29 +1009,45 @@ hba_status_t serve_impl(hba_t h, const hba_arrival_t* arr, uint64_t n, hba_serve
     g.max_batch = c.max_batch;
     g.time_limit_ns = c.time_limit_ns;
     g.max_ticks = c.max_ticks;
-    std::vector<void*> bufs;
-    auto get = [&](size_t bytes) -> void* {
-        void* p = nullptr;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
-        bufs.push_back(p);
-        return p;
-    };
-    const size_t mb = c.max_batch;
-    g.queue = (uint32_t*)get(4ull * g.qcap);
-    g.wheel = (uint32_t*)get(4ull * W * C);
-    g.wheel_cnt = (uint32_t*)get(4ull * W);
-    g.t_frees = (uint64_t*)get(8 * mb);
-    g.t_fid = (uint32_t*)get(4 * mb);
-    g.t_sizes = (uint64_t*)get(8 * mb);
-    g.t_aid = (uint32_t*)get(4 * mb);
-    g.t_out = (uint64_t*)get(8 * mb);
-    g.gi = (uint32_t*)get(4 * hba::GATHER_WORDS * mb);
-    g.scr = (uint32_t*)get(4 * hba::SCRATCH_WORDS_PER_FREE * mb);
-    g.ctl = (hba::ServeCtl*)get(sizeof(hba::ServeCtl));
+    if (h->serve_qcap < c.queue_depth || h->serve_batch < c.max_batch) {
+        // first run, or one larger than any before: (re)allocate for the
+        // largest queue and tick seen so far
+        const uint32_t qcap = std::max(h->serve_qcap, c.queue_depth), bmax = std::max(h->serve_batch, c.max_batch);
+        for (void*& p : h->serve_buf) {
+            cudaFree(p);
+            p = nullptr;
+        }
+        h->serve_qcap = h->serve_batch = 0;
+        const size_t B = bmax;
+        const size_t bytes[hba_s::SERVE_BUFS] = {4ull * qcap, 4ull * W * B, 4ull * W, 8 * B, 4 * B, 8 * B, 4 * B, 8 * B,
+                                                 4 * hba::GATHER_WORDS * B, 4 * hba::SCRATCH_WORDS_PER_FREE * B,
+                                                 sizeof(hba::ServeCtl)};
+        for (int i = 0; i < hba_s::SERVE_BUFS; ++i) {
+            if (cudaMalloc(&h->serve_buf[i], bytes[i]) != cudaSuccess) {
+                (void)cudaGetLastError();
+                for (void*& p : h->serve_buf) {
+                    cudaFree(p);
+                    p = nullptr;
+                }
+                return HBA_ERR_OUT_OF_MEMORY;
+            }
+        }
+        h->serve_qcap = qcap;
+        h->serve_batch = bmax;
+    }
+    g.queue = (uint32_t*)h->serve_buf[0];
+    g.wheel = (uint32_t*)h->serve_buf[1];
+    g.wheel_cnt = (uint32_t*)h->serve_buf[2];
+    g.t_frees = (uint64_t*)h->serve_buf[3];
+    g.t_fid = (uint32_t*)h->serve_buf[4];
+    g.t_sizes = (uint64_t*)h->serve_buf[5];
+    g.t_aid = (uint32_t*)h->serve_buf[6];
+    g.t_out = (uint64_t*)h->serve_buf[7];
+    g.gi = (uint32_t*)h->serve_buf[8];
+    g.scr = (uint32_t*)h->serve_buf[9];
+    g.ctl = (hba::ServeCtl*)h->serve_buf[10];
     hba_status_t r = HBA_OK;
-    for (void* p : bufs) if (!p) r = HBA_ERR_OUT_OF_MEMORY;
-    if (bufs.size() != 11) r = HBA_ERR_OUT_OF_MEMORY;
-    if (r == HBA_OK) {
+    {
         static SmemLimits L{};
         static bool have = false;
         if (!have) {
@@ -1038,7 +1075,6 @@ hba_status_t serve_impl(hba_t h, const hba_arrival_t* arr, uint64_t n, hba_serve
             r = HBA_ERR_CUDA;
         if (r == HBA_OK && rep->status == hba::SERVE_WHEEL_FULL) r = HBA_ERR_STATE;
     }
-    for (void* p : bufs) cudaFree(p);
     return r;
 }
 
@@ -1050,26 +1086,58 @@ constexpr uint32_t STATIC_GI_WORDS = hba::GATHER_WORDS * HBA_STATIC_MAX_FREES;
 constexpr uint32_t STATIC_WORDS = (hba::GATHER_WORDS + hba::SCRATCH_WORDS_PER_FREE) * HBA_STATIC_MAX_FREES;
 static __device__ __align__(256) uint32_t g_static_scratch[STATIC_WORDS];
 
-constexpr int STATIC_MAX_DEVICES = 64;
+// Device address of g_static_scratch in the caller's current context, or
+// nullptr on failure.  Host code cannot use the symbol's name as a device
+// pointer, and the address differs between contexts: the module holding the
+// array is loaded once per context, so after cudaDeviceReset, or under a
+// context other than the device's primary one, the array lives elsewhere.
+// The address is therefore looked up (cudaGetSymbolAddress, with the
+// caller's context current) the first time each context calls, and kept
+// under the context's unique id, which the driver never hands out twice in
+// one process.  Without the driver's context calls it is looked up on every
+// call.
+using CtxGetCurrentFn = int (*)(void**);
+using CtxGetIdFn = int (*)(void*, unsigned long long*);
 std::mutex g_static_mu;
-uint32_t* g_static_addr[STATIC_MAX_DEVICES] = {};
+std::vector<std::pair<unsigned long long, uint32_t*>> g_static_addr;  // (context id, address)
 
-// Device address of g_static_scratch on the current device, looked up once
-// per device with that device current (host code cannot use the symbol's
-// name as a device pointer).  nullptr on failure.
-uint32_t* static_scratch_address() {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= STATIC_MAX_DEVICES) return nullptr;
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return nullptr;
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
         }
-        g_static_addr[dev] = static_cast<uint32_t*>(p);
+        (void)cudaGetLastError();
     }
-    return g_static_addr[dev];
+    if (!get_current || !get_id) return false;
+    void* ctx = nullptr;
+    return get_current(&ctx) == 0 && ctx && get_id(ctx, id) == 0;
+}
+
+uint32_t* static_scratch_address() {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (have_id)
+        for (const auto& e : g_static_addr)
+            if (e.first == id) return e.second;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    // the lookup makes the device's primary context current if none was
+    if (have_id || current_context_id(&id)) g_static_addr.emplace_back(id, static_cast<uint32_t*>(p));
+    return static_cast<uint32_t*>(p);
 }
 
 hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
@@ -1203,8 +1271,8 @@ hba_status_t hba_create(uint64_t arena_bytes, uint64_t min_block, int policy, hb
     return hba_create_ex(arena_bytes, min_block, policy, 65536, out);
 }
 
-hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, uint64_t min_block, int policy,
-                              uint32_t max_total_frees, hba_t* out) {
+hba_status_t hba_multi_create_ex(uint32_t n_arenas, const uint64_t* arena_bytes, uint64_t min_block, int policy,
+                                 uint32_t max_total_frees, uint32_t max_total_allocs, hba_t* out) {
     if (!out || !arena_bytes || n_arenas == 0 || !known_policy(policy)) return HBA_ERR_INVALID_ARGUMENT;
     std::vector<Arena> init(n_arenas);
     uint64_t base = 0;
@@ -1221,6 +1289,10 @@ hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, ui
     h->total_granules = base;
     h->max_batch = max_total_frees;
     hba_status_t r = alloc_meta(h, init, max_total_frees, 0);
+    if (r == HBA_OK && max_total_allocs) {
+        r = make_pipeline(h, max_total_frees, max_total_allocs, (uint64_t)n_arenas + 1);
+        h->stage_allocs = max_total_allocs;
+    }
     if (r == HBA_OK) r = alloc_policy(h, policy);
     if (r == HBA_OK) r = reset_impl(h, 0);
     if (r == HBA_OK && cudaDeviceSynchronize() != cudaSuccess) r = HBA_ERR_CUDA;
@@ -1231,6 +1303,11 @@ hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, ui
     }
     *out = h;
     return HBA_OK;
+}
+
+hba_status_t hba_multi_create(uint32_t n_arenas, const uint64_t* arena_bytes, uint64_t min_block, int policy,
+                              uint32_t max_total_frees, hba_t* out) {
+    return hba_multi_create_ex(n_arenas, arena_bytes, min_block, policy, max_total_frees, 0, out);
 }
 
 hba_status_t hba_destroy(hba_t h) {
@@ -1439,14 +1516,10 @@ hba_status_t hba_set_shape(hba_t h, uint32_t threads, uint32_t ctas, uint32_t sm
     return HBA_OK;
 }
 
-hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64_t* d_frees, uint32_t nf_total,
-                            const uint32_t* d_alloc_rowptr, const uint64_t* d_sizes, uint32_t na_total,
-                            uint64_t* d_out, uint8_t* d_free_status, hba_stream_t stream) {
-    if (!h || !d_free_rowptr || !d_alloc_rowptr) return HBA_ERR_INVALID_ARGUMENT;
-    if (nf_total > h->scr_frees) return HBA_ERR_INVALID_ARGUMENT;
-    if ((nf_total && !d_frees) || (na_total && (!d_sizes || !d_out))) return HBA_ERR_INVALID_ARGUMENT;
-    cudaStream_t s = (cudaStream_t)stream;
-    StreamOrder order(h, s);
+namespace {
+hba_status_t multi_step_impl(hba_t h, const uint32_t* d_free_rowptr, const uint64_t* d_frees, uint32_t nf_total,
+                             const uint32_t* d_alloc_rowptr, const uint64_t* d_sizes, uint32_t na_total,
+                             uint64_t* d_out, uint8_t* d_free_status, cudaStream_t s) {
     const uint32_t n = h->n_arenas;
     if (h->policy == HBA_POLICY_TLSF)
         return launch_tlsf(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes, na_total,
@@ -1500,6 +1573,69 @@ hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64
     if (e != cudaSuccess) return HBA_ERR_CUDA;
     ++h->launches;
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
+}
+}  // namespace
+
+hba_status_t hba_multi_step(hba_t h, const uint32_t* d_free_rowptr, const uint64_t* d_frees, uint32_t nf_total,
+                            const uint32_t* d_alloc_rowptr, const uint64_t* d_sizes, uint32_t na_total,
+                            uint64_t* d_out, uint8_t* d_free_status, hba_stream_t stream) {
+    if (!h || !d_free_rowptr || !d_alloc_rowptr) return HBA_ERR_INVALID_ARGUMENT;
+    if (nf_total > h->scr_frees) return HBA_ERR_INVALID_ARGUMENT;
+    if ((nf_total && !d_frees) || (na_total && (!d_sizes || !d_out))) return HBA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    StreamOrder order(h, s);
+    return multi_step_impl(h, d_free_rowptr, d_frees, nf_total, d_alloc_rowptr, d_sizes, na_total, d_out,
+                           d_free_status, s);
+}
+
+hba_status_t hba_multi_step_host_async(hba_t h, const uint32_t* h_free_rowptr, const uint64_t* h_frees,
+                                       uint32_t nf_total, const uint32_t* h_alloc_rowptr, const uint64_t* h_sizes,
+                                       uint32_t na_total, uint64_t* h_out, uint8_t* h_free_status,
+                                       hba_stream_t stream) {
+    if (!h || !h->stage_allocs || !h_free_rowptr || !h_alloc_rowptr) return HBA_ERR_INVALID_ARGUMENT;
+    if (nf_total > h->scr_frees || na_total > h->stage_allocs) return HBA_ERR_INVALID_ARGUMENT;
+    if ((nf_total && !h_frees) || (na_total && (!h_sizes || !h_out))) return HBA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rows = 4ull * ((size_t)h->n_arenas + 1);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HBA_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    const bool captured = cs != cudaStreamCaptureStatusNone;
+    // inside a capture every step stays on the captured stream, in order,
+    // through the first slot
+    hba_s::Slot& q = h->slot[captured ? 0 : h->next_slot];
+    cudaStream_t si = captured ? s : h->s_in, sr = captured ? s : h->s_run, so = captured ? s : h->s_out;
+    if (!captured) {
+        h->next_slot ^= 1;
+        // the slot's previous results must be out before its inputs are replaced
+        if (q.used) HBA_CUDA_TRY(cudaStreamWaitEvent(si, q.out, 0));
+    }
+    HBA_CUDA_TRY(cudaMemcpyAsync(q.fr, h_free_rowptr, rows, cudaMemcpyHostToDevice, si));
+    HBA_CUDA_TRY(cudaMemcpyAsync(q.ar, h_alloc_rowptr, rows, cudaMemcpyHostToDevice, si));
+    if (nf_total) HBA_CUDA_TRY(cudaMemcpyAsync(q.f, h_frees, 8ull * nf_total, cudaMemcpyHostToDevice, si));
+    if (na_total) HBA_CUDA_TRY(cudaMemcpyAsync(q.s, h_sizes, 8ull * na_total, cudaMemcpyHostToDevice, si));
+    if (!captured) {
+        HBA_CUDA_TRY(cudaEventRecord(q.in, si));
+        HBA_CUDA_TRY(cudaStreamWaitEvent(sr, q.in, 0));
+    }
+    hba_status_t r;
+    {
+        StreamOrder order(h, sr);
+        r = multi_step_impl(h, q.fr, q.f, nf_total, q.ar, q.s, na_total, q.o, h_free_status ? q.st : nullptr, sr);
+    }
+    if (r != HBA_OK) return r;
+    if (!captured) {
+        HBA_CUDA_TRY(cudaEventRecord(q.done, sr));
+        HBA_CUDA_TRY(cudaStreamWaitEvent(so, q.done, 0));
+    }
+    if (na_total) HBA_CUDA_TRY(cudaMemcpyAsync(h_out, q.o, 8ull * na_total, cudaMemcpyDeviceToHost, so));
+    if (nf_total && h_free_status)
+        HBA_CUDA_TRY(cudaMemcpyAsync(h_free_status, q.st, nf_total, cudaMemcpyDeviceToHost, so));
+    if (!captured) {
+        HBA_CUDA_TRY(cudaEventRecord(q.out, so));
+        q.used = true;
+        HBA_CUDA_TRY(cudaStreamWaitEvent(s, q.out, 0));
+    }
+    return HBA_OK;
 }
 
 }  // extern "C"

@@ -109,26 +109,53 @@ def hba_multi_step(h: int, d_free_rowptr: int, d_frees: int, nf_total: int, d_al
                                                   d_sizes, na_total, d_out, d_free_status, stream))
 
 
+def hba_multi_create_ex(arena_bytes, min_block: int, policy: int = HBA_POLICY_SEGFIT, max_total_frees: int = 1 << 22,
+                        max_total_allocs: int = 0) -> int:
+    a = np.ascontiguousarray(arena_bytes, dtype=np.uint64)
+    h = ctypes.c_void_p()
+    check("hba_multi_create_ex", _lib().hba_multi_create_ex(a.size, a.ctypes.data, min_block, policy, max_total_frees,
+                                                            max_total_allocs, ctypes.byref(h)))
+    return h.value
+
+
+def hba_multi_step_host_async(h: int, h_free_rowptr: int, h_frees: int, nf_total: int, h_alloc_rowptr: int,
+                              h_sizes: int, na_total: int, h_out: int, h_free_status: int, stream: int = 0) -> None:
+    check("hba_multi_step_host_async",
+          _lib().hba_multi_step_host_async(h, h_free_rowptr, h_frees, nf_total, h_alloc_rowptr, h_sizes, na_total,
+                                           h_out, h_free_status, stream))
+
+
 def hba_set_shape(h: int, threads: int, ctas: int = 0, smem_bytes: int = 0) -> None:
     check("hba_set_shape", _lib().hba_set_shape(h, threads, ctas, smem_bytes))
 
 
 HBA_REJECTED = 0xFFFFFFFFFFFFFFFE
+HBA_ERR_STATE = 5
 
 
 def hba_serve_run(h: int, d_arrivals: int, n: int, d_served: int, d_log: int, log_cap: int,
                   queue_depth: int = 0, max_batch: int = 0, bucket_ns: int = 0, time_limit_ns: int = 0,
                   max_ticks: int = 0, stream: int = 0) -> dict:
+    """Returns the run's report.  When the run stopped on a full
+    free-timing wheel (HBA_ERR_STATE), the HbaError raised carries the
+    report as ``.report``."""
     cfg = ServeConfig(queue_depth, max_batch, bucket_ns, time_limit_ns, max_ticks)
     rep = ServeReport()
-    check("hba_serve_run", _lib().hba_serve_run(h, d_arrivals, n, d_served, d_log, log_cap, ctypes.byref(cfg),
-                                                ctypes.byref(rep), stream))
+    code = _lib().hba_serve_run(h, d_arrivals, n, d_served, d_log, log_cap, ctypes.byref(cfg), ctypes.byref(rep),
+                                stream)
+    if code == HBA_ERR_STATE:
+        err = HbaError("hba_serve_run", code)
+        err.report = rep.as_dict()
+        raise err
+    check("hba_serve_run", code)
     return rep.as_dict()
 
 
 def serve(alloc: "Allocator", arrivals: np.ndarray, log_cap: int | None = None, **cfg):
     """Run the serving loop on ``arrivals`` (uint64[n, 3]: arrival ns, bytes,
-    hold ns).  Returns ``(served uint64[n, 3], log uint32[], report)``."""
+    hold ns).  Returns ``(served uint64[n, 3], log uint32[], report)``.  If
+    the run stopped on a full free-timing wheel, the HbaError raised carries
+    ``.report``, ``.served`` and ``.log`` of the run."""
     torch = _torch()
     arr = np.ascontiguousarray(arrivals, dtype=np.uint64).reshape(-1, 3)
     n = arr.shape[0]
@@ -137,8 +164,14 @@ def serve(alloc: "Allocator", arrivals: np.ndarray, log_cap: int | None = None, 
     d_served = torch.empty((max(n, 1), 3), dtype=torch.int64, device=dev)
     cap = log_cap if log_cap is not None else 4 * n + 1024
     d_log = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
-    rep = hba_serve_run(alloc.h, _ptr(d_arr), n, _ptr(d_served), _ptr(d_log), cap, **cfg,
-                        stream=_stream_ptr(None))
+    try:
+        rep = hba_serve_run(alloc.h, _ptr(d_arr), n, _ptr(d_served), _ptr(d_log), cap, **cfg,
+                            stream=_stream_ptr(None))
+    except HbaError as e:
+        if hasattr(e, "report"):
+            e.served = d_served[:n].cpu().numpy().view(np.uint64)
+            e.log = d_log[:min(cap, e.report["log_words"])].cpu().numpy().view(np.uint32)
+        raise
     served = d_served[:n].cpu().numpy().view(np.uint64)
     log = d_log[:min(cap, rep["log_words"])].cpu().numpy().view(np.uint32)
     return served, log, rep
@@ -247,9 +280,13 @@ class Allocator:
 class MultiAllocator:
     """Many independent arenas; one launch applies one batch to all of them."""
 
-    def __init__(self, arena_bytes, min_block: int, max_total_frees: int = 1 << 22, policy: str = "segfit"):
+    def __init__(self, arena_bytes, min_block: int, max_total_frees: int = 1 << 22, policy: str = "segfit",
+                 max_total_allocs: int = 0):
+        """``max_total_allocs`` > 0 gives the handle staging for
+        hba_multi_step_host_async (batches from host buffers)."""
         self.policy = policy
-        self.h = hba_multi_create(arena_bytes, min_block, POLICIES[policy], max_total_frees)
+        self.h = (hba_multi_create_ex(arena_bytes, min_block, POLICIES[policy], max_total_frees, max_total_allocs)
+                  if max_total_allocs else hba_multi_create(arena_bytes, min_block, POLICIES[policy], max_total_frees))
         self.n = len(arena_bytes)
 
     def close(self):
@@ -271,6 +308,5 @@ class MultiAllocator:
         return hba_export_state(self.h, arena)
 
 
-__all__ = [n for n in dir() if n.startswith("hba_")] + ["Allocator", "MultiAllocator", "HbaError", "HBA_FAIL",
-                                                          "HBA_STATIC_MAX_FREES", "HBA_REJECTED", "serve",
-                                                          "log_batches"]
+__all__ = ([n for n in dir() if n.startswith(("hba_", "HBA_"))]
+           + ["Allocator", "MultiAllocator", "HbaError", "serve", "log_batches"])
