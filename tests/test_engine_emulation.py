@@ -15,10 +15,11 @@ import pytest
 from _helpers import oracle_trace
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "paper_2405_07079_gb300", "csrc", "hba_emu.cpp")
-HDR = os.path.join(ROOT, "paper_2405_07079_gb300", "csrc", "hba_engine.cuh")
-TLSF_HDR = os.path.join(ROOT, "paper_2405_07079_gb300", "csrc", "hba_tlsf.cuh")
-OUT = os.path.join(ROOT, "paper_2405_07079_gb300", "_build", "libhba_emu_test.so")
+CSRC = os.path.join(ROOT, "paper_2405_07079_gb300", "csrc")
+SRC = os.path.join(ROOT, "tests", "emu", "hba_emu.cpp")
+HDR = os.path.join(CSRC, "hba_engine.cuh")
+TLSF_HDR = os.path.join(CSRC, "hba_tlsf.cuh")
+OUT = os.path.join(ROOT, "tests", "emu", "_build", "libhba_emu_test.so")
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +27,7 @@ def emu():
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
     if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(map(os.path.getmtime, (SRC, HDR, TLSF_HDR))):
         tmp = OUT + f".{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-o", tmp, SRC])
         os.replace(tmp, OUT)
     lib = ctypes.CDLL(OUT)
     vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
