@@ -1,22 +1,30 @@
 #!/usr/bin/env python3
 """Throughput of the header-free batched allocator on one GB300 (or N replicas).
 
-Workload (default ``large``): one 16 GiB arena, min block 512 B, a 10M-op
-trace in batches of 65,536 (70 % power-of-two sizes 4 KiB..2 MiB, 30 %
-log-uniform 256 B..256 MiB, geometric lifetimes with mean 1,000 ops).  A step
-is one batch: its frees, then its allocations, in one kernel launch.
+Default workload (``multi``): the batched form.  4,096 independent arenas,
+log-uniform 64 MiB..1 GiB (min block 256 B), each receiving U{0..2048}
+requests per batch (the large trace's size mix scaled to the arena,
+geometric lifetimes with mean 1,000 ops), 200 batches.  A step is one batch
+of every arena: a prep grid, then one multi-arena launch.
 
 1. The trace is recorded untimed: the seeded client drives the GPU allocator
    closed loop (it frees what the allocator gave it).
-2. The allocator is reset and the recorded batches are replayed: W warm-up
-   steps, then K timed steps, each bracketed by CUDA events on the launching
-   stream; between steps a 256 MiB buffer is written to flush L2 (untimed);
-   when the trace wraps the allocator is reset (untimed).
-3. e2e: the same replay through the host-buffer entry points (pinned host
-   buffers; the copies and the result read-back inside the timed region):
-   ``hba_step_host_async`` with three steps in flight, the host reading each
-   step's result two steps later (the reported ``e2e``), and the synchronous
-   ``hba_step_host`` beside it.
+2. The launch shape is autotuned on the first batches (untimed).
+3. The allocator is reset and the recorded batches are replayed: W warm-up
+   steps, then K timed steps (default one pass), each bracketed by CUDA
+   events on the launching stream; between steps a 256 MiB buffer is written
+   to flush L2 (untimed).
+4. e2e: the same replay through ``hba_multi_step_host_async`` from pinned
+   host buffers, three steps in flight, the copies and the result read-back
+   inside the timed region.
+5. Beside it: the plain form on the same requests (one handle and launch per
+   arena; results must be equal), the plain single-arena large trace, the
+   oracle sharded over the host cores, and cudaMalloc / cudaMallocAsync on
+   the same operations.
+
+``--workload large|tiny|frag|usage|objects`` times the plain single-arena
+form instead (one 16 GiB arena, batches of 65,536, for ``large``), with its
+e2e through ``hba_step_host_async``; ``--workload serve`` the serving loop.
 
 ``--impl reference`` times the CPU oracle (the sequential statement of
 Algorithms 4/5) on the same workload, one batch per step.
@@ -54,10 +62,6 @@ BYTES_ALLOC_FAIL = 16
 BYTES_FREE_OK = 216
 BYTES_FREE_REJECTED = 9
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per engine launch on the large workload, from an
-# ncu capture of that kernel (profiles/); None until the current kernel has
-# been captured.
-K_SINGLE_LARGE_DRAM_BYTES = 159_744
 
 
 def _peaks():
@@ -378,6 +382,159 @@ def e2e_host_calls(alloc, batches, steps, sptr, pipelined):
     return elapsed, n_ops, h2d, d2h
 
 
+def multi_e2e(ma, batches, steps, sptr):
+    """The batched form end to end through the public host-buffer entry
+    point: ``steps`` batches (wrapping with a reset) from pinned host
+    buffers through hba_multi_step_host_async, E2E_DEPTH calls in flight, the
+    host waiting for and reading step k's first offset before it issues step
+    k + E2E_DEPTH - 1.  Timed on the host, copies and read-back included.
+    Returns (seconds, ops, H2D bytes, D2H bytes)."""
+    import torch
+
+    from paper_2405_07079_gb300 import hba_multi_step_host_async, hba_reset
+
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    nb = min(len(batches), steps)
+    host = [(pin(b["hfrow"].view(np.int32)), pin(b["harow"].view(np.int32)), pin(b["hf"].view(np.int64)),
+             pin(b["hs"].view(np.int64))) for b in batches[:nb]]
+    na_max = max(b["na"] for b in batches[:nb])
+    houts = [torch.empty(max(1, na_max), dtype=torch.int64).pin_memory() for _ in range(E2E_DEPTH)]
+    done = [torch.cuda.Event() for _ in range(E2E_DEPTH)]
+    stream = torch.cuda.current_stream()
+    hba_reset(ma.h, sptr)
+    torch.cuda.synchronize()
+    n_ops = h2d = d2h = seen = pos = 0
+    t0 = time.perf_counter()
+    for k in range(steps):
+        if pos == nb:
+            hba_reset(ma.h, sptr)
+            pos = 0
+        b, (hfr, har, hf, hs) = batches[pos], host[pos]
+        pos += 1
+        j = k % E2E_DEPTH
+        if k >= E2E_DEPTH - 1:
+            i = (k - E2E_DEPTH + 1) % E2E_DEPTH
+            done[i].synchronize()
+            seen ^= int(houts[i][0])
+        hba_multi_step_host_async(ma.h, hfr.data_ptr(), hf.data_ptr() if b["nf"] else 0, b["nf"], har.data_ptr(),
+                                  hs.data_ptr() if b["na"] else 0, b["na"], houts[j].data_ptr() if b["na"] else 0,
+                                  0, sptr)
+        done[j].record(stream)
+        n_ops += b["ops"]
+        h2d += 8 * (b["nf"] + b["na"]) + 2 * hfr.numel() * 4
+        d2h += 8 * b["na"]
+    stream.synchronize()
+    return time.perf_counter() - t0, n_ops, h2d, d2h
+
+
+def l2_copy_peak(dev, mib=24, reps=30) -> dict:
+    """An L2 bandwidth ceiling measured here: a device-to-device copy of a
+    ``mib`` MiB buffer into another (both resident in the 129 MB L2), best
+    of ``reps`` after warm-up, CUDA events; read + write bytes per second."""
+    import torch
+
+    n = mib << 20
+    a = torch.empty(n, dtype=torch.uint8, device=dev).fill_(1)
+    b = torch.empty(n, dtype=torch.uint8, device=dev)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    stream = torch.cuda.current_stream()
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.copy_(a)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return {"gbs": 2 * n / best / 1e9, "how": f"torch copy_ of a {mib} MiB device buffer into another (both "
+                                               f"L2-resident), best of {reps} after 5 warm-up copies, CUDA events; "
+                                               "read + write bytes"}
+
+
+def plain_large_figure(dev, steps=None) -> dict:
+    """The plain single-arena form on the large trace (one 16 GiB arena,
+    batches of 65,536): recorded untimed, then one pass replayed with an L2
+    flush between steps, as the plain bench mode times it."""
+    import torch
+
+    from paper_2405_07079_gb300 import Allocator, workloads
+
+    wl = workloads.large()
+    with Allocator(wl.arena, wl.min_block, threads=1024) as alloc:
+        batches = record_trace(wl, alloc, dev)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.current_stream()
+        alloc.reset()
+        n = len(batches) if steps is None else min(steps, len(batches))
+        ms, served = [], 0
+        for b in batches[:n]:
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            alloc.step(b["f"] if b["nf"] else None, b["s"] if b["na"] else None, out=b["out"], status=b["st"])
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            f, stat, s_, o = b["host"]
+            served += int((stat == 0).sum()) + int((o != FAIL).sum())
+    t = sum(ms) / 1e3
+    ops = sum(b["ops"] for b in batches[:n])
+    return {"workload": wl.name + ": " + wl.note, "steps": n, "value": ops / t, "served_ops_per_s": served / t,
+            "unit": UNIT, "ms_per_step": 1e3 * t / n,
+            "form": "plain single arena: prep grid + engine kernel per batch (k_single<1024>)",
+            "l2": "flushed between steps (256 MiB write, untimed)"}
+
+
+def multi_kernel_name(policy, shape, n_arenas, n_sms, wpc=8) -> str:
+    """The batch kernel a multi-arena launch of this shape runs (the
+    library's own choice, restated)."""
+    if policy == "tlsf":
+        return "k_tlsf<4>"
+    if policy in FIT_POLICIES:
+        return "k_fits<256>"
+    if policy == "bitmask":
+        return "k_bitmask<256>"
+    if isinstance(shape, str):
+        return "k_multi"
+    threads, ctas = shape[0], shape[1]
+    if threads == 32:
+        need = -(-n_arenas // wpc)
+        grid = min(ctas, need) if ctas else need
+        return "k_prep + k_multi_warp<2>" if grid <= 2 * n_sms else "k_prep + k_multi_warp<4>"
+    return f"k_prep + k_multi<{threads}>"
+
+
+def kernel_sources_digest() -> str:
+    """A digest of the CUDA sources and the public header: DRAM traffic
+    taken with ncu is quoted only while the kernels are the ones captured."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2405_07079_gb300", "csrc", "hba_*")))
+    for path in files + [os.path.join(ROOT, "include", "hba.h")]:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per step from an
+# ncu capture, with the algorithmic bytes of the captured steps: keyed by the
+# kernel-source digest it was taken on, and by the kernel.
+PROFILED_TRAFFIC = {}
+
+
+def profiled_traffic(kernel: str, algorithmic_bytes_per_step: float):
+    """DRAM traffic per step for this kernel from its ncu capture, scaled to
+    this run's algorithmic bytes per step (traffic grows with the requests a
+    step carries), or None when no capture of the current sources exists."""
+    rec = PROFILED_TRAFFIC.get((kernel_sources_digest(), kernel))
+    if rec is None:
+        return None
+    return rec["dram_bytes_per_step"] * algorithmic_bytes_per_step / rec["algorithmic_bytes_per_step"]
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
@@ -445,6 +602,10 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return None
     peak, peak_src = _peaks()
+    bound, peak_note = "hbm", f"{peak_src} hbm_gbs"
+    if wl.arena // wl.min_block * 16 <= 32 << 20:  # a record table that stays in L2
+        l2 = l2_copy_peak(dev)
+        bound, peak, peak_note = "l2", l2["gbs"], "measured here: " + l2["how"]
     achieved_gbs = nbytes / busy_s / 1e9
     lat = sorted(step_ms)
     line = {
@@ -466,12 +627,13 @@ def run_gpu(args, rank, world, local_rank):
                                        else alloc_threads(args)),
                    "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
                    "ops_per_step_mean": ops / max(1, args.steps)},
-        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": bound, "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak,
-                     "traffic": (K_SINGLE_LARGE_DRAM_BYTES
-                                 if args.workload == "large" and alloc_threads(args) == 1024 and args.ctas < 2
-                                 and args.policy == "segfit" else None),
-                     "peak_source": f"{peak_src} hbm_gbs",
+                     "traffic": (profiled_traffic(f"k_prep + k_single<{alloc_threads(args)}>",
+                                                  nbytes / max(1, args.steps))
+                                 if args.workload == "large" and args.ctas < 2 and args.policy == "segfit"
+                                 else None),
+                     "peak_source": peak_note,
                      "kernel": ("k_tlsf<1>" if args.policy == "tlsf" else
                                 "k_fits<256>" if args.policy in FIT_POLICIES else
                                 "k_bitmask<256>" if args.policy == "bitmask" else
@@ -511,7 +673,8 @@ def run_multi(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     A = workloads.multi_arena_sizes(args.arenas)
     gen = workloads.MultiLifetimes(A, n_batches=args.batches)
-    ma = MultiAllocator(A, 256, max_total_frees=args.arenas * 2048 + 1, policy=args.policy)
+    cap = args.arenas * 2048 + 1
+    ma = MultiAllocator(A, 256, max_total_frees=cap, policy=args.policy, max_total_allocs=cap)
     t_rec = time.time()
     batches = []
     while (b := gen.next_batch()) is not None:
@@ -528,6 +691,7 @@ def run_multi(args, rank, world, local_rank):
         n_ok, n_fok = int((o != FAIL).sum()), int((stat == 0).sum())
         d["bytes"] = (BYTES_ALLOC_OK * n_ok + BYTES_ALLOC_FAIL * (s.size - n_ok)
                       + BYTES_FREE_OK * n_fok + BYTES_FREE_REJECTED * (f.size - n_fok))
+        d["served"] = n_ok + n_fok
         d["ref_out"] = o.copy()
         d["ref_st"] = stat.copy()
         batches.append(d)
@@ -581,8 +745,14 @@ def run_multi(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     busy_s = sum(step_ms) / 1e3
     ops = sum(batches[i]["ops"] for i in idx)
+    served = sum(batches[i]["served"] for i in idx)
     nbytes = sum(batches[i]["bytes"] for i in idx)
-    (busy_all,), (ops_all,) = reduce_over_ranks([busy_s], [ops], world, dev)
+    # e2e through the public host-buffer entry point, from a fresh state
+    sptr = int(stream.cuda_stream)
+    e2e_s, e2e_ops, e2e_h2d, e2e_d2h = multi_e2e(ma, batches, steps, sptr)
+    (busy_all, e2e_all_s), (ops_all, served_all, e2e_all) = reduce_over_ranks(
+        [busy_s, e2e_s], [ops, served, e2e_ops], world, dev)
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     # the plain form on the same requests: the first P arenas, one handle and
     # one launch per arena per batch; results must equal the batched form's
@@ -609,6 +779,7 @@ def run_multi(args, rank, world, local_rank):
     for a in plain:
         a.close()
     ma.close()
+    large = plain_large_figure(dev) if args.policy == "segfit" and not args.no_plain_large else None
     if rank != 0:
         return None
     extra = {}
@@ -639,35 +810,50 @@ def run_multi(args, rank, world, local_rank):
     peak, peak_src = _peaks()
     achieved = nbytes / busy_s / 1e9
     lat = sorted(step_ms)
+    kernel = multi_kernel_name(args.policy, best, args.arenas, n_sms)
+    plain_v = plain_ops / (plain_ms / 1e3)
     line = {
         "metric": METRIC, "value": ops_all / busy_all, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * busy_all / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "served_ops_per_s": served_all / busy_all,
         "config": {"policy": args.policy,
                    "workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
                                f"min block 256 B, U{{0..2048}} requests per arena per batch, {nb} batches",
                    "form": ("batched: one launch per batch, one warp per arena (k_tlsf<4>)" if args.policy == "tlsf"
                             else "batched: one launch per batch, one CTA per arena (k_fits<256>)"
                             if args.policy in FIT_POLICIES
+                            else "batched: one launch per batch, one CTA per pool (k_bitmask<256>)"
+                            if args.policy == "bitmask"
                             else "batched: prep grid + one multi-arena launch per batch"),
                    "parallelism": f"replicas x{world}",
                    "shape": (best if isinstance(best, str) else
                              {"threads": best[0], "ctas": best[1], "smem_bytes": best[2]}),
-                   "l2": "flushed between steps (256 MiB write, untimed)", "ops_per_step_mean": ops / steps,
+                   "l2": "flushed between steps (256 MiB write, untimed); the record tables (about 87 GB) "
+                         "are far larger than L2", "ops_per_step_mean": ops / steps,
                    "record_s": round(t_rec, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
-                     "kernel": ("k_tlsf<4>" if args.policy == "tlsf" else "k_fits<256>"
-                                if args.policy in FIT_POLICIES else "k_multi"),
+                     "traffic": profiled_traffic(kernel, nbytes / steps), "peak_source": f"{peak_src} hbm_gbs",
+                     "kernel": kernel,
+                     "timed": "CUDA events around each step's launches (the prep grid and the batch kernel)",
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "unit": "per batch of all arenas"},
-        "plain_form_same_requests": {"arenas": P, "batches": nb_plain, "value": plain_ops / (plain_ms / 1e3),
-                                     "unit": UNIT, "results_equal": True},
+        "e2e": {"value": e2e_all / e2e_all_s, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d // max(1, steps),
+                "d2h_bytes_per_step": e2e_d2h // max(1, steps), "api": "hba_multi_step_host_async",
+                "form": (f"pinned host buffers; {E2E_DEPTH} steps in flight; each step's offsets are read on the "
+                         f"host {E2E_DEPTH - 1} steps later; no L2 flush between steps")},
+        "plain_form_same_requests": {"arenas": P, "batches": nb_plain, "value": plain_v, "unit": UNIT,
+                                     "form": "one handle and one hba_step launch per arena per batch",
+                                     "results_equal": True},
+        "batched_over_plain": (ops_all / busy_all) / plain_v,
         "autotune_ms": {f"t{t}_c{c}_s{m}": round(v, 3) for (t, c, m), v in sorted(table.items())},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    if large is not None:
+        line["plain_single_arena_large"] = large
+        line["batched_over_plain_large"] = (ops_all / busy_all) / large["value"]
     line.update(extra)
     return line
 
@@ -766,6 +952,15 @@ def run_serve(args, rank, world, local_rank):
             torch.cuda.synchronize()
             extra["cuda_allocators"][mode] = cuda_replay.replay(ops_l, mode, sptr)
     best = max(sweep, key=lambda r: r["ops_per_s"])
+    l2 = l2_copy_peak(dev)
+    b_alg = (BYTES_ALLOC_OK * best["alloc_ok"] + BYTES_ALLOC_FAIL * best["alloc_fail"]
+             + BYTES_FREE_OK * best["frees"])
+    roof = {"bound": "l2", "achieved": b_alg / best["elapsed_s"] / 1e9, "peak": l2["gbs"], "unit": "GB/s",
+            "frac": b_alg / best["elapsed_s"] / 1e9 / l2["gbs"], "traffic": None,
+            "peak_source": "measured here: " + l2["how"], "kernel": "k_serve",
+            "at_lambda": best["lambda_req_s"],
+            "note": "the 80 GiB arena's record table (84 MB) and list heads fit in L2",
+            "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free"}
     (sec_all,), (ops_all,) = reduce_over_ranks([best["elapsed_s"]], [best["ops_per_s"] * best["elapsed_s"]], world,
                                                torch.device("cuda", local_rank))
     if rank != 0:
@@ -780,6 +975,7 @@ def run_serve(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "latency_us": {"p50": best["p50_us"], "p99": best["p99_us"], "unit": "arrival to result, admitted requests",
                        "at_lambda": best["lambda_req_s"]},
+        "roofline": roof,
         "sweep": sweep, "plain_form_same_batches": plain,
         "serving_over_plain_at_best": (best["ops_per_s"] / plain[-1]["ops_per_s"]
                                        if plain and plain[-1]["lambda_req_s"] == best["lambda_req_s"] else None),
@@ -837,33 +1033,85 @@ def cpu_baseline(wl, policy="segfit") -> dict:
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if args.workload == "multi":
+        return run_reference_multi(args, world)
+    if args.workload == "serve":
+        return {"impl": "reference", "unavailable": "the serving loop has no oracle arm: its oracle replays the "
+                                                    "device's tick log, which needs the GPU run first"}
     from paper_2405_07079_gb300 import workloads
 
+    steps = 1530 if args.steps is None else args.steps
     wl = {"large": workloads.large, "tiny": workloads.tiny, "frag": workloads.frag,
           "usage": workloads.usage, "objects": workloads.objects}[args.workload]()
-    t, ops, k = oracle_steps(wl, n_steps=args.steps, warmup=args.warmup, policy=args.policy)
+    t, ops, k = oracle_steps(wl, n_steps=steps, warmup=args.warmup, policy=args.policy)
     v = ops / t
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": wl.name + ": " + wl.note, "policy": args.policy,
                        "parallelism": "single host thread",
                        "form": "sequential CPU oracle, one batch per step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"batches {args.warmup}..{args.warmup + args.steps - 1} of the trace "
+                             "sample": f"batches {args.warmup}..{args.warmup + steps - 1} of the trace "
                                        "(wrapping to a fresh oracle), oracle calls timed"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_reference_multi(args, world):
+    """The oracle arm of the batched form: the same 4,096-arena workload,
+    one oracle per arena, closed loop; a step is one batch of every arena,
+    applied arena by arena on one host thread (oracle calls timed)."""
+    import oracle
+    from paper_2405_07079_gb300 import workloads
+
+    oracle.build()
+    A = workloads.multi_arena_sizes(args.arenas)
+    steps = 20 if not args.steps else args.steps
+    gen = workloads.MultiLifetimes(A, n_batches=args.warmup + steps)
+    orcs = [_make_oracle(oracle, int(a), 256, args.policy) for a in A]
+    t_or, ops, k = 0.0, 0, 0
+    while (b := gen.next_batch()) is not None:
+        frow, f, arow, s = b
+        outs = []
+        t0 = time.perf_counter()
+        for i in range(A.size):
+            o, _ = orcs[i].batch(f[frow[i]:frow[i + 1]], s[arow[i]:arow[i + 1]])
+            outs.append(o)
+        dt = time.perf_counter() - t0
+        gen.feed(np.concatenate(outs))
+        k += 1
+        if k > args.warmup:
+            t_or += dt
+            ops += f.size + s.size
+    v = ops / t_or
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_or / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"policy": args.policy,
+                       "workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
+                                   f"min block 256 B, U{{0..2048}} requests per arena per batch",
+                       "parallelism": "single host thread",
+                       "form": "sequential CPU oracle per arena, one batch of all arenas per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"batches {args.warmup}..{args.warmup + steps - 1} of the batched trace "
+                                       f"({ops} requests), every arena; oracle calls timed"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1530)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: one pass over the recorded batches for the batched form, "
+                         "1,530 = ten passes over the large trace for the plain form)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=["large", "tiny", "frag", "usage", "objects", "multi", "serve"],
-                    default="large")
+                    default="multi",
+                    help="multi (default): the batched form, 4,096 arenas in one launch per batch; large, tiny, "
+                         "frag, usage, objects: the plain single-arena form; serve: the serving loop")
     ap.add_argument("--policy", choices=["segfit", "tlsf", "first", "next", "best", "bitmask"], default="segfit",
                     help="segregated fit (§5.1), two-level segregated fit (§5.2), a sequential fit on "
                          "address-sorted lists (§4), or the bitmask pool (§3.2); the serving loop is segfit only")
@@ -881,6 +1129,8 @@ def main():
                     help="single arena: batch cluster size (0 or 1 = prep grid + engine; 2..8 = engine CTA + gathering CTAs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cuda-baseline", action="store_true")
+    ap.add_argument("--no-plain-large", action="store_true",
+                    help="batched form: skip the plain single-arena large-trace figure")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -897,10 +1147,12 @@ def main():
                 ap.error("the serving loop runs segregated fit only")
             line = run_serve(args, rank, world, local_rank)
         elif args.workload == "multi":
-            if args.steps == 1530:
+            if args.steps is None:
                 args.steps = 0  # one pass over the recorded batches
             line = run_multi(args, rank, world, local_rank)
         else:
+            if args.steps is None:
+                args.steps = 1530
             line = run_gpu(args, rank, world, local_rank)
         if world > 1:
             import torch

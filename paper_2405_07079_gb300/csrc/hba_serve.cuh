@@ -141,6 +141,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
         }
         __syncthreads();
         if (Q.stop) break;
+        HBA_PROF(40);
         const uint64_t now = Q.now;
         // 1: arrivals (sorted by time: the due ones are a prefix of each window)
         for (int pass = 0; pass < 64; ++pass) {
@@ -169,6 +170,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
             __syncthreads();
             if (m < (uint32_t)NT) break;
         }
+        HBA_PROF(41);
         // 2: due frees: every wheel bucket that has ended
         if (tid == 0) {
             uint32_t nb = 0, total = 0;
@@ -201,6 +203,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
         if (tid == NT - 1) Q.freed_bytes = (uint64_t)fb;
         for (uint32_t bi = tid; bi < nb; bi += NT) g.wheel_cnt[(Q.bfirst + bi) % g.W] = 0;
         __syncthreads();
+        HBA_PROF(42);
         // 3: admission from the queue head while the rounded sizes fit
         {
             const uint32_t qsize = Q.q_tail - Q.q_head;
@@ -239,6 +242,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
             }
         }
         __syncthreads();
+        HBA_PROF(43);
         const uint32_t na = Q.na;
         if (nf == 0 && na == 0) {
             if (tid == 0) {
@@ -271,11 +275,13 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
             }
         }
         __syncthreads();
+        HBA_PROF(44);
         StepArgs a{g.ar, g.rec, g.t_frees, nf, nullptr, g.t_sizes, na, g.t_out, g.scr, g.gi, nf, 0, WAIT_NONE,
                    staged ? 1u : 0u, 0};
         arena_step<NT>(S, a, dyn, dyn_words);
         if (tid == 0) Q.now = globaltimer_ns() - Q.t0;
         __syncthreads();
+        HBA_PROF(45);
         const uint64_t done = Q.now;
         // 5: results, wheel, log
         int64_t ok_n = 0;
@@ -317,6 +323,7 @@ __device__ void serve_loop(Smem<NT>& S, ServeSmem<NT>& Q, const ServeArgs& g, ui
         __syncthreads();
         if (tid == 0) Q.log_pos = lp + need;  // past the capacity: the log is incomplete
         __syncthreads();
+        HBA_PROF(46);
     }
     if (tid == 0) {
         ServeCtl* c = g.ctl;
