@@ -522,7 +522,11 @@ def kernel_sources_digest() -> str:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per step from an
 # ncu capture, with the algorithmic bytes of the captured steps: keyed by the
 # kernel-source digest it was taken on, and by the kernel.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    # profiles/k_multi_warp_batched4096.txt: the default batched command, 20 timed steps
+    ("c88b0ecc4fbb596b", "k_prep + k_multi_warp<4>"): {"dram_bytes_per_step": 990.2e6,
+                                                        "algorithmic_bytes_per_step": 804.8e6},
+}
 
 
 def profiled_traffic(kernel: str, algorithmic_bytes_per_step: float):
@@ -569,7 +573,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clocks:
+    with ClockSampler(local_rank) as clocks, torch.cuda.nvtx.range("timed"):
         for k in range(args.steps):
             if pos == nb:
                 alloc.reset(); pos = 0
@@ -671,7 +675,7 @@ def run_multi(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    A = workloads.multi_arena_sizes(args.arenas)
+    A = workloads.multi_arena_sizes(args.arenas, lo=args.arena_min << 20, hi=args.arena_max << 20)
     gen = workloads.MultiLifetimes(A, n_batches=args.batches)
     cap = args.arenas * 2048 + 1
     ma = MultiAllocator(A, 256, max_total_frees=cap, policy=args.policy, max_total_allocs=cap)
@@ -729,7 +733,7 @@ def run_multi(args, rank, world, local_rank):
     torch.cuda.synchronize()
     from paper_2405_07079_gb300 import hba_launch_count
     launches0 = hba_launch_count(ma.h)
-    with ClockSampler(local_rank) as clocks:
+    with ClockSampler(local_rank) as clocks, torch.cuda.nvtx.range("timed"):
         for k in range(steps):
             if pos == nb:
                 ma_reset(); pos = 0
@@ -818,8 +822,9 @@ def run_multi(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "served_ops_per_s": served_all / busy_all,
         "config": {"policy": args.policy,
-                   "workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform 64 MiB-1 GiB, "
-                               f"min block 256 B, U{{0..2048}} requests per arena per batch, {nb} batches",
+                   "workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform "
+                               f"{args.arena_min} MiB-{args.arena_max} MiB, min block 256 B, U{{0..2048}} requests "
+                               f"per arena per batch, {nb} batches",
                    "form": ("batched: one launch per batch, one warp per arena (k_tlsf<4>)" if args.policy == "tlsf"
                             else "batched: one launch per batch, one CTA per arena (k_fits<256>)"
                             if args.policy in FIT_POLICIES
@@ -1066,7 +1071,7 @@ def run_reference_multi(args, world):
     from paper_2405_07079_gb300 import workloads
 
     oracle.build()
-    A = workloads.multi_arena_sizes(args.arenas)
+    A = workloads.multi_arena_sizes(args.arenas, lo=args.arena_min << 20, hi=args.arena_max << 20)
     steps = 20 if not args.steps else args.steps
     gen = workloads.MultiLifetimes(A, n_batches=args.warmup + steps)
     orcs = [_make_oracle(oracle, int(a), 256, args.policy) for a in A]
@@ -1119,6 +1124,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--arenas", type=int, default=4096)
     ap.add_argument("--batches", type=int, default=200)
+    ap.add_argument("--arena-min", type=int, default=64, help="batched form: smallest arena, MiB")
+    ap.add_argument("--arena-max", type=int, default=1024, help="batched form: largest arena, MiB")
     ap.add_argument("--plain-arenas", type=int, default=64)
     ap.add_argument("--oracle-arenas", type=int, default=256,
                     help="batched form: arenas the oracle baseline runs (whole sequences)")
