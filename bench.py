@@ -176,7 +176,7 @@ def record_trace(wl, alloc, dev, space=None):
                           st_["free_bytes"]))
         batches.append({"f": df, "s": ds, "out": out, "st": st, "nf": f.size, "na": s.size,
                         "host": (f, stat, s, o),
-                        "ops": f.size + s.size, "bytes": nbytes,
+                        "ops": f.size + s.size, "served": n_ok + n_fok, "bytes": nbytes,
                         "hf": torch.from_numpy(f.view(np.int64).copy()).pin_memory(),
                         "hs": torch.from_numpy(s.view(np.int64).copy()).pin_memory()})
     return batches
@@ -538,6 +538,9 @@ PROFILED_TRAFFIC = {
     # profiles/k_multi_warp_batched4096.txt: the default batched command, 20 timed steps
     ("c88b0ecc4fbb596b", "k_prep + k_multi_warp<4>"): {"dram_bytes_per_step": 990.2e6,
                                                         "algorithmic_bytes_per_step": 804.8e6},
+    # profiles/k_single_tiny_k_serve_l2.txt: the tiny trace, 6 timed launches; one 50 ms serving run
+    ("c88b0ecc4fbb596b", "k_single<128>"): {"dram_bytes_per_step": 163.2e3, "algorithmic_bytes_per_step": 10.7e3},
+    ("c88b0ecc4fbb596b", "k_serve"): {"dram_bytes_per_step": 6.74e6, "algorithmic_bytes_per_step": 14.26e6},
 }
 
 
@@ -602,14 +605,15 @@ def run_gpu(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     busy_s = sum(step_ms) / 1e3
     ops = sum(batches[i]["ops"] for i in idx)
+    served = sum(batches[i]["served"] for i in idx)
     nbytes = sum(batches[i]["bytes"] for i in idx)
 
     # e2e through the public host-buffer entry points, from a fresh state
     e2e_s, e2e_ops, e2e_h2d, e2e_d2h = e2e_host_calls(alloc, batches, args.steps, sptr, pipelined=True)
     sync_s, sync_ops, _, _ = e2e_host_calls(alloc, batches, args.steps, sptr, pipelined=False)
 
-    (busy_s, e2e_s, sync_s), (ops_all, e2e_all, sync_all) = reduce_over_ranks(
-        [busy_s, e2e_s, sync_s], [ops, e2e_ops, sync_ops], world, dev)
+    (busy_s, e2e_s, sync_s), (ops_all, e2e_all, sync_all, served_all) = reduce_over_ranks(
+        [busy_s, e2e_s, sync_s], [ops, e2e_ops, sync_ops, served], world, dev)
     stats = alloc.stats()
     cuda_cmp = None
     if rank == 0 and not args.no_cuda_baseline:
@@ -618,6 +622,9 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return None
     peak, peak_src = _peaks()
+    # one launch a step where the engine gathers its own frees (small batches)
+    plain_kernel = (f"k_single<{alloc_threads(args)}>" if launches <= args.steps
+                    else f"k_prep + k_single<{alloc_threads(args)}>")
     bound, peak_note = "hbm", f"{peak_src} hbm_gbs"
     if wl.arena // wl.min_block * 16 <= 32 << 20:  # a record table that stays in L2
         l2 = l2_copy_peak(dev)
@@ -628,6 +635,7 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": ops_all / busy_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * busy_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "served_ops_per_s": served_all / busy_s,
         "config": {"workload": wl.name + ": " + wl.note, "policy": args.policy, "parallelism": f"replicas x{world}",
                    "form": ("two-level segregated fit: one warp applies the batch (k_tlsf<1>)"
                             if args.policy == "tlsf" else
@@ -645,16 +653,14 @@ def run_gpu(args, rank, world, local_rank):
                    "ops_per_step_mean": ops / max(1, args.steps)},
         "roofline": {"bound": bound, "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak,
-                     "traffic": (profiled_traffic(f"k_prep + k_single<{alloc_threads(args)}>",
-                                                  nbytes / max(1, args.steps))
-                                 if args.workload == "large" and args.ctas < 2 and args.policy == "segfit"
-                                 else None),
+                     "traffic": (profiled_traffic(plain_kernel, nbytes / max(1, args.steps))
+                                 if args.ctas < 2 and args.policy == "segfit" else None),
                      "peak_source": peak_note,
                      "kernel": ("k_tlsf<1>" if args.policy == "tlsf" else
                                 "k_fits<256>" if args.policy in FIT_POLICIES else
                                 "k_bitmask<256>" if args.policy == "bitmask" else
                                 f"k_single_cl<{alloc_threads(args)}>" if args.ctas >= 2
-                                else f"k_prep + k_single<{alloc_threads(args)}>"),
+                                else plain_kernel),
                      "bytes_model": "168 B per served alloc, 16 B per failed alloc, 216 B per applied free, 9 B per rejected free"},
         "latency_us": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "unit": "per batch of one step"},
@@ -973,7 +979,7 @@ def run_serve(args, rank, world, local_rank):
     b_alg = (BYTES_ALLOC_OK * best["alloc_ok"] + BYTES_ALLOC_FAIL * best["alloc_fail"]
              + BYTES_FREE_OK * best["frees"])
     roof = {"bound": "l2", "achieved": b_alg / best["elapsed_s"] / 1e9, "peak": l2["gbs"], "unit": "GB/s",
-            "frac": b_alg / best["elapsed_s"] / 1e9 / l2["gbs"], "traffic": None,
+            "frac": b_alg / best["elapsed_s"] / 1e9 / l2["gbs"], "traffic": profiled_traffic("k_serve", b_alg),
             "peak_source": "measured here: " + l2["how"], "kernel": "k_serve",
             "at_lambda": best["lambda_req_s"],
             "note": "the 80 GiB arena's record table (84 MB) and list heads fit in L2",
