@@ -568,6 +568,59 @@ def test_multi_step_host_async_matches_oracles(gpu_lib):
     plain.close()
 
 
+def test_multi_step_host_async_in_a_captured_graph(gpu_lib):
+    """hba_multi_step_host_async captured into a CUDA graph: capturing runs
+    nothing; each replay applies the captured batch from the same pinned
+    host buffers (rewritten between replays) and writes the results back;
+    results equal the per-arena oracles batch after batch."""
+    import torch
+
+    from paper_2405_07079_gb300 import MultiAllocator, hba_multi_step_host_async
+    from paper_2405_07079_gb300 import workloads as W
+
+    A = W.multi_arena_sizes(64, lo=1 << 20, hi=4 << 20)
+    trace, orcs = _multi_oracle_trace(A, n_batches=4, max_ops=64, mean_life=50)
+    nf_max = max(t[1].size for t in trace)
+    na_max = max(t[3].size for t in trace)
+    m = MultiAllocator(A, 256, max_total_frees=max(1, nf_max), max_total_allocs=na_max)
+    try:
+        hfr = torch.zeros(A.size + 1, dtype=torch.int32).pin_memory()
+        har = torch.zeros(A.size + 1, dtype=torch.int32).pin_memory()
+        hf = torch.zeros(max(1, nf_max), dtype=torch.int64).pin_memory()
+        hs = torch.zeros(max(1, na_max), dtype=torch.int64).pin_memory()
+        ho = torch.zeros(max(1, na_max), dtype=torch.int64).pin_memory()
+        hst = torch.zeros(max(1, nf_max), dtype=torch.uint8).pin_memory()
+        # a graph replays fixed sizes: capture one call per distinct (nf, na) of the trace
+        graphs = {}
+        cap = torch.cuda.Stream()
+        for frow, f, arow, s, out, st in trace:
+            key = (f.size, s.size)
+            if key in graphs:
+                continue
+            g = torch.cuda.CUDAGraph()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+                hba_multi_step_host_async(m.h, hfr.data_ptr(), hf.data_ptr(), f.size, har.data_ptr(),
+                                          hs.data_ptr(), s.size, ho.data_ptr(), hst.data_ptr(),
+                                          int(cap.cuda_stream))
+            graphs[key] = g
+        torch.cuda.synchronize()
+        assert m.stats()["alloc_ok"] + m.stats()["alloc_fail"] == 0  # capturing ran nothing
+        for b, (frow, f, arow, s, out, st) in enumerate(trace):
+            hfr.numpy()[:] = frow.view(np.int32)
+            har.numpy()[:] = arow.view(np.int32)
+            hf.numpy()[:f.size] = f.view(np.int64)
+            hs.numpy()[:s.size] = s.view(np.int64)
+            graphs[(f.size, s.size)].replay()
+            torch.cuda.synchronize()
+            assert np.array_equal(ho.numpy().view(np.uint64)[:s.size], out), f"batch {b}"
+            assert np.array_equal(hst.numpy()[:f.size], st), f"batch {b} frees"
+        for i in range(A.size):
+            assert np.array_equal(m.export_state(i), orcs[i].export_state()), i
+    finally:
+        m.close()
+
+
 def test_calls_on_two_streams_are_ordered(gpu_lib):
     """Batches issued back to back on two different streams, with no host
     synchronisation between them: the handle orders the second after the
@@ -1096,8 +1149,10 @@ def test_bitmask_invalid_frees_and_pool_limit(gpu_lib):
         Allocator((786_432 + 1) * 8, 8, policy="bitmask")
 
 
-def test_bitmask_multi_pool(gpu_lib):
-    """Independent pools of different sizes, one CTA each, in one launch."""
+@pytest.mark.parametrize("hi", [520, 8192])
+def test_bitmask_multi_pool(gpu_lib, hi):
+    """Independent pools of different sizes, one CTA each, in one launch;
+    objects up to 65 units, and up to 1,024 units (runs across many words)."""
     import torch
 
     import oracle
@@ -1110,7 +1165,7 @@ def test_bitmask_multi_pool(gpu_lib):
     sizes_a = (rng.integers(64, 20_000, n) * 8).astype(np.uint64)
     m = MultiAllocator(sizes_a, 8, max_total_frees=1 << 16, policy="bitmask")
     orcs = [oracle.BitmaskOracle(int(x), 8) for x in sizes_a]
-    clients = [W.TinyRandom(n_ops=10**9, batch=int(rng.integers(1, 200)), p_free=0.45, lo=1, hi=520,
+    clients = [W.TinyRandom(n_ops=10**9, batch=int(rng.integers(1, 200)), p_free=0.45, lo=1, hi=hi,
                             seed=W.BASE_SEED + 700 + i) for i in range(n)]
     for b in range(10):
         fr, sz, exp_o, exp_s = [], [], [], []
