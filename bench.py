@@ -623,8 +623,8 @@ def run_gpu(args, rank, world, local_rank):
         return None
     peak, peak_src = _peaks()
     # one launch a step where the engine gathers its own frees (small batches)
-    plain_kernel = (f"k_single<{alloc_threads(args)}>" if launches <= args.steps
-                    else f"k_prep + k_single<{alloc_threads(args)}>")
+    eng = f"k_single<{alloc_threads(args)}" + (", two-level lists>" if args.policy == "tlsf" else ">")
+    plain_kernel = eng if launches <= args.steps else "k_prep + " + eng
     bound, peak_note = "hbm", f"{peak_src} hbm_gbs"
     if wl.arena // wl.min_block * 16 <= 32 << 20:  # a record table that stays in L2
         l2 = l2_copy_peak(dev)
@@ -637,7 +637,8 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "served_ops_per_s": served_all / busy_s,
         "config": {"workload": wl.name + ": " + wl.note, "policy": args.policy, "parallelism": f"replicas x{world}",
-                   "form": ("two-level segregated fit: one warp applies the batch (k_tlsf<1>)"
+                   "form": ("two-level segregated fit through the batch engine (512 lists: first level in the "
+                            "bitmap word, second level in shared memory)"
                             if args.policy == "tlsf" else
                             f"{args.policy} fit on address-sorted lists: one CTA applies the batch (k_fits<256>)"
                             if args.policy in FIT_POLICIES else
@@ -646,18 +647,16 @@ def run_gpu(args, rank, world, local_rank):
                             "plain single arena: one thread-block cluster per batch (engine CTA + CTAs that "
                             "gather the frees' records into its shared memory and pre-fill failures)"
                             if args.ctas >= 2 else "plain single arena: prep grid + engine kernel per batch"),
-                   "threads_per_cta": (32 if args.policy == "tlsf"
-                                       else 256 if args.policy in FIT_POLICIES + ("bitmask",)
+                   "threads_per_cta": (256 if args.policy in FIT_POLICIES + ("bitmask",)
                                        else alloc_threads(args)),
                    "l2": "flushed between steps (256 MiB write, untimed)", "trace_batches": nb,
                    "ops_per_step_mean": ops / max(1, args.steps)},
         "roofline": {"bound": bound, "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak,
                      "traffic": (profiled_traffic(plain_kernel, nbytes / max(1, args.steps))
-                                 if args.ctas < 2 and args.policy == "segfit" else None),
+                                 if args.ctas < 2 and args.policy in ("segfit", "tlsf") else None),
                      "peak_source": peak_note,
-                     "kernel": ("k_tlsf<1>" if args.policy == "tlsf" else
-                                "k_fits<256>" if args.policy in FIT_POLICIES else
+                     "kernel": ("k_fits<256>" if args.policy in FIT_POLICIES else
                                 "k_bitmask<256>" if args.policy == "bitmask" else
                                 f"k_single_cl<{alloc_threads(args)}>" if args.ctas >= 2
                                 else plain_kernel),

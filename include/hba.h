@@ -30,10 +30,13 @@
  * the first-level one.  A free block of z bytes is in list (floor(log2 z),
  * the four bits below the leading one); an allocation takes the head of the
  * lowest non-empty list whose lower bound is >= s' (every block there
- * fits).  TLSF handles run one warp per arena, applying the requests one by
- * one; hba_serve_run rejects them, hba_set_shape has no effect on them.  The
- * canonical state lists the 64 x 16 byte lists, then the first-level bitmap,
- * then the 64 second-level bitmaps.
+ * fits).  A single-arena TLSF handle runs its batches through the same
+ * parallel batch engine as segregated fit (the 512 lists with the first
+ * bitmap level in the engine's bitmap word, the second level in shared
+ * memory); a multi-arena TLSF handle runs one warp per arena, applying the
+ * requests one by one.  hba_serve_run rejects TLSF handles.  The canonical
+ * state lists the 64 x 16 byte lists, then the first-level bitmap, then the
+ * 64 second-level bitmaps.
  *
  * HBA_POLICY_FIRST_FIT, _NEXT_FIT and _BEST_FIT are the sequential fits of
  * §4 on the address-sorted free and in-use lists of §3.1 (Algorithm 1

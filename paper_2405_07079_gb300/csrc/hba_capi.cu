@@ -116,19 +116,22 @@ namespace {
 // kernel takes a per-CTA budget that leaves room for several CTAs per SM.
 constexpr uint32_t MULTI_DYN_BYTES_DEFAULT = 24 * 1024;
 
-template <int NT>
+// POL: the class layout (0 segregated fit; 1 two-level segregated fit,
+// whose list heads and bitmaps are tl).
+template <int NT, int POL = 0>
 __global__ void __launch_bounds__(NT, 1) k_single(Arena* ar, Rec* rec, const uint64_t* frees, uint32_t nf,
                                                uint8_t* st, const uint64_t* sizes, uint32_t na,
                                                uint64_t* out, uint32_t* scr, const uint32_t* gi,
-                                               uint32_t dyn_words, uint32_t prefilled, uint32_t self_gather) {
-    __shared__ hba::Smem<NT> S;
+                                               uint32_t dyn_words, uint32_t prefilled, uint32_t self_gather,
+                                               hba::TlsfLists* tl) {
+    __shared__ hba::Smem<NT, POL> S;
     extern __shared__ __align__(16) uint32_t dyn[];
     // waits for the preceding prep grid (gathered records, pre-filled
     // failures) once it has read the arena header; or, with no prep grid,
     // gathers itself
     hba::StepArgs a{ar, rec, frees, nf, st, sizes, na, out, scr, gi, nf, prefilled,
-                    self_gather ? hba::WAIT_NONE : hba::WAIT_GRID, 0, self_gather};
-    hba::arena_step<NT>(S, a, dyn, dyn_words);
+                    self_gather ? hba::WAIT_NONE : hba::WAIT_GRID, 0, self_gather, tl};
+    hba::arena_step<NT, POL>(S, a, dyn, dyn_words);
 }
 
 // Single arena as one thread-block cluster: CTA 0 runs the engine; CTAs
@@ -261,6 +264,8 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_multi_warp(Arena* ars, Rec* 
 // Largest dynamic shared memory a CTA of k_single<NT> / k_multi<NT> can get.
 struct SmemLimits {
     uint32_t single_dyn = 0, multi_dyn = 0;  // bytes
+    uint32_t single_dyn_tl = 0;               // k_single<NT, 1> (two-level segregated fit)
+    uint32_t alloc_words_tl = 0;
     uint32_t alloc_words = 0;                 // minimum dynamic words (alloc phase)
     uint32_t cluster_max = 0;                 // largest batch cluster that fits (0: none)
     uint32_t sms = 0;                         // SMs of the device (warp mode)
@@ -277,6 +282,11 @@ SmemLimits set_smem_limits() {
     if (cudaFuncGetAttributes(&fa, k_single<NT>) == cudaSuccess) {
         L.single_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
         cudaFuncSetAttribute(k_single<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn);
+    }
+    L.alloc_words_tl = hba::alloc_dyn_words<NT, 1>();
+    if (cudaFuncGetAttributes(&fa, k_single<NT, 1>) == cudaSuccess) {
+        L.single_dyn_tl = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_single<NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn_tl);
     }
     if (cudaFuncGetAttributes(&fa, k_multi<NT>) == cudaSuccess) {
         L.multi_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
@@ -330,6 +340,11 @@ SmemLimits set_smem_limits_warp() {
     if (cudaFuncGetAttributes(&fa, k_single<32>) == cudaSuccess) {
         L.single_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
         cudaFuncSetAttribute(k_single<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn);
+    }
+    L.alloc_words_tl = hba::alloc_dyn_words<32, 1>();
+    if (cudaFuncGetAttributes(&fa, k_single<32, 1>) == cudaSuccess) {
+        L.single_dyn_tl = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_single<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.single_dyn_tl);
     }
     if (cudaFuncGetAttributes(&fa, k_multi_warp<2>) == cudaSuccess) {
         const uint32_t total = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
@@ -666,8 +681,12 @@ cudaError_t launch_cluster(void (*k)(KArgs...), uint32_t n, uint32_t block, uint
 // the handle asks for a cluster of 2..8 CTAs and the device holds one, a
 // batch cluster (engine + gathering CTAs).  gi / scr: the gather buffer and
 // the free-phase scratch to use.
-hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
-                           uint32_t na, uint64_t* out, cudaStream_t s, uint32_t* gi, uint32_t* scr) {
+// One batch of a single-arena handle: the prep grid when the batch needs it,
+// then the engine (POL: the class layout of the handle's policy).
+template <int POL>
+hba_status_t launch_single_p(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
+                             uint32_t na, uint64_t* out, cudaStream_t s, uint32_t* gi, uint32_t* scr) {
+    hba::TlsfLists* tl = POL ? h->d_tlsf : nullptr;
     Arena* ar = h->d_arenas;
     Rec* rec = h->d_rec;
     // CTA width: the handle's, or by batch size (small batches pay less per
@@ -675,8 +694,8 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     const uint32_t nt = h->threads ? h->threads : (std::max(nf, na) <= AUTO_SMALL_BATCH ? 128u : 1024u);
     const int li = limit_index(nt);
     const SmemLimits& L = g_limits[li];
-    const uint32_t maxdyn = L.single_dyn;
-    const uint32_t base = 4 * L.alloc_words;
+    const uint32_t maxdyn = POL ? L.single_dyn_tl : L.single_dyn;
+    const uint32_t base = 4 * (POL ? L.alloc_words_tl : L.alloc_words);
     uint32_t dyn;
     if (h->smem_bytes) {
         dyn = std::max(base, std::min(h->smem_bytes, maxdyn));
@@ -690,7 +709,7 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     const uint32_t dw = dyn / 4;
     const bool fill = na >= PREFILL_MIN;
     cudaError_t e;
-    if (nt >= 256 && h->single_ctas >= 2 && L.cluster_max >= 2 && (nf || fill)) {
+    if (POL == 0 && nt >= 256 && h->single_ctas >= 2 && L.cluster_max >= 2 && (nf || fill)) {
         const uint32_t ncl = std::min(h->single_ctas, L.cluster_max);
         const uint32_t staged = nf && hba::stage_fits(nf, dw) ? 1u : 0u;
         const uint32_t pf = fill ? 1u : 0u;
@@ -712,16 +731,22 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
     const uint32_t pf = pre ? 1u : 0u;
     const uint32_t* g = gi;
     switch (nt) {
-        case 32: e = launch_pdl(k_single<32>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
-        case 64: e = launch_pdl(k_single<64>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
-        case 128: e = launch_pdl(k_single<128>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
-        case 256: e = launch_pdl(k_single<256>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
-        case 512: e = launch_pdl(k_single<512>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
-        default: e = launch_pdl(k_single<1024>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self); break;
+        case 32: e = launch_pdl(k_single<32, POL>, 1, 32, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self, tl); break;
+        case 64: e = launch_pdl(k_single<64, POL>, 1, 64, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self, tl); break;
+        case 128: e = launch_pdl(k_single<128, POL>, 1, 128, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self, tl); break;
+        case 256: e = launch_pdl(k_single<256, POL>, 1, 256, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self, tl); break;
+        case 512: e = launch_pdl(k_single<512, POL>, 1, 512, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self, tl); break;
+        default: e = launch_pdl(k_single<1024, POL>, 1, 1024, dyn, s, pdl, ar, rec, frees, nf, st, sizes, na, out, scr, g, dw, pf, self, tl); break;
     }
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
     ++h->launches;
     return HBA_OK;
+}
+
+hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
+                           uint32_t na, uint64_t* out, cudaStream_t s, uint32_t* gi, uint32_t* scr) {
+    return h->policy == HBA_POLICY_TLSF ? launch_single_p<1>(h, frees, nf, st, sizes, na, out, s, gi, scr)
+                                        : launch_single_p<0>(h, frees, nf, st, sizes, na, out, s, gi, scr);
 }
 
 // A TLSF batch: one warp for a single arena, else four arenas per CTA.
@@ -783,10 +808,6 @@ hba_status_t step_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t* st,
                        uint32_t na, uint64_t* out, cudaStream_t s) {
     if (!h || h->n_arenas != 1) return HBA_ERR_INVALID_ARGUMENT;
     if ((nf && !frees) || (na && (!sizes || !out))) return HBA_ERR_INVALID_ARGUMENT;
-    if (h->policy == HBA_POLICY_TLSF) {
-        if (nf == 0 && na == 0) return HBA_OK;
-        return launch_tlsf(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
-    }
     if (is_fit(h->policy)) {
         if (nf == 0 && na == 0) return HBA_OK;
         return launch_fits(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
@@ -1146,8 +1167,6 @@ hba_status_t step_static_impl(hba_t h, const uint64_t* frees, uint32_t nf, uint8
     if ((nf && !frees) || (na && (!sizes || !out))) return HBA_ERR_INVALID_ARGUMENT;
     if (nf > HBA_STATIC_MAX_FREES) return HBA_ERR_INVALID_ARGUMENT;
     if (nf == 0 && na == 0) return HBA_OK;
-    if (h->policy == HBA_POLICY_TLSF)  // needs no scratch
-        return launch_tlsf(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     if (is_fit(h->policy)) return launch_fits(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     if (h->policy == HBA_POLICY_BITMASK) return launch_bitmask(h, nullptr, frees, nf, st, nullptr, sizes, na, out, s);
     uint32_t* base = static_scratch_address();

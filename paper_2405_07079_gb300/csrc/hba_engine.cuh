@@ -59,6 +59,7 @@
 // jumping, where any value read is a valid ancestor); warp-level exchanges
 // (ballots, shuffles) have host versions written over the 32 lanes.
 #pragma once
+#include <type_traits>
 #include <stddef.h>
 #include <stdint.h>
 #include <string.h>
@@ -78,13 +79,13 @@
 #define HBA_DEV __device__ __forceinline__
 // NT == 32 is the warp mode: each warp of a CTA runs its own arena, the
 // "barrier" is the warp's own __syncwarp and the thread index is the lane.
-#define HBA_FOR_THREADS(tid) for (int tid = hba_tid<NT>(); tid < NT; tid += NT)
-#define HBA_SYNC() hba_sync<NT>()
-template <int NT>
+#define HBA_FOR_THREADS(tid) for (int tid = hba_tid<NT, POL>(); tid < NT; tid += NT)
+#define HBA_SYNC() hba_sync<NT, POL>()
+template <int NT, int POL = 0>
 __device__ __forceinline__ int hba_tid() {
     return NT == 32 ? (int)(threadIdx.x & 31u) : (int)threadIdx.x;
 }
-template <int NT>
+template <int NT, int POL = 0>
 __device__ __forceinline__ void hba_sync() {
     if (NT == 32) __syncwarp();
     else __syncthreads();
@@ -218,6 +219,41 @@ HBA_HD uint32_t ctz64(uint64_t v) {
 #endif
 // ceil(log2 v) for v >= 1
 HBA_HD uint32_t clog2(uint32_t v) { return v <= 1 ? 0u : flog2(v - 1) + 1u; }
+
+// ---- two-level segregated fit (§5.2): lists and their arithmetic ---------
+// Sizes in granules.  With 16 lists per class (the paper gives no count),
+// the list of a free block of r granules is (f, s): f = floor(log2 r) and s
+// the four bits below the leading one, so list (f, s) holds the sizes
+// [2^f + s 2^f / 16, 2^f + (s + 1) 2^f / 16); its index is 16 f + s.
+constexpr uint32_t TL_SLB = 4;                 // log2 of the lists per class
+constexpr uint32_t TL_SL = 1u << TL_SLB;       // 16
+constexpr uint32_t TL_FL = 32;                 // granule classes (G < 2^29)
+constexpr uint32_t TL_NL = TL_FL * TL_SL;      // 512 lists
+constexpr uint32_t TL_NONE = 0xFFFFFFFFu;
+
+static_assert(TL_FL == 32, "one second-level mask per lane of a warp");
+
+struct TlsfLists {
+    uint32_t flmask;           // bit f <=> slmask[f] != 0
+    uint32_t pad;
+    uint16_t slmask[TL_FL];    // bit s of slmask[f] <=> list (f, s) non-empty
+    uint32_t heads[TL_NL];     // list f * 16 + s: first block (granule), NIL if empty
+};
+
+// List of a free block of r >= 1 granules.
+HBA_HD uint32_t tl_list(uint32_t r) {
+    const uint32_t f = flog2(r);
+    const uint32_t top = f >= TL_SLB ? r >> (f - TL_SLB) : r << (TL_SLB - f);  // 16 + s
+    return f * TL_SL + (top - TL_SL);
+}
+
+// Lowest list whose lower bound is >= r: r rounded up to a list bound.
+HBA_HD uint32_t tl_bound(uint32_t r) {
+    const uint32_t f = flog2(r);
+    const uint32_t up = f >= TL_SLB ? r + ((1u << (f - TL_SLB)) - 1u) : r;  // r < 2^29: no overflow
+    return tl_list(up);
+}
+
 
 // ---- memory helpers ------------------------------------------------------
 #ifdef HBA_EMULATE
@@ -358,18 +394,25 @@ enum : uint8_t { CL_NONE = 0, CL_FAIL = 1, CL_CARVE = 2, CL_OTHER = 3 };
 // counter slots (per warp, plus one row for single-thread updates)
 enum : int { C_AOK = 0, C_AFAIL, C_FOK, C_FFAIL, C_USEDG, C_REQ, C_NOSPLIT, C_BLOCKS, NCNT };
 
-template <int NT>
+// POL selects the class layout of the free lists: 0, segregated fit (§5.1:
+// 32 classes, a block of r granules in class floor(log2 r), one bitmap
+// word); 1, two-level segregated fit (§5.2: the 512 lists above, the first
+// level in the bitmap word, the second level per class in tsl).
+template <int NT, int POL = 0>
 struct Smem {
     static constexpr int NW = NT >= 32 ? NT / 32 : 1;
     static constexpr int NSEG = NT >= 16 ? NT / 16 : 1;  // segments of the push order
+    static constexpr int NCLS = POL ? (int)TL_NL : NBINS;
+    using ccl_t = typename std::conditional<POL == 0, uint8_t, uint16_t>::type;
     uint64_t A;          // arena bytes
-    uint64_t mask;       // bitmap of classes whose list is non-empty (X excluded)
-    uint32_t heads[NBINS];
+    uint64_t mask;       // bitmap of classes (POL 1: first level) whose list is non-empty (X excluded)
+    uint32_t tsl[POL ? TL_FL : 1];  // POL 1: second-level bitmap of each first-level class
+    uint32_t heads[NCLS];
     uint32_t G, lg;
     // the most recent remainder X: virtual head of class xL while xok
     uint32_t xok, xg, xsz, xright, xL, xprev;
     uint32_t c0g, c0sz, c0prev;  // X when the current round classified its lanes
-    Rec hc[NBINS];       // record of each list head (alloc phase), refilled asynchronously
+    Rec hc[NCLS];        // record of each list head (alloc phase), refilled asynchronously
     // loop control
     uint32_t p, r, cont, evb[2], nul, nruns, flag[3];
     // free phase: run leaders (applied frees with nothing applied to their
@@ -385,23 +428,68 @@ struct Smem {
     uint32_t* cst;       // start granule of each carve lane
     uint32_t* sgr;       // rounded sizes in granules (0: invalid request)
     uint8_t* cls;        // class of each lane in the current round
-    uint8_t* ccl;        // size class c of each lane
+    ccl_t* ccl;          // size class c (the threshold class) of each lane
     int64_t wc[NW + 1][NCNT];
     int64_t warp_tot[32];
     uint32_t wlast[32];  // start of the highest carve lane of each warp (NIL: none)
     uint32_t wcm[32];    // carve lanes of each warp in the current round
-    uint32_t segf[NSEG][NBINS];  // oldest run of each class per push segment
-    uint32_t segl[NSEG][NBINS];  // newest run of each class per push segment
+    uint32_t segf[NSEG][POL ? 1 : NBINS];  // oldest run of each class per push segment (POL 0)
+    uint32_t segl[NSEG][POL ? 1 : NBINS];  // newest run of each class per push segment (POL 0)
     uint32_t cnt[NT];
 };
 
 // words of dynamic shared memory the alloc phase carves for NT lanes
-template <int NT>
-HBA_HD uint32_t alloc_dyn_words() { return 2 * NT + 2 * NT + 4 * NT + NT + NT + NT / 4 + NT / 4 + 8; }
+template <int NT, int POL = 0>
+HBA_HD uint32_t alloc_dyn_words() { return 2 * NT + 2 * NT + 4 * NT + NT + NT + NT / 4 + (POL ? NT / 2 : NT / 4) + 8; }
+
+// ---- the class layout (POL) ---------------------------------------------
+constexpr uint32_t CLS_NONE = 0xFFFFFFFFu;
+// class of a free block of r granules
+template <int POL>
+HBA_HD uint32_t cls_push(uint32_t r) { return POL ? tl_list(r) : flog2(r); }
+// lowest class whose every block fits a request of sg granules
+template <int POL>
+HBA_HD uint32_t cls_req(uint32_t sg) { return POL ? tl_bound(sg) : clog2(sg); }
+// Lowest non-empty class at or above t, with class xl counted non-empty
+// when xok (the virtual remainder X); CLS_NONE if none.  mask: the bitmap
+// word (POL 1: the first level; the second level is S.tsl).
+template <int NT, int POL>
+HBA_HD uint32_t cls_first(const Smem<NT, POL>& S, uint64_t mask, uint32_t t, bool xok, uint32_t xl) {
+    if constexpr (POL == 0) {
+        const uint64_t cand = ((mask | (xok ? (1ull << xl) : 0ull)) >> t) << t;
+        return cand ? ctz64(cand) : CLS_NONE;
+    } else {
+        const uint32_t f = t >> TL_SLB, sb = t & (TL_SL - 1);
+        const uint32_t xf = xl >> TL_SLB, xb = 1u << (xl & (TL_SL - 1));
+        uint32_t here = S.tsl[f] | (xok && xf == f ? xb : 0u);
+        here &= 0xFFFFu << sb;
+        if (here) return (f << TL_SLB) + ctz64(here);
+        uint64_t fl = mask | (xok ? (1ull << xf) : 0ull);
+        fl = (fl >> (f + 1)) << (f + 1);
+        if (!fl) return CLS_NONE;
+        const uint32_t f2 = ctz64(fl);
+        const uint32_t sl = S.tsl[f2] | (xok && xf == f2 ? xb : 0u);
+        return (f2 << TL_SLB) + ctz64(sl);
+    }
+}
+// Mark class k non-empty or empty (one thread).
+template <int NT, int POL>
+HBA_HD void cls_mark(Smem<NT, POL>& S, uint64_t& mask, uint32_t k, bool nonempty) {
+    if constexpr (POL == 0) {
+        if (nonempty) mask |= 1ull << k;
+        else mask &= ~(1ull << k);
+    } else {
+        const uint32_t f = k >> TL_SLB, b = 1u << (k & (TL_SL - 1));
+        const uint32_t sl = nonempty ? (S.tsl[f] | b) : (S.tsl[f] & ~b);
+        S.tsl[f] = sl;
+        if (sl) mask |= 1ull << f;
+        else mask &= ~(1ull << f);
+    }
+}
 
 // ---- warp-aggregated counters and votes (call convergently) --------------
-template <int NT>
-HBA_DEV void warp_count(Smem<NT>& S, int tid, int k, bool pred) {
+template <int NT, int POL = 0>
+HBA_DEV void warp_count(Smem<NT, POL>& S, int tid, int k, bool pred) {
 #ifdef HBA_EMULATE
     S.wc[tid / 32][k] += pred ? 1 : 0;
 #else
@@ -409,8 +497,8 @@ HBA_DEV void warp_count(Smem<NT>& S, int tid, int k, bool pred) {
     if ((tid & 31) == 0) S.wc[tid >> 5][k] += __popc(b);
 #endif
 }
-template <int NT>
-HBA_DEV void warp_sum(Smem<NT>& S, int tid, int k, int64_t v) {
+template <int NT, int POL = 0>
+HBA_DEV void warp_sum(Smem<NT, POL>& S, int tid, int k, int64_t v) {
 #ifdef HBA_EMULATE
     S.wc[tid / 32][k] += v;
 #else
@@ -420,8 +508,8 @@ HBA_DEV void warp_sum(Smem<NT>& S, int tid, int k, int64_t v) {
 #endif
 }
 // single-thread counter update (its own row: never races with warp_*)
-template <int NT>
-HBA_DEV void single_add(Smem<NT>& S, int k, int64_t v) { S.wc[Smem<NT>::NW][k] += v; }
+template <int NT, int POL = 0>
+HBA_DEV void single_add(Smem<NT, POL>& S, int k, int64_t v) { S.wc[Smem<NT, POL>::NW][k] += v; }
 
 HBA_DEV void prefetch_l2(const void* p) {
 #ifdef HBA_EMULATE
@@ -461,25 +549,25 @@ HBA_DEV void rec_copy_wait() {
 // (also stored in v[tid]); warps outside the window contribute nothing, do
 // no shuffles and leave their v[] untouched.  One barrier inside; on return
 // only the caller's own v[tid] may be read without another barrier.
-template <int NT>
+template <int NT, int POL = 0>
 HBA_DEV bool warp_in_window(int wid, uint32_t lo, uint32_t hi) {
     const uint32_t w0 = (uint32_t)wid * 32u, w1 = w0 + 32u;
     return w0 < hi && lo < w1;
 }
-template <int NT>
-HBA_DEV int64_t scan_incl_i64(Smem<NT>& S, int64_t* v, uint32_t lo, uint32_t hi) {
+template <int NT, int POL = 0>
+HBA_DEV int64_t scan_incl_i64(Smem<NT, POL>& S, int64_t* v, uint32_t lo, uint32_t hi) {
 #ifdef HBA_EMULATE
     int64_t run = 0;
     for (int i = 0; i < NT; ++i)
-        if (warp_in_window<NT>(i / 32, lo, hi)) {
+        if (warp_in_window<NT, POL>(i / 32, lo, hi)) {
             run += v[i];
             v[i] = run;
         }
     (void)S;
     return 0;
 #else
-    const int tid = hba_tid<NT>(), lane = tid & 31, wid = tid >> 5;
-    const bool act = warp_in_window<NT>(wid, lo, hi);
+    const int tid = hba_tid<NT, POL>(), lane = tid & 31, wid = tid >> 5;
+    const bool act = warp_in_window<NT, POL>(wid, lo, hi);
     int64_t x = act ? v[tid] : 0;
     if (act) {
 #pragma unroll
@@ -510,8 +598,8 @@ HBA_DEV int64_t scan_incl_i64(Smem<NT>& S, int64_t* v, uint32_t lo, uint32_t hi)
 
 // Exclusive prefix sum of c[0..NT) in place; *total receives the sum.
 // Followed by a barrier.
-template <int NT>
-HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
+template <int NT, int POL = 0>
+HBA_DEV void scan_excl_u32(Smem<NT, POL>& S, uint32_t* c, uint32_t* total) {
 #ifdef HBA_EMULATE
     uint32_t run = 0;
     for (int i = 0; i < NT; ++i) {
@@ -522,7 +610,7 @@ HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
     *total = run;
     (void)S;
 #else
-    const int tid = hba_tid<NT>(), lane = tid & 31, wid = tid >> 5;
+    const int tid = hba_tid<NT, POL>(), lane = tid & 31, wid = tid >> 5;
     int64_t own = c[tid];
     int64_t x = own;
 #pragma unroll
@@ -544,7 +632,7 @@ HBA_DEV void scan_excl_u32(Smem<NT>& S, uint32_t* c, uint32_t* total) {
     }
     c[tid] = (uint32_t)(x - own);
     if (tid == NT - 1) *total = (uint32_t)x;
-    hba_sync<NT>();
+    hba_sync<NT, POL>();
 #endif
 }
 
@@ -573,6 +661,7 @@ struct StepArgs {
                            // records itself (small batches), into the free
                            // phase's shared-memory layout or, when that does
                            // not fit, into gi
+    TlsfLists* tl;         // two-level segregated fit (POL 1): the arena's list heads and bitmaps
 };
 constexpr uint32_t WAIT_NONE = 0, WAIT_GRID = 1, WAIT_CLUSTER = 2;
 
@@ -608,12 +697,12 @@ struct XReg {
     uint32_t xok, xg, xsz, xL, xprev, xright, lg, G;
     int64_t aok, afail, usedg, req, nosplit;
 };
-template <int NT>
-HBA_DEV XReg x_load(const Smem<NT>& S) {
+template <int NT, int POL = 0>
+HBA_DEV XReg x_load(const Smem<NT, POL>& S) {
     return XReg{S.mask, S.xok, S.xg, S.xsz, S.xL, S.xprev, S.xright, S.lg, S.G, 0, 0, 0, 0, 0};
 }
-template <int NT>
-HBA_DEV void x_store(Smem<NT>& S, const XReg& X) {
+template <int NT, int POL = 0>
+HBA_DEV void x_store(Smem<NT, POL>& S, const XReg& X) {
     S.mask = X.mask;
     S.xok = X.xok;
     S.xg = X.xg;
@@ -621,7 +710,7 @@ HBA_DEV void x_store(Smem<NT>& S, const XReg& X) {
     S.xL = X.xL;
     S.xprev = X.xprev;
     S.xright = X.xright;
-    int64_t* c = S.wc[Smem<NT>::NW];
+    int64_t* c = S.wc[Smem<NT, POL>::NW];
     c[C_AOK] += X.aok;
     c[C_AFAIL] += X.afail;
     c[C_USEDG] += X.usedg;
@@ -631,8 +720,8 @@ HBA_DEV void x_store(Smem<NT>& S, const XReg& X) {
 
 // Push the virtual remainder X at the head of its list and write its record
 // (one thread).
-template <int NT>
-HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec, XReg& X, bool cache = false) {
+template <int NT, int POL = 0>
+HBA_DEV void materialize_x(Smem<NT, POL>& S, Rec* rec, XReg& X, bool cache = false) {
     const uint32_t b = X.xL, old = S.heads[b];
     const Rec r{mkx(X.xsz, ST_FREE), X.xprev, old, NIL};
     str(rec, X.xg, r);
@@ -642,7 +731,7 @@ HBA_DEV void materialize_x(Smem<NT>& S, Rec* rec, XReg& X, bool cache = false) {
     }
     if (old != NIL) rec[old].w = X.xg;
     S.heads[b] = X.xg;
-    X.mask |= 1ull << b;
+    cls_mark<NT, POL>(S, X.mask, b, true);
     if (X.xright < X.G) rec[X.xright].y = X.xg;
     X.xok = 0;
 }
@@ -713,8 +802,8 @@ HBA_HD uint64_t* gt_slots(uint32_t nf, uint32_t* dyn, uint32_t dyn_words, uint32
 
 constexpr uint32_t FL_WIN = 4;  // flag: this free is applied
 
-template <int NT>
-HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
+template <int NT, int POL = 0>
+HBA_DEV void free_phase(Smem<NT, POL>& S, const StepArgs& a) {
     const uint32_t nf = a.nf;
     Rec* rec = a.rec;
     const uint32_t hcap = gt_capacity(nf);
@@ -983,7 +1072,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                     n = rec[n].z;
                     if (++guard > S.G) { S.err = ERR_LIST_WALK; n = NIL; break; }
                 }
-                if (pv == NIL) S.heads[flog2(sz_of(r.x))] = n;
+                if (pv == NIL) S.heads[cls_push<POL>(sz_of(r.x))] = n;
                 else rec[pv].z = n;
                 if (n != NIL) rec[n].w = pv;
             }
@@ -1034,7 +1123,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
                 for (uint32_t k = 0; k < nlead; ++k) {
                     const uint32_t j = S.lead[k];
                     const uint32_t H = lh[j];
-                    const uint32_t b = flog2(rend[j] - H);
+                    const uint32_t b = cls_push<POL>(rend[j] - H);
                     const uint32_t old = S.heads[b];
                     rec[H].z = old;
                     rec[H].w = NIL;
@@ -1054,7 +1143,7 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             S.cnt[tid] = c;
         }
         HBA_SYNC();
-        scan_excl_u32<NT>(S, S.cnt, &S.flag[0]);
+        scan_excl_u32<NT, POL>(S, S.cnt, &S.flag[0]);
         nruns = S.flag[0];
         HBA_FOR_THREADS(tid) {
             const uint32_t lo = tid * per, hi = lo + per < nf ? lo + per : nf;
@@ -1064,9 +1153,10 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
         }
         HBA_SYNC();
         HBA_PROF(7);
+        if constexpr (POL == 0) {
         // F8a: the merged blocks are pushed in run order.  Split that order into
         // NSEG segments; inside each, link consecutive runs of the same class.
-        constexpr int NSEG = Smem<NT>::NSEG;
+        constexpr int NSEG = Smem<NT, POL>::NSEG;
         HBA_FOR_THREADS(tid) {
             if (tid < NSEG) {
                 uint32_t* F = S.segf[tid];
@@ -1109,15 +1199,98 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
             }
         }
         HBA_SYNC();
+        } else {
+            // F8 (two-level lists, too many for per-segment arrays): each run
+            // finds the previous run of its list in push order (one warp, 32
+            // runs at a time, the last run seen of each list in a table that
+            // borrows the head-record cache, idle here); every run then links
+            // below it that run, or the list's old head; the newest run of
+            // each list becomes its head.
+            uint32_t* last = reinterpret_cast<uint32_t*>(S.hc);  // TL_NL entries
+            HBA_FOR_THREADS(tid) {
+                for (uint32_t c = tid; c < TL_NL; c += NT) last[c] = NIL;
+            }
+            HBA_SYNC();
+            HBA_FOR_THREADS(tid) {
+#ifdef HBA_EMULATE
+                if (tid == 0) {
+                    for (uint32_t k = 0; k < nruns; ++k) {
+                        const uint32_t j = runs[k];
+                        const uint32_t c = cls_push<POL>(rend[j] - lh[j]);
+                        root[k] = last[c];
+                        last[c] = k;
+                    }
+                }
+#else
+                if ((tid >> 5) == 0) {
+                    const uint32_t lane = (uint32_t)tid & 31u;
+                    for (uint32_t c0 = 0; c0 < nruns; c0 += 32) {  // same trip count in the warp
+                        const uint32_t k = c0 + lane;
+                        const bool v = k < nruns;
+                        uint32_t c = TL_NL + lane;  // idle lanes: a list of their own
+                        if (v) {
+                            const uint32_t j = runs[k];
+                            c = cls_push<POL>(rend[j] - lh[j]);
+                        }
+                        const unsigned mm = __match_any_sync(0xffffffffu, c);
+                        const unsigned lower = mm & ((1u << lane) - 1u);
+                        if (v) root[k] = lower ? c0 + (31u - (uint32_t)__clz(lower)) : last[c];
+                        __syncwarp();
+                        if (v && (mm >> lane) == 1u) last[c] = k;  // the newest of its list so far
+                        __syncwarp();
+                    }
+                }
+#endif
+            }
+            HBA_SYNC();
+            HBA_FOR_THREADS(tid) {
+                for (uint32_t k = tid; k < nruns; k += NT) {
+                    const uint32_t j = runs[k];
+                    const uint32_t H = lh[j];
+                    const uint32_t pk = root[k];
+                    const uint32_t below = pk != NIL ? lh[runs[pk]] : S.heads[cls_push<POL>(rend[j] - H)];
+                    rec[H].z = below;
+                    if (below != NIL) rec[below].w = H;
+                }
+            }
+            HBA_SYNC();
+            HBA_FOR_THREADS(tid) {
+                for (uint32_t c = tid; c < TL_NL; c += NT) {
+                    const uint32_t k = last[c];
+                    if (k != NIL) {
+                        const uint32_t H = lh[runs[k]];
+                        rec[H].w = NIL;
+                        S.heads[c] = H;
+                    }
+                }
+            }
+            HBA_SYNC();
+        }
+    }
+    if constexpr (POL == 1) {  // the second level, from the heads
+        HBA_FOR_THREADS(tid) {
+            for (uint32_t f = tid; f < TL_FL; f += NT) {
+                uint32_t m = 0;
+                for (uint32_t sb = 0; sb < TL_SL; ++sb)
+                    if (S.heads[f * TL_SL + sb] != NIL) m |= 1u << sb;
+                S.tsl[f] = m;
+            }
+        }
+        HBA_SYNC();
     }
     HBA_FOR_THREADS(tid) {
         if (tid == 0) {
             uint64_t m = 0;
-            for (int b = 0; b < NBINS; ++b)
-                if (S.heads[b] != NIL) m |= 1ull << b;
+            if constexpr (POL == 0) {
+                for (int b = 0; b < NBINS; ++b)
+                    if (S.heads[b] != NIL) m |= 1ull << b;
+            } else {
+                for (uint32_t f = 0; f < TL_FL; ++f)
+                    if (S.tsl[f]) m |= 1ull << f;
+            }
             S.mask = m;
             int64_t fok = 0;
-            for (int w2 = 0; w2 <= Smem<NT>::NW; ++w2) fok += S.wc[w2][C_FOK];
+            for (int w2 = 0; w2 <= Smem<NT, POL>::NW; ++w2) fok += S.wc[w2][C_FOK];
             single_add(S, C_FFAIL, (int64_t)nf - fok);
             // every run becomes one block
             single_add(S, C_BLOCKS, (int64_t)nruns - fok - (int64_t)S.nul);
@@ -1134,18 +1307,16 @@ HBA_DEV void free_phase(Smem<NT>& S, const StepArgs& a) {
 // Apply request i alone against the current state (one thread, X in
 // registers): the general step of Algorithm 4 -- fail, carve from X, or pop
 // another list.
-template <int NT>
-HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, uint64_t s, uint32_t sg,
+template <int NT, int POL = 0>
+HBA_DEV void seq_request(Smem<NT, POL>& S, const StepArgs& a, XReg& X, uint32_t i, uint64_t s, uint32_t sg,
                          uint32_t c) {
     Rec* rec = a.rec;
-    const uint64_t M = X.mask | (X.xok ? (1ull << X.xL) : 0ull);
-    const uint64_t cand = sg ? (M >> c) << c : 0ull;
-    if (!cand) {
+    const uint32_t k = sg ? cls_first<NT, POL>(S, X.mask, c, X.xok, X.xL) : CLS_NONE;
+    if (k == CLS_NONE) {
         if (!a.prefilled) a.out[i] = FAIL64;
         ++X.afail;
         return;
     }
-    const uint32_t k = ctz64(cand);
     if (X.xok && k == X.xL) {
         // carve the front of X
         const uint32_t start = X.xg;
@@ -1159,16 +1330,16 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
             if (X.xright < X.G) rec[X.xright].y = start;
             ++X.nosplit;
         } else {
-            X.xL = flog2(X.xsz);
+            X.xL = cls_push<POL>(X.xsz);
         }
     } else {
         // pop the head of list k (its record is cached); the old X becomes a
         // listed block first
-        if (X.xok) materialize_x<NT>(S, rec, X, true);
+        if (X.xok) materialize_x<NT, POL>(S, rec, X, true);
         const uint32_t Y = S.heads[k];
         if (Y >= X.G) {  // bitmap and heads disagree: record, fail the request
             S.err = ERR_EMPTY_HEAD;
-            X.mask &= ~(1ull << k);
+            cls_mark<NT, POL>(S, X.mask, k, false);
             if (!a.prefilled) a.out[i] = FAIL64;
             ++X.afail;
             return;
@@ -1178,7 +1349,7 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
         const uint32_t nxt = ry.z;
         S.heads[k] = nxt;
         if (nxt == NIL) {
-            X.mask &= ~(1ull << k);
+            cls_mark<NT, POL>(S, X.mask, k, false);
         } else {
             rec[nxt].w = NIL;
             rec_copy_async(&S.hc[k], rec + nxt);  // the new head, for a later pop
@@ -1192,7 +1363,7 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
             X.xsz = ysz - sg;
             X.xprev = Y;
             X.xright = Y + ysz;
-            X.xL = flog2(ysz - sg);
+            X.xL = cls_push<POL>(ysz - sg);
         } else {
             ++X.nosplit;
         }
@@ -1207,8 +1378,8 @@ HBA_DEV void seq_request(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t i, ui
 // prev_adj at the start of the round when there is none.  Lanes below r are
 // never carves.  GPU: ballot and shuffle inside the warp, per-warp last
 // carves (S.wlast) across warps.  Call convergently.
-template <int NT>
-HBA_DEV uint32_t prev_carve_start(Smem<NT>& S, int tid, uint32_t r, bool carve, uint32_t start) {
+template <int NT, int POL = 0>
+HBA_DEV uint32_t prev_carve_start(Smem<NT, POL>& S, int tid, uint32_t r, bool carve, uint32_t start) {
 #ifdef HBA_EMULATE
     (void)carve;
     (void)start;
@@ -1230,8 +1401,8 @@ HBA_DEV uint32_t prev_carve_start(Smem<NT>& S, int tid, uint32_t r, bool carve, 
 // Start granule of the last carve lane in [r, e), or X's prev_adj at the
 // start of the round when there is none (one thread, after the verify
 // barrier: per-warp carve masks in S.wcm).
-template <int NT>
-HBA_DEV uint32_t last_carve_below(Smem<NT>& S, uint32_t r, uint32_t e) {
+template <int NT, int POL = 0>
+HBA_DEV uint32_t last_carve_below(Smem<NT, POL>& S, uint32_t r, uint32_t e) {
     if (e <= r) return S.c0prev;
     const uint32_t hi = e - 1;
     int w = (int)(hi >> 5);
@@ -1264,10 +1435,10 @@ HBA_DEV void x_bcast(XReg& X) {
 // lanes in a row that pop no list (carves from X and failures: the lanes
 // that block-wide or warp-wide rounds resolve in parallel), or more than
 // QUIET_FIRST before any further pop; returns the first lane not applied.
-template <int NT>
-HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
+template <int NT, int POL = 0>
+HBA_DEV uint32_t seq_run(Smem<NT, POL>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
                          uint32_t more) {
-    seq_request<NT>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
+    seq_request<NT, POL>(S, a, X, p + q, S.s64[q], S.sgr[q], S.ccl[q]);
     ++q;
     const uint32_t end = q + more < stop ? q + more : stop;
     uint32_t quiet = 0, quiet_max = QUIET_FIRST;
@@ -1276,8 +1447,8 @@ HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, ui
         const uint32_t sg = S.sgr[q], c = S.ccl[q];
         bool pop = false;
         if (sg) {
-            const uint64_t cand = ((X.mask | (X.xok ? (1ull << X.xL) : 0ull)) >> c) << c;
-            pop = cand && !(X.xok && ctz64(cand) == X.xL);
+            const uint32_t k = cls_first<NT, POL>(S, X.mask, c, X.xok, X.xL);
+            pop = k != CLS_NONE && !(X.xok && k == X.xL);
         }
         if (pop) {
             quiet = 0;
@@ -1285,7 +1456,7 @@ HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, ui
         } else if (++quiet > quiet_max) {
             break;
         }
-        seq_request<NT>(S, a, X, p + q, S.s64[q], sg, c);
+        seq_request<NT, POL>(S, a, X, p + q, S.s64[q], sg, c);
         HBA_PROF(27);
     }
     return q;
@@ -1299,8 +1470,8 @@ HBA_DEV uint32_t seq_run(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, ui
 // block-wide rounds take over).  X is replicated in the warp's registers.
 // Returns the first lane not applied.
 #ifdef HBA_EMULATE
-template <int NT>
-HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
+template <int NT, int POL = 0>
+HBA_DEV uint32_t warp_stretch(Smem<NT, POL>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
                               uint32_t lane) {
     (void)lane;
     Rec* rec = a.rec;
@@ -1314,9 +1485,8 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
             const uint32_t i = q + l, sg = S.sgr[i], c = S.ccl[i];
             cl[l] = CL_FAIL;
             if (sg) {
-                const uint64_t M = X.mask | (X.xok ? (1ull << X.xL) : 0ull);
-                const uint64_t cand = (M >> c) << c;
-                if (cand) cl[l] = (X.xok && ctz64(cand) == X.xL) ? CL_CARVE : CL_OTHER;
+                const uint32_t k = cls_first<NT, POL>(S, X.mask, c, X.xok, X.xL);
+                if (k != CLS_NONE) cl[l] = (X.xok && k == X.xL) ? CL_CARVE : CL_OTHER;
             }
             run += cl[l] == CL_CARVE ? sg : 0;
             P[l] = run;
@@ -1330,14 +1500,9 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
                 const uint64_t bc = P[l] - sg;
                 start[l] = X.xg + (uint32_t)bc;
                 const int64_t before = (int64_t)X.xsz - (int64_t)bc;
-                uint64_t M = X.mask;
-                uint32_t Lt = 64;
-                if (before > 0) {
-                    Lt = flog2((uint32_t)before);
-                    M |= 1ull << Lt;
-                }
-                const uint64_t cand = (M >> c) << c;
-                if (!(cand && ctz64(cand) == Lt)) e = true;
+                if (before <= 0 || cls_first<NT, POL>(S, X.mask, c, true, cls_push<POL>((uint32_t)before)) !=
+                                       cls_push<POL>((uint32_t)before))
+                    e = true;
             }
             if (e) ev = l;
         }
@@ -1367,19 +1532,19 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
                 if (X.xright < X.G) rec[X.xright].y = X.xprev;
                 ++X.nosplit;
             } else {
-                X.xL = flog2(X.xsz);
+                X.xL = cls_push<POL>(X.xsz);
             }
         }
         q += ev;
         HBA_PROF(25);
         if (ev == nl) break;
-        q = seq_run<NT>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
+        q = seq_run<NT, POL>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
     }
     return q;
 }
 #else
-template <int NT>
-HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
+template <int NT, int POL = 0>
+HBA_DEV uint32_t warp_stretch(Smem<NT, POL>& S, const StepArgs& a, XReg& X, uint32_t p, uint32_t q, uint32_t stop,
                               uint32_t lane) {
     constexpr unsigned FULL = 0xffffffffu;
     Rec* rec = a.rec;
@@ -1396,9 +1561,8 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
             s = S.s64[i];
             cl = CL_FAIL;
             if (sg) {
-                const uint64_t M = X.mask | (X.xok ? (1ull << X.xL) : 0ull);
-                const uint64_t cand = (M >> c) << c;
-                if (cand) cl = (X.xok && ctz64(cand) == X.xL) ? CL_CARVE : CL_OTHER;
+                const uint32_t k = cls_first<NT, POL>(S, X.mask, c, X.xok, X.xL);
+                if (k != CLS_NONE) cl = (X.xok && k == X.xL) ? CL_CARVE : CL_OTHER;
             }
         }
         uint64_t P = cl == CL_CARVE ? sg : 0;
@@ -1413,14 +1577,9 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
             const uint64_t bc = P - sg;
             start = X.xg + (uint32_t)bc;
             const int64_t before = (int64_t)X.xsz - (int64_t)bc;
-            uint64_t M = X.mask;
-            uint32_t Lt = 64;
-            if (before > 0) {
-                Lt = flog2((uint32_t)before);
-                M |= 1ull << Lt;
-            }
-            const uint64_t cand = (M >> c) << c;
-            if (!(cand && ctz64(cand) == Lt)) e = true;
+            if (before <= 0 || cls_first<NT, POL>(S, X.mask, c, true, cls_push<POL>((uint32_t)before)) !=
+                                   cls_push<POL>((uint32_t)before))
+                e = true;
         }
         const unsigned eb = __ballot_sync(FULL, e);
         const uint32_t ev = eb ? (uint32_t)(__ffs(eb) - 1) : nl;
@@ -1455,16 +1614,17 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
                 if (lane == 0 && X.xright < X.G) rec[X.xright].y = X.xprev;
                 ++X.nosplit;
             } else {
-                X.xL = flog2(X.xsz);
+                X.xL = cls_push<POL>(X.xsz);
             }
         }
         q += ev;
         if (lane == 0) HBA_PROF(25);
         if (ev == nl) break;
         uint32_t qn = 0;
-        if (lane == 0) qn = seq_run<NT>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
+        if (lane == 0) qn = seq_run<NT, POL>(S, a, X, p, q, stop, ev == 0 ? SERIAL_LANES : 0);
         q = __shfl_sync(FULL, qn, 0);
         x_bcast(X);
+        if constexpr (POL == 1) __syncwarp();  // the second-level bitmap lane 0 changed
     }
     return q;
 }
@@ -1474,23 +1634,23 @@ HBA_DEV uint32_t warp_stretch(Smem<NT>& S, const StepArgs& a, XReg& X, uint32_t 
 // emulation): advance X past the carves resolved in parallel, apply the event
 // lane alone, go on with warp-wide rounds when events are dense, and publish
 // where the next round starts.
-template <int NT>
-HBA_DEV void round_tail(Smem<NT>& S, const StepArgs& a, uint32_t p, uint32_t r, uint32_t nres, uint32_t n_here,
+template <int NT, int POL = 0>
+HBA_DEV void round_tail(Smem<NT, POL>& S, const StepArgs& a, uint32_t p, uint32_t r, uint32_t nres, uint32_t n_here,
                         uint32_t lane) {
     Rec* rec = a.rec;
-    XReg X = x_load<NT>(S);
+    XReg X = x_load<NT, POL>(S);
     const int64_t gave = nres > r ? S.val[nres - 1] : 0;
     if (gave > 0) {
         X.xg = S.c0g + (uint32_t)gave;
         X.xsz = S.c0sz - (uint32_t)gave;
-        X.xprev = last_carve_below<NT>(S, r, nres);
+        X.xprev = last_carve_below<NT, POL>(S, r, nres);
         X.usedg += gave;
         if (X.xsz == 0) {
             X.xok = 0;
             if (lane == 0 && X.xright < X.G) rec[X.xright].y = X.xprev;
             ++X.nosplit;
         } else {
-            X.xL = flog2(X.xsz);
+            X.xL = cls_push<POL>(X.xsz);
         }
     }
     uint32_t next = n_here;
@@ -1498,28 +1658,29 @@ HBA_DEV void round_tail(Smem<NT>& S, const StepArgs& a, uint32_t p, uint32_t r, 
         // the event lane, and when (almost) nothing came before it, the next
         // few one by one
         uint32_t qn = 0;
-        if (lane == 0) qn = seq_run<NT>(S, a, X, p, nres, n_here, nres - r <= SERIAL_AFTER ? SERIAL_LANES : 0);
+        if (lane == 0) qn = seq_run<NT, POL>(S, a, X, p, nres, n_here, nres - r <= SERIAL_AFTER ? SERIAL_LANES : 0);
 #ifdef HBA_EMULATE
         next = qn;
 #else
         next = __shfl_sync(0xffffffffu, qn, 0);
+        if constexpr (POL == 1) __syncwarp();  // the second-level bitmap lane 0 changed
 #endif
         x_bcast(X);
         if (next < n_here && nres - r < STRETCH_BELOW) {
             const uint32_t stop = next + STRETCH_LANES < n_here ? next + STRETCH_LANES : n_here;
-            next = warp_stretch<NT>(S, a, X, p, next, stop, lane);
+            next = warp_stretch<NT, POL>(S, a, X, p, next, stop, lane);
         }
     }
     if (lane == 0) {
-        x_store<NT>(S, X);
+        x_store<NT, POL>(S, X);
         S.r = next;
         S.cont = next < n_here;
         if (!S.cont) S.p = p + n_here;
     }
 }
 
-template <int NT>
-HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
+template <int NT, int POL = 0>
+HBA_DEV void alloc_phase(Smem<NT, POL>& S, const StepArgs& a) {
     const uint32_t na = a.na;
     Rec* rec = a.rec;
     const uint32_t lg = S.lg;
@@ -1534,12 +1695,22 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             S.cst = d + 8 * NT;
             S.sgr = d + 9 * NT;
             S.cls = reinterpret_cast<uint8_t*>(d + 10 * NT);
-            S.ccl = reinterpret_cast<uint8_t*>(d + 10 * NT + NT / 4 + 4);
+            S.ccl = reinterpret_cast<typename Smem<NT, POL>::ccl_t*>(d + 10 * NT + NT / 4 + 4);
             S.p = 0;
             S.xok = 0;
             // the record of every list head, for the pops of this phase
-            for (int b = 0; b < NBINS; ++b)
-                if (S.heads[b] != NIL) rec_copy_async(&S.hc[b], rec + S.heads[b]);
+            if constexpr (POL == 0) {
+                for (int b = 0; b < NBINS; ++b)
+                    if (S.heads[b] != NIL) rec_copy_async(&S.hc[b], rec + S.heads[b]);
+            } else {  // the non-empty lists, from the two bitmap levels
+                for (uint64_t fm = S.mask; fm; fm &= fm - 1) {
+                    const uint32_t f = ctz64(fm);
+                    for (uint32_t sm = S.tsl[f]; sm; sm &= sm - 1) {
+                        const uint32_t b = (f << TL_SLB) + ctz64(sm);
+                        rec_copy_async(&S.hc[b], rec + S.heads[b]);
+                    }
+                }
+            }
         }
     }
     HBA_SYNC();
@@ -1603,15 +1774,15 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                         if (i + NT < na) u64_copy_async(&S.stg[(par ^ 1u) * NT + tid], a.sizes + i + NT);
                         if (s != 0 && s <= S.A) {
                             sg = (uint32_t)((s + mbm) >> lg);
-                            c = clog2(sg);
+                            c = cls_req<POL>(sg);
                         }
                     }
                     S.sgr[tid] = sg;
-                    S.ccl[tid] = (uint8_t)c;
+                    S.ccl[tid] = (typename Smem<NT, POL>::ccl_t)c;
                     S.s64[tid] = s;
                     if (tid == 0) S.evb[0] = NT;
                 }
-                if (warp_in_window<NT>(tid >> 5, r, n_here)) {
+                if (warp_in_window<NT, POL>(tid >> 5, r, n_here)) {
                     uint8_t cl = CL_NONE;
                     const uint32_t sg = S.sgr[tid];
                     if ((uint32_t)tid >= r && (uint32_t)tid < n_here) {
@@ -1619,10 +1790,9 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                             cl = CL_FAIL;
                         } else {
                             const uint32_t c = S.ccl[tid];
-                            const uint64_t M = S.mask | (S.xok ? (1ull << S.xL) : 0ull);
-                            const uint64_t cand = (M >> c) << c;
-                            if (!cand) cl = CL_FAIL;
-                            else cl = (S.xok && ctz64(cand) == S.xL) ? CL_CARVE : CL_OTHER;
+                            const uint32_t k = cls_first<NT, POL>(S, S.mask, c, S.xok, S.xL);
+                            if (k == CLS_NONE) cl = CL_FAIL;
+                            else cl = (S.xok && k == S.xL) ? CL_CARVE : CL_OTHER;
                         }
                     }
                     S.cls[tid] = cl;
@@ -1636,12 +1806,12 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                 }
             }
             HBA_PROF(12);
-            scan_incl_i64<NT>(S, S.val, r, n_here);
+            scan_incl_i64<NT, POL>(S, S.val, r, n_here);
             HBA_PROF(13);
             // B: verify; carve lanes record their start; per-warp carve
             // lanes and last carve
             HBA_FOR_THREADS(tid) {
-                const bool wact = warp_in_window<NT>(tid >> 5, r, n_here);
+                const bool wact = warp_in_window<NT, POL>(tid >> 5, r, n_here);
                 if (wact) {
                     const uint8_t cl = S.cls[tid];
                     const bool carve = cl == CL_CARVE;
@@ -1652,15 +1822,10 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                         const uint32_t sg = S.sgr[tid];
                         start = S.c0g + (uint32_t)(P - sg);
                         const int64_t before = (int64_t)S.c0sz - (P - (int64_t)sg);
-                        uint64_t M = S.mask;
-                        uint32_t Lt = 64;
-                        if (before > 0) {
-                            Lt = flog2((uint32_t)before);
-                            M |= 1ull << Lt;
-                        }
                         const uint32_t c = S.ccl[tid];
-                        const uint64_t cand = (M >> c) << c;
-                        if (!(cand && ctz64(cand) == Lt)) e = true;
+                        if (before <= 0 || cls_first<NT, POL>(S, S.mask, c, true, cls_push<POL>((uint32_t)before)) !=
+                                               cls_push<POL>((uint32_t)before))
+                            e = true;
                     }
                     S.cst[tid] = start;
 #ifdef HBA_EMULATE
@@ -1698,13 +1863,13 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
             // events only touch records outside the carved range and results
             // of lanes >= nres, so they run beside the resolve.
             HBA_FOR_THREADS(tid) {
-                if (warp_in_window<NT>(tid >> 5, r, nres)) {
+                if (warp_in_window<NT, POL>(tid >> 5, r, nres)) {
                     const uint8_t cl = S.cls[tid];
                     const bool act = (uint32_t)tid >= r && (uint32_t)tid < nres;
                     const bool is_fail = act && cl == CL_FAIL;
                     const bool is_carve = act && cl == CL_CARVE;
                     const uint32_t start = S.cst[tid];
-                    const uint32_t prev = prev_carve_start<NT>(S, tid, r, cl == CL_CARVE, start);
+                    const uint32_t prev = prev_carve_start<NT, POL>(S, tid, r, cl == CL_CARVE, start);
                     if (is_fail && !a.prefilled) a.out[p + tid] = FAIL64;
                     if (is_carve) {
                         const uint32_t sg = S.sgr[tid];
@@ -1716,11 +1881,11 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
                     warp_sum(S, tid, C_REQ, is_carve ? (int64_t)S.s64[tid] : 0);
                 }
 #ifdef HBA_EMULATE
-                if (tid == 0) round_tail<NT>(S, a, p, r, nres, n_here, 0);
+                if (tid == 0) round_tail<NT, POL>(S, a, p, r, nres, n_here, 0);
 #else
                 if ((tid >> 5) == 0) {
                     HBA_PROF(16);
-                    round_tail<NT>(S, a, p, r, nres, n_here, (uint32_t)(tid & 31));
+                    round_tail<NT, POL>(S, a, p, r, nres, n_here, (uint32_t)(tid & 31));
                     HBA_PROF(20);
                 }
 #endif
@@ -1744,9 +1909,9 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
     }
     HBA_FOR_THREADS(tid) {
         if (tid == 0 && S.xok) {
-            XReg X = x_load<NT>(S);
-            materialize_x<NT>(S, rec, X);
-            x_store<NT>(S, X);
+            XReg X = x_load<NT, POL>(S);
+            materialize_x<NT, POL>(S, rec, X);
+            x_store<NT, POL>(S, X);
         }
         rec_copy_wait();  // no copy may land in shared memory after this arena
     }
@@ -1755,15 +1920,20 @@ HBA_DEV void alloc_phase(Smem<NT>& S, const StepArgs& a) {
 }
 
 // One batch of one arena.  All threads of the CTA call this.  dyn/dyn_words:
-// dynamic shared memory (at least alloc_dyn_words<NT>() words).
-template <int NT>
-HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t dyn_words) {
+// dynamic shared memory (at least alloc_dyn_words<NT, POL>() words).
+template <int NT, int POL = 0>
+HBA_DEV void arena_step(Smem<NT, POL>& S, const StepArgs& a, uint32_t* dyn, uint32_t dyn_words) {
     HBA_FOR_THREADS(tid) {
-        for (int b = tid; b < NBINS; b += NT) S.heads[b] = a.ar->heads[b];
-        for (int q = tid; q < (Smem<NT>::NW + 1) * NCNT; q += NT) (&S.wc[0][0])[q] = 0;
+        if constexpr (POL == 0) {
+            for (int b = tid; b < NBINS; b += NT) S.heads[b] = a.ar->heads[b];
+        } else {
+            for (uint32_t b = tid; b < TL_NL; b += NT) S.heads[b] = a.tl->heads[b];
+            for (uint32_t f = tid; f < TL_FL; f += NT) S.tsl[f] = a.tl->slmask[f];
+        }
+        for (int q = tid; q < (Smem<NT, POL>::NW + 1) * NCNT; q += NT) (&S.wc[0][0])[q] = 0;
         if (tid == 0) {
             S.A = a.ar->arena_bytes;
-            S.mask = a.ar->mask;
+            S.mask = POL ? (uint64_t)a.tl->flmask : a.ar->mask;
             S.G = a.ar->G;
             S.lg = a.ar->lg;
             S.xok = 0;
@@ -1826,13 +1996,19 @@ HBA_DEV void arena_step(Smem<NT>& S, const StepArgs& a, uint32_t* dyn, uint32_t 
         b.gstride = a.nf;
     }
     HBA_PROF(0);
-    if (b.nf) free_phase<NT>(S, b);
-    if (b.na) alloc_phase<NT>(S, b);
+    if (b.nf) free_phase<NT, POL>(S, b);
+    if (b.na) alloc_phase<NT, POL>(S, b);
     HBA_FOR_THREADS(tid) {
-        for (int b = tid; b < NBINS; b += NT) a.ar->heads[b] = S.heads[b];
+        if constexpr (POL == 0) {
+            for (int b = tid; b < NBINS; b += NT) a.ar->heads[b] = S.heads[b];
+        } else {
+            for (uint32_t b = tid; b < TL_NL; b += NT) a.tl->heads[b] = S.heads[b];
+            for (uint32_t f = tid; f < TL_FL; f += NT) a.tl->slmask[f] = (uint16_t)S.tsl[f];
+            if (tid == 0) a.tl->flmask = (uint32_t)S.mask;
+        }
         if (tid == 0) {
             int64_t c[NCNT] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int w = 0; w <= Smem<NT>::NW; ++w)
+            for (int w = 0; w <= Smem<NT, POL>::NW; ++w)
                 for (int k = 0; k < NCNT; ++k) c[k] += S.wc[w][k];
             Arena* ar = a.ar;
             ar->mask = S.mask;

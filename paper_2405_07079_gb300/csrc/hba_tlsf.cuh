@@ -38,34 +38,8 @@
 
 namespace hba {
 
-constexpr uint32_t TL_SLB = 4;                 // log2 of the lists per class
-constexpr uint32_t TL_SL = 1u << TL_SLB;       // 16
-constexpr uint32_t TL_FL = 32;                 // granule classes (G < 2^29)
-constexpr uint32_t TL_NL = TL_FL * TL_SL;      // 512 lists
-constexpr uint32_t TL_NONE = 0xFFFFFFFFu;
-
-static_assert(TL_FL == 32, "one second-level mask per lane of a warp");
-
-struct TlsfLists {
-    uint32_t flmask;           // bit f <=> slmask[f] != 0
-    uint32_t pad;
-    uint16_t slmask[TL_FL];    // bit s of slmask[f] <=> list (f, s) non-empty
-    uint32_t heads[TL_NL];     // list f * 16 + s: first block (granule), NIL if empty
-};
-
-// List of a free block of r >= 1 granules.
-HBA_HD uint32_t tl_list(uint32_t r) {
-    const uint32_t f = flog2(r);
-    const uint32_t top = f >= TL_SLB ? r >> (f - TL_SLB) : r << (TL_SLB - f);  // 16 + s
-    return f * TL_SL + (top - TL_SL);
-}
-
-// Lowest list whose lower bound is >= r: r rounded up to a list bound.
-HBA_HD uint32_t tl_bound(uint32_t r) {
-    const uint32_t f = flog2(r);
-    const uint32_t up = f >= TL_SLB ? r + ((1u << (f - TL_SLB)) - 1u) : r;  // r < 2^29: no overflow
-    return tl_list(up);
-}
+// The list constants, TlsfLists, tl_list and tl_bound are in hba_engine.cuh
+// (the batch engine runs this policy too).
 
 // Lowest non-empty list at or above list t, or TL_NONE.
 HBA_HD uint32_t tl_find(const TlsfLists& L, uint32_t t) {

@@ -27,12 +27,14 @@ struct Emu {
     uint32_t dyn_words = 600;
     int staged = 0;  // write the gathered records straight into the shared-memory layout
     int self = 0;    // the engine gathers its frees' records itself
+    int tlsf = 0;    // two-level segregated fit (the engine's POL 1)
+    TlsfLists tl;
 };
 
-template <int NT>
+template <int NT, int POL>
 void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
          uint32_t na, uint64_t* out) {
-    Smem<NT>* S = new Smem<NT>();
+    Smem<NT, POL>* S = new Smem<NT, POL>();
     if (e->scr.size() < (size_t)SCRATCH_WORDS_PER_FREE * nf) e->scr.resize((size_t)SCRATCH_WORDS_PER_FREE * nf);
     // the gather that a separate grid does on the GPU
     std::vector<uint32_t> gi((size_t)GATHER_WORDS * nf + 1);
@@ -40,10 +42,10 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
         for (uint32_t j = 0; j < nf; ++j)
             gather_free(e->rec.data(), e->ar.arena_bytes, e->ar.G, e->ar.lg, frees[j], gi.data(), nf, j);
     StepArgs a{&e->ar, e->rec.data(), frees, nf, st, sizes, na, out, e->scr.data(), gi.data(), nf, 0, WAIT_NONE, 0,
-               e->self ? 1u : 0u};
+               e->self ? 1u : 0u, POL ? &e->tl : nullptr};
     // "shared memory": at least what the alloc phase needs, plus a test knob so
     // that both placements of the free-phase arrays run
-    const uint32_t words = std::max(alloc_dyn_words<NT>(), e->dyn_words);
+    const uint32_t words = std::max(alloc_dyn_words<NT, POL>(), e->dyn_words);
     std::vector<uint64_t> dyn(words / 2 + 1);
     uint32_t* d = reinterpret_cast<uint32_t*>(dyn.data());
     if (!e->self && e->staged && nf && stage_fits(nf, words)) {
@@ -51,7 +53,7 @@ void run(Emu* e, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t
         memcpy(d, gi.data(), sizeof(uint32_t) * GATHER_WORDS * nf);
         a.staged = 1;
     }
-    arena_step<NT>(*S, a, d, words);
+    arena_step<NT, POL>(*S, a, d, words);
     delete S;
 }
 }  // namespace
@@ -77,14 +79,38 @@ void emu_set_dyn(void* h, uint32_t words) { ((Emu*)h)->dyn_words = words; }
 void emu_set_staged(void* h, int staged) { ((Emu*)h)->staged = staged; }
 void emu_set_self(void* h, int self) { ((Emu*)h)->self = self; }
 
+// Two-level segregated fit through the batch engine (POL 1): the lists start
+// as one free block, like the TLSF handles'.
+void emu_set_tlsf(void* h) {
+    Emu* e = (Emu*)h;
+    e->tlsf = 1;
+    tl_init_host(&e->tl, e->ar.G);
+    e->ar.mask = e->tl.flmask;
+}
+
+size_t emu_export_tlsf(void* h, uint64_t* buf, size_t cap) {
+    Emu* e = (Emu*)h;
+    return tl_export(e->ar, e->tl, e->rec.data(), buf, cap);
+}
+
 int emu_step(void* h, const uint64_t* frees, uint32_t nf, uint8_t* st, const uint64_t* sizes,
              uint32_t na, uint64_t* out) {
     Emu* e = (Emu*)h;
+    if (e->tlsf) {
+        switch (e->nt) {
+            case 4: run<4, 1>(e, frees, nf, st, sizes, na, out); break;
+            case 32: run<32, 1>(e, frees, nf, st, sizes, na, out); break;
+            case 256: run<256, 1>(e, frees, nf, st, sizes, na, out); break;
+            case 1024: run<1024, 1>(e, frees, nf, st, sizes, na, out); break;
+            default: return 1;
+        }
+        return 0;
+    }
     switch (e->nt) {
-        case 4: run<4>(e, frees, nf, st, sizes, na, out); break;
-        case 32: run<32>(e, frees, nf, st, sizes, na, out); break;
-        case 256: run<256>(e, frees, nf, st, sizes, na, out); break;
-        case 1024: run<1024>(e, frees, nf, st, sizes, na, out); break;
+        case 4: run<4, 0>(e, frees, nf, st, sizes, na, out); break;
+        case 32: run<32, 0>(e, frees, nf, st, sizes, na, out); break;
+        case 256: run<256, 0>(e, frees, nf, st, sizes, na, out); break;
+        case 1024: run<1024, 0>(e, frees, nf, st, sizes, na, out); break;
         default: return 1;
     }
     return 0;

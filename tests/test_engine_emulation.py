@@ -41,6 +41,9 @@ def emu():
     lib.emu_set_dyn.argtypes = [vp, u32]
     lib.emu_set_staged.argtypes = [vp, ctypes.c_int]
     lib.emu_set_self.argtypes = [vp, ctypes.c_int]
+    lib.emu_set_tlsf.argtypes = [vp]
+    lib.emu_export_tlsf.restype = ctypes.c_size_t
+    lib.emu_export_tlsf.argtypes = [vp, vp, ctypes.c_size_t]
     lib.emu_tlsf_create.restype = vp
     lib.emu_tlsf_create.argtypes = [u64, u64]
     lib.emu_tlsf_destroy.argtypes = [vp]
@@ -52,9 +55,12 @@ def emu():
 
 
 class Emu:
-    def __init__(self, lib, A, mb, nt, dyn_words=None, staged=False, self_gather=False):
+    def __init__(self, lib, A, mb, nt, dyn_words=None, staged=False, self_gather=False, tlsf=False):
         self.lib, self.h = lib, lib.emu_create(A, mb, nt)
         assert self.h
+        self.tlsf = tlsf
+        if tlsf:
+            lib.emu_set_tlsf(self.h)
         if dyn_words is not None:
             lib.emu_set_dyn(self.h, dyn_words)
         lib.emu_set_staged(self.h, int(staged))
@@ -70,9 +76,10 @@ class Emu:
         return out, st
 
     def export_state(self):
-        n = self.lib.emu_export(self.h, None, 0)
+        fn = self.lib.emu_export_tlsf if self.tlsf else self.lib.emu_export
+        n = fn(self.h, None, 0)
         b = np.empty(n, np.uint64)
-        self.lib.emu_export(self.h, b.ctypes.data, n)
+        fn(self.h, b.ctypes.data, n)
         return b
 
     def stats(self):
@@ -242,3 +249,57 @@ def test_tlsf_ops_on_small_random_arenas(emu):
     for mb, G in ((8, 37), (16, 200), (256, 1000), (8, 3)):
         _check_tlsf(emu, W.Workload("t", mb * G, mb, lambda: W.TinyRandom(n_ops=3000, batch=7, p_free=0.45,
                                                                         lo=1, hi=mb * G // 3 + 1)))
+
+
+def _check_engine_tlsf(emu, wl, nt, every=1, dyn_words=None, self_gather=False):
+    """Two-level segregated fit through the parallel batch engine (the
+    engine's second class layout) against the TLSF oracle: every result,
+    every free status, the canonical state (lists and both bitmap levels)
+    and the counters."""
+    trace, o = oracle_trace(wl, policy="tlsf")
+    e = Emu(emu, wl.arena, wl.min_block, nt, dyn_words, False, self_gather, tlsf=True)
+    import oracle as _o
+    ref = _o.Oracle(wl.arena, wl.min_block, "tlsf")
+    try:
+        for b, (f, s, out, st) in enumerate(trace):
+            go, gs = e.batch(f, s)
+            ref.batch(f, s)
+            assert np.array_equal(go, out), f"batch {b} allocs"
+            assert np.array_equal(gs, st), f"batch {b} frees"
+            if b % every == 0:
+                assert np.array_equal(e.export_state(), ref.export_state()), f"batch {b} state"
+        assert np.array_equal(e.export_state(), o.export_state())
+        assert e.stats() == list(o.stats().values())
+    finally:
+        e.close()
+
+
+@pytest.mark.parametrize("nt", [4, 32, 256, 1024])
+def test_engine_tlsf_tiny(emu, nt):
+    from paper_2405_07079_gb300 import workloads as W
+
+    _check_engine_tlsf(emu, W.tiny(n_ops=4000 if nt == 4 else 8000), nt, every=3)
+
+
+@pytest.mark.parametrize("nt,dyn_words", [(32, None), (256, 0), (256, 1 << 20), (1024, 1 << 20)])
+def test_engine_tlsf_lifetimes(emu, nt, dyn_words):
+    """Many runs a batch (the push by same-list predecessors), free phases in
+    shared memory and in global scratch."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    wl = W.Workload("life", 1 << 26, 512, lambda: W.Lifetimes(n_ops=60_000, batch=4096, mean_life=300,
+                                                            scale=1 / 64, min_size=512))
+    _check_engine_tlsf(emu, wl, nt, every=4, dyn_words=dyn_words)
+
+
+def test_engine_tlsf_usage_and_small_arenas(emu):
+    from paper_2405_07079_gb300 import workloads as W
+
+    _check_engine_tlsf(emu, W.usage(n_ops=1500, batch=16), 256, every=5)
+    rng = np.random.default_rng(12)
+    for _ in range(40):
+        mb = int(rng.choice([8, 16, 256]))
+        A = mb * int(rng.integers(1, 300))
+        wl = W.Workload("small", A, mb, lambda A=A, mb=mb: W.TinyRandom(n_ops=400, batch=int(rng.integers(1, 40)),
+                                                                       lo=1, hi=A))
+        _check_engine_tlsf(emu, wl, int(rng.choice([4, 32])))

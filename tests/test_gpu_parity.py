@@ -702,6 +702,16 @@ def test_tlsf_large_reduced(gpu_lib):
     _run(wl, state_every=5, policy="tlsf")
 
 
+def test_tlsf_large_full(gpu_lib):
+    """Two-level segregated fit on the full large trace (16 GiB arena, 10M
+    ops in batches of 65,536) through the batch engine, the launch
+    configuration the benchmark times: every result of every batch, the
+    state every 50 batches, and a 16 GiB canary arena left untouched."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    _run(W.large(), threads=1024, state_every=50, canary=True, policy="tlsf")
+
+
 def test_tlsf_frag_reduced(gpu_lib):
     from paper_2405_07079_gb300 import workloads as W
 
