@@ -501,8 +501,6 @@ def plain_large_figure(dev, steps=None) -> dict:
 def multi_kernel_name(policy, shape, n_arenas, n_sms, wpc=8) -> str:
     """The batch kernel a multi-arena launch of this shape runs (the
     library's own choice, restated)."""
-    if policy == "tlsf":
-        return "k_tlsf<4>"
     if policy in FIT_POLICIES:
         return "k_fits<256>"
     if policy == "bitmask":
@@ -510,11 +508,13 @@ def multi_kernel_name(policy, shape, n_arenas, n_sms, wpc=8) -> str:
     if isinstance(shape, str):
         return "k_multi"
     threads, ctas = shape[0], shape[1]
+    tl = ", two-level lists" if policy == "tlsf" else ""
     if threads == 32:
-        need = -(-n_arenas // wpc)
+        from paper_2405_07079_gb300.tune import WARP_ARENAS_PER_CTA_TLSF
+        need = -(-n_arenas // (WARP_ARENAS_PER_CTA_TLSF if tl else wpc))
         grid = min(ctas, need) if ctas else need
-        return "k_prep + k_multi_warp<2>" if grid <= 2 * n_sms else "k_prep + k_multi_warp<4>"
-    return f"k_prep + k_multi<{threads}>"
+        return f"k_prep + k_multi_warp<{2 if grid <= 2 * n_sms else 4}{tl}>"
+    return f"k_prep + k_multi<{threads}{tl}>"
 
 
 def kernel_sources_digest() -> str:
@@ -717,9 +717,7 @@ def run_multi(args, rank, world, local_rank):
         d["ref_st"] = stat.copy()
         batches.append(d)
     t_rec = time.time() - t_rec
-    if args.policy == "tlsf":
-        best, table = "one warp per arena (two-level segregated fit)", {}
-    elif args.policy in FIT_POLICIES:
+    if args.policy in FIT_POLICIES:
         best, table = f"one CTA per arena ({args.policy} fit)", {}
     elif args.shape:
         best = tuple(int(x) for x in args.shape.split(","))
@@ -842,8 +840,7 @@ def run_multi(args, rank, world, local_rank):
                    "workload": f"batched-{args.arenas}: {args.arenas} arenas log-uniform "
                                f"{args.arena_min} MiB-{args.arena_max} MiB, min block 256 B, U{{0..2048}} requests "
                                f"per arena per batch, {nb} batches",
-                   "form": ("batched: one launch per batch, one warp per arena (k_tlsf<4>)" if args.policy == "tlsf"
-                            else "batched: one launch per batch, one CTA per arena (k_fits<256>)"
+                   "form": ("batched: one launch per batch, one CTA per arena (k_fits<256>)"
                             if args.policy in FIT_POLICIES
                             else "batched: one launch per batch, one CTA per pool (k_bitmask<256>)"
                             if args.policy == "bitmask"

@@ -30,11 +30,11 @@
  * the first-level one.  A free block of z bytes is in list (floor(log2 z),
  * the four bits below the leading one); an allocation takes the head of the
  * lowest non-empty list whose lower bound is >= s' (every block there
- * fits).  A single-arena TLSF handle runs its batches through the same
- * parallel batch engine as segregated fit (the 512 lists with the first
- * bitmap level in the engine's bitmap word, the second level in shared
- * memory); a multi-arena TLSF handle runs one warp per arena, applying the
- * requests one by one.  hba_serve_run rejects TLSF handles.  The canonical
+ * fits).  TLSF handles run their batches through the same parallel batch
+ * engine as segregated fit (the 512 lists with the first bitmap level in
+ * the engine's bitmap word, the second level in shared memory), in the same
+ * launch shapes (hba_set_shape), except that warp mode runs four arenas per
+ * CTA instead of eight.  hba_serve_run rejects TLSF handles.  The canonical
  * state lists the 64 x 16 byte lists, then the first-level bitmap, then the
  * 64 second-level bitmaps.
  *
@@ -323,12 +323,14 @@ hba_status_t hba_multi_step_host_async(hba_t h, const uint32_t* h_free_rowptr, c
 
 /* Launch shape of the handle's batch kernel: threads per CTA (one of 64,
  * 128, 256, 512, 1024: a CTA applies one arena's batch; or 32: warp mode,
- * every warp applies its own arena's batch, 8 arenas per CTA; a new
+ * every warp applies its own arena's batch, 8 arenas per CTA (4 for
+ * TLSF); a new
  * single-arena handle picks per batch: 128 for batches of at most 256 frees
  * and 256 allocations, else 1024); number of
  * CTAs: for a multi-arena handle, the grid (0 = enough for every arena;
- * fewer CTAs loop over the arenas); for a single-arena handle with 256 or
- * more threads, the size of the batch's thread-block cluster (0 or 1 = no
+ * fewer CTAs loop over the arenas); for a single-arena segregated-fit
+ * handle with 256 or more threads, the size of the batch's thread-block
+ * cluster (0 or 1 = no
  * cluster: a separate grid gathers the frees' records and pre-fills
  * failures, then the engine runs; 2..8 = the engine CTA plus CTAs that
  * gather the records straight into its shared memory and pre-fill failures,

@@ -188,13 +188,13 @@ __global__ void __launch_bounds__(NT, 1) k_single_cl(Arena* ar, Rec* rec, const 
     hba::cluster_wait();
 }
 
-template <int NT>
+template <int NT, int POL = 0>
 __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint32_t* frow,
                                               const uint64_t* frees, uint8_t* st, const uint32_t* arow,
                                               const uint64_t* sizes, uint64_t* out, uint32_t* scr,
                                               const uint32_t* gi, uint32_t nf_total, uint32_t n_arenas,
-                                              uint32_t dyn_words, uint32_t prefilled) {
-    __shared__ hba::Smem<NT> S;
+                                              uint32_t dyn_words, uint32_t prefilled, hba::TlsfLists* tl) {
+    __shared__ hba::Smem<NT, POL> S;
     extern __shared__ __align__(16) uint32_t dyn[];
     bool first = true;  // the first arena waits for the prep grid (after its header)
     for (uint32_t a = blockIdx.x; a < n_arenas; a += gridDim.x) {
@@ -214,31 +214,40 @@ __global__ void __launch_bounds__(NT) k_multi(Arena* ars, Rec* pool, const uint3
                            prefilled,
                            first ? hba::WAIT_GRID : hba::WAIT_NONE,
                            0,
-                           0};
+                           0,
+                           POL ? tl + a : nullptr};
         first = false;
-        hba::arena_step<NT>(S, args, dyn, dyn_words);
+        hba::arena_step<NT, POL>(S, args, dyn, dyn_words);
     }
 }
 
 // Warp mode: every warp of a CTA runs its own arenas (arena_step<32>, whose
-// barriers are __syncwarp), WPC arenas per CTA at a time.  For many small
+// barriers are __syncwarp), W arenas per CTA at a time.  For many small
 // arena batches, where a CTA per arena would spend its time in barriers.
+// Segregated fit runs WPC warps per CTA; the two-level lists, whose per-arena
+// shared state is four times larger (512 list heads and their cached
+// records), run WPC_TL.
 constexpr int WPC = 8;
+#ifndef HBA_WPC_TL
+#define HBA_WPC_TL 4
+#endif
+constexpr int WPC_TL = HBA_WPC_TL;
 // MINB: at least this many CTAs per SM, a register budget for ptxas.  Two
 // builds: 2 CTAs per SM (more registers, no spills) when the grid fits the
 // SMs at that occupancy, 4 when it does not (more CTAs resident at once).
-template <int MINB>
-__global__ void __launch_bounds__(WPC * 32, MINB) k_multi_warp(Arena* ars, Rec* pool, const uint32_t* frow,
-                                                          const uint64_t* frees, uint8_t* st, const uint32_t* arow,
-                                                          const uint64_t* sizes, uint64_t* out, uint32_t* scr,
-                                                          const uint32_t* gi, uint32_t nf_total, uint32_t n_arenas,
-                                                          uint32_t warp_dyn_words, uint32_t prefilled) {
-    __shared__ hba::Smem<32> S[WPC];
+template <int MINB, int POL = 0, int W = WPC>
+__global__ void __launch_bounds__(W * 32, MINB) k_multi_warp(Arena* ars, Rec* pool, const uint32_t* frow,
+                                                        const uint64_t* frees, uint8_t* st, const uint32_t* arow,
+                                                        const uint64_t* sizes, uint64_t* out, uint32_t* scr,
+                                                        const uint32_t* gi, uint32_t nf_total, uint32_t n_arenas,
+                                                        uint32_t warp_dyn_words, uint32_t prefilled,
+                                                        hba::TlsfLists* tl) {
+    __shared__ hba::Smem<32, POL> S[W];
     extern __shared__ __align__(16) uint32_t dyn[];
     bool first = true;  // the first arena waits for the prep grid (after its header)
     const uint32_t w = threadIdx.x >> 5;
     uint32_t* mine = dyn + (size_t)w * warp_dyn_words;
-    for (uint32_t a = blockIdx.x * WPC + w; a < n_arenas; a += gridDim.x * WPC) {
+    for (uint32_t a = blockIdx.x * W + w; a < n_arenas; a += gridDim.x * W) {
         const uint32_t f0 = frow[a], f1 = frow[a + 1], a0 = arow[a], a1 = arow[a + 1];
         Arena* ar = ars + a;
         hba::StepArgs args{ar,
@@ -255,9 +264,10 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_multi_warp(Arena* ars, Rec* 
                            prefilled,
                            first ? hba::WAIT_GRID : hba::WAIT_NONE,
                            0,
-                           0};
+                           0,
+                           POL ? tl + a : nullptr};
         first = false;
-        hba::arena_step<32>(S[w], args, mine, warp_dyn_words);
+        hba::arena_step<32, POL>(S[w], args, mine, warp_dyn_words);
     }
 }
 
@@ -265,6 +275,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_multi_warp(Arena* ars, Rec* 
 struct SmemLimits {
     uint32_t single_dyn = 0, multi_dyn = 0;  // bytes
     uint32_t single_dyn_tl = 0;               // k_single<NT, 1> (two-level segregated fit)
+    uint32_t multi_dyn_tl = 0;                // k_multi<NT, 1> (warp mode: k_multi_warp<., 1>, per warp)
     uint32_t alloc_words_tl = 0;
     uint32_t alloc_words = 0;                 // minimum dynamic words (alloc phase)
     uint32_t cluster_max = 0;                 // largest batch cluster that fits (0: none)
@@ -291,6 +302,10 @@ SmemLimits set_smem_limits() {
     if (cudaFuncGetAttributes(&fa, k_multi<NT>) == cudaSuccess) {
         L.multi_dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
         cudaFuncSetAttribute(k_multi<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.multi_dyn);
+    }
+    if (cudaFuncGetAttributes(&fa, k_multi<NT, 1>) == cudaSuccess) {
+        L.multi_dyn_tl = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_multi<NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.multi_dyn_tl);
     }
     if (NT >= 256 && cudaFuncGetAttributes(&fa, k_single_cl<NT>) == cudaSuccess) {
         const uint32_t dyn = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
@@ -351,6 +366,12 @@ SmemLimits set_smem_limits_warp() {
         cudaFuncSetAttribute(k_multi_warp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
         cudaFuncSetAttribute(k_multi_warp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
         L.multi_dyn = (total / WPC) & ~15u;  // per warp
+    }
+    if (cudaFuncGetAttributes(&fa, k_multi_warp<2, 1, WPC_TL>) == cudaSuccess) {
+        const uint32_t total = (uint32_t)((optin - (int)fa.sharedSizeBytes - 1024) & ~15);
+        cudaFuncSetAttribute(k_multi_warp<2, 1, WPC_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
+        cudaFuncSetAttribute(k_multi_warp<4, 1, WPC_TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
+        L.multi_dyn_tl = (total / WPC_TL) & ~15u;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -449,28 +470,10 @@ __global__ void k_extent(const Arena* ars, const Rec* pool, uint32_t n_arenas, u
     }
 }
 
-// Two-level segregated fit: one warp per arena, WPC arenas per CTA, the
-// grid striding over the arenas.  frow / arow: each arena's row offsets into
-// frees / sizes (n_arenas + 1 entries), or null for a single arena, whose
-// requests are frees[0, nf) and sizes[0, na).
-template <int WPC>
-__global__ void __launch_bounds__(WPC * 32) k_tlsf(Arena* ars, hba::TlsfLists* lists, Rec* pool, uint32_t n_arenas,
-                                                  const uint32_t* frow, const uint64_t* frees, uint8_t* fstat,
-                                                  uint32_t nf, const uint32_t* arow, const uint64_t* sizes,
-                                                  uint64_t* out, uint32_t na) {
-    __shared__ hba::TlsfLists Lw[WPC];
-    const uint32_t w = threadIdx.x >> 5;
-    for (uint32_t a = blockIdx.x * WPC + w; a < n_arenas; a += gridDim.x * WPC) {
-        const uint32_t f0 = frow ? frow[a] : 0u, f1 = frow ? frow[a + 1] : nf;
-        const uint32_t a0 = arow ? arow[a] : 0u, a1 = arow ? arow[a + 1] : na;
-        Arena& ar = ars[a];
-        hba::tl_arena_warp(ar, lists[a], pool + ar.rec_base, Lw[w], frees, fstat, f0, f1, sizes, out, a0, a1);
-        __syncwarp();
-    }
-}
-
 // Sequential fits: one CTA per arena, the grid striding over the arenas.
-// frow / arow as for k_tlsf.
+// frow / arow: each arena's row offsets into frees / sizes (n_arenas + 1
+// entries), or null for a single arena, whose requests are frees[0, nf) and
+// sizes[0, na).
 template <int NT>
 __global__ void __launch_bounds__(NT) k_fits(Arena* ars, hba::FitHdr* hdr, hba::FitBlk* fpool, hba::FitBlk* upool,
                                             uint32_t n_arenas, const uint32_t* frow, const uint64_t* frees,
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(NT) k_fits(Arena* ars, hba::FitHdr* hdr, hba::
 }
 
 // Bitmask pools: one CTA per pool, both bitmaps in dynamic shared memory
-// (2 x bm_wmax words).  frow / arow as for k_tlsf.
+// (2 x bm_wmax words).  frow / arow as for k_fits.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_bitmask(Arena* ars, hba::BmHdr* hdr, uint64_t* gF, uint64_t* gS,
                                                uint32_t n_arenas, uint32_t wmax, const uint32_t* frow,
@@ -747,22 +750,6 @@ hba_status_t launch_single(hba_t h, const uint64_t* frees, uint32_t nf, uint8_t*
                            uint32_t na, uint64_t* out, cudaStream_t s, uint32_t* gi, uint32_t* scr) {
     return h->policy == HBA_POLICY_TLSF ? launch_single_p<1>(h, frees, nf, st, sizes, na, out, s, gi, scr)
                                         : launch_single_p<0>(h, frees, nf, st, sizes, na, out, s, gi, scr);
-}
-
-// A TLSF batch: one warp for a single arena, else four arenas per CTA.
-hba_status_t launch_tlsf(hba_t h, const uint32_t* frow, const uint64_t* frees, uint32_t nf, uint8_t* st,
-                         const uint32_t* arow, const uint64_t* sizes, uint32_t na, uint64_t* out, cudaStream_t s) {
-    const uint32_t n = h->n_arenas;
-    if (n == 1) {
-        k_tlsf<1><<<1, 32, 0, s>>>(h->d_arenas, h->d_tlsf, h->d_rec, 1u, frow, frees, st, nf, arow, sizes, out, na);
-    } else {
-        const uint32_t sms = g_limits[5].sms ? g_limits[5].sms : 152u;
-        const uint32_t grid = std::min((n + 3u) / 4u, 16u * sms);
-        k_tlsf<4><<<grid, 128, 0, s>>>(h->d_arenas, h->d_tlsf, h->d_rec, n, frow, frees, st, nf, arow, sizes, out,
-                                        na);
-    }
-    ++h->launches;
-    return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
 }
 
 bool is_fit(int policy) {
@@ -1540,9 +1527,7 @@ hba_status_t multi_step_impl(hba_t h, const uint32_t* d_free_rowptr, const uint6
                              const uint32_t* d_alloc_rowptr, const uint64_t* d_sizes, uint32_t na_total,
                              uint64_t* d_out, uint8_t* d_free_status, cudaStream_t s) {
     const uint32_t n = h->n_arenas;
-    if (h->policy == HBA_POLICY_TLSF)
-        return launch_tlsf(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes, na_total,
-                           d_out, s);
+    const bool tl = h->policy == HBA_POLICY_TLSF;
     if (is_fit(h->policy))
         return launch_fits(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes, na_total,
                            d_out, s);
@@ -1550,27 +1535,35 @@ hba_status_t multi_step_impl(hba_t h, const uint32_t* d_free_rowptr, const uint6
         return launch_bitmask(h, d_free_rowptr, d_frees, nf_total, d_free_status, d_alloc_rowptr, d_sizes,
                               na_total, d_out, s);
     if (h->m_threads == 32) {
-        // warp mode: WPC arenas per CTA, per-warp dynamic shared memory
+        // warp mode: WPC (WPC_TL) arenas per CTA, per-warp dynamic shared memory
         const SmemLimits& L = g_limits[5];
-        uint32_t per = std::min(h->smem_bytes ? h->smem_bytes : 4u * L.alloc_words + 2048u, L.multi_dyn);
-        per = (std::max(per, 4u * L.alloc_words) + 15u) & ~15u;
-        const uint32_t need = (n + WPC - 1) / WPC;
+        const uint32_t aw = tl ? L.alloc_words_tl : L.alloc_words;
+        const uint32_t wpc = tl ? WPC_TL : WPC;
+        uint32_t per = std::min(h->smem_bytes ? h->smem_bytes : 4u * aw + 2048u, tl ? L.multi_dyn_tl : L.multi_dyn);
+        per = (std::max(per, 4u * aw) + 15u) & ~15u;
+        const uint32_t need = (n + wpc - 1) / wpc;
         const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, need) : need;
         bool pdl = false;
         const bool pre = launch_prep(h, d_free_rowptr, d_frees, nf_total, h->d_gi, d_out, na_total, s, &pdl);
         if (cudaGetLastError() != cudaSuccess) return HBA_ERR_CUDA;
-        auto k = grid <= 2 * L.sms ? k_multi_warp<2> : k_multi_warp<4>;
-        cudaError_t e = launch_pdl(k, grid, WPC * 32, per * WPC, s, pdl, h->d_arenas, h->d_rec, d_free_rowptr,
-                                   d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr,
-                                   (const uint32_t*)h->d_gi, nf_total, n, per / 4, pre ? 1u : 0u);
+        const bool two = grid <= 2 * L.sms;
+        cudaError_t e =
+            tl ? launch_pdl(two ? k_multi_warp<2, 1, WPC_TL> : k_multi_warp<4, 1, WPC_TL>, grid, WPC_TL * 32,
+                            per * WPC_TL, s, pdl, h->d_arenas, h->d_rec, d_free_rowptr, d_frees, d_free_status,
+                            d_alloc_rowptr, d_sizes, d_out, h->d_scr, (const uint32_t*)h->d_gi, nf_total, n, per / 4,
+                            pre ? 1u : 0u, h->d_tlsf)
+               : launch_pdl(two ? k_multi_warp<2> : k_multi_warp<4>, grid, WPC * 32, per * WPC, s, pdl, h->d_arenas,
+                            h->d_rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, h->d_scr,
+                            (const uint32_t*)h->d_gi, nf_total, n, per / 4, pre ? 1u : 0u, (hba::TlsfLists*)nullptr);
         if (e != cudaSuccess) return HBA_ERR_CUDA;
         ++h->launches;
         return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;
     }
     const uint32_t grid = h->m_ctas ? std::min(h->m_ctas, n) : n;
     const int li = limit_index(h->m_threads);
-    const uint32_t base = 4 * g_limits[li].alloc_words;
-    uint32_t dyn = std::min(h->smem_bytes ? h->smem_bytes : MULTI_DYN_BYTES_DEFAULT, g_limits[li].multi_dyn);
+    const uint32_t base = 4 * (tl ? g_limits[li].alloc_words_tl : g_limits[li].alloc_words);
+    uint32_t dyn = std::min(h->smem_bytes ? h->smem_bytes : MULTI_DYN_BYTES_DEFAULT,
+                            tl ? g_limits[li].multi_dyn_tl : g_limits[li].multi_dyn);
     dyn = (std::max(dyn, base) + 15u) & ~15u;
     const uint32_t dw = dyn / 4;
     bool pdl = false;
@@ -1582,13 +1575,18 @@ hba_status_t multi_step_impl(hba_t h, const uint32_t* d_free_rowptr, const uint6
     uint32_t* scr = h->d_scr;
     const uint32_t* gi = h->d_gi;
     cudaError_t e;
+    hba::TlsfLists* lists = h->d_tlsf;
+#define HBA_MULTI(NTV, POLV)                                                                                     \
+    launch_pdl(k_multi<NTV, POLV>, grid, NTV, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status,         \
+               d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf, POLV ? lists : nullptr)
     switch (h->m_threads) {
-        case 64: e = launch_pdl(k_multi<64>, grid, 64, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
-        case 128: e = launch_pdl(k_multi<128>, grid, 128, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
-        case 512: e = launch_pdl(k_multi<512>, grid, 512, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
-        case 1024: e = launch_pdl(k_multi<1024>, grid, 1024, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
-        default: e = launch_pdl(k_multi<256>, grid, 256, dyn, s, pdl, ar, rec, d_free_rowptr, d_frees, d_free_status, d_alloc_rowptr, d_sizes, d_out, scr, gi, nf_total, n, dw, pf); break;
+        case 64: e = tl ? HBA_MULTI(64, 1) : HBA_MULTI(64, 0); break;
+        case 128: e = tl ? HBA_MULTI(128, 1) : HBA_MULTI(128, 0); break;
+        case 512: e = tl ? HBA_MULTI(512, 1) : HBA_MULTI(512, 0); break;
+        case 1024: e = tl ? HBA_MULTI(1024, 1) : HBA_MULTI(1024, 0); break;
+        default: e = tl ? HBA_MULTI(256, 1) : HBA_MULTI(256, 0); break;
     }
+#undef HBA_MULTI
     if (e != cudaSuccess) return HBA_ERR_CUDA;
     ++h->launches;
     return cudaGetLastError() == cudaSuccess ? HBA_OK : HBA_ERR_CUDA;

@@ -23,15 +23,11 @@
 // the extent scan and the canonical export of the blocks carry over; the
 // list heads and bitmaps live in a TlsfLists per arena.
 //
-// Execution: one warp per arena.  Frees, then allocations, are applied one
-// by one in index order (by lane 0), which is the sequential semantics by
-// construction.  The warp helps in two places where no state changes:
-//   - before each group of 32 frees, every lane prefetches into L2 the
-//     records its free will read (its block and both neighbours);
-//   - allocations are classified 32 at a time against the current bitmaps:
-//     a request with no qualifying list fails without changing anything, so
-//     the requests before the first one that succeeds are resolved together,
-//     and only that one is applied by lane 0 before the next window.
+// Execution: the batch engine (hba_engine.cuh, class layout POL 1) applies
+// TLSF batches on the GPU, as it does segregated-fit ones.  This file keeps
+// the list operations one at a time: the serial batch below is the host
+// emulation's second implementation of the policy, and the export and
+// initial state serve every TLSF handle.
 #pragma once
 
 #include "hba_engine.cuh"
@@ -161,8 +157,7 @@ HBA_HD uint32_t tl_take(TlsfLists& L, Rec* rec, uint32_t G, uint32_t k, uint32_t
     return Y;
 }
 
-// Whole batch, one op at a time (the host emulation and the reference for
-// the warp version below).
+// Whole batch, one op at a time (the host emulation).
 HBA_HD void tl_batch_serial(TlsfLists& L, Rec* rec, uint64_t A, uint32_t G, uint32_t lg, const uint64_t* frees,
                             uint32_t nf, uint8_t* fstat, const uint64_t* sizes, uint32_t na, uint64_t* out,
                             TlCount& c) {
@@ -245,80 +240,5 @@ inline size_t tl_export(const Arena& ar, const TlsfLists& L, const Rec* rec, uin
     return n;
 }
 
-#ifndef HBA_EMULATE
-// One batch of one arena by one warp.  Lw: the warp's copy of the arena's
-// lists in shared memory (loaded here, stored back at the end).  Requests:
-// frees[f0, f1) and sizes[a0, a1), results at the same indices.
-__device__ inline void tl_arena_warp(Arena& ar, TlsfLists& Lg, Rec* rec, TlsfLists& Lw, const uint64_t* frees,
-                                     uint8_t* fstat, uint32_t f0, uint32_t f1, const uint64_t* sizes,
-                                     uint64_t* out, uint32_t a0, uint32_t a1) {
-    constexpr unsigned FULL = 0xffffffffu;
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t A = ar.arena_bytes;
-    const uint32_t G = ar.G, lg = ar.lg;
-    for (uint32_t k = lane; k < TL_NL; k += 32) {
-        const uint32_t h = Lg.heads[k];
-        Lw.heads[k] = h;
-        if (h != NIL && a1 > a0) prefetch_l2(rec + h);  // the heads the allocations may pop
-    }
-    Lw.slmask[lane] = Lg.slmask[lane];  // TL_FL == 32
-    if (lane == 0) Lw.flmask = Lg.flmask;
-    __syncwarp();
-    TlCount c;
-    // frees in index order; each group of 32 has its records prefetched first
-    for (uint32_t j0 = f0; j0 < f1; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        if (j < f1) {
-            const uint64_t off = frees[j];
-            if (off < A && (off & ((1ull << lg) - 1)) == 0) {
-                const uint32_t g = (uint32_t)(off >> lg);
-                const Rec r = rec[g];  // may be out of date by the time it is applied: only a hint
-                if (r.y != NIL && r.y < G) prefetch_l2(rec + r.y);
-                const uint32_t rt = g + sz_of(r.x);
-                if (rt < G) prefetch_l2(rec + rt);
-            }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            const uint32_t je = f1 - j0 < 32u ? f1 : j0 + 32;
-            for (uint32_t q = j0; q < je; ++q) {
-                const uint32_t st = tl_free_one(Lw, rec, A, G, lg, frees[q], c);
-                if (fstat) fstat[q] = (uint8_t)st;
-            }
-        }
-        __syncwarp();
-    }
-    // allocations in index order, classified 32 at a time
-    for (uint32_t i = a0; i < a1;) {
-        const uint32_t n = a1 - i < 32u ? a1 - i : 32u;
-        uint32_t r = 0;
-        bool ok = false;
-        if (lane < n) {
-            r = tl_granules(sizes[i + lane], A, lg);
-            ok = r && r <= G && tl_find(Lw, tl_bound(r)) != TL_NONE;
-        }
-        const unsigned bal = __ballot_sync(FULL, ok);
-        const uint32_t e = bal ? (uint32_t)__ffs((int)bal) - 1u : n;  // first request that is served
-        if (lane < e) out[i + lane] = FAIL64;
-        const uint32_t re = __shfl_sync(FULL, r, e < 32u ? e : 0u);
-        if (lane == 0) {
-            c.afail += e;
-            if (e < n) {
-                const uint32_t k = tl_find(Lw, tl_bound(re));
-                out[i + e] = (uint64_t)tl_take(Lw, rec, G, k, re, c) << lg;
-                c.req += (int64_t)sizes[i + e];
-            }
-        }
-        __syncwarp();
-        i += e < n ? e + 1 : n;
-    }
-    for (uint32_t k = lane; k < TL_NL; k += 32) Lg.heads[k] = Lw.heads[k];
-    Lg.slmask[lane] = Lw.slmask[lane];
-    if (lane == 0) {
-        Lg.flmask = Lw.flmask;
-        tl_apply_counts(ar, Lw, c);
-    }
-}
-#endif
 
 }  // namespace hba

@@ -19,16 +19,18 @@ THREADS = (32, 64, 128, 256)
 GRID_WAVES = (0, 1, 2, 4, 8)    # 0 = one CTA per arena; k = k CTAs per SM
 SMEM_BYTES = (0, 24 * 1024)     # 0 = default per-CTA (per-warp in warp mode) budget
 WARP_ARENAS_PER_CTA = 8         # warp mode: arenas (warps) per CTA, fixed at build time
+WARP_ARENAS_PER_CTA_TLSF = 4    # the same for the two-level lists (larger per-arena shared state)
 CTA_DEFAULT_SMEM = 24 * 1024    # the library's default per-CTA budget outside warp mode
 
 
-def effective_launch(threads: int, ctas: int, smem: int, n_arenas: int) -> tuple:
+def effective_launch(threads: int, ctas: int, smem: int, n_arenas: int, policy: str = "segfit") -> tuple:
     """The launch a shape gives for n_arenas (the library's own rule,
-    restated): warp mode runs ceil(n / 8) CTAs unless fewer are asked for;
-    otherwise one CTA per arena unless fewer are asked for; a zero budget is
-    the default one.  Shapes with the same launch are timed once."""
+    restated): warp mode runs ceil(n / 8) CTAs (TLSF: ceil(n / 4)) unless
+    fewer are asked for; otherwise one CTA per arena unless fewer are asked
+    for; a zero budget is the default one.  Shapes with the same launch are
+    timed once."""
     if threads == 32:
-        need = -(-n_arenas // WARP_ARENAS_PER_CTA)
+        need = -(-n_arenas // (WARP_ARENAS_PER_CTA_TLSF if policy == "tlsf" else WARP_ARENAS_PER_CTA))
         return (32, min(ctas, need) if ctas else need, smem)
     return (threads, min(ctas, n_arenas) if ctas else n_arenas, smem or CTA_DEFAULT_SMEM)
 
@@ -52,7 +54,7 @@ def autotune_multi(ma: MultiAllocator, batches, n_probe: int = 3, threads=THREAD
     table, seen = {}, {}
     for t, w, sm in itertools.product(threads, waves, smem):
         ctas = 0 if w == 0 else w * sms
-        eff = effective_launch(t, ctas, sm, ma.n)
+        eff = effective_launch(t, ctas, sm, ma.n, ma.policy)
         if eff in seen:  # the same launch as a shape already timed
             continue
         seen[eff] = (t, ctas, sm)
@@ -72,8 +74,8 @@ def autotune_multi(ma: MultiAllocator, batches, n_probe: int = 3, threads=THREAD
     best = min(table, key=table.get)
     # name the best launch by its plainest shape (one CTA per arena when the
     # grid asked for is not smaller)
-    eff = effective_launch(*best, ma.n)
-    plain = (best[0], 0, best[2]) if effective_launch(best[0], 0, best[2], ma.n) == eff else best
+    eff = effective_launch(*best, ma.n, ma.policy)
+    plain = (best[0], 0, best[2]) if effective_launch(best[0], 0, best[2], ma.n, ma.policy) == eff else best
     best = plain
     hba_set_shape(ma.h, *best)
     hba_reset(ma.h, int(stream.cuda_stream))

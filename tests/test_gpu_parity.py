@@ -795,9 +795,12 @@ def test_tlsf_host_entry_points_and_serving_refusal(gpu_lib):
             serve(a, arr)
 
 
-def test_tlsf_multi_arena_matches_per_arena_oracles(gpu_lib):
-    """Independent TLSF arenas, one warp each, in one launch: arena i's
-    results equal a TLSF oracle run of arena i's sub-trace."""
+@pytest.mark.parametrize("shape", [(32, 0), (32, 40), (64, 152), (128, 0), (256, 0)])
+def test_tlsf_multi_arena_matches_per_arena_oracles(gpu_lib, shape):
+    """Independent TLSF arenas in one launch of the batch engine with the
+    two-level lists, one warp each (32 threads, four arenas per CTA) or one
+    CTA each; a grid smaller than it needs makes CTAs loop over arenas.
+    Arena i's results equal a TLSF oracle run of arena i's sub-trace."""
     import torch
 
     import oracle
@@ -810,6 +813,7 @@ def test_tlsf_multi_arena_matches_per_arena_oracles(gpu_lib):
     sizes_a = (rng.integers(1, 64, n) * 256 * 1024 + rng.integers(0, 4, n) * 256).astype(np.uint64)
     mb = 256
     m = MultiAllocator(sizes_a, mb, max_total_frees=1 << 18, policy="tlsf")
+    m.set_shape(*shape)
     orcs = [oracle.Oracle(int(x), mb, "tlsf") for x in sizes_a]
     clients = [W.Lifetimes(n_ops=10**9, batch=int(rng.integers(0, 700)), mean_life=200,
                            seed=W.BASE_SEED + 300 + i, scale=float(x) / (16 * GiB), min_size=256)

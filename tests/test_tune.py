@@ -20,3 +20,10 @@ def test_candidate_count_for_the_full_batched_configuration():
     seen = {effective_launch(t, 0 if w == 0 else w * 152, s, 4096)
             for t, w, s in itertools.product(THREADS, GRID_WAVES, SMEM_BYTES)}
     assert len(seen) == 21
+
+
+def test_tlsf_warp_mode_runs_four_arenas_per_cta():
+    # the two-level lists run four arenas (warps) per CTA in warp mode
+    assert effective_launch(32, 0, 0, 4096, "tlsf") == effective_launch(32, 1216, 0, 4096, "tlsf") == (32, 1024, 0)
+    assert effective_launch(32, 608, 0, 4096, "tlsf") == (32, 608, 0)
+    assert effective_launch(128, 0, 0, 100, "tlsf") == effective_launch(128, 0, 0, 100)
