@@ -9,9 +9,14 @@
 // else the lowest start of all; a run never wraps past the end of the pool.
 //
 // One CTA per pool.  Both bitmaps are copied into shared memory for the
-// batch and written back at the end.  Frees are applied one at a time by
-// lane 0 of warp 0 (the warp loads 32 offsets at a time), a few word
-// operations each.  An allocation is a CTA-wide scan:
+// batch and written back at the end.  Frees are resolved NT at a time, in
+// parallel: a free's validity and block end do not depend on the other
+// frees of the batch (see the free phase below).  Allocations are applied
+// one at a time in index order by warp 0, which holds the rover in
+// registers and takes the rover itself when k units from it are free, else
+// looks for the lowest start in the BM_QUICK words from the rover's word on,
+// 32 words a step.  A request it does not settle there (or of more than 64
+// units) goes to a CTA-wide scan:
 //   k <= 64: thread t takes word w and computes the mask of starts in w that
 //     have k free units, across w and w + 1 (128-bit AND of the shifted
 //     words, built by doubling); the lowest start is an atomicMin, and the
@@ -98,51 +103,25 @@ __device__ __forceinline__ uint64_t bm_run_starts(uint64_t lo, uint64_t hi, uint
     return yl;
 }
 
+// Words from the rover's word that warp 0 searches before it hands a
+// request to the whole CTA.
+#ifndef HBA_BM_QUICK
+#define HBA_BM_QUICK 256
+#endif
+constexpr uint32_t BM_QUICK = HBA_BM_QUICK;
+
+constexpr uint32_t BM_HT = 512;  // hash slots of a chunk of frees (at least twice NT)
+
 template <int NT>
 struct BmSmem {
-    uint64_t sz[NT];  // the current group of request sizes
-    uint32_t rover, kfail, found, found_any;
+    static_assert(BM_HT >= 2 * NT && (BM_HT & (BM_HT - 1)) == 0, "free hash table");
+    uint32_t rover, kfail, found, found_any, esc;
     uint32_t wmin[NT / 32];  // per-warp minima of the long-run search
+    uint32_t hkey[BM_HT];    // frees of a chunk: start unit of each slot (NONE: empty)
+    uint32_t hidx[BM_HT];    //   the lowest free index (in the chunk) naming it
     int64_t cnt[6];  // alloc_ok, alloc_fail, free_ok, free_fail, used units, requested bytes
     uint32_t err;
 };
-
-// Free the block that starts at byte offset off (one thread).
-template <int NT>
-__device__ void bm_free_one(BmSmem<NT>& S_, uint64_t* F, uint64_t* S, uint32_t W, uint32_t N, uint32_t lg,
-                            uint64_t off, uint8_t* fstat, uint32_t j) {
-    uint32_t st = 1;
-    if ((off & ((1ull << lg) - 1)) == 0 && (off >> lg) < N) {
-        const uint32_t p = (uint32_t)(off >> lg);
-        const uint32_t pw = p >> 6, pb = p & 63;
-        if ((S[pw] >> pb) & 1ull) {
-            // the block ends at the next free or marked unit, or the pool's end
-            const uint64_t above = pb == 63 ? 0ull : ~0ull << (pb + 1);
-            const uint64_t stop = (F[pw] | S[pw]) & above;
-            uint32_t e;
-            if (stop) {
-                e = (pw << 6) + ctz64(stop);
-            } else {
-                uint32_t x = pw + 1;
-                while (x < W && (F[x] | S[x]) == 0ull) ++x;
-                e = x < W ? (x << 6) + ctz64(F[x] | S[x]) : N;
-            }
-            if (e > N) e = N;
-            for (uint32_t q = p; q < e;) {  // set F over [p, e), a word piece at a time
-                const uint32_t qw = q >> 6, qb = q & 63;
-                const uint32_t take = min(64u - qb, e - q);
-                const uint64_t m = take == 64 ? ~0ull : ((1ull << take) - 1ull) << qb;
-                F[qw] |= m;
-                q += take;
-            }
-            S[pw] &= ~(1ull << pb);
-            S_.cnt[4] -= (int64_t)(e - p);
-            st = 0;
-        }
-    }
-    if (fstat) fstat[j] = (uint8_t)st;
-    ++S_.cnt[st ? 3 : 2];
-}
 
 // Lowest start of k > 64 free units (whole CTA; F in shared memory, W
 // words): at or after the rover if there is one, else the lowest of all;
@@ -200,6 +179,25 @@ __device__ uint32_t bm_long_search(BmSmem<NT>& S_, const uint64_t* F, uint32_t W
     return r;
 }
 
+// Allocation of k units at p (p + k <= N): clear F over [p, p + k), mark
+// p, write the result (one thread; the caller moves the rover).
+template <int NT>
+__device__ void bm_take(BmSmem<NT>& S_, uint64_t* F, uint64_t* S, uint32_t lg, uint32_t p, uint32_t k, uint64_t sz,
+                        uint64_t* res) {
+    for (uint32_t q = p; q < p + k;) {
+        const uint32_t qw = q >> 6, qb = q & 63;
+        const uint32_t take = min(64u - qb, p + k - q);
+        const uint64_t m = take == 64 ? ~0ull : ((1ull << take) - 1ull) << qb;
+        F[qw] &= ~m;
+        q += take;
+    }
+    S[p >> 6] |= 1ull << (p & 63);
+    *res = (uint64_t)p << lg;
+    ++S_.cnt[0];
+    S_.cnt[4] += k;
+    S_.cnt[5] += (int64_t)sz;
+}
+
 // The bitmaps of one pool in shared memory: F (free) and S (starts), W words each.
 template <int NT>
 __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint64_t* gS, uint64_t* F, uint64_t* S,
@@ -218,86 +216,202 @@ __device__ void bm_pool(BmSmem<NT>& S_, Arena& ar, BmHdr& H, uint64_t* gF, uint6
         S_.err = 0;
     }
     __syncthreads();
-    // ---- frees, one by one (lane 0 of warp 0; the warp loads 32 offsets at a time)
-    if (t < 32) {
-        for (uint32_t j0 = f0; j0 < f1; j0 += 32) {
-            const uint64_t mine = j0 + t < f1 ? frees[j0 + t] : 0ull;
-            const uint32_t nq = f1 - j0 < 32u ? f1 - j0 : 32u;
-            for (uint32_t q = 0; q < nq; ++q) {
-                const uint64_t off = __shfl_sync(0xffffffffu, mine, q);  // every lane, every step
-                if (t == 0) bm_free_one(S_, F, S, W, N, lg, off, fstat, j0 + q);
-                __syncwarp();
+    // ---- frees, NT at a time.  A free is valid when it names a unit
+    // boundary inside the pool whose start bit is set; its block ends at the
+    // next free or marked unit.  No other free of the batch moves that end
+    // (a free only turns a marked start into free units), so the frees of a
+    // chunk are resolved together: validity and ends first, then the bit
+    // updates.  Of several frees of one block the lowest index applies and
+    // the others are rejected, as they are one by one (the start bit is gone
+    // by their turn); a later chunk finds the bit gone.
+    constexpr uint32_t NONE = 0xFFFFFFFFu;
+    for (uint32_t j0 = f0; j0 < f1; j0 += NT) {
+        const uint32_t j = j0 + t;
+        uint32_t p = NONE;
+        if (j < f1) {
+            const uint64_t off = frees[j];
+            if ((off & ((1ull << lg) - 1)) == 0 && (off >> lg) < N) {
+                const uint32_t q = (uint32_t)(off >> lg);
+                if ((S[q >> 6] >> (q & 63)) & 1ull) p = q;
             }
         }
+        for (uint32_t h = t; h < BM_HT; h += NT) {
+            S_.hkey[h] = NONE;
+            S_.hidx[h] = NONE;
+        }
+        __syncthreads();
+        uint32_t slot = 0;
+        if (p != NONE) {  // at most NT keys in BM_HT >= 2 NT slots: a free slot is always found
+            slot = (p * 2654435761u) & (BM_HT - 1);
+            for (uint32_t probe = 0; probe < BM_HT; ++probe) {
+                const uint32_t key = atomicCAS(&S_.hkey[slot], NONE, p);
+                if (key == NONE || key == p) break;
+                slot = (slot + 1) & (BM_HT - 1);
+            }
+            atomicMin(&S_.hidx[slot], t);
+        }
+        __syncthreads();
+        const bool ok = p != NONE && S_.hidx[slot] == t;
+        uint32_t e = 0;
+        if (ok) {
+            const uint32_t pw = p >> 6, pb = p & 63;
+            const uint64_t above = pb == 63 ? 0ull : ~0ull << (pb + 1);
+            const uint64_t stop = (F[pw] | S[pw]) & above;
+            if (stop) {
+                e = (pw << 6) + ctz64(stop);
+            } else {
+                uint32_t x = pw + 1;
+                while (x < W && (F[x] | S[x]) == 0ull) ++x;
+                e = x < W ? (x << 6) + ctz64(F[x] | S[x]) : N;
+            }
+            if (e > N) e = N;
+        }
+        __syncthreads();  // every end is known before any bit changes
+        if (ok) {
+            for (uint32_t q = p; q < e;) {  // set F over [p, e), a word piece at a time
+                const uint32_t qw = q >> 6, qb = q & 63;
+                const uint32_t take = min(64u - qb, e - q);
+                const uint64_t m = take == 64 ? ~0ull : ((1ull << take) - 1ull) << qb;
+                atomicOr(reinterpret_cast<unsigned long long*>(&F[qw]), (unsigned long long)m);
+                q += take;
+            }
+            atomicAnd(reinterpret_cast<unsigned long long*>(&S[p >> 6]), ~(1ull << (p & 63)));
+        }
+        if (j < f1 && fstat) fstat[j] = ok ? 0 : 1;
+        const uint32_t n_ok = __popc(__ballot_sync(0xffffffffu, ok));
+        const uint32_t n_bad = __popc(__ballot_sync(0xffffffffu, j < f1 && !ok));
+        const uint32_t units = __reduce_add_sync(0xffffffffu, ok ? e - p : 0u);
+        if ((t & 31) == 0) {
+            if (n_ok) atomicAdd(reinterpret_cast<unsigned long long*>(&S_.cnt[2]), (unsigned long long)n_ok);
+            if (n_bad) atomicAdd(reinterpret_cast<unsigned long long*>(&S_.cnt[3]), (unsigned long long)n_bad);
+            if (units) atomicAdd(reinterpret_cast<unsigned long long*>(&S_.cnt[4]), (unsigned long long)(-(int64_t)units));
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    // ---- allocations, one by one, each a CTA-wide run search
+    // ---- allocations in index order.  Warp 0 applies them one by one and
+    // looks for each run in the BM_QUICK words from the rover's word on
+    // (32 words a step, no block barrier); that finds the lowest start at or
+    // after the rover whenever there is one in those words.  A request it
+    // does not settle (no start there, or more than 64 units) is searched by
+    // the whole CTA, after which warp 0 goes on.
     const uint64_t P = (uint64_t)N << lg;
-    for (uint32_t i = a0; i < a1; ++i) {
-        if ((i - a0) % NT == 0) {  // the next NT sizes, loaded together
-            __syncthreads();
-            if (i + t < a1) S_.sz[t] = sizes[i + t];
-            __syncthreads();
-        }
-        const uint64_t sz = S_.sz[(i - a0) % NT];
-        const uint32_t k = (sz == 0 || sz > P) ? 0u : (uint32_t)((sz + (1ull << lg) - 1) >> lg);
-        if (k == 0 || k > N || k >= S_.kfail) {  // uniform: S_.kfail changes behind barriers
-            if (t == 0) {
-                out[i] = FAIL64;
-                ++S_.cnt[1];
+    uint32_t i = a0;
+    while (true) {
+        if (t < 32) {
+            uint32_t rover = S_.rover, kfail = S_.kfail;  // warp-uniform; stored back below
+            uint32_t esc = a1;
+            for (uint32_t j0 = i; j0 < a1 && esc == a1; j0 += 32) {
+                const uint64_t mine = j0 + t < a1 ? sizes[j0 + t] : 0ull;
+                const uint32_t nq = a1 - j0 < 32u ? a1 - j0 : 32u;
+                for (uint32_t q = 0; q < nq; ++q) {
+                    const uint64_t sz = __shfl_sync(0xffffffffu, mine, q);  // every lane, every step
+                    const uint32_t k = (sz == 0 || sz > P) ? 0u : (uint32_t)((sz + (1ull << lg) - 1) >> lg);
+                    if (k == 0 || k > N || k >= kfail) {
+                        if (t == 0) {
+                            out[j0 + q] = FAIL64;
+                            ++S_.cnt[1];
+                        }
+                        continue;
+                    }
+                    if (k > 64) {
+                        esc = j0 + q;
+                        break;
+                    }
+                    uint32_t p = NONE;
+                    if (rover + k <= N) {  // the rover itself, when k units from it are free
+                        const uint32_t w = rover >> 6, b = rover & 63;
+                        uint64_t v = F[w] >> b;
+                        if (b && w + 1 < W) v |= F[w + 1] << (64 - b);
+                        const uint64_t m = k == 64 ? ~0ull : (1ull << k) - 1ull;
+                        if ((v & m) == m) p = rover;
+                    }
+                    const uint32_t w0 = rover >> 6;
+                    const uint32_t wend = p != NONE ? w0 : (W - w0 < BM_QUICK ? W : w0 + BM_QUICK);
+                    for (uint32_t c0 = w0; c0 < wend; c0 += 32) {
+                        const uint32_t w = c0 + t;
+                        uint64_t v = 0;
+                        if (w < wend) {
+                            v = bm_run_starts(F[w], w + 1 < W ? F[w + 1] : 0ull, k);
+                            if (w == w0) v &= (rover & 63) ? ~0ull << (rover & 63) : ~0ull;
+                        }
+                        const unsigned bal = __ballot_sync(0xffffffffu, v != 0);
+                        if (bal) {
+                            const int src = __ffs((int)bal) - 1;
+                            const uint64_t vv = __shfl_sync(0xffffffffu, v, src);
+                            p = ((c0 + (uint32_t)src) << 6) + ctz64(vv);
+                            break;
+                        }
+                    }
+                    if (p == NONE) {
+                        esc = j0 + q;
+                        break;
+                    }
+                    if (p + k > N) {  // the lowest start runs off the end: nothing of k units is free
+                        if (t == 0) {
+                            out[j0 + q] = FAIL64;
+                            ++S_.cnt[1];
+                        }
+                        kfail = k;
+                        continue;
+                    }
+                    if (t == 0) bm_take(S_, F, S, lg, p, k, sz, out + j0 + q);
+                    rover = p + k;
+                    __syncwarp();
+                }
             }
-            continue;
+            if (t == 0) {
+                S_.esc = esc;
+                S_.rover = rover;
+                S_.kfail = kfail;
+            }
         }
+        __syncthreads();
+        const uint32_t e = S_.esc;
+        if (e >= a1) break;
+        // request e by the whole CTA: pass 0, starts >= rover in words
+        // [w0, W); pass 1, words [0, min(w0 + 1, W)); runs of more than 64
+        // units by the segment search
+        const uint64_t sz = sizes[e];
+        const uint32_t k = (uint32_t)((sz + (1ull << lg) - 1) >> lg);
         const uint32_t rover = S_.rover;
         if (k > 64) {
             const uint32_t p = bm_long_search<NT>(S_, F, W, rover, k);
             if (t == 0) S_.found = p;
             __syncthreads();
         } else {
-        const uint32_t w0 = rover >> 6 < W ? rover >> 6 : W;
-        if (t == 0) S_.found = 0xFFFFFFFFu;
-        __syncthreads();
-        // pass 0: starts >= rover in words [w0, W); pass 1: words [0, min(w0 + 1, W))
-        for (int pass = 0; pass < 2; ++pass) {
-            const uint32_t wlo = pass == 0 ? w0 : 0u;
-            const uint32_t whi = pass == 0 ? W : (w0 + 1 < W ? w0 + 1 : W);
-            for (uint32_t c0 = wlo; c0 < whi; c0 += NT) {
-                const uint32_t w = c0 + t;
-                if (w < whi) {
-                    uint64_t v = bm_run_starts(F[w], w + 1 < W ? F[w + 1] : 0ull, k);
-                    if (pass == 0 && w == w0) v &= (rover & 63) ? ~0ull << (rover & 63) : ~0ull;
-                    if (v) atomicMin(&S_.found, (w << 6) + ctz64(v));
+            const uint32_t w0 = rover >> 6 < W ? rover >> 6 : W;
+            if (t == 0) S_.found = 0xFFFFFFFFu;
+            __syncthreads();
+            for (int pass = 0; pass < 2; ++pass) {
+                const uint32_t wlo = pass == 0 ? w0 : 0u;
+                const uint32_t whi = pass == 0 ? W : (w0 + 1 < W ? w0 + 1 : W);
+                for (uint32_t c0 = wlo; c0 < whi; c0 += NT) {
+                    const uint32_t w = c0 + t;
+                    if (w < whi) {
+                        uint64_t v = bm_run_starts(F[w], w + 1 < W ? F[w + 1] : 0ull, k);
+                        if (pass == 0 && w == w0) v &= (rover & 63) ? ~0ull << (rover & 63) : ~0ull;
+                        if (v) atomicMin(&S_.found, (w << 6) + ctz64(v));
+                    }
+                    __syncthreads();
+                    const bool got = S_.found != 0xFFFFFFFFu;
+                    __syncthreads();
+                    if (got) break;
                 }
-                __syncthreads();
-                const bool got = S_.found != 0xFFFFFFFFu;
-                __syncthreads();
-                if (got) break;
+                if (S_.found != 0xFFFFFFFFu) break;
             }
-            if (S_.found != 0xFFFFFFFFu) break;
-        }
         }
         if (t == 0) {
             const uint32_t p = S_.found;
-            if (p == 0xFFFFFFFFu || p + k > N) {
-                out[i] = FAIL64;
+            if (p == NONE || p + k > N) {
+                out[e] = FAIL64;
                 ++S_.cnt[1];
                 S_.kfail = k;
             } else {
-                for (uint32_t q = p; q < p + k;) {  // clear F over [p, p + k)
-                    const uint32_t qw = q >> 6, qb = q & 63;
-                    const uint32_t take = min(64u - qb, p + k - q);
-                    const uint64_t m = take == 64 ? ~0ull : ((1ull << take) - 1ull) << qb;
-                    F[qw] &= ~m;
-                    q += take;
-                }
-                S[p >> 6] |= 1ull << (p & 63);
+                bm_take(S_, F, S, lg, p, k, sz, out + e);
                 S_.rover = p + k;
-                out[i] = (uint64_t)p << lg;
-                ++S_.cnt[0];
-                S_.cnt[4] += k;
-                S_.cnt[5] += (int64_t)sz;
             }
         }
+        i = e + 1;
         __syncthreads();
     }
     for (uint32_t w = t; w < W; w += NT) {

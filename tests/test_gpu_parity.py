@@ -1163,6 +1163,50 @@ def test_bitmask_invalid_frees_and_pool_limit(gpu_lib):
         Allocator((786_432 + 1) * 8, 8, policy="bitmask")
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bitmask_many_frees_with_repeats(gpu_lib, seed):
+    """Batches of up to 900 frees (several chunks of the kernel's parallel
+    free phase): neighbouring blocks freed together, blocks of up to 300
+    units (several words), the same block named twice in one chunk and in
+    different chunks, interior, misaligned and out-of-pool offsets; every
+    status, result and the state against the oracle."""
+    import oracle
+
+    rng = np.random.default_rng(900 + seed)
+    unit, units = 8, 64 * 700
+    pool = units * unit
+    o = oracle.BitmaskOracle(pool, unit)
+    held, trace = [], []
+
+    def batch(frees, sizes):
+        f = np.array(frees, np.uint64)
+        s = np.array(sizes, np.uint64)
+        out, st = o.batch(f, s)
+        trace.append((f, s, out, st))
+        return [int(x) for x in out if x != FAIL]
+
+    for _ in range(8):
+        held += batch([], (rng.integers(1, 300, 500) * unit - rng.integers(0, unit, 500)).tolist())
+    for _ in range(12):
+        held.sort()
+        a = int(rng.integers(0, max(1, len(held) - 400)))
+        run = held[a:a + int(rng.integers(50, 400))]          # neighbours, freed together
+        other = [held[int(i)] for i in rng.choice(len(held), min(len(held), 200), replace=False)]
+        picks = run + other
+        frees = list(picks)
+        frees += [picks[int(i)] for i in rng.integers(0, len(picks), 60)]      # repeats, anywhere
+        frees += [h + unit for h in other[:40]] + [h + 3 for h in other[40:60]]  # interior, misaligned
+        frees += [pool, pool + unit, 2 * pool]
+        frees = [frees[int(i)] for i in rng.permutation(len(frees))]
+        freed = set(picks)
+        held = [h for h in held if h not in freed]
+        held += batch(frees, (rng.integers(1, 300, int(rng.integers(0, 300))) * unit).tolist())
+    o2 = oracle.BitmaskOracle(pool, unit)
+    for f, s, _, _ in trace:
+        o2.batch(f, s)
+    _run_bitmask(trace, o2, pool, unit, state_every=2)
+
+
 @pytest.mark.parametrize("hi", [520, 8192])
 def test_bitmask_multi_pool(gpu_lib, hi):
     """Independent pools of different sizes, one CTA each, in one launch;
