@@ -517,15 +517,20 @@ def multi_kernel_name(policy, shape, n_arenas, n_sms, wpc=8) -> str:
     return f"k_prep + k_multi<{threads}{tl}>"
 
 
+# The sources the batch engine's kernels (k_prep, k_single, k_multi,
+# k_multi_warp, k_serve) are built from; the other policies' headers do not
+# enter them.
+ENGINE_SOURCES = ("paper_2405_07079_gb300/csrc/hba_engine.cuh", "paper_2405_07079_gb300/csrc/hba_capi.cu",
+                  "paper_2405_07079_gb300/csrc/hba_serve.cuh", "include/hba.h")
+
+
 def kernel_sources_digest() -> str:
-    """A digest of the CUDA sources and the public header: DRAM traffic
-    taken with ncu is quoted only while the kernels are the ones captured."""
-    import glob
+    """A digest of the engine kernels' sources: DRAM traffic taken with ncu
+    is quoted only while the kernels are the ones captured."""
     import hashlib
 
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2405_07079_gb300", "csrc", "hba_*")))
-    for path in files + [os.path.join(ROOT, "include", "hba.h")]:
+    for path in (os.path.join(ROOT, p) for p in ENGINE_SOURCES):
         with open(path, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
