@@ -541,11 +541,11 @@ def kernel_sources_digest() -> str:
 # kernel-source digest it was taken on, and by the kernel.
 PROFILED_TRAFFIC = {
     # profiles/k_multi_warp_batched4096.txt: the default batched command, 20 timed steps
-    ("c88b0ecc4fbb596b", "k_prep + k_multi_warp<4>"): {"dram_bytes_per_step": 990.2e6,
-                                                        "algorithmic_bytes_per_step": 804.8e6},
+    ("eed269d8444ba035", "k_prep + k_multi_warp<4>"): {"dram_bytes_per_step": 990.2e6,
+                                                        "algorithmic_bytes_per_step": 804.75e6},
     # profiles/k_single_tiny_k_serve_l2.txt: the tiny trace, 6 timed launches; one 50 ms serving run
-    ("c88b0ecc4fbb596b", "k_single<128>"): {"dram_bytes_per_step": 163.2e3, "algorithmic_bytes_per_step": 10.7e3},
-    ("c88b0ecc4fbb596b", "k_serve"): {"dram_bytes_per_step": 6.74e6, "algorithmic_bytes_per_step": 14.26e6},
+    ("eed269d8444ba035", "k_single<128>"): {"dram_bytes_per_step": 162.6e3, "algorithmic_bytes_per_step": 10.71e3},
+    ("eed269d8444ba035", "k_serve"): {"dram_bytes_per_step": 6.747e6, "algorithmic_bytes_per_step": 14.27e6},
 }
 
 
