@@ -60,9 +60,9 @@ inline size_t fit_export(const Arena& ar, const FitHdr& H, const FitBlk* fa, con
 }
 
 #ifndef HBA_EMULATE
-// Free and used arrays are worked on in shared memory when the batch cannot
-// grow either past FIT_RES entries (frees add at most one free entry each,
-// allocations at most one used entry each).
+// Free and used arrays are worked on in shared memory while each holds at
+// most FIT_RES entries; an insert that would pass that moves both to global
+// memory for the rest of the batch.
 #ifndef HBA_FIT_RES
 #define HBA_FIT_RES 4096u
 #endif
@@ -188,6 +188,21 @@ __device__ uint32_t fit_pick(FitSmem<NT>& S, const FitBlk* fa, uint32_t s, uint3
     return (uint32_t)(S.best & 0xffffffffu);
 }
 
+// Before an insert into a full shared-memory array: both arrays to global
+// memory for the rest of the batch (every thread calls it; kept out of line,
+// off the batch loop's path).
+template <int NT>
+__device__ __noinline__ void fit_spill(FitSmem<NT>& S, const FitBlk* fa, const FitBlk* ua, FitBlk* gfa, FitBlk* gua,
+                                       uint32_t gcap) {
+    const uint32_t t = threadIdx.x;
+    __syncthreads();
+    for (uint32_t q = t; q < S.nf; q += NT) gfa[q] = fa[q];
+    for (uint32_t q = t; q < S.nu; q += NT) gua[q] = ua[q];
+    __syncthreads();
+    if (t == 0) S.cap = gcap;
+    __syncthreads();
+}
+
 // One arena's batch.  fa / ua: the arena's free and used arrays (capacity
 // cap each); H: its header.
 template <int NT>
@@ -197,13 +212,18 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, Fit
     const uint32_t t = threadIdx.x;
     const uint64_t A = ar.arena_bytes;
     const uint32_t lg = ar.lg, fit = H.fit;
-    // the arrays in shared memory (res: 2 x FIT_RES entries) when they stay small enough
+    // the arrays in shared memory (res: 2 x FIT_RES entries) while they fit
     const uint32_t nf0 = H.nfree, nu0 = H.nused;
-    const bool resident = res != nullptr && (uint64_t)nf0 + (f1 - f0) + 1 <= FIT_RES &&
-                          (uint64_t)nu0 + (a1 - a0) <= FIT_RES;
+    bool resident = res != nullptr && nf0 < FIT_RES && nu0 < FIT_RES;
     FitBlk* fa = resident ? res : gfa;
     FitBlk* ua = resident ? res + FIT_RES : gua;
     const uint32_t cap = resident ? FIT_RES : gcap;
+    auto spill = [&]() {
+        fit_spill<NT>(S, fa, ua, gfa, gua, gcap);
+        fa = gfa;
+        ua = gua;
+        resident = false;
+    };
     if (resident) {
         for (uint32_t q = t; q < nf0; q += NT) fa[q] = gfa[q];
         for (uint32_t q = t; q < nu0; q += NT) ua[q] = gua[q];
@@ -259,7 +279,7 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, Fit
         if (t == 0) {
             const bool jl = q > 0 && fa[q - 1].a + fa[q - 1].z == g;
             const bool jr = q < S.nf && fa[q].a == g + size;
-            uint32_t mode = 0;  // 0 insert, 1 left, 2 right, 3 both
+            uint32_t mode = 0;  // 0 insert, 1 left, 2 right, 3 both (4: insert after moving to global memory)
             if (jl && jr) {
                 fa[q - 1].z += size + fa[q].z;
                 mode = 3;
@@ -271,12 +291,17 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, Fit
                 fa[q].z += size;
                 mode = 2;
             }
+            if (mode == 0 && resident && S.nf >= FIT_RES) mode = 4;  // the insert needs global memory first
+            else if (mode == 0 && S.nf >= S.cap) S.err = ERR_LIST_WALK;  // cannot happen: cap > granules / 2
             S.v[3] = mode;
-            if (mode == 0 && S.nf >= S.cap) S.err = ERR_LIST_WALK;  // cannot happen: cap > granules / 2
             S.dirty = 1;
         }
         __syncthreads();
-        const uint32_t mode = S.v[3];
+        uint32_t mode = S.v[3];
+        if (mode == 4) {
+            spill();
+            mode = 0;
+        }
         if (mode == 3) {
             fit_remove<NT>(fa, S.nf, q);
             if (t == 0) --S.nf;
@@ -353,6 +378,7 @@ __device__ void fit_arena(FitSmem<NT>& S, Arena& ar, FitHdr& H, FitBlk* gfa, Fit
                 fit_remove<NT>(fa, S.nf, c);
                 if (t == 0) --S.nf;
             }
+            if (resident && S.nu >= FIT_RES) spill();
             const uint32_t pu = fit_count_le<NT>(ua, S.nu, addr, false);
             if (S.nu < S.cap) {
                 fit_insert<NT>(ua, S.nu, pu, FitBlk{addr, s});

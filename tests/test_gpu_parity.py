@@ -443,14 +443,14 @@ def test_batched_generator_matches_per_arena_oracles(gpu_lib, threads):
         ma.close()
 
 
-def _multi_oracle_trace(A, n_batches, max_ops, mean_life, mb=256):
+def _multi_oracle_trace(A, n_batches, max_ops, mean_life, mb=256, policy="segfit"):
     """The batched workload over arenas A, closed loop against one oracle
     per arena: [(frow, frees, arow, sizes, out, status)], and the oracles."""
     import oracle
     from paper_2405_07079_gb300 import workloads as W
 
     gen = W.MultiLifetimes(A, n_batches=n_batches, max_ops=max_ops, mean_life=mean_life)
-    orcs = [oracle.Oracle(int(a), mb) for a in A]
+    orcs = [oracle.Oracle(int(a), mb, policy) for a in A]
     trace = []
     while (b := gen.next_batch()) is not None:
         frow, f, arow, s = b
@@ -465,7 +465,7 @@ def _multi_oracle_trace(A, n_batches, max_ops, mean_life, mb=256):
     return trace, orcs
 
 
-def _multi_replay(A, trace, orcs, threads, ctas, mb=256, canaries=0):
+def _multi_replay(A, trace, orcs, threads, ctas, mb=256, canaries=0, policy="segfit"):
     """Replay a batched trace through one multi-arena handle of the given
     launch shape: every offset and free status of every batch, and every
     arena's final state, equal the per-arena oracles'.  The first
@@ -478,7 +478,7 @@ def _multi_replay(A, trace, orcs, threads, ctas, mb=256, canaries=0):
 
     dev = torch.device("cuda")
     guards = [torch.full((int(A[i]),), 0xA5, dtype=torch.uint8, device=dev) for i in range(canaries)]
-    m = MultiAllocator(A, mb, max_total_frees=max(1, max(t[1].size for t in trace)))
+    m = MultiAllocator(A, mb, max_total_frees=max(1, max(t[1].size for t in trace)), policy=policy)
     m.set_shape(threads, ctas, 0)
     try:
         for b, (frow, f, arow, s, out, st) in enumerate(trace):
@@ -509,6 +509,19 @@ def test_multi_arena_large_grids(gpu_lib, threads, ctas):
     A = W.multi_arena_sizes(2700, lo=1 << 20, hi=4 << 20)
     trace, orcs = _multi_oracle_trace(A, n_batches=8, max_ops=512, mean_life=300)
     _multi_replay(A, trace, orcs, threads, ctas, canaries=4)
+
+
+@pytest.mark.parametrize("threads,ctas", [(32, 0), (128, 608)])
+def test_tlsf_multi_arena_large_grids(gpu_lib, threads, ctas):
+    """TLSF over 2,700 arenas of 1-4 MiB: warp mode with more CTAs than two
+    per SM (four arenas per CTA, the build for four CTAs per SM), and 608
+    CTAs of 128 threads looping over the arenas (the shape family the
+    autotuner picks for TLSF on the full batched configuration)."""
+    from paper_2405_07079_gb300 import workloads as W
+
+    A = W.multi_arena_sizes(2700, lo=1 << 20, hi=4 << 20)
+    trace, orcs = _multi_oracle_trace(A, n_batches=8, max_ops=512, mean_life=300, policy="tlsf")
+    _multi_replay(A, trace, orcs, threads, ctas, canaries=2, policy="tlsf")
 
 
 def test_multi_arena_full_config_autotuned_shape(gpu_lib):
@@ -933,6 +946,44 @@ def test_fits_lifetimes_large_lists(gpu_lib, fit):
     wl = W.Workload("life", 256 * MiB, 512, lambda: W.Lifetimes(n_ops=60_000, batch=4096, mean_life=400))
     trace, o = _hal_trace(wl, fit)
     _run_fit(trace, o, wl.arena, wl.min_block, fit, state_every=3)
+
+
+@pytest.mark.parametrize("fit", ["first", "next", "best"])
+def test_fits_arrays_past_shared_memory(gpu_lib, fit):
+    """The kernel keeps the free and used arrays in shared memory while each
+    holds at most 4,096 entries: a batch whose allocations push the used
+    array past that (the arrays move to global memory mid-batch), batches
+    that start in global memory, and batches that start in shared memory
+    again after frees; partial frees in between."""
+    import oracle
+
+    rng = np.random.default_rng({"first": 31, "next": 32, "best": 33}[fit])
+    arena, mb = 16 * MiB, 256
+    o = oracle.HalOracle(arena, mb, fit)
+    held, trace = [], []
+
+    def batch(frees, sizes):
+        f = np.array(frees, np.uint64)
+        s_ = np.array(sizes, np.uint64)
+        out, st = o.batch(f, s_)
+        trace.append((f, s_, out, st))
+        return [int(x) for x in out if x != FAIL]
+
+    small = lambda n: (rng.integers(1, 9, n) * mb - rng.integers(0, mb, n)).tolist()
+    held += batch([], small(3000))
+    held += batch([], small(2500))                        # 5,500 used entries: past 4,096 mid-batch
+    rng.shuffle(held)
+    fr, held = held[:2000], held[2000:]
+    held += batch(fr, small(800))                         # starts in global memory
+    rng.shuffle(held)
+    fr, held = held[:3900], held[3900:]
+    part = [h + mb for h in held[:150]]                    # partial frees: keep the first unit
+    held += batch(fr + part, small(300))
+    held += batch([], small(4500))                        # starts in shared memory, grows past it again
+    rng.shuffle(held)
+    batch(held, small(50))
+    assert max(len(t[1]) for t in trace) >= 2500
+    _run_fit(trace, o, arena, mb, fit, state_every=1)
 
 
 @pytest.mark.parametrize("fit", ["first", "next", "best"])
