@@ -824,6 +824,48 @@ def test_bitmask_oracle_equals_block_list_random(seed):
     assert [int(x) for x in o.export_state()] == r.export_state()
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_bitmask_frees_commute(seed):
+    """The frees of one batch commute: applied in any order they leave the
+    same pool, and the free statuses move with the frees, except that among
+    frees of one block the first in the order applied succeeds.  (A free
+    only turns a marked block start into free units, so no free moves the
+    end of another block; the GPU resolves a batch's frees at once on this
+    property.)  Checked on the oracle by replaying one pool's history and then
+    one free batch in its order and in a shuffled order."""
+    rng = np.random.default_rng(7100 + seed)
+    u = 8
+    N = int(rng.integers(64, 3000))
+    hist = []
+    o = oracle.BitmaskOracle(N * u, u)
+    held = []
+    for _ in range(12):  # a fragmented pool: objects of 1-80 units, some freed
+        fr = [held[int(i)] for i in rng.choice(len(held), len(held) // 3, replace=False)] if held else []
+        sz = (rng.integers(1, 80, int(rng.integers(5, 60))) * u).tolist()
+        out, _ = o.batch(np.array(fr, np.uint64), np.array(sz, np.uint64))
+        hist.append((fr, sz))
+        held = [h for h in held if h not in fr] + [int(x) for x in out if x != FAIL]
+    frees = [held[int(i)] for i in rng.choice(len(held), min(len(held), 40), replace=False)]
+    frees += [frees[int(i)] for i in rng.integers(0, len(frees), 8)]          # the same block twice
+    frees += [h + u for h in frees[:5]] + [int(rng.integers(0, N + 2)) * u]    # interior, anywhere
+    perm = rng.permutation(len(frees))
+
+    def run(order):
+        p = oracle.BitmaskOracle(N * u, u)
+        for fr, sz in hist:
+            p.batch(np.array(fr, np.uint64), np.array(sz, np.uint64))
+        _, st = p.batch(np.array(order, np.uint64), np.array([], np.uint64))
+        return p.export_state(), [int(x) for x in st]
+
+    s1, st1 = run(frees)
+    s2, st2 = run([frees[i] for i in perm])
+    assert np.array_equal(s1, s2)
+    assert sum(1 for x in st1 if x == 0) == sum(1 for x in st2 if x == 0)
+    ok1 = {frees[i] for i, x in enumerate(st1) if x == 0}
+    ok2 = {frees[perm[i]] for i, x in enumerate(st2) if x == 0}
+    assert ok1 == ok2 and len(ok1) >= 10
+
+
 def test_bitmask_oracle_equals_block_list_exhaustive():
     """Every sequence of four ops from a small alphabet on pools of 3 and 7
     units."""
