@@ -546,6 +546,9 @@ PROFILED_TRAFFIC = {
     # profiles/k_single_tiny_k_serve_l2.txt: the tiny trace, 6 timed launches; one 50 ms serving run
     ("eed269d8444ba035", "k_single<128>"): {"dram_bytes_per_step": 162.6e3, "algorithmic_bytes_per_step": 10.71e3},
     ("eed269d8444ba035", "k_serve"): {"dram_bytes_per_step": 6.747e6, "algorithmic_bytes_per_step": 14.27e6},
+    # profiles/k_single_large16GiB.txt: the large trace, 30 timed steps, both kernels
+    ("eed269d8444ba035", "k_prep + k_single<1024>"): {"dram_bytes_per_step": 559.5e3,
+                                                       "algorithmic_bytes_per_step": 2.087e6},
 }
 
 
